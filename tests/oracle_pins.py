@@ -1,0 +1,311 @@
+"""Pins of the oracle to facts other than itself.
+
+Each ``check_*`` takes the path of an oracle library build and raises
+AssertionError when the oracle disagrees with the paper or the mathematics.
+``test_oracle_pins.py`` runs them on the real build; ``test_oracle_mutants.py``
+runs them on builds with planted mistakes and requires each mistake to be
+caught by at least one pin.
+"""
+from __future__ import annotations
+
+import math
+import os
+import random
+from fractions import Fraction
+
+import numpy as np
+
+import oracle
+from oracle import exact
+from oracle import PROG_AXPBY, PROG_CG, PROG_D, PROG_E
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+U64 = 2.0 ** -53
+
+
+def _eq_bits_or_nan(a: np.ndarray, b: np.ndarray) -> bool:
+    a = np.asarray(a)
+    b = np.asarray(b)
+    if a.shape != b.shape:
+        return False
+    both_nan = np.isnan(a) & np.isnan(b)
+    same = (a == b) | both_nan
+    return bool(np.all(same))
+
+
+# ------------------------------------------------------------- elementwise --
+
+def check_figure1_golden(path):
+    """Figure 1 worked example d = a + (b - c), hand-computed values."""
+    rows = [list(map(float, l.split())) for l in open(os.path.join(GOLDEN, "figure1_d_eq_a_plus_b_minus_c.txt"))
+            if l.strip() and not l.startswith("#")]
+    cols = list(zip(*rows))
+    for dt in (np.float64, np.float32):
+        a, b, c, want = (np.array(col, dtype=dt) for col in cols)
+        d = np.zeros_like(a)
+        oracle.eval_program(PROG_D, [a, b, c, d], path=path)
+        assert _eq_bits_or_nan(d, want), (dt, d, want)
+
+
+def check_d_integer_identity(path):
+    """Integers below 2^50 (FP64) / 2^22 (FP32): every node is exact, so the
+    result must equal exact integer arithmetic."""
+    rng = np.random.default_rng(11)
+    for dt, lim in ((np.float64, 2 ** 50), (np.float32, 2 ** 22)):
+        n = 10007
+        ints = [rng.integers(-lim, lim, n) for _ in range(3)]
+        a, b, c = (x.astype(dt) for x in ints)
+        d = np.zeros(n, dtype=dt)
+        oracle.eval_program(PROG_D, [a, b, c, d], path=path)
+        want = ints[0] + (ints[1] - ints[2])
+        assert np.array_equal(d.astype(np.float64), want.astype(np.float64)), dt
+
+
+def check_e_and_axpby_exact(path):
+    """alpha = 1.5, beta = -0.25 and multiples of 4: e = alpha a + beta b - c d
+    and y = alpha x + beta y are exact in both formats."""
+    rng = np.random.default_rng(12)
+    alpha, beta = 1.5, -0.25
+    for dt in (np.float64, np.float32):
+        n = 4099
+        A = rng.integers(-2 ** 10, 2 ** 10, n) * 4
+        B = rng.integers(-2 ** 10, 2 ** 10, n) * 4
+        C = rng.integers(-2 ** 10, 2 ** 10, n)
+        D = rng.integers(-2 ** 10, 2 ** 10, n)
+        a, b, c, d = (x.astype(dt) for x in (A, B, C, D))
+        e = np.zeros(n, dtype=dt)
+        oracle.eval_program(PROG_E, [a, b, c, d, e], [alpha, beta], path=path)
+        want = [Fraction(3, 2) * int(x) - Fraction(1, 4) * int(y) - int(z) * int(w) for x, y, z, w in zip(A, B, C, D)]
+        assert all(Fraction(float(g)) == w for g, w in zip(e, want)), dt
+        x, y = a.copy(), b.copy()
+        oracle.eval_program(PROG_AXPBY, [x, y], [alpha, beta], path=path)
+        want = [Fraction(3, 2) * int(p) - Fraction(1, 4) * int(q) for p, q in zip(A, B)]
+        assert all(Fraction(float(g)) == w for g, w in zip(y, want)), dt
+        assert np.array_equal(x, a), "x must be left untouched"
+
+
+def random_program(rng: random.Random, nvecs: int, nscal: int, max_len: int = 20):
+    """A random well-typed postfix program over nvecs vectors / nscal scalars.
+    Keeps stack depth <= 6, ends with an empty stack and has >= 1 output."""
+    prog = []
+    stack = []  # 'v' or 's'
+    outputs = 0
+    while True:
+        can_finish = len(stack) == 0 and outputs > 0
+        if can_finish and (len(prog) >= max_len or rng.random() < 0.15):
+            return prog
+        choices = []
+        if len(stack) < 6:
+            choices += ["VEC"] * 3
+            if nscal:
+                choices += ["SCAL"]
+        if len(stack) >= 2 and stack[-1] == "v" and stack[-2] == "v":
+            choices += ["ADD", "SUB", "MUL", "DOT"]
+        if len(stack) >= 2 and stack[-1] == "v" and stack[-2] == "s":
+            choices += ["SMUL"] * 3
+        if stack and stack[-1] == "v":
+            choices += ["NEG", "STORE", "STORE", "SUMSQ"]
+        if not choices:
+            # scalar on top with no vector to scale: push a vector to consume it
+            choices = ["VEC"]
+        op = rng.choice(choices)
+        if op == "VEC":
+            prog.append(("VEC", rng.randrange(nvecs))); stack.append("v")
+        elif op == "SCAL":
+            prog.append(("SCAL", rng.randrange(nscal))); stack.append("s")
+        elif op in ("ADD", "SUB", "MUL"):
+            prog.append((op, 0)); stack.pop()
+        elif op == "SMUL":
+            prog.append((op, 0)); stack.pop(); stack.pop(); stack.append("v")
+        elif op == "NEG":
+            prog.append((op, 0))
+        elif op == "STORE":
+            prog.append(("STORE", rng.randrange(nvecs))); stack.pop(); outputs += 1
+        elif op == "DOT":
+            prog.append((op, 0)); stack.pop(); stack.pop(); outputs += 1
+        elif op == "SUMSQ":
+            prog.append((op, 0)); stack.pop(); outputs += 1
+        if len(prog) > 40:
+            # force termination: drain the stack
+            while stack:
+                if stack[-1] == "s":
+                    prog.append(("VEC", 0)); prog.append(("SMUL", 0)); stack[-1] = "v"
+                    continue
+                prog.append(("STORE", rng.randrange(nvecs))); stack.pop(); outputs += 1
+            return prog
+
+
+def _check_against_exact(prog, vecs, scalars, dt, path):
+    ours = [v.copy() for v in vecs]
+    red = oracle.eval_program(prog, ours, scalars, path=path)
+    want, red_exact, red_abs = exact.exact_program(prog, vecs, scalars, dt)
+    for k, (got, w) in enumerate(zip(ours, want)):
+        assert _eq_bits_or_nan(got.astype(np.float64), np.array(w, dtype=np.float64)), (prog, k)
+    # Reductions: a sequential FP64 sum obeys |err| <= gamma_n sum|terms|
+    # (Higham, Eq. 3.5), with the exact terms as reference.
+    n = len(vecs[0]) if vecs else 0
+    assert len(red) == len(red_exact)
+    for r, re, ra in zip(red, red_exact, red_abs):
+        err = abs(Fraction(r) - re)
+        bound = Fraction(exact.gamma(n + 1, U64)) * ra
+        assert err <= bound, (prog, float(err), float(bound))
+
+
+def check_brute_force_random_programs(path, count=60):
+    """Random well-typed programs on tiny n, against per-element exact
+    rational arithmetic with one rounding per node."""
+    rng = random.Random(5)
+    nrng = np.random.default_rng(5)
+    for t in range(count):
+        dt = np.float64 if t % 2 == 0 else np.float32
+        nvecs = rng.randint(1, 6)
+        nscal = rng.randint(0, 3)
+        prog = random_program(rng, nvecs, nscal)
+        n = rng.choice([0, 1, 2, 3, 5, 7, 8, 9, 15, 16, 17, 31, 33, 63, 64, 71])
+        vecs = [nrng.uniform(-1, 1, n).astype(dt) for _ in range(nvecs)]
+        scalars = list(nrng.uniform(-2, 2, nscal))
+        _check_against_exact(prog, vecs, scalars, dt, path)
+
+
+def check_tail_lengths(path):
+    """Every n in 0..64 and 2^k + 7 (k <= 9): the body/tail split of the
+    paper's loop template must not matter (Listing 2: the tail elements get
+    the same scalar operation)."""
+    nrng = np.random.default_rng(6)
+    sizes = list(range(0, 65)) + [2 ** k + 7 for k in range(3, 10)]
+    for n in sizes:
+        for dt in (np.float64, np.float32):
+            vecs = [nrng.uniform(-1, 1, n).astype(dt) for _ in range(5)]
+            _check_against_exact(PROG_E if n % 2 else PROG_D, vecs, [1.5, -0.25], dt, path)
+
+
+def check_cg_store_then_load(path):
+    """STORE k followed by VEC k reads the stored value (r is updated before
+    rho = r.r and p = r + beta p), exact on small integers."""
+    rng = np.random.default_rng(7)
+    for dt in (np.float64, np.float32):
+        n = 777
+        R = rng.integers(-100, 100, n)
+        Q = rng.integers(-100, 100, n)
+        P = rng.integers(-100, 100, n)
+        r, q, p = (x.astype(dt) for x in (R, Q, P))
+        red = oracle.eval_program(PROG_CG, [r, q, p], [2.0, -0.5], path=path)
+        Rn = R - 2 * Q
+        assert np.array_equal(r.astype(np.int64), Rn)
+        assert np.array_equal(p.astype(np.float64), (Rn - 0.5 * P).astype(np.float64))
+        assert red[0] == float(int(np.sum(Rn * Rn)))
+
+
+def check_special_values(path):
+    """IEEE special cases: NaN propagates, inf - inf = NaN, -(+0) = -0,
+    (-0) + (-0) = -0, FP32 subnormals are kept (no flush to zero)."""
+    for dt in (np.float64, np.float32):
+        a = np.array([np.nan, np.inf, 0.0, -0.0, 1.0], dtype=dt)
+        b = np.array([1.0, np.inf, 0.0, -0.0, np.nan], dtype=dt)
+        out = np.zeros(5, dtype=dt)
+        oracle.eval_program([("VEC", 0), ("VEC", 1), ("SUB", 0), ("STORE", 2)], [a, b, out], path=path)
+        assert np.isnan(out[0]) and np.isnan(out[1]) and np.isnan(out[4])
+        assert out[2] == 0 and not np.signbit(out[2])  # 0 - 0 = +0
+        assert out[3] == 0 and not np.signbit(out[3])  # -0 - -0 = +0
+        oracle.eval_program([("VEC", 0), ("VEC", 1), ("ADD", 0), ("STORE", 2)], [a, b, out], path=path)
+        assert np.signbit(out[3]) and out[3] == 0  # -0 + -0 = -0
+        z = np.zeros(3, dtype=dt)
+        oracle.eval_program([("VEC", 0), ("NEG", 0), ("STORE", 1)], [np.zeros(3, dtype=dt), z], path=path)
+        assert np.all(np.signbit(z))
+    tiny = np.array([2.0 ** -149] * 4, dtype=np.float32)
+    out = np.zeros(4, dtype=np.float32)
+    oracle.eval_program([("VEC", 0), ("VEC", 0), ("ADD", 0), ("STORE", 1)], [tiny, out], path=path)
+    assert np.all(out == np.float32(2.0 ** -148))
+
+
+def check_invalid_programs(path):
+    bad = [
+        [("ADD", 0)],
+        [("VEC", 0), ("SCAL", 0), ("SMUL", 0), ("STORE", 0)],  # operands in wrong order
+        [("VEC", 0), ("VEC", 0)],  # leftover stack
+        [("VEC", 5), ("STORE", 0)],  # vector index out of range
+        [("SCAL", 0), ("STORE", 0)],  # storing a scalar
+    ]
+    for prog in bad:
+        v = [np.zeros(4), np.zeros(4)]
+        try:
+            oracle.eval_program(prog, v, [1.0], path=path)
+        except oracle.OracleProgramError:
+            continue
+        raise AssertionError(f"accepted invalid program {prog}")
+
+
+# -------------------------------------------------------------- reductions --
+
+def check_dot_closed_forms(path):
+    """sum_{i<n} i = n(n-1)/2 and sum i^2 = (n-1)n(2n-1)/6, exact in FP64
+    while below 2^53."""
+    for n in (0, 1, 2, 7, 1000, 2 ** 16 + 7, 2 ** 20):
+        for dt in (np.float64, np.float32):
+            if dt == np.float32 and n > 2 ** 24:
+                continue
+            x = np.arange(n, dtype=dt)
+            y = np.ones(n, dtype=dt)
+            assert oracle.dot(x, y, path=path) == n * (n - 1) // 2, (n, dt)
+            if n <= 2 ** 17:
+                s2 = (n - 1) * n * (2 * n - 1) // 6
+                assert oracle.dot(x, x, path=path) == s2, (n, dt)
+                assert oracle.eval_program([("VEC", 0), ("SUMSQ", 0)], [x], path=path)[0] == s2
+                assert oracle.eval_program([("VEC", 0), ("VEC", 1), ("DOT", 0)], [x, y], path=path)[0] == n * (n - 1) // 2
+
+
+def check_nrm2_closed_forms(path):
+    """nrm2(0..n-1) = correctly rounded sqrt of the exact integer sum of
+    squares; math.sqrt is correctly rounded (IEEE 754)."""
+    for n in (0, 1, 2, 3, 10, 1000, 2 ** 17):
+        for dt in (np.float64, np.float32):
+            x = np.arange(n, dtype=dt)
+            s2 = (n - 1) * n * (2 * n - 1) // 6 if n else 0
+            assert oracle.nrm2(x, path=path) == math.sqrt(s2), (n, dt)
+            assert oracle.nrm2(-x, path=path) == math.sqrt(s2), (n, dt)
+
+
+def check_nrm2_scaling(path):
+    """c * ones(4^k) has norm c * 2^k exactly, including c = 2^+-600 whose
+    squares overflow / underflow FP64 without scaling."""
+    for dt, cs in ((np.float64, (2.0 ** 600, 2.0 ** -600, 3.0, 2.0 ** -1000)), (np.float32, (2.0 ** 100, 2.0 ** -100, 3.0))):
+        for c in cs:
+            for k in (0, 1, 3, 6):
+                x = np.full(4 ** k, c, dtype=dt)
+                assert oracle.nrm2(x, path=path) == c * 2 ** k, (dt, c, k, oracle.nrm2(x, path=path))
+
+
+def check_dot_error_bound(path):
+    """Plain sequential FP64 dot: |err| <= gamma_n sum|x_i y_i| (Higham,
+    Eq. 3.5) against the exactly rounded reference; and FP32 inputs are
+    widened, so the same FP64 bound holds."""
+    rng = np.random.default_rng(8)
+    for n in (1000, 2 ** 16 + 7, 2 ** 20):
+        for dt in (np.float64, np.float32):
+            x = rng.uniform(-1, 1, n).astype(dt)
+            y = rng.uniform(-1, 1, n).astype(dt)
+            got = oracle.dot(x, y, path=path)
+            ref = exact.exact_dot(x, y)
+            bound = exact.gamma(n, U64) * exact.abs_dot(x, y)
+            assert abs(got - ref) <= bound, (n, dt, got, ref, bound)
+            got_p = oracle.eval_program([("VEC", 0), ("VEC", 1), ("DOT", 0)], [x, y], path=path)[0]
+            assert abs(got_p - ref) <= bound
+            nr = oracle.nrm2(x, path=path)
+            nref = exact.exact_nrm2(x)
+            assert abs(nr - nref) <= (exact.gamma(n + 2, U64) + 2 * U64) * nref, (n, dt)
+
+
+ALL_CHECKS = [
+    check_figure1_golden,
+    check_d_integer_identity,
+    check_e_and_axpby_exact,
+    check_brute_force_random_programs,
+    check_tail_lengths,
+    check_cg_store_then_load,
+    check_special_values,
+    check_invalid_programs,
+    check_dot_closed_forms,
+    check_nrm2_closed_forms,
+    check_nrm2_scaling,
+    check_dot_error_bound,
+]

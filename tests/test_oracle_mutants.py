@@ -1,0 +1,81 @@
+"""Planted mistakes in the oracle must be caught by its pins (CPU only).
+
+Each mutant is a copy of oracle.c with one plausible mistake -- a swapped
+operand, a dropped term or element, a wrong index or sign, a missing
+widening, FMA contraction left on -- compiled to a scratch library.  The pin
+checks of ``oracle_pins`` must reject every one of them."""
+import os
+import platform
+
+import pytest
+
+import oracle
+import oracle_pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+# (name, original text, occurrence index, replacement)
+MUTANTS = [
+    ("f64_sub_swapped", "t[i] = a[i] - b[i];", 0, "t[i] = b[i] - a[i];"),
+    ("f32_sub_swapped", "t[i] = a[i] - b[i];", 1, "t[i] = b[i] - a[i];"),
+    ("f64_add_drops_last", "for (int64_t i = 0; i < n; ++i) t[i] = a[i] + b[i];", 0,
+     "for (int64_t i = 0; i + 1 < n; ++i) t[i] = a[i] + b[i]; if (n > 0) t[n - 1] = 0;"),
+    ("f32_wrong_scalar", "st[sp].s = (float)scal[k];", 0, "st[sp].s = (float)scal[0];"),
+    ("f64_store_skips_first", "for (int64_t i = 0; i < n; ++i) vecs[k][i] = v[i];", 0,
+     "for (int64_t i = 1; i < n; ++i) vecs[k][i] = v[i];"),
+    ("f32_load_reversed", "for (int64_t i = 0; i < n; ++i) t[i] = vecs[k][i];", 1,
+     "for (int64_t i = 0; i < n; ++i) t[i] = vecs[k][n - 1 - i];"),
+    ("f64_mul_is_add", "t[i] = a[i] * b[i];", 0, "t[i] = a[i] + b[i];"),
+    ("f32_smul_wrong_operand", "t[i] = s * v[i];", 1, "t[i] = s * s;"),
+    ("f64_neg_noop", "v[i] = -v[i];", 0, "v[i] = v[i];"),
+    ("f32_neg_noop", "v[i] = -v[i];", 1, "v[i] = v[i];"),
+    ("f64_dot_program_uses_a_twice", "acc = acc + a[i] * b[i];", 0, "acc = acc + a[i] * a[i];"),
+    ("f32_sumsq_wrong_index", "acc = acc + (double)a[i] * (double)a[i];", 0,
+     "acc = acc + (double)a[i] * (double)a[0];"),
+    ("dot_f64_drops_last", "for (int64_t i = 0; i < n; ++i) acc = acc + x[i] * y[i];", 0,
+     "for (int64_t i = 0; i + 1 < n; ++i) acc = acc + x[i] * y[i];"),
+    ("dot_f32_not_widened", "acc = acc + (double)x[i] * (double)y[i];", 0,
+     "acc = acc + (double)(x[i] * y[i]);"),
+    ("nrm2_f64_scale_sign", "return ldexp(sqrt(acc), e);", 0, "return ldexp(sqrt(acc), -e);"),
+    ("nrm2_f64_no_scaling", "double t = ldexp(x[i], -e);", 0, "double t = x[i]; e = 0;"),
+    ("nrm2_f32_no_sqrt", "  return sqrt(acc);\n}", 0, "  return acc;\n}"),
+]
+
+
+def _mutate(text, old, occ, new):
+    parts = text.split(old)
+    assert len(parts) >= occ + 2, f"anchor {old!r} occurrence {occ} missing"
+    return old.join(parts[: occ + 1]) + new + old.join(parts[occ + 1:])
+
+
+def _pins_fail(path):
+    for check in oracle_pins.ALL_CHECKS:
+        try:
+            check(path)
+        except Exception:
+            return check.__name__
+    return None
+
+
+@pytest.mark.parametrize("name,old,occ,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, old, occ, new):
+    text = open(SRC).read()
+    src = tmp_path / f"{name}.c"
+    src.write_text(_mutate(text, old, occ, new))
+    lib = oracle.build(str(src), str(tmp_path / f"lib{name}.so"))
+    assert _pins_fail(lib) is not None, f"mutant {name} passed every pin"
+
+
+def test_unfused_oracle_is_immune_to_fma_contraction(tmp_path):
+    """Every node of the oracle writes its own temporary array, so even a
+    build with FMA contraction on (gcc's default on aarch64) has nothing to
+    contract between nodes: all pins still pass.  The product build keeps
+    contraction off all the same."""
+    import subprocess
+    extra = ["-ffp-contract=fast"]
+    if platform.machine() in ("x86_64", "AMD64"):
+        extra.append("-mfma")
+    cflags = [f for f in oracle.CFLAGS if f != "-ffp-contract=off"]
+    out = str(tmp_path / "libfma.so")
+    subprocess.run(["gcc", *cflags, *extra, "-o", out, SRC, "-lm"], check=True)
+    assert _pins_fail(out) is None
