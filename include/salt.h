@@ -1,0 +1,255 @@
+/*
+ * salt.h -- C ABI of the SALT fused vector-expression library for GB300
+ * (sm_103a).
+ *
+ * The paper (Progsch, Ineichen, Adelmann, "A New Vectorization Technique for
+ * Expression Templates in C++", arXiv:1109.1264) builds, at compile time, an
+ * expression tree of vector operations (Section 2, Figure 1: d = a + (b - c)
+ * as Store<Vector, ExprAdd<Vector, ExprSub<Vector, Vector>>>) and evaluates
+ * it lazily in ONE loop over the elements when it is assigned, or when a dot
+ * product or norm consumes it (Section 2).  Section 4 assembles that loop from
+ * three parts: a vectorizer (Section 3), loop templates that issue bursts of
+ * loads, operations and stores (Section 4.3) and the tree's per-node methods
+ * (Section 4.2, Listing 1), selected by an execute function (Section 4.1,
+ * Figure 2).  Section 5 benchmarks xDOT, xSCAL, xAXPY and an out-of-place
+ * scaling.
+ *
+ * This library takes the expression tree as a postfix PROGRAM at run time,
+ * validates and types it on the host, and runs it as one fused GPU kernel:
+ * each operand element is read from HBM once and each result element written
+ * once.
+ *
+ * Conventions for every entry point below:
+ *  - Vectors are dense, contiguous, caller-owned DEVICE memory of the
+ *    call's dtype, each 16-byte aligned (cudaMalloc / torch allocations are).
+ *    The library never frees or retains them.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on that stream; results are valid once the caller has
+ *    synchronised with it.
+ *  - Reduction results are written as double to caller-owned DEVICE memory.
+ *  - Argument and program errors are detected on the host and returned before
+ *    anything is launched.  CUDA failures return SALT_ERR_CUDA; the text of
+ *    the last error of the calling thread is available from
+ *    salt_last_error().
+ *  - The library owns only small per-(device, stream) workspaces for
+ *    reduction partials, created on the first reducing call on that stream
+ *    (so make that first call before capturing the stream into a CUDA graph)
+ *    and kept until salt_release_workspaces() or process exit.  Calls that
+ *    reduce on the SAME stream are ordered; calls on different streams use
+ *    different workspaces.
+ *  - n == 0 is valid: nothing is written to vectors and every reduction
+ *    result is 0.
+ */
+#ifndef SALT_H
+#define SALT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Element types. */
+typedef enum { SALT_F32 = 0, SALT_F64 = 1 } salt_dtype;
+
+/* Status codes. */
+typedef enum {
+  SALT_OK = 0,
+  SALT_ERR_ARG = 1,      /* bad size, count, NULL pointer, bad flag          */
+  SALT_ERR_PROGRAM = 2,  /* malformed or ill-typed program                    */
+  SALT_ERR_DTYPE = 3,    /* unknown dtype, or operands of different dtypes    */
+  SALT_ERR_ALIGN = 4,    /* a vector pointer is not 16-byte aligned           */
+  SALT_ERR_ALIAS = 5,    /* an output overlaps another operand's memory       */
+  SALT_ERR_BUDGET = 6,   /* request larger than a budget or capacity          */
+  SALT_ERR_TIMEOUT = 7,  /* a bounded host wait ran out                       */
+  SALT_ERR_CUDA = 8,     /* a CUDA runtime call failed                        */
+  SALT_ERR_NOTFOUND = 9  /* unknown request / handle                          */
+} salt_status;
+
+/* Program opcodes (one byte each).  The program is the expression tree in
+ * postfix order (Section 2, Figure 1); evaluation is per element, so every
+ * node sees element i of its operands only.
+ *   VEC k    push vector operand k (reads element i of vecs[k]; after a
+ *            STORE k earlier in the program it reads the stored value)
+ *   SCAL k   push scalar operand k (a loop constant: the paper's
+ *            load_once/TemporaryStorage, Section 4.2)
+ *   ADD      pop b, pop a, push a + b        (ExprAdd, Figure 1)
+ *   SUB      pop b, pop a, push a - b        (ExprSub, Figure 1)
+ *   MUL      pop b, pop a, push a * b        (elementwise product)
+ *   SMUL     pop v (vector), pop s (scalar), push s * v   (xSCAL / xAXPY)
+ *   NEG      pop a, push -a
+ *   STORE k  pop a, assign it to vector k   (Store root, Figure 1)
+ *   DOT      pop b, pop a, accumulate sum_i a_i * b_i into the next result
+ *   SUMSQ    pop a, accumulate sum_i a_i * a_i into the next result
+ * Every node computes in the program's dtype, round-to-nearest-even, with no
+ * fused multiply-add, in exactly this order: elementwise results are
+ * bit-identical to evaluating the tree one node at a time.  Scalars are given
+ * as double and rounded once to float for an F32 program.  Reductions: see
+ * salt_dot. */
+typedef enum {
+  SALT_OP_VEC = 0,
+  SALT_OP_SCAL = 1,
+  SALT_OP_ADD = 2,
+  SALT_OP_SUB = 3,
+  SALT_OP_MUL = 4,
+  SALT_OP_SMUL = 5,
+  SALT_OP_NEG = 6,
+  SALT_OP_STORE = 7,
+  SALT_OP_DOT = 8,
+  SALT_OP_SUMSQ = 9
+} salt_opcode;
+
+typedef struct {
+  uint8_t op;  /* salt_opcode                                   */
+  uint8_t arg; /* operand index for VEC / SCAL / STORE, else 0  */
+} salt_insn;
+
+#define SALT_MAX_PROG 32  /* instructions per program       */
+#define SALT_MAX_VECS 8   /* vector operands per program    */
+#define SALT_MAX_SCALS 8  /* scalar operands per program    */
+#define SALT_MAX_STACK 8  /* evaluation stack depth         */
+#define SALT_MAX_REDS 4   /* DOT / SUMSQ results per program */
+
+/* Reduction flags. */
+#define SALT_DEFAULT 0
+/* F32 only: plain FP32 accumulation and FP32 combination, no compensation
+ * (a comparison mode; less accurate). */
+#define SALT_PLAIN 1
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t salt_version(void);
+
+/* Text of a status code (static storage). */
+const char* salt_status_str(int32_t status);
+
+/* Text of the last error reported on the calling thread ("" if none). */
+const char* salt_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * salt_check_program -- host-only validation and typing of a program
+ * (no GPU needed).  Checks opcodes, operand indices against nvecs / nscal,
+ * operand types (ADD/SUB/MUL/DOT take two vectors, SMUL a scalar below a
+ * vector, NEG/STORE/SUMSQ a vector), stack depth <= SALT_MAX_STACK, an empty
+ * stack at the end, at least one STORE or reduction, <= SALT_MAX_REDS
+ * reductions.
+ * Outputs (any may be NULL):
+ *   nred_out      number of DOT/SUMSQ results,
+ *   compiled_out  1 if the program has a compile-time instantiation (the
+ *                 fast path; the paper's expression templates, Section 2),
+ *                 0 if it runs on the generic interpreter kernel.
+ * Returns SALT_OK or SALT_ERR_PROGRAM / SALT_ERR_ARG. */
+salt_status salt_check_program(const salt_insn* prog, int32_t nprog, int32_t nvecs,
+                               int32_t nscal, int32_t* nred_out, int32_t* compiled_out);
+
+/* ---------------------------------------------------------------------------
+ * salt_eval -- evaluate a fused expression program over n elements
+ * (Section 2 lazy evaluation at the Store root / dot / norm; Section 4 loop).
+ *   prog, nprog      the postfix program (host memory, read during the call)
+ *   dtype            SALT_F32 or SALT_F64, the type of every vector
+ *   n                element count (>= 0)
+ *   vecs, nvecs      host array of nvecs device pointers; vecs[k] is operand
+ *                    k.  Only operands the program names must be non-NULL.
+ *   scalars, nscal   host array of scalar operands (read during the call)
+ *   red_out          device array of >= nred doubles receiving the DOT/SUMSQ
+ *                    results in program order; may be NULL if nred == 0
+ *   stream           cudaStream_t
+ * Aliasing: an operand that is stored may be read by the same program only
+ * through the same operand index (exact in-place update, e.g. y = a*x + b*y).
+ * If a stored operand's memory overlaps any other named operand's memory the
+ * call returns SALT_ERR_ALIAS.  Two read-only operands may share memory.
+ * Errors: SALT_ERR_ARG, SALT_ERR_PROGRAM, SALT_ERR_DTYPE, SALT_ERR_ALIGN,
+ * SALT_ERR_ALIAS (nothing launched), SALT_ERR_CUDA. */
+salt_status salt_eval(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                      void* const* vecs, int32_t nvecs, const double* scalars, int32_t nscal,
+                      double* red_out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * salt_axpby -- y <- alpha*x + beta*y (Section 5's xAXPY generalised; xSCAL
+ * when x is not used is salt_eval's SCAL VEC SMUL STORE).  Same as
+ * salt_eval of  SCAL0 VEC0 SMUL SCAL1 VEC1 SMUL ADD STORE1  with
+ * vecs = {x, y}: beta*y is always computed (no beta == 0 shortcut, so NaN
+ * in y propagates).  x and y must not overlap unless x == y.
+ * Errors as salt_eval. */
+salt_status salt_axpby(int32_t dtype, int64_t n, double alpha, const void* x, double beta,
+                       void* y, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * salt_dot -- *out = sum_i x_i * y_i  (Section 5, xDOT; Section 2: the dot
+ * product is where the tree is evaluated).
+ *   out    device pointer to one double
+ *   flags  SALT_DEFAULT or SALT_PLAIN
+ * F64: per-thread FP64 fused multiply-add accumulation, FP64 warp / block /
+ *      cross-block combination in a fixed order (deterministic for given n).
+ * F32 (default): per-thread FP32 TwoProduct + TwoSum compensated
+ *      accumulation (Ogita, Rump and Oishi 2005, "Accurate sum and dot
+ *      product", Dot2), each thread's (sum, correction) pair widened to FP64,
+ *      FP64 combination.  SALT_PLAIN: FP32 accumulation and combination.
+ * The summation order differs from a sequential loop (as the paper's own
+ * unrolled loop differs: per-unroll accumulators combined by reduction(),
+ * Section 4.2); results are reproducible run to run for the same n. */
+salt_status salt_dot(int32_t dtype, int64_t n, const void* x, const void* y, double* out,
+                     int32_t flags, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * salt_nrm2 -- *out = sqrt(sum_i x_i^2) without overflow or underflow for
+ * any finite input (the norm of Section 2).  Per element, |x_i| is sorted
+ * into small / medium / big ranges and squared after scaling by a power of
+ * two (Blue, ACM TOMS 4(1), 1978, "A portable Fortran program to find the
+ * Euclidean norm of a vector"), three accumulators per thread (the medium one
+ * compensated in F32), FP64 combination and final square root.
+ *   out    device pointer to one double; flags as salt_dot. */
+salt_status salt_nrm2(int32_t dtype, int64_t n, const void* x, double* out, int32_t flags,
+                      void* stream);
+
+/* ---------------------------------------------------------------------------
+ * salt_fill_uniform -- x[i] = element (offset + i) of the counter-based
+ * uniform[-1, 1) stream keyed by `key`: z = key + (offset + i + 1) *
+ * 0x9E3779B97F4A7C15 (mod 2^64), h = SplitMix64 finaliser of z (Steele, Lea,
+ * Flood 2014); F64 value 2*(h >> 11)*2^-53 - 1, F32 value
+ * 2*(h >> 40)*2^-24 - 1 (both exact).  Synthetic-input generator so that
+ * multi-GB operands need no host upload.  Errors: SALT_ERR_ARG,
+ * SALT_ERR_DTYPE, SALT_ERR_ALIGN, SALT_ERR_CUDA. */
+salt_status salt_fill_uniform(int32_t dtype, int64_t n, uint64_t key, int64_t offset, void* x,
+                              void* stream);
+
+/* Free every workspace the library holds (call with no library work in
+ * flight).  Returns SALT_OK or SALT_ERR_CUDA. */
+salt_status salt_release_workspaces(void);
+
+/* ---------------------------------------------------------------------------
+ * Launch configuration (the paper chose its loop unrolling and the number
+ * of instruction packages per loop "by trial", Section 4.3; here an autotuner
+ * chooses unroll depth, vector width and block/grid shape per program shape,
+ * dtype and size bucket).
+ *   unroll        vector accesses per operand per thread per tile (1, 2, 4)
+ *   vec_bytes     bytes per vector access (16 or 32)
+ *   block         threads per block (64..1024, multiple of 32)
+ *   blocks_per_sm resident blocks per SM the grid is sized for (1..32)
+ * salt_tune_set pins a configuration for (program, dtype, n bucket) where the
+ * bucket is floor(log2(max(n,1))); salt_tune_get reports the configuration a
+ * call would use.  Returns SALT_ERR_ARG for an invalid configuration or
+ * SALT_ERR_PROGRAM for a program without a compile-time instantiation. */
+typedef struct {
+  int32_t unroll;
+  int32_t vec_bytes;
+  int32_t block;
+  int32_t blocks_per_sm;
+} salt_launch_cfg;
+
+salt_status salt_tune_set(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                          const salt_launch_cfg* cfg);
+salt_status salt_tune_get(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                          salt_launch_cfg* cfg);
+/* Forget every pinned configuration. */
+salt_status salt_tune_clear(void);
+
+/* Number of kernel launches this library has issued on the calling process
+ * (all threads), for accounting in benchmarks. */
+int64_t salt_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SALT_H */

@@ -1,0 +1,531 @@
+// The C ABI (include/salt.h): argument checks, the execute function that
+// picks a kernel and its launch shape, per-stream reduction workspaces.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+
+#include "../../include/salt.h"
+#include "fused.cuh"
+#include "host.h"
+#include "interp.cuh"
+#include "reduce.cuh"
+#include "registry.h"
+
+namespace salt {
+
+// ------------------------------------------------------------------ state --
+static thread_local std::string t_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+static salt_status set_error(salt_status st, const std::string& msg) {
+  t_last_error = msg;
+  return st;
+}
+static salt_status cuda_error(cudaError_t e, const char* where) {
+  return set_error(SALT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+Registry& registry() {
+  static Registry r;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    register_f32_vb16(r);
+    register_f32_vb32(r);
+    register_f64_vb16(r);
+    register_f64_vb32(r);
+    register_misc(r);
+  });
+  return r;
+}
+
+struct DevInfo {
+  int sms = 0;
+};
+static std::mutex g_dev_mu;
+static std::map<int, DevInfo> g_dev;
+
+static salt_status device_info(int* dev, DevInfo* info) {
+  cudaError_t e = cudaGetDevice(dev);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  auto it = g_dev.find(*dev);
+  if (it == g_dev.end()) {
+    DevInfo d;
+    e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, *dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaDeviceGetAttribute");
+    it = g_dev.emplace(*dev, d).first;
+  }
+  *info = it->second;
+  return SALT_OK;
+}
+
+// Reduction workspace: per-block partials and the last-block ticket, one per
+// (device, stream) so that reductions on different streams never share it.
+constexpr int kMaxBlocksPerSM = 32;
+constexpr int kPartialsPerBlock = 4;
+struct Workspace {
+  double* partials = nullptr;
+  unsigned* ticket = nullptr;
+  int capacity_blocks = 0;
+};
+static std::mutex g_ws_mu;
+static std::map<std::pair<int, cudaStream_t>, Workspace> g_ws;
+
+static salt_status workspace(int dev, const DevInfo& info, cudaStream_t s, Workspace* out) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  auto key = std::make_pair(dev, s);
+  auto it = g_ws.find(key);
+  if (it != g_ws.end()) {
+    *out = it->second;
+    return SALT_OK;
+  }
+  Workspace w;
+  w.capacity_blocks = info.sms * kMaxBlocksPerSM;
+  const size_t bytes = (size_t)w.capacity_blocks * kPartialsPerBlock * sizeof(double) + 256;
+  void* mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, bytes);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(workspace)");
+  // The ticket must be zero before the first launch; every launch leaves it
+  // at zero again.  A synchronous memset keeps this independent of `s`.
+  e = cudaMemset(mem, 0, bytes);
+  if (e != cudaSuccess) {
+    cudaFree(mem);
+    return cuda_error(e, "cudaMemset(workspace)");
+  }
+  w.ticket = (unsigned*)mem;
+  w.partials = (double*)((char*)mem + 256);
+  g_ws.emplace(key, w);
+  *out = w;
+  return SALT_OK;
+}
+
+// --------------------------------------------------------------- tuning ---
+// Key: (kernel family, dtype, log2 bucket).  Family: shape id, 100 + special
+// id, or 200 for the interpreter.
+using TuneKey = std::tuple<int, int, int>;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, salt_launch_cfg> g_tune;
+
+static int bucket_of(int64_t n) {
+  int b = 0;
+  while (b < 62 && (int64_t(1) << (b + 1)) <= n) ++b;
+  return b;
+}
+
+static bool cfg_valid(const salt_launch_cfg& c) {
+  return unroll_index(c.unroll) >= 0 && vb_index(c.vec_bytes) >= 0 && c.block >= 64 &&
+         c.block <= 256 && c.block % 32 == 0 && c.blocks_per_sm >= 1 &&
+         c.blocks_per_sm <= kMaxBlocksPerSM && c.block * c.blocks_per_sm <= 2048;
+}
+
+static salt_launch_cfg default_cfg(int family, int dt) {
+  salt_launch_cfg c;
+  c.unroll = 2;
+  c.vec_bytes = 16;
+  c.block = 256;
+  c.blocks_per_sm = 0;  // 0: as many as fit (occupancy)
+  (void)family;
+  (void)dt;
+  return c;
+}
+
+static salt_launch_cfg lookup_cfg(int family, int dt, int64_t n) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(TuneKey(family, dt, bucket_of(n)));
+  return it != g_tune.end() ? it->second : default_cfg(family, dt);
+}
+
+static int occupancy_blocks(const void* kernel, int block, size_t smem) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return nb < 1 ? 1 : nb;
+}
+
+static int grid_for(int64_t n, int64_t tile_elems, int sms, int bps) {
+  int64_t want = (n + tile_elems - 1) / tile_elems;
+  int64_t cap = (int64_t)sms * bps;
+  if (want > cap) want = cap;
+  if (want < 1) want = 1;
+  return (int)want;
+}
+
+// ------------------------------------------------------------ arguments ---
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+static salt_status check_dtype(int32_t dt) {
+  if (dt != SALT_F32 && dt != SALT_F64) return set_error(SALT_ERR_DTYPE, "dtype must be SALT_F32 or SALT_F64");
+  return SALT_OK;
+}
+
+// ------------------------------------------------------------ execution ---
+struct EvalArgs {
+  const salt_insn* prog;
+  int nprog;
+  int dt;
+  int64_t n;
+  void* const* vecs;
+  int nvecs;
+  const double* scalars;
+  int nscal;
+  double* red_out;
+  cudaStream_t stream;
+};
+
+template <typename T>
+static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, const DevInfo& info) {
+  Registry& reg = registry();
+  const int shape = find_shape(c);
+  const int dt = sizeof(T) == 4 ? DT_F32 : DT_F64;
+  // 32-byte vectors need 32-byte aligned operands.
+  bool all32 = true;
+  for (int k = 0; k < c.nvec; ++k) all32 = all32 && aligned(a.vecs[c.vec_user[k]], 32);
+
+  Workspace ws;
+  if (c.nred > 0) {
+    salt_status st = workspace(dev, info, a.stream, &ws);
+    if (st != SALT_OK) return st;
+  }
+
+  if (shape >= 0) {
+    salt_launch_cfg cfg = lookup_cfg(shape, dt, a.n);
+    if (cfg.vec_bytes == 32 && !all32) cfg.vec_bytes = 16;
+    const KernelEntry& ke = reg.fused[shape][dt][unroll_index(cfg.unroll)][vb_index(cfg.vec_bytes)];
+    int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy_blocks(ke.kernel, cfg.block, 0);
+    if (bps > kMaxBlocksPerSM) bps = kMaxBlocksPerSM;
+    const int64_t vec = cfg.vec_bytes / (int64_t)sizeof(T);
+    const int grid = grid_for(a.n, (int64_t)cfg.unroll * cfg.block * vec, info.sms, bps);
+    MapParams<T> p;
+    memset(&p, 0, sizeof p);
+    for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]];
+    for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
+    p.n = a.n;
+    p.red_out = a.red_out;
+    p.partials = ws.partials;
+    p.ticket = ws.ticket;
+    cudaError_t e = ke.launch(&p, grid, cfg.block, 0, a.stream);
+    g_launches.fetch_add(1);
+    if (e != cudaSuccess) return cuda_error(e, "fused kernel launch");
+    return SALT_OK;
+  }
+
+  // Generic interpreter.
+  InterpParams<T> p;
+  memset(&p, 0, sizeof p);
+  int len = 0;
+  if (!lower(c, p.code, &len))
+    return set_error(SALT_ERR_PROGRAM, "program too long for the interpreter after lowering");
+  p.len = len;
+  p.nred = c.nred;
+  p.load_mask = c.load_mask;
+  p.store_mask = c.store_mask;
+  for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]];
+  for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
+  p.n = a.n;
+  p.red_out = a.red_out;
+  p.partials = ws.partials;
+  p.ticket = ws.ticket;
+  salt_launch_cfg cfg = lookup_cfg(200, dt, a.n);
+  if (cfg.vec_bytes == 32 && !all32) cfg.vec_bytes = 16;
+  const KernelEntry& ke = reg.interp[dt][vb_index(cfg.vec_bytes)];
+  const size_t smem = (size_t)kRegs * cfg.block * cfg.vec_bytes;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(ke.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
+  }
+  int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy_blocks(ke.kernel, cfg.block, smem);
+  if (bps > kMaxBlocksPerSM) bps = kMaxBlocksPerSM;
+  const int64_t vec = cfg.vec_bytes / (int64_t)sizeof(T);
+  const int grid = grid_for(a.n, (int64_t)cfg.block * vec, info.sms, bps);
+  cudaError_t e = ke.launch(&p, grid, cfg.block, smem, a.stream);
+  g_launches.fetch_add(1);
+  if (e != cudaSuccess) return cuda_error(e, "interpreter kernel launch");
+  return SALT_OK;
+}
+
+static salt_status eval_impl(const EvalArgs& a) {
+  salt_status st = check_dtype(a.dt);
+  if (st != SALT_OK) return st;
+  if (a.n < 0) return set_error(SALT_ERR_ARG, "n must be >= 0");
+  Analysis an;
+  std::string err;
+  st = analyse(a.prog, a.nprog, a.nvecs, a.nscal, &an, &err);
+  if (st != SALT_OK) return set_error(st, err);
+  if (an.used_vecs && !a.vecs) return set_error(SALT_ERR_ARG, "vecs is NULL");
+  if (an.used_scals && !a.scalars) return set_error(SALT_ERR_ARG, "scalars is NULL");
+  if (an.nred > 0 && !a.red_out) return set_error(SALT_ERR_ARG, "red_out is NULL but the program reduces");
+  if (a.red_out && !aligned(a.red_out, 8)) return set_error(SALT_ERR_ALIGN, "red_out must be 8-byte aligned");
+  const size_t es = a.dt == SALT_F32 ? 4 : 8;
+  for (int k = 0; k < a.nvecs && a.n > 0; ++k) {
+    if (!((an.used_vecs >> k) & 1u)) continue;
+    if (!a.vecs[k]) {
+      char b[96];
+      snprintf(b, sizeof b, "vector operand %d is NULL", k);
+      return set_error(SALT_ERR_ARG, b);
+    }
+    if (!aligned(a.vecs[k], 16)) {
+      char b[96];
+      snprintf(b, sizeof b, "vector operand %d is not 16-byte aligned", k);
+      return set_error(SALT_ERR_ALIGN, b);
+    }
+  }
+  // An output may share memory with an input only through the same operand
+  // index (exact in-place update).
+  const uintptr_t bytes = (uintptr_t)a.n * es;
+  for (int i = 0; i < a.nvecs; ++i) {
+    if (!((an.used_vecs >> i) & 1u)) continue;
+    for (int j = i + 1; j < a.nvecs; ++j) {
+      if (!((an.used_vecs >> j) & 1u)) continue;
+      if (!(((an.stored_vecs >> i) | (an.stored_vecs >> j)) & 1u)) continue;
+      const uintptr_t pi = (uintptr_t)a.vecs[i], pj = (uintptr_t)a.vecs[j];
+      if (bytes > 0 && pi < pj + bytes && pj < pi + bytes) {
+        char b[128];
+        snprintf(b, sizeof b, "operands %d and %d overlap and one of them is stored", i, j);
+        return set_error(SALT_ERR_ALIAS, b);
+      }
+    }
+  }
+  int dev = 0;
+  DevInfo info;
+  st = device_info(&dev, &info);
+  if (st != SALT_OK) return st;
+  if (a.n == 0) {
+    if (an.nred > 0) {
+      cudaError_t e = cudaMemsetAsync(a.red_out, 0, sizeof(double) * an.nred, a.stream);
+      if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+    }
+    return SALT_OK;
+  }
+  Canonical c;
+  canonicalise(a.prog, a.nprog, &c);
+  return a.dt == SALT_F32 ? run_eval<float>(a, c, dev, info) : run_eval<double>(a, c, dev, info);
+}
+
+// Reductions with their own kernels (nrm2, plain F32 dot).
+static salt_status run_special(int special, int dt, int64_t n, const void* x, const void* y,
+                               double* out, cudaStream_t s) {
+  int dev = 0;
+  DevInfo info;
+  salt_status st = device_info(&dev, &info);
+  if (st != SALT_OK) return st;
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double), s);
+    return e == cudaSuccess ? SALT_OK : cuda_error(e, "cudaMemsetAsync");
+  }
+  Workspace ws;
+  st = workspace(dev, info, s, &ws);
+  if (st != SALT_OK) return st;
+  salt_launch_cfg cfg = lookup_cfg(100 + special, dt, n);
+  if (cfg.vec_bytes == 32 && !(aligned(x, 32) && (!y || aligned(y, 32)))) cfg.vec_bytes = 16;
+  const KernelEntry& ke = registry().special[special][dt][unroll_index(cfg.unroll)][vb_index(cfg.vec_bytes)];
+  int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy_blocks(ke.kernel, cfg.block, 0);
+  if (bps > kMaxBlocksPerSM) bps = kMaxBlocksPerSM;
+  const int64_t vec = cfg.vec_bytes / (dt == DT_F32 ? 4 : 8);
+  const int grid = grid_for(n, (int64_t)cfg.unroll * cfg.block * vec, info.sms, bps);
+  cudaError_t e;
+  if (special == SPECIAL_DOT_PLAIN) {
+    DotParams p{x, y, n, out, ws.partials, ws.ticket};
+    e = ke.launch(&p, grid, cfg.block, 0, s);
+  } else {
+    NrmParams p{x, n, out, ws.partials, ws.ticket};
+    e = ke.launch(&p, grid, cfg.block, 0, s);
+  }
+  g_launches.fetch_add(1);
+  return e == cudaSuccess ? SALT_OK : cuda_error(e, "reduction kernel launch");
+}
+
+}  // namespace salt
+
+using namespace salt;
+
+// ================================================================== C ABI ==
+extern "C" {
+
+int32_t salt_version(void) { return 10000; }
+
+const char* salt_status_str(int32_t st) {
+  switch (st) {
+    case SALT_OK: return "SALT_OK";
+    case SALT_ERR_ARG: return "SALT_ERR_ARG";
+    case SALT_ERR_PROGRAM: return "SALT_ERR_PROGRAM";
+    case SALT_ERR_DTYPE: return "SALT_ERR_DTYPE";
+    case SALT_ERR_ALIGN: return "SALT_ERR_ALIGN";
+    case SALT_ERR_ALIAS: return "SALT_ERR_ALIAS";
+    case SALT_ERR_BUDGET: return "SALT_ERR_BUDGET";
+    case SALT_ERR_TIMEOUT: return "SALT_ERR_TIMEOUT";
+    case SALT_ERR_CUDA: return "SALT_ERR_CUDA";
+    case SALT_ERR_NOTFOUND: return "SALT_ERR_NOTFOUND";
+    default: return "unknown status";
+  }
+}
+
+const char* salt_last_error(void) { return t_last_error.c_str(); }
+
+salt_status salt_check_program(const salt_insn* prog, int32_t nprog, int32_t nvecs, int32_t nscal,
+                               int32_t* nred_out, int32_t* compiled_out) {
+  Analysis an;
+  std::string err;
+  salt_status st = analyse(prog, nprog, nvecs, nscal, &an, &err);
+  if (st != SALT_OK) return set_error(st, err);
+  if (nred_out) *nred_out = an.nred;
+  if (compiled_out) {
+    Canonical c;
+    canonicalise(prog, nprog, &c);
+    *compiled_out = find_shape(c) >= 0 ? 1 : 0;
+  }
+  return SALT_OK;
+}
+
+salt_status salt_eval(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                      void* const* vecs, int32_t nvecs, const double* scalars, int32_t nscal,
+                      double* red_out, void* stream) {
+  EvalArgs a{prog, nprog, dtype, n, vecs, nvecs, scalars, nscal, red_out, (cudaStream_t)stream};
+  return eval_impl(a);
+}
+
+salt_status salt_axpby(int32_t dtype, int64_t n, double alpha, const void* x, double beta, void* y,
+                       void* stream) {
+  static const salt_insn prog[] = {{SALT_OP_SCAL, 0}, {SALT_OP_VEC, 0}, {SALT_OP_SMUL, 0},
+                                   {SALT_OP_SCAL, 1}, {SALT_OP_VEC, 1}, {SALT_OP_SMUL, 0},
+                                   {SALT_OP_ADD, 0},  {SALT_OP_STORE, 1}};
+  void* vecs[2] = {const_cast<void*>(x), y};
+  const double sc[2] = {alpha, beta};
+  if (x == y && x != nullptr) {
+    // x == y: same memory through two operand indices, one stored; express it
+    // with one operand so the in-place rule holds.
+    static const salt_insn prog1[] = {{SALT_OP_SCAL, 0}, {SALT_OP_VEC, 0}, {SALT_OP_SMUL, 0},
+                                      {SALT_OP_SCAL, 1}, {SALT_OP_VEC, 0}, {SALT_OP_SMUL, 0},
+                                      {SALT_OP_ADD, 0},  {SALT_OP_STORE, 0}};
+    EvalArgs a{prog1, 8, dtype, n, vecs, 1, sc, 2, nullptr, (cudaStream_t)stream};
+    return eval_impl(a);
+  }
+  EvalArgs a{prog, 8, dtype, n, vecs, 2, sc, 2, nullptr, (cudaStream_t)stream};
+  return eval_impl(a);
+}
+
+salt_status salt_dot(int32_t dtype, int64_t n, const void* x, const void* y, double* out,
+                     int32_t flags, void* stream) {
+  salt_status st = check_dtype(dtype);
+  if (st != SALT_OK) return st;
+  if (flags != SALT_DEFAULT && flags != SALT_PLAIN) return set_error(SALT_ERR_ARG, "unknown flags");
+  if (n < 0) return set_error(SALT_ERR_ARG, "n must be >= 0");
+  if (!out) return set_error(SALT_ERR_ARG, "out is NULL");
+  if (!aligned(out, 8)) return set_error(SALT_ERR_ALIGN, "out must be 8-byte aligned");
+  if (n > 0 && (!x || !y)) return set_error(SALT_ERR_ARG, "x or y is NULL");
+  if (!aligned(x, 16) || !aligned(y, 16)) return set_error(SALT_ERR_ALIGN, "x and y must be 16-byte aligned");
+  if (dtype == SALT_F32 && flags == SALT_PLAIN)
+    return run_special(SPECIAL_DOT_PLAIN, DT_F32, n, x, y, out, (cudaStream_t)stream);
+  static const salt_insn prog[] = {{SALT_OP_VEC, 0}, {SALT_OP_VEC, 1}, {SALT_OP_DOT, 0}};
+  void* vecs[2] = {const_cast<void*>(x), const_cast<void*>(y)};
+  EvalArgs a{prog, 3, dtype, n, vecs, 2, nullptr, 0, out, (cudaStream_t)stream};
+  return eval_impl(a);
+}
+
+salt_status salt_nrm2(int32_t dtype, int64_t n, const void* x, double* out, int32_t flags,
+                      void* stream) {
+  salt_status st = check_dtype(dtype);
+  if (st != SALT_OK) return st;
+  if (flags != SALT_DEFAULT && flags != SALT_PLAIN) return set_error(SALT_ERR_ARG, "unknown flags");
+  if (n < 0) return set_error(SALT_ERR_ARG, "n must be >= 0");
+  if (!out) return set_error(SALT_ERR_ARG, "out is NULL");
+  if (!aligned(out, 8)) return set_error(SALT_ERR_ALIGN, "out must be 8-byte aligned");
+  if (n > 0 && !x) return set_error(SALT_ERR_ARG, "x is NULL");
+  if (!aligned(x, 16)) return set_error(SALT_ERR_ALIGN, "x must be 16-byte aligned");
+  const int special = (dtype == SALT_F32 && flags == SALT_PLAIN) ? SPECIAL_NRM2_PLAIN : SPECIAL_NRM2;
+  return run_special(special, dtype == SALT_F32 ? DT_F32 : DT_F64, n, x, nullptr, out,
+                     (cudaStream_t)stream);
+}
+
+salt_status salt_fill_uniform(int32_t dtype, int64_t n, uint64_t key, int64_t offset, void* x,
+                              void* stream) {
+  salt_status st = check_dtype(dtype);
+  if (st != SALT_OK) return st;
+  if (n < 0 || offset < 0) return set_error(SALT_ERR_ARG, "n and offset must be >= 0");
+  if (n == 0) return SALT_OK;
+  if (!x) return set_error(SALT_ERR_ARG, "x is NULL");
+  if (!aligned(x, dtype == SALT_F32 ? 4 : 8)) return set_error(SALT_ERR_ALIGN, "x is misaligned");
+  int dev = 0;
+  DevInfo info;
+  st = device_info(&dev, &info);
+  if (st != SALT_OK) return st;
+  const int block = 256;
+  int64_t want = (n + block - 1) / block;
+  const int64_t cap = (int64_t)info.sms * 8;
+  const int grid = (int)(want < cap ? want : cap);
+  const int dt = dtype == SALT_F32 ? DT_F32 : DT_F64;
+  FillParams p{x, n, key, offset};
+  cudaError_t e = registry().fill[dt].launch(&p, grid, block, 0, (cudaStream_t)stream);
+  g_launches.fetch_add(1);
+  return e == cudaSuccess ? SALT_OK : cuda_error(e, "fill kernel launch");
+}
+
+salt_status salt_release_workspaces(void) {
+  std::lock_guard<std::mutex> lk(g_ws_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  salt_status st = SALT_OK;
+  for (auto& kv : g_ws) {
+    cudaSetDevice(kv.first.first);
+    cudaError_t e = cudaFree(kv.second.ticket);
+    if (e != cudaSuccess) st = cuda_error(e, "cudaFree(workspace)");
+  }
+  cudaSetDevice(cur);
+  g_ws.clear();
+  return st;
+}
+
+static salt_status tune_family(const salt_insn* prog, int32_t nprog, int* family) {
+  Analysis an;
+  std::string err;
+  salt_status st = analyse(prog, nprog, kMaxVecs, kMaxScals, &an, &err);
+  if (st != SALT_OK) return set_error(st, err);
+  Canonical c;
+  canonicalise(prog, nprog, &c);
+  const int s = find_shape(c);
+  *family = s >= 0 ? s : 200;
+  return SALT_OK;
+}
+
+salt_status salt_tune_set(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                          const salt_launch_cfg* cfg) {
+  salt_status st = check_dtype(dtype);
+  if (st != SALT_OK) return st;
+  if (!cfg || !cfg_valid(*cfg)) return set_error(SALT_ERR_ARG, "invalid launch configuration");
+  int fam = 0;
+  st = tune_family(prog, nprog, &fam);
+  if (st != SALT_OK) return st;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[TuneKey(fam, dtype == SALT_F32 ? DT_F32 : DT_F64, bucket_of(n))] = *cfg;
+  return SALT_OK;
+}
+
+salt_status salt_tune_get(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                          salt_launch_cfg* cfg) {
+  salt_status st = check_dtype(dtype);
+  if (st != SALT_OK) return st;
+  if (!cfg) return set_error(SALT_ERR_ARG, "cfg is NULL");
+  int fam = 0;
+  st = tune_family(prog, nprog, &fam);
+  if (st != SALT_OK) return st;
+  *cfg = lookup_cfg(fam, dtype == SALT_F32 ? DT_F32 : DT_F64, n);
+  return SALT_OK;
+}
+
+salt_status salt_tune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
+  return SALT_OK;
+}
+
+int64_t salt_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// Device building blocks shared by the SALT kernels: exact per-node
+// arithmetic, 128/256-bit vector memory access (the paper's vectorizer,
+// Section 3), reduction accumulators and deterministic block combination.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "prog.cuh"
+
+namespace salt {
+
+// ---------------------------------------------------------------------------
+// Arithmetic of one tree node: one correctly rounded IEEE operation, never
+// contracted into an FMA (the _rn intrinsics are exempt from contraction),
+// so a fused loop produces the same bits as evaluating node by node.
+template <typename T> struct Arith;
+template <> struct Arith<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+};
+template <> struct Arith<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+};
+
+// ---------------------------------------------------------------------------
+// The vectorizer: VB-byte vectors of T (VB = 16 or 32).  32-byte accesses are
+// the sm_100-family ld/st .v8.b32 / .v4.b64 forms.
+template <typename T, int VB>
+struct __align__(VB) VecT {
+  static constexpr int N = VB / (int)sizeof(T);
+  T e[N];
+};
+
+// RO: the operand is never written by this kernel, so the non-coherent
+// read-only path may be used.
+template <bool RO>
+__device__ __forceinline__ void vload(VecT<float, 16>& v, const float* p) {
+  if (RO)
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+        : "=f"(v.e[0]), "=f"(v.e[1]), "=f"(v.e[2]), "=f"(v.e[3]) : "l"(p));
+  else
+    asm volatile("ld.global.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.e[0]), "=f"(v.e[1]), "=f"(v.e[2]), "=f"(v.e[3]) : "l"(p) : "memory");
+}
+template <bool RO>
+__device__ __forceinline__ void vload(VecT<float, 32>& v, const float* p) {
+  if (RO)
+    asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(v.e[0]), "=f"(v.e[1]), "=f"(v.e[2]), "=f"(v.e[3]), "=f"(v.e[4]), "=f"(v.e[5]),
+          "=f"(v.e[6]), "=f"(v.e[7]) : "l"(p));
+  else
+    asm volatile("ld.global.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v.e[0]), "=f"(v.e[1]), "=f"(v.e[2]), "=f"(v.e[3]), "=f"(v.e[4]), "=f"(v.e[5]),
+                   "=f"(v.e[6]), "=f"(v.e[7]) : "l"(p) : "memory");
+}
+template <bool RO>
+__device__ __forceinline__ void vload(VecT<double, 16>& v, const double* p) {
+  if (RO)
+    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0,%1}, [%2];" : "=d"(v.e[0]), "=d"(v.e[1]) : "l"(p));
+  else
+    asm volatile("ld.global.L1::no_allocate.v2.f64 {%0,%1}, [%2];"
+                 : "=d"(v.e[0]), "=d"(v.e[1]) : "l"(p) : "memory");
+}
+template <bool RO>
+__device__ __forceinline__ void vload(VecT<double, 32>& v, const double* p) {
+  if (RO)
+    asm("ld.global.nc.L1::no_allocate.v4.f64 {%0,%1,%2,%3}, [%4];"
+        : "=d"(v.e[0]), "=d"(v.e[1]), "=d"(v.e[2]), "=d"(v.e[3]) : "l"(p));
+  else
+    asm volatile("ld.global.L1::no_allocate.v4.f64 {%0,%1,%2,%3}, [%4];"
+                 : "=d"(v.e[0]), "=d"(v.e[1]), "=d"(v.e[2]), "=d"(v.e[3]) : "l"(p) : "memory");
+}
+
+__device__ __forceinline__ void vstore(float* p, const VecT<float, 16>& v) {
+  asm volatile("st.global.v4.f32 [%0], {%1,%2,%3,%4};"
+               :: "l"(p), "f"(v.e[0]), "f"(v.e[1]), "f"(v.e[2]), "f"(v.e[3]) : "memory");
+}
+__device__ __forceinline__ void vstore(float* p, const VecT<float, 32>& v) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+               :: "l"(p), "f"(v.e[0]), "f"(v.e[1]), "f"(v.e[2]), "f"(v.e[3]), "f"(v.e[4]),
+                  "f"(v.e[5]), "f"(v.e[6]), "f"(v.e[7]) : "memory");
+}
+__device__ __forceinline__ void vstore(double* p, const VecT<double, 16>& v) {
+  asm volatile("st.global.v2.f64 [%0], {%1,%2};" :: "l"(p), "d"(v.e[0]), "d"(v.e[1]) : "memory");
+}
+__device__ __forceinline__ void vstore(double* p, const VecT<double, 32>& v) {
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};"
+               :: "l"(p), "d"(v.e[0]), "d"(v.e[1]), "d"(v.e[2]), "d"(v.e[3]) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Reduction accumulators (the paper's per-unroll Storage with a reduction()
+// method, Section 4.2).
+
+// F32, compensated: TwoProduct (via FMA) + TwoSum, i.e. Ogita-Rump-Oishi
+// Dot2.  s carries the running sum, c the accumulated rounding errors.
+struct AccF32 {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float ep = __fmaf_rn(a, b, -p);        // a*b - p exactly
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, p);
+    const float es = __fadd_rn(__fsub_rn(s, z), __fsub_rn(p, __fsub_rn(t, z)));  // s + p - t exactly
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(es, ep));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// F32, plain: FP32 fused multiply-add accumulation (the comparison mode).
+struct AccF32Plain {
+  float s = 0.f;
+  __device__ __forceinline__ void add_prod(float a, float b) { s = __fmaf_rn(a, b, s); }
+  __device__ __forceinline__ float value() const { return s; }
+};
+
+// F64: FP64 fused multiply-add accumulation (one FP64 instruction per term).
+struct AccF64 {
+  double s = 0.0;
+  __device__ __forceinline__ void add_prod(double a, double b) { s = __fma_rn(a, b, s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+template <typename T> struct AccOf;
+template <> struct AccOf<float> { using type = AccF32; };
+template <> struct AccOf<double> { using type = AccF64; };
+
+// ---------------------------------------------------------------------------
+// Deterministic block sum: butterfly within each warp, then warp 0 folds the
+// per-warp sums.  The order depends only on blockDim.  Valid in thread 0.
+template <typename R>
+__device__ __forceinline__ R block_sum(R v, R* smem /* >= 32 entries */) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();  // smem may still be read by a previous call
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  const int nw = (blockDim.x + 31) >> 5;
+  if (warp == 0) {
+    v = lane < nw ? smem[lane] : R(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// Cross-block combination: every block deposits NV partial values; the last
+// block to finish (atomic ticket, no waiting) adds them up in block order and
+// hands the NV totals to `finish` in thread 0, then re-arms the ticket.
+// Returns true in the last block.
+template <typename R, int NV>
+__device__ __forceinline__ bool grid_combine(R (&vals)[NV], R* partials, unsigned* ticket,
+                                             R* smem) {
+  R tot[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) tot[k] = block_sum<R>(vals[k], smem);
+  __shared__ bool is_last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) partials[(size_t)blockIdx.x * NV + k] = tot[k];
+    __threadfence();
+    const unsigned t = atomicAdd(ticket, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    R acc = R(0);
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+      acc += ((volatile R*)partials)[(size_t)b * NV + k];
+    vals[k] = block_sum<R>(acc, smem);
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+}  // namespace salt

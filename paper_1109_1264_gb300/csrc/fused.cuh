@@ -1,0 +1,188 @@
+// The fused loop: the GPU form of the paper's loop templates (Section 4.2,
+// Listing 2; Section 4.3).
+//
+// Each thread walks tiles in grid-stride order.  Per tile it issues, like one
+// of the paper's instruction packages, a burst of U vector loads for every
+// loaded operand, then the tree's operations on every element in registers,
+// then a burst of U vector stores for every stored operand.  Elements past the
+// last whole tile are finished by a guarded vector pass and a scalar pass,
+// with the same per-element operations (the paper's single_op tail).
+#pragma once
+
+#include "common.cuh"
+
+namespace salt {
+
+template <typename T>
+struct MapParams {
+  T* v[kMaxVecs];       // operand k (canonical numbering); NULL if unused
+  T sc[kMaxScals];      // scalar operands, already in T
+  int64_t n;            // element count
+  double* red_out;      // device, one double per reduction
+  void* partials;       // workspace: gridDim.x * NR values
+  unsigned* ticket;     // workspace: zero between launches
+};
+
+// Per-element evaluation of program P: node I at compile-time stack depth.
+template <class P, int I, typename T, class Acc>
+__device__ __forceinline__ void exec_node(T (&st)[kMaxStack + 1], T (&v)[kMaxVecs],
+                                          const T (&sc)[kMaxScals], Acc (&acc)[kMaxReds]) {
+  if constexpr (I < P::len) {
+    constexpr int op = P::op(I), a = P::arg(I), d = P::depth_before(I);
+    if constexpr (op == OP_VEC) {
+      st[d] = v[a];
+    } else if constexpr (op == OP_SCAL) {
+      st[d] = sc[a];
+    } else if constexpr (op == OP_ADD) {
+      st[d - 2] = Arith<T>::add(st[d - 2], st[d - 1]);
+    } else if constexpr (op == OP_SUB) {
+      st[d - 2] = Arith<T>::sub(st[d - 2], st[d - 1]);
+    } else if constexpr (op == OP_MUL || op == OP_SMUL) {
+      st[d - 2] = Arith<T>::mul(st[d - 2], st[d - 1]);
+    } else if constexpr (op == OP_NEG) {
+      st[d - 1] = -st[d - 1];
+    } else if constexpr (op == OP_STORE) {
+      v[a] = st[d - 1];
+    } else if constexpr (op == OP_DOT) {
+      acc[P::red_index(I)].add_prod(st[d - 2], st[d - 1]);
+    } else if constexpr (op == OP_SUMSQ) {
+      acc[P::red_index(I)].add_prod(st[d - 1], st[d - 1]);
+    }
+    exec_node<P, I + 1>(st, v, sc, acc);
+  }
+}
+
+template <class P, typename T, class Acc>
+__device__ __forceinline__ void exec_elem(T (&v)[kMaxVecs], const T (&sc)[kMaxScals],
+                                          Acc (&acc)[kMaxReds]) {
+  T st[kMaxStack + 1];
+  exec_node<P, 0>(st, v, sc, acc);
+}
+
+// One thread's work on NE consecutive elements held in per-operand arrays.
+template <class P, typename T, class Acc, int NE>
+__device__ __forceinline__ void exec_chunk(T (&x)[kMaxVecs][NE], const T (&sc)[kMaxScals],
+                                           Acc (&acc)[kMaxReds]) {
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    T v[kMaxVecs];
+#pragma unroll
+    for (int s = 0; s < kMaxVecs; ++s) v[s] = x[s][e];
+    exec_elem<P>(v, sc, acc);
+#pragma unroll
+    for (int s = 0; s < kMaxVecs; ++s)
+      if ((P::store_mask() >> s) & 1u) x[s][e] = v[s];
+  }
+}
+
+template <class P, typename T, int U, int VB>
+__global__ void __launch_bounds__(256) fused_kernel(const MapParams<T> p) {
+  constexpr int VEC = VB / (int)sizeof(T);
+  constexpr unsigned LM = P::load_mask(), SMASK = P::store_mask();
+  constexpr int NR = P::nred();
+  using Acc = typename AccOf<T>::type;
+  using V = VecT<T, VB>;
+
+  T sc[kMaxScals];
+#pragma unroll
+  for (int k = 0; k < kMaxScals; ++k) sc[k] = p.sc[k];
+  Acc acc[kMaxReds];
+
+  const int64_t n = p.n;
+  const int64_t bd = blockDim.x;
+  const int64_t TE = (int64_t)U * bd * VEC;  // elements per tile
+  const int64_t ntiles = n / TE;
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t base = tile * TE + (int64_t)threadIdx.x * VEC;
+    T x[kMaxVecs][U * VEC];
+    // load burst
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int s = 0; s < kMaxVecs; ++s) {
+        if ((LM >> s) & 1u) {
+          V t;
+          if ((SMASK >> s) & 1u) vload<false>(t, p.v[s] + base + u * bd * VEC);
+          else vload<true>(t, p.v[s] + base + u * bd * VEC);
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) x[s][u * VEC + e] = t.e[e];
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) x[s][u * VEC + e] = T(0);
+        }
+      }
+    }
+    // operation burst
+    exec_chunk<P, T, Acc, U * VEC>(x, sc, acc);
+    // store burst
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int s = 0; s < kMaxVecs; ++s) {
+        if ((SMASK >> s) & 1u) {
+          V t;
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) t.e[e] = x[s][u * VEC + e];
+          vstore(p.v[s] + base + u * bd * VEC, t);
+        }
+      }
+    }
+  }
+
+  // Remainder after the whole tiles: first whole vectors, one per thread of
+  // the grid, then single elements.
+  const int64_t rbase = ntiles * TE;
+  const int64_t nvr = (n - rbase) / VEC;
+  const int64_t gid = (int64_t)blockIdx.x * bd + threadIdx.x;
+  const int64_t gstride = (int64_t)gridDim.x * bd;
+  for (int64_t j = gid; j < nvr; j += gstride) {
+    const int64_t off = rbase + j * VEC;
+    T x[kMaxVecs][VEC];
+#pragma unroll
+    for (int s = 0; s < kMaxVecs; ++s) {
+      if ((LM >> s) & 1u) {
+        V t;
+        if ((SMASK >> s) & 1u) vload<false>(t, p.v[s] + off);
+        else vload<true>(t, p.v[s] + off);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) x[s][e] = t.e[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) x[s][e] = T(0);
+      }
+    }
+    exec_chunk<P, T, Acc, VEC>(x, sc, acc);
+#pragma unroll
+    for (int s = 0; s < kMaxVecs; ++s) {
+      if ((SMASK >> s) & 1u) {
+        V t;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) t.e[e] = x[s][e];
+        vstore(p.v[s] + off, t);
+      }
+    }
+  }
+  for (int64_t i = rbase + nvr * VEC + gid; i < n; i += gstride) {
+    T x[kMaxVecs][1];
+#pragma unroll
+    for (int s = 0; s < kMaxVecs; ++s) x[s][0] = ((LM >> s) & 1u) ? p.v[s][i] : T(0);
+    exec_chunk<P, T, Acc, 1>(x, sc, acc);
+#pragma unroll
+    for (int s = 0; s < kMaxVecs; ++s)
+      if ((SMASK >> s) & 1u) p.v[s][i] = x[s][0];
+  }
+
+  if constexpr (NR > 0) {
+    __shared__ double smem[32];
+    double vals[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) vals[r] = acc[r].value();
+    if (grid_combine<double, NR>(vals, (double*)p.partials, p.ticket, smem) && threadIdx.x == 0) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) p.red_out[r] = vals[r];
+    }
+  }
+}
+
+}  // namespace salt

@@ -1,0 +1,227 @@
+// Program validation, canonicalisation and lowering (host only).
+#include "host.h"
+
+#include <cstdio>
+
+namespace salt {
+
+static const char* op_name(int op) {
+  static const char* names[] = {"VEC", "SCAL", "ADD", "SUB", "MUL", "SMUL", "NEG", "STORE", "DOT", "SUMSQ"};
+  return op >= 0 && op < 10 ? names[op] : "?";
+}
+
+salt_status analyse(const salt_insn* prog, int nprog, int nvecs, int nscal, Analysis* out,
+                    std::string* err) {
+  char buf[160];
+  auto fail = [&](salt_status st, const char* msg) {
+    if (err) *err = msg;
+    return st;
+  };
+  if (!prog) return fail(SALT_ERR_ARG, "program pointer is NULL");
+  if (nprog < 1 || nprog > kMaxProg) {
+    snprintf(buf, sizeof buf, "program length %d outside 1..%d", nprog, kMaxProg);
+    return fail(SALT_ERR_ARG, buf);
+  }
+  if (nvecs < 0 || nvecs > kMaxVecs || nscal < 0 || nscal > kMaxScals)
+    return fail(SALT_ERR_ARG, "operand counts outside 0..8");
+  Analysis a;
+  char stack[kMaxProg + 1];  // 'v' vector, 's' scalar
+  int sp = 0, outputs = 0;
+  for (int pc = 0; pc < nprog; ++pc) {
+    const int op = prog[pc].op, arg = prog[pc].arg;
+    auto bad = [&](const char* why) {
+      snprintf(buf, sizeof buf, "node %d (%s %d): %s", pc, op_name(op), arg, why);
+      return fail(SALT_ERR_PROGRAM, buf);
+    };
+    switch (op) {
+      case OP_VEC:
+        if (arg >= nvecs) return bad("vector operand index out of range");
+        a.used_vecs |= 1u << arg;
+        stack[sp++] = 'v';
+        break;
+      case OP_SCAL:
+        if (arg >= nscal) return bad("scalar operand index out of range");
+        a.used_scals |= 1u << arg;
+        stack[sp++] = 's';
+        break;
+      case OP_ADD:
+      case OP_SUB:
+      case OP_MUL:
+      case OP_DOT:
+        if (sp < 2) return bad("needs two operands");
+        if (stack[sp - 1] != 'v' || stack[sp - 2] != 'v') return bad("operands must be vectors");
+        sp -= 2;
+        if (op == OP_DOT) {
+          ++a.nred;
+          ++outputs;
+        } else {
+          stack[sp++] = 'v';
+        }
+        break;
+      case OP_SMUL:
+        if (sp < 2) return bad("needs two operands");
+        if (stack[sp - 1] != 'v' || stack[sp - 2] != 's')
+          return bad("needs a scalar below a vector");
+        sp -= 2;
+        stack[sp++] = 'v';
+        break;
+      case OP_NEG:
+        if (sp < 1) return bad("needs an operand");
+        if (stack[sp - 1] != 'v') return bad("operand must be a vector");
+        break;
+      case OP_STORE:
+      case OP_SUMSQ:
+        if (sp < 1) return bad("needs an operand");
+        if (stack[sp - 1] != 'v') return bad("operand must be a vector");
+        if (op == OP_STORE) {
+          if (arg >= nvecs) return bad("vector operand index out of range");
+          a.used_vecs |= 1u << arg;
+          a.stored_vecs |= 1u << arg;
+        } else {
+          ++a.nred;
+        }
+        --sp;
+        ++outputs;
+        break;
+      default:
+        return bad("unknown opcode");
+    }
+    if (sp > kMaxStack) return bad("stack deeper than 8");
+    if (sp > a.max_depth) a.max_depth = sp;
+    if (a.nred > kMaxReds) return bad("more than 4 reductions");
+  }
+  if (sp != 0) {
+    snprintf(buf, sizeof buf, "%d value(s) left on the stack at the end", sp);
+    return fail(SALT_ERR_PROGRAM, buf);
+  }
+  if (outputs == 0) return fail(SALT_ERR_PROGRAM, "program has no STORE, DOT or SUMSQ");
+  if (out) *out = a;
+  return SALT_OK;
+}
+
+void canonicalise(const salt_insn* prog, int nprog, Canonical* c) {
+  int vmap[kMaxVecs], smap[kMaxScals];
+  for (int k = 0; k < kMaxVecs; ++k) vmap[k] = -1;
+  for (int k = 0; k < kMaxScals; ++k) smap[k] = -1;
+  Canonical r;
+  uint32_t seen = 0;
+  for (int pc = 0; pc < nprog; ++pc) {
+    const int op = prog[pc].op, arg = prog[pc].arg;
+    int carg = 0;
+    if (op == OP_VEC || op == OP_STORE) {
+      if (vmap[arg] < 0) {
+        vmap[arg] = r.nvec;
+        r.vec_user[r.nvec++] = arg;
+      }
+      carg = vmap[arg];
+      if (op == OP_VEC && !((seen >> carg) & 1u)) r.load_mask |= 1u << carg;
+      seen |= 1u << carg;
+      if (op == OP_STORE) r.store_mask |= 1u << carg;
+    } else if (op == OP_SCAL) {
+      if (smap[arg] < 0) {
+        smap[arg] = r.nscal;
+        r.scal_user[r.nscal++] = arg;
+      }
+      carg = smap[arg];
+    }
+    if (op == OP_DOT || op == OP_SUMSQ) ++r.nred;
+    r.code[r.len++] = pack(op, carg);
+  }
+  *c = r;
+}
+
+namespace {
+struct ShapeCode {
+  int len;
+  int code[kMaxProg];
+};
+#define SALT_SHAPE_CODE(name, ...) {Prog_##name::len, {__VA_ARGS__}},
+const ShapeCode kShapeCodes[NUM_SHAPES] = {SALT_SHAPE_LIST(SALT_SHAPE_CODE)};
+#undef SALT_SHAPE_CODE
+}  // namespace
+
+int find_shape(const Canonical& c) {
+  for (int s = 0; s < NUM_SHAPES; ++s) {
+    const ShapeCode& sc = kShapeCodes[s];
+    if (sc.len != c.len) continue;
+    bool eq = true;
+    for (int i = 0; i < c.len && eq; ++i) eq = sc.code[i] == c.code[i];
+    if (eq) return s;
+  }
+  return -1;
+}
+
+bool lower(const Canonical& c, RegInsn* code, int* len) {
+  // Symbolic stack: each entry names the register holding its value (an
+  // operand register 0..7 as long as the value is an unmodified operand, or
+  // the depth register 8 + d), or a scalar index.
+  struct Ent {
+    bool scalar;
+    int reg;
+  };
+  Ent st[kMaxStack + 1];
+  int sp = 0, n = 0, r = 0;
+  auto emit = [&](uint8_t op, int dst, int a, int b) {
+    if (n >= kMaxRegCode) return false;
+    code[n++] = RegInsn{op, (uint8_t)dst, (uint8_t)a, (uint8_t)b};
+    return true;
+  };
+  for (int pc = 0; pc < c.len; ++pc) {
+    const int op = c.code[pc] / 16, arg = c.code[pc] % 16;
+    switch (op) {
+      case OP_VEC: st[sp++] = {false, arg}; break;
+      case OP_SCAL: st[sp++] = {true, arg}; break;
+      case OP_ADD:
+      case OP_SUB:
+      case OP_MUL: {
+        const Ent b = st[--sp], a = st[--sp];
+        const uint8_t io = op == OP_ADD ? I_ADD : op == OP_SUB ? I_SUB : I_MUL;
+        if (!emit(io, 8 + sp, a.reg, b.reg)) return false;
+        st[sp] = {false, 8 + sp};
+        ++sp;
+        break;
+      }
+      case OP_SMUL: {
+        const Ent v = st[--sp], s = st[--sp];
+        if (!emit(I_SMUL, 8 + sp, v.reg, s.reg)) return false;
+        st[sp] = {false, 8 + sp};
+        ++sp;
+        break;
+      }
+      case OP_NEG: {
+        const Ent a = st[--sp];
+        if (!emit(I_NEG, 8 + sp, a.reg, 0)) return false;
+        st[sp] = {false, 8 + sp};
+        ++sp;
+        break;
+      }
+      case OP_STORE: {
+        const Ent a = st[--sp];
+        // Entries still on the stack that alias operand `arg` must keep the
+        // old value: copy them to their depth register first.
+        for (int d = 0; d < sp; ++d) {
+          if (!st[d].scalar && st[d].reg == arg) {
+            if (!emit(I_COPY, 8 + d, arg, 0)) return false;
+            st[d].reg = 8 + d;
+          }
+        }
+        if (a.reg != arg && !emit(I_COPY, arg, a.reg, 0)) return false;
+        break;
+      }
+      case OP_DOT: {
+        const Ent b = st[--sp], a = st[--sp];
+        if (!emit(I_DOT, r++, a.reg, b.reg)) return false;
+        break;
+      }
+      case OP_SUMSQ: {
+        const Ent a = st[--sp];
+        if (!emit(I_SUMSQ, r++, a.reg, a.reg)) return false;
+        break;
+      }
+    }
+  }
+  *len = n;
+  return true;
+}
+
+}  // namespace salt

@@ -1,0 +1,224 @@
+"""ctypes binding of ``libsalt.so`` (C ABI in ``include/salt.h``).
+
+Argument marshalling only: every function here converts Python / torch
+arguments to the C types of the entry point with the same name and calls it;
+all computation happens in the library's CUDA kernels.  Device memory and
+streams come from PyTorch.  There is no fallback: if the library is missing
+the import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsalt.so")
+
+F32, F64 = 0, 1
+OK, ERR_ARG, ERR_PROGRAM, ERR_DTYPE, ERR_ALIGN, ERR_ALIAS, ERR_BUDGET, ERR_TIMEOUT, ERR_CUDA, ERR_NOTFOUND = range(10)
+DEFAULT, PLAIN = 0, 1
+OPS = {"VEC": 0, "SCAL": 1, "ADD": 2, "SUB": 3, "MUL": 4, "SMUL": 5, "NEG": 6, "STORE": 7,
+       "DOT": 8, "SUMSQ": 9}
+MAX_PROG, MAX_VECS, MAX_SCALS, MAX_STACK, MAX_REDS = 32, 8, 8, 8, 4
+
+# Symbols that include/salt.h declares (checked by the test suite).
+EXPORTS = ["salt_version", "salt_status_str", "salt_last_error", "salt_check_program", "salt_eval",
+           "salt_axpby", "salt_dot", "salt_nrm2", "salt_fill_uniform", "salt_release_workspaces",
+           "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count"]
+
+
+class Insn(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_uint8), ("arg", ctypes.c_uint8)]
+
+
+class LaunchCfg(ctypes.Structure):
+    _fields_ = [("unroll", ctypes.c_int32), ("vec_bytes", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32)]
+
+
+class SaltError(RuntimeError):
+    def __init__(self, status: int, name: str, message: str):
+        super().__init__(f"{name}: {message}")
+        self.status = status
+        self.name = name
+        self.message = message
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built; run paper_1109_1264_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    i32, i64, u64, vp, dp = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(Insn)
+    sig = {
+        "salt_version": (i32, []),
+        "salt_status_str": (ctypes.c_char_p, [i32]),
+        "salt_last_error": (ctypes.c_char_p, []),
+        "salt_check_program": (i32, [ip, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+        "salt_eval": (i32, [ip, i32, i32, i64, ctypes.POINTER(vp), i32, dp, i32, vp, vp]),
+        "salt_axpby": (i32, [i32, i64, ctypes.c_double, vp, ctypes.c_double, vp, vp]),
+        "salt_dot": (i32, [i32, i64, vp, vp, vp, i32, vp]),
+        "salt_nrm2": (i32, [i32, i64, vp, vp, i32, vp]),
+        "salt_fill_uniform": (i32, [i32, i64, u64, i64, vp, vp]),
+        "salt_release_workspaces": (i32, []),
+        "salt_tune_set": (i32, [ip, i32, i32, i64, ctypes.POINTER(LaunchCfg)]),
+        "salt_tune_get": (i32, [ip, i32, i32, i64, ctypes.POINTER(LaunchCfg)]),
+        "salt_tune_clear": (i32, []),
+        "salt_launch_count": (i64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status: int) -> None:
+    if status != OK:
+        raise SaltError(status, lib.salt_status_str(status).decode(), lib.salt_last_error().decode())
+
+
+# ------------------------------------------------------------ marshalling --
+
+def program(prog) -> tuple[ctypes.Array, int]:
+    """[(name, arg), ...] or [(opcode, arg), ...] -> (salt_insn array, length)."""
+    arr = (Insn * max(len(prog), 1))()
+    for i, (op, arg) in enumerate(prog):
+        arr[i].op = OPS[op] if isinstance(op, str) else int(op)
+        arr[i].arg = int(arg)
+    return arr, len(prog)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise SaltError(ERR_DTYPE, "SALT_ERR_DTYPE", f"unsupported dtype {t.dtype}")
+
+
+def _stream_ptr(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else int(t.data_ptr())
+
+
+def _common_dtype(tensors) -> int:
+    codes = {_dtype_code(t) for t in tensors if t is not None}
+    if len(codes) > 1:
+        raise SaltError(ERR_DTYPE, "SALT_ERR_DTYPE", "operands of one call must share a dtype")
+    return codes.pop() if codes else F32
+
+
+def _n_of(tensors) -> int:
+    ns = {t.numel() for t in tensors if t is not None}
+    if len(ns) > 1:
+        raise SaltError(ERR_ARG, "SALT_ERR_ARG", "operands of one call must have the same length")
+    return ns.pop() if ns else 0
+
+
+def _contig(tensors) -> None:
+    for t in tensors:
+        if t is not None and not t.is_contiguous():
+            raise SaltError(ERR_ARG, "SALT_ERR_ARG", "operands must be contiguous")
+
+
+# ------------------------------------------------------------- entry points --
+
+def salt_version() -> int:
+    return lib.salt_version()
+
+
+def salt_check_program(prog, nvecs: int, nscal: int) -> tuple[int, bool]:
+    """Returns (number of reductions, has a compiled instantiation)."""
+    arr, n = program(prog)
+    nred = ctypes.c_int32()
+    comp = ctypes.c_int32()
+    _check(lib.salt_check_program(arr, n, nvecs, nscal, ctypes.byref(nred), ctypes.byref(comp)))
+    return nred.value, bool(comp.value)
+
+
+def salt_eval(prog, vecs, scalars=(), red_out=None, n: int | None = None, stream=None) -> None:
+    """Run ``prog`` over the torch CUDA tensors ``vecs`` (all float32 or all
+    float64, same length).  DOT/SUMSQ results go to ``red_out`` (a float64 CUDA
+    tensor with one entry per reduction)."""
+    _contig(vecs)
+    dt = _common_dtype(vecs)
+    if n is None:
+        n = _n_of(vecs)
+    arr, m = program(prog)
+    ptrs = (ctypes.c_void_p * max(len(vecs), 1))(*[_ptr(v) for v in vecs])
+    sc = (ctypes.c_double * max(len(scalars), 1))(*[float(s) for s in scalars])
+    _check(lib.salt_eval(arr, m, dt, int(n), ptrs, len(vecs), sc, len(scalars), _ptr(red_out),
+                         _stream_ptr(stream)))
+
+
+def salt_axpby(alpha: float, x, beta: float, y, stream=None) -> None:
+    """y <- alpha*x + beta*y."""
+    _contig([x, y])
+    dt = _common_dtype([x, y])
+    _check(lib.salt_axpby(dt, _n_of([x, y]), float(alpha), _ptr(x), float(beta), _ptr(y), _stream_ptr(stream)))
+
+
+def salt_dot(x, y, out, plain: bool = False, stream=None) -> None:
+    """out[0] <- sum x_i y_i (out: float64 CUDA tensor)."""
+    _contig([x, y])
+    dt = _common_dtype([x, y])
+    _check(lib.salt_dot(dt, _n_of([x, y]), _ptr(x), _ptr(y), _ptr(out), PLAIN if plain else DEFAULT,
+                        _stream_ptr(stream)))
+
+
+def salt_nrm2(x, out, plain: bool = False, stream=None) -> None:
+    """out[0] <- ||x||_2."""
+    _contig([x])
+    _check(lib.salt_nrm2(_dtype_code(x), x.numel(), _ptr(x), _ptr(out), PLAIN if plain else DEFAULT,
+                         _stream_ptr(stream)))
+
+
+def salt_fill_uniform(x, key: int, offset: int = 0, stream=None) -> None:
+    """x[i] <- counter-based uniform[-1, 1) value (offset + i) of stream ``key``."""
+    _contig([x])
+    _check(lib.salt_fill_uniform(_dtype_code(x), x.numel(), int(key) & 0xFFFFFFFFFFFFFFFF, int(offset),
+                                 _ptr(x), _stream_ptr(stream)))
+
+
+def salt_release_workspaces() -> None:
+    _check(lib.salt_release_workspaces())
+
+
+def salt_tune_set(prog, dtype: int, n: int, unroll: int, vec_bytes: int, block: int, blocks_per_sm: int) -> None:
+    arr, m = program(prog)
+    cfg = LaunchCfg(unroll, vec_bytes, block, blocks_per_sm)
+    _check(lib.salt_tune_set(arr, m, dtype, int(n), ctypes.byref(cfg)))
+
+
+def salt_tune_get(prog, dtype: int, n: int) -> dict:
+    arr, m = program(prog)
+    cfg = LaunchCfg()
+    _check(lib.salt_tune_get(arr, m, dtype, int(n), ctypes.byref(cfg)))
+    return {"unroll": cfg.unroll, "vec_bytes": cfg.vec_bytes, "block": cfg.block,
+            "blocks_per_sm": cfg.blocks_per_sm}
+
+
+def salt_tune_clear() -> None:
+    _check(lib.salt_tune_clear())
+
+
+def salt_launch_count() -> int:
+    return lib.salt_launch_count()
+
+
+def salt_last_error() -> str:
+    return lib.salt_last_error().decode()
+
+
+def salt_status_str(status: int) -> str:
+    return lib.salt_status_str(status).decode()

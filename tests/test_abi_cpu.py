@@ -1,0 +1,139 @@
+"""The C ABI without a GPU: exported symbols, program validation, argument
+errors (all detected on the host before any launch), tuning table, and a
+loud failure instead of any CPU fallback when no device exists."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "salt.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*[A-Za-z_][\w\s\*]*?\b(salt_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(saltlib):
+    names = declared_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(saltlib.lib, name), name
+    assert sorted(saltlib.EXPORTS) == names
+
+
+def test_version_and_status_strings(saltlib):
+    assert saltlib.salt_version() >= 10000
+    assert saltlib.salt_status_str(saltlib.ERR_ALIAS) == "SALT_ERR_ALIAS"
+    assert saltlib.salt_status_str(99) == "unknown status"
+
+
+D = [("VEC", 0), ("VEC", 1), ("VEC", 2), ("SUB", 0), ("ADD", 0), ("STORE", 3)]
+CG = [("VEC", 0), ("SCAL", 0), ("VEC", 1), ("SMUL", 0), ("SUB", 0), ("STORE", 0), ("VEC", 0), ("SUMSQ", 0),
+      ("VEC", 0), ("SCAL", 1), ("VEC", 2), ("SMUL", 0), ("ADD", 0), ("STORE", 2)]
+
+
+def test_check_program_valid(saltlib):
+    assert saltlib.salt_check_program(D, 4, 0) == (0, True)
+    # same tree with operands renumbered is still the compiled shape
+    D2 = [("VEC", 3), ("VEC", 0), ("VEC", 1), ("SUB", 0), ("ADD", 0), ("STORE", 2)]
+    assert saltlib.salt_check_program(D2, 4, 0) == (0, True)
+    assert saltlib.salt_check_program(CG, 3, 2) == (1, True)
+    assert saltlib.salt_check_program([("VEC", 0), ("VEC", 1), ("DOT", 0)], 2, 0) == (1, True)
+    # not instantiated: runs on the interpreter
+    odd = [("VEC", 0), ("NEG", 0), ("VEC", 1), ("MUL", 0), ("STORE", 1), ("VEC", 1), ("VEC", 0), ("DOT", 0)]
+    assert saltlib.salt_check_program(odd, 2, 0) == (1, False)
+
+
+@pytest.mark.parametrize("prog,nv,ns,status", [
+    ([], 1, 0, 1),
+    ([("VEC", 0)] * 33, 1, 0, 1),
+    ([("ADD", 0)], 1, 0, 2),
+    ([("VEC", 0), ("SCAL", 0), ("SMUL", 0), ("STORE", 0)], 1, 1, 2),
+    ([("VEC", 0), ("VEC", 0)], 1, 0, 2),
+    ([("VEC", 1), ("STORE", 0)], 1, 0, 2),
+    ([("SCAL", 0), ("STORE", 0)], 1, 1, 2),
+    ([("VEC", 0), ("STORE", 0), ("VEC", 0), ("NEG", 0)], 1, 0, 2),
+    ([("VEC", 0)] * 9 + [("ADD", 0)] * 8 + [("STORE", 0)], 1, 0, 2),
+    ([("VEC", 0), ("SUMSQ", 0)] * 5, 1, 0, 2),
+    ([(12, 0)], 1, 0, 2),
+    ([("VEC", 0), ("NEG", 0)], 1, 0, 2),
+    ([("SCAL", 0), ("VEC", 0), ("SMUL", 0), ("STORE", 0)], 9, 0, 1),
+])
+def test_check_program_rejects(saltlib, prog, nv, ns, status):
+    with pytest.raises(saltlib.SaltError) as ei:
+        saltlib.salt_check_program(prog, nv, ns)
+    assert ei.value.status == status, ei.value
+
+
+def _raw_eval(saltlib, prog, dtype, n, ptrs, scalars=(), red=None):
+    arr, m = saltlib.program(prog)
+    p = (ctypes.c_void_p * max(len(ptrs), 1))(*ptrs)
+    sc = (ctypes.c_double * max(len(scalars), 1))(*scalars)
+    return saltlib.lib.salt_eval(arr, m, dtype, n, p, len(ptrs), sc, len(scalars), red, None)
+
+
+BASE = 0x7F0000000000  # fake device addresses: never dereferenced, the host rejects first
+
+
+def test_eval_argument_errors(saltlib):
+    ok = [BASE, BASE + 2 ** 20, BASE + 2 ** 21, BASE + 2 ** 22]
+    assert _raw_eval(saltlib, D, 2, 10, ok) == saltlib.ERR_DTYPE
+    assert _raw_eval(saltlib, D, 0, -1, ok) == saltlib.ERR_ARG
+    assert _raw_eval(saltlib, D, 0, 10, [ok[0], ok[1] + 8, ok[2], ok[3]]) == saltlib.ERR_ALIGN
+    assert _raw_eval(saltlib, D, 0, 10, [ok[0], None, ok[2], ok[3]]) == saltlib.ERR_ARG
+    # output overlapping an input through a different operand index
+    assert _raw_eval(saltlib, D, 1, 100, [ok[0], ok[1], ok[2], ok[0] + 16]) == saltlib.ERR_ALIAS
+    assert "overlap" in saltlib.salt_last_error()
+    # identical pointers for two read-only operands are fine (fails later, on the missing GPU)
+    assert _raw_eval(saltlib, D, 1, 100, [ok[0], ok[0], ok[0], ok[3]]) == saltlib.ERR_CUDA
+    # reduction without a result buffer
+    assert _raw_eval(saltlib, [("VEC", 0), ("SUMSQ", 0)], 0, 10, ok[:1], red=None) == saltlib.ERR_ARG
+    assert _raw_eval(saltlib, [("VEC", 0), ("SUMSQ", 0)], 0, 10, ok[:1], red=BASE + 4) == saltlib.ERR_ALIGN
+    # scalars referenced but not given
+    arr, m = saltlib.program([("SCAL", 0), ("VEC", 0), ("SMUL", 0), ("STORE", 0)])
+    p = (ctypes.c_void_p * 1)(BASE)
+    assert saltlib.lib.salt_eval(arr, m, 0, 10, p, 1, None, 1, None, None) == saltlib.ERR_ARG
+
+
+def test_no_cpu_fallback_without_gpu(saltlib):
+    """A valid call on a machine without a GPU fails loudly (SALT_ERR_CUDA);
+    nothing is computed on the host."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    ok = [BASE, BASE + 2 ** 20, BASE + 2 ** 21, BASE + 2 ** 22]
+    assert _raw_eval(saltlib, D, 1, 10, ok) == saltlib.ERR_CUDA
+    assert saltlib.lib.salt_dot(0, 10, BASE, BASE, BASE, 0, None) == saltlib.ERR_CUDA
+    assert saltlib.lib.salt_nrm2(1, 10, BASE, BASE, 0, None) == saltlib.ERR_CUDA
+
+
+def test_dot_nrm2_argument_errors(saltlib):
+    L = saltlib.lib
+    assert L.salt_dot(0, 10, BASE, BASE, BASE, 7, None) == saltlib.ERR_ARG
+    assert L.salt_dot(3, 10, BASE, BASE, BASE, 0, None) == saltlib.ERR_DTYPE
+    assert L.salt_dot(0, 10, BASE + 4, BASE, BASE, 0, None) == saltlib.ERR_ALIGN
+    assert L.salt_dot(0, 10, BASE, BASE, None, 0, None) == saltlib.ERR_ARG
+    assert L.salt_nrm2(1, -3, BASE, BASE, 0, None) == saltlib.ERR_ARG
+    assert L.salt_nrm2(1, 10, BASE + 8, BASE, 0, None) == saltlib.ERR_ALIGN
+    assert L.salt_axpby(0, 10, 1.0, BASE, 1.0, BASE + 16, None) == saltlib.ERR_ALIAS
+    assert L.salt_fill_uniform(0, -1, 1, 0, BASE, None) == saltlib.ERR_ARG
+
+
+def test_tune_table(saltlib):
+    saltlib.salt_tune_clear()
+    default = saltlib.salt_tune_get(D, saltlib.F32, 1 << 20)
+    assert default["block"] == 256
+    saltlib.salt_tune_set(D, saltlib.F32, 1 << 20, 4, 32, 128, 8)
+    assert saltlib.salt_tune_get(D, saltlib.F32, (1 << 21) - 1) == {"unroll": 4, "vec_bytes": 32, "block": 128,
+                                                                    "blocks_per_sm": 8}
+    assert saltlib.salt_tune_get(D, saltlib.F32, 1 << 21) == default  # other bucket
+    assert saltlib.salt_tune_get(D, saltlib.F64, 1 << 20) == default  # other dtype
+    for bad in ((3, 16, 128, 4), (2, 8, 128, 4), (2, 16, 100, 4), (2, 16, 512, 4), (2, 16, 256, 9)):
+        with pytest.raises(saltlib.SaltError):
+            saltlib.salt_tune_set(D, saltlib.F32, 1 << 20, *bad)
+    saltlib.salt_tune_clear()
+    assert saltlib.salt_tune_get(D, saltlib.F32, 1 << 20) == default
