@@ -1,0 +1,418 @@
+"""Benchmark of the SALT hot path on GB300.
+
+One step = one pass of the BLAS-1 sweep's top size through the library:
+for FP32 and FP64, n = 2^28 elements,
+  e = alpha*a + beta*b - c o d   (fused 4-operand expression, salt_eval)
+  y = alpha*x + beta*y           (salt_axpby)
+  dot(x, y)                      (salt_dot)
+  nrm2(x)                        (salt_nrm2)
+with alpha = 1.5, beta = -0.25 and inputs uniform[-1, 1) from the
+counter-based generator.  value = algorithmic bytes moved by the step (each
+operand element read once, each result written once) / device time, summed
+over ranks (each rank is an independent replica).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead (the reference arm of this repository: there is no other
+implementation of the paper's method to run).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fused vector-expr HBM GB/s (% of peak), batched vs plain; served p50/p99 µs"
+ALPHA, BETA = 1.5, -0.25
+DTYPES = ("f32", "f64")
+# (op, bytes moved per element in units of the element size, flops per element)
+OPS = {"e": (5, 5), "axpby": (3, 3), "dot": (2, 2), "nrm2": (1, 2)}
+# FP64 instructions per element of each op's kernel (ALU roofline of FP64)
+F64_INSTR = {"e": 5, "axpby": 3, "dot": 1, "nrm2": 1}
+ES = {"f32": 4, "f64": 8}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured", float(p.get("sm_max_mhz", 2070.0))
+    except Exception:
+        return 6800.0, "fallback", 2070.0
+
+
+# FP64 ALU peak from unit counts and clocks: 2 FP64 instructions per clock per
+# SM (GB300), 152 SMs, at the maximum SM clock.
+def f64_alu_peak_gops(sm_mhz: float) -> float:
+    return 2 * 152 * sm_mhz * 1e6 / 1e9
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1109_1264_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", gpu_id], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for_smi(torch) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(0).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+    return vis or "0"
+
+
+# ---------------------------------------------------------------- workload --
+class Workload:
+    """Device buffers of one dtype: a, b, c, d inputs, out for e, y for axpby."""
+
+    def __init__(self, torch, salt, dt: str, n: int, seed: int = 0):
+        tdt = torch.float32 if dt == "f32" else torch.float64
+        self.dt, self.n = dt, n
+        self.a, self.b, self.c, self.d = (torch.empty(n, dtype=tdt, device="cuda") for _ in range(4))
+        self.out = torch.empty(n, dtype=tdt, device="cuda")
+        self.y = torch.empty(n, dtype=tdt, device="cuda")
+        self.red = torch.zeros(2, dtype=torch.float64, device="cuda")
+        for k, t in enumerate((self.a, self.b, self.c, self.d, self.y)):
+            salt.salt_fill_uniform(t, key=seed * 16 + k + 1)
+
+    def ops(self, salt):
+        """(name, callable) of the step, in order."""
+        from paper_1109_1264_gb300.programs import PROG_E
+        return [
+            ("e", lambda: salt.salt_eval(PROG_E, [self.a, self.b, self.c, self.d, self.out], [ALPHA, BETA])),
+            ("axpby", lambda: salt.salt_axpby(ALPHA, self.a, BETA, self.y)),
+            ("dot", lambda: salt.salt_dot(self.a, self.b, self.red[0:1])),
+            ("nrm2", lambda: salt.salt_nrm2(self.c, self.red[1:2])),
+        ]
+
+
+def algorithmic_bytes(n: int) -> dict:
+    return {(dt, op): OPS[op][0] * ES[dt] * n for dt in DTYPES for op in OPS}
+
+
+# ---------------------------------------------------------------- CPU leg --
+def oracle_pass(n: int, seed: int = 0):
+    """Run the step's ops on the CPU oracle once at size n; returns (seconds,
+    algorithmic bytes)."""
+    import numpy as np
+
+    import oracle
+    from paper_1109_1264_gb300 import inputs
+    total_t, total_b = 0.0, 0
+    for dt in DTYPES:
+        npdt = np.float32 if dt == "f32" else np.float64
+        a, b, c, d, y = (inputs.hash_uniform(seed * 16 + k + 1, n, npdt) for k in range(5))
+        out = np.empty_like(a)
+        t0 = time.perf_counter()
+        oracle.eval_program(oracle.PROG_E, [a, b, c, d, out], [ALPHA, BETA])
+        oracle.eval_program(oracle.PROG_AXPBY, [a, y], [ALPHA, BETA])
+        oracle.dot(a, b)
+        oracle.nrm2(c)
+        total_t += time.perf_counter() - t0
+        total_b += sum(OPS[op][0] for op in OPS) * ES[dt] * n
+    return total_t, total_b
+
+
+def cpu_baseline(n_sample: int, budget_s: float = 12.0) -> dict:
+    import oracle
+    oracle.build()
+    t, b, passes = 0.0, 0, 0
+    while passes < 1 or (t < budget_s and passes < 50):
+        dt, db = oracle_pass(n_sample)
+        t += dt
+        b += db
+        passes += 1
+    return {"value": round(b / t / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"e, axpby, dot, nrm2 x FP32/FP64 at n=2^{n_sample.bit_length() - 1}, {passes} pass(es), "
+                      f"single-threaded C oracle (unfused, one loop per node)"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    n_sample = 1 << args.cpu_log2
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_pass(n_sample)
+    t, b = 0.0, 0
+    for _ in range(args.steps):
+        dt, db = oracle_pass(n_sample)
+        t += dt
+        b += db
+    value = b / t / 1e9
+    sample = (f"e, axpby, dot, nrm2 x FP32/FP64 at n=2^{args.cpu_log2} per step (1/{1 << (args.log2n - args.cpu_log2)} "
+              f"of the workload), single-threaded C oracle")
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"BLAS-1 sweep top size, sampled at n=2^{args.cpu_log2} on the host CPU",
+                       "n": n_sample},
+            "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm --
+def traffic_for(kernel: str, n: int):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on
+    the current kernel sources (scaled from the captured size to n)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    ent = t.get(kernel)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return int(ent["dram_bytes_per_launch"] * n / ent["n"])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="salt", choices=["salt", "reference"])
+    ap.add_argument("--log2n", type=int, default=28)
+    ap.add_argument("--cpu-log2", type=int, default=22)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_1109_1264_gb300 import salt
+
+    n = 1 << args.log2n
+    loads = {dt: Workload(torch, salt, dt, n, seed=rank) for dt in DTYPES}
+    steps = []
+    for dt in DTYPES:
+        for name, fn in loads[dt].ops(salt):
+            steps.append((dt, name, fn))
+    abytes = algorithmic_bytes(n)
+    step_bytes = sum(abytes[(dt, op)] for dt, op, _ in steps)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        for _, _, fn in steps:
+            fn()
+    barrier()
+
+    clocks = ClockSampler(gpu_id_for_smi(torch))
+    time.sleep(0.3)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(steps) + 1)] for _ in range(args.steps)]
+    launches0 = salt.salt_launch_count()
+    barrier()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        for i, (_, _, fn) in enumerate(steps):
+            fn()
+            ev[k][i + 1].record(stream)
+    t_end.record(stream)
+    barrier()
+    launches = salt.salt_launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = tt.item()
+
+    per_kernel = {}
+    for i, (dt, name, _) in enumerate(steps):
+        per_kernel[(dt, name)] = sum(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)) / args.steps
+
+    ms_per_step = total_ms / args.steps
+    value = world * step_bytes * args.steps / (total_ms * 1e-3) / 1e9
+    hbm_peak, peak_kind, sm_max = load_peaks()
+    alu_peak = f64_alu_peak_gops(sm_max)
+
+    # dominant kernel and its roofline
+    (ddt, dop), dms = max(per_kernel.items(), key=lambda kv: kv[1])
+    achieved_gbs = abytes[(ddt, dop)] / (dms * 1e-3) / 1e9
+    roof = {"kernel": f"{dop}_{ddt}", "ms": round(dms, 4)}
+    hbm_frac = achieved_gbs / hbm_peak
+    if ddt == "f64":
+        achieved_gops = F64_INSTR[dop] * n / (dms * 1e-3) / 1e9
+        alu_frac = achieved_gops / alu_peak
+        # the binding roof is the one whose lower bound on time is larger
+        t_hbm = abytes[(ddt, dop)] / (hbm_peak * 1e9)
+        t_alu = F64_INSTR[dop] * n / (alu_peak * 1e9)
+        if t_alu > t_hbm:
+            roof.update({"bound": "alu", "achieved": round(achieved_gops / 1e3, 4), "peak": round(alu_peak / 1e3, 4),
+                         "unit": "TFLOP/s", "frac": round(alu_frac, 4),
+                         "peak_note": "FP64: 2 instr/clk/SM x 152 SMs x max SM clock (one instruction per flop)",
+                         "hbm_achieved_gbs": round(achieved_gbs, 1), "hbm_frac": round(hbm_frac, 4)})
+        else:
+            roof.update({"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(hbm_frac, 4), "alu_frac": round(alu_frac, 4)})
+    else:
+        roof.update({"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                     "frac": round(hbm_frac, 4)})
+    roof["peak_kind"] = peak_kind
+    roof["traffic"] = traffic_for(f"{dop}_{ddt}", n)
+    roof["algorithmic_bytes"] = abytes[(ddt, dop)]
+
+    result = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic: counter-based uniform[-1,1) (SplitMix64) operands, alpha=1.5, beta=-0.25",
+        "config": {"workload": "BLAS-1 sweep top size: e=alpha*a+beta*b-c*d, y=alpha*x+beta*y, dot, nrm2; "
+                               "FP32 and FP64; n=2^%d" % args.log2n,
+                   "n": n, "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush needed)"},
+        "frac_of_measured_hbm": round(value / world / hbm_peak, 4),
+        "roofline": roof,
+        "per_kernel_ms": {f"{op}_{dt}": round(ms, 4) for (dt, op), ms in per_kernel.items()},
+        "per_kernel_gbs": {f"{op}_{dt}": round(abytes[(dt, op)] / (ms * 1e-3) / 1e9, 1)
+                           for (dt, op), ms in per_kernel.items()},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+
+    if not args.no_e2e:
+        result["e2e"] = e2e_measure(torch, salt, loads, args, world, steps, abytes)
+    del loads
+    torch.cuda.empty_cache()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(1 << args.cpu_log2)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e_measure(torch, salt, loads, args, world, steps, abytes):
+    """The same step through the public API with host buffers: per step, the
+    inputs are copied from pinned host memory, the ops run, and the results
+    (e's output, the updated y, dot and nrm2) are read back."""
+    from paper_1109_1264_gb300.programs import PROG_E
+    host = {}
+    h2d = d2h = 0
+    for dt, w in loads.items():
+        hs = {k: torch.empty(w.n, dtype=w.a.dtype, pin_memory=True) for k in ("a", "b", "c", "d", "y", "out", "y_out")}
+        for k in ("a", "b", "c", "d", "y"):
+            hs[k].copy_(getattr(w, k))
+        hs["red"] = torch.empty(2, dtype=torch.float64, pin_memory=True)
+        host[dt] = hs
+        h2d += 5 * w.n * ES[dt]
+        d2h += 2 * w.n * ES[dt] + 16
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for dt, w in loads.items():
+            hs = host[dt]
+            for k in ("a", "b", "c", "d", "y"):
+                getattr(w, k).copy_(hs[k], non_blocking=True)
+            salt.salt_eval(PROG_E, [w.a, w.b, w.c, w.d, w.out], [ALPHA, BETA])
+            salt.salt_axpby(ALPHA, w.a, BETA, w.y)
+            salt.salt_dot(w.a, w.b, w.red[0:1])
+            salt.salt_nrm2(w.c, w.red[1:2])
+            hs["out"].copy_(w.out, non_blocking=True)
+            hs["y_out"].copy_(w.y, non_blocking=True)
+            hs["red"].copy_(w.red, non_blocking=True)
+
+    k = max(3, min(args.steps, 10))
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    step_bytes = sum(abytes[(dt, op)] for dt, op, _ in steps)
+    return {"value": round(world * step_bytes * k / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
+            "ms_per_step": round(ms / k, 3)}
+
+
+if __name__ == "__main__":
+    main()
