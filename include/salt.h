@@ -213,6 +213,34 @@ salt_status salt_nrm2(int32_t dtype, int64_t n, const void* x, double* out, int3
 salt_status salt_fill_uniform(int32_t dtype, int64_t n, uint64_t key, int64_t offset, void* x,
                               void* stream);
 
+/* ---------------------------------------------------------------------------
+ * salt_dot_noalloc -- *out = sum_i x_i * y_i, like salt_dot with
+ * SALT_DEFAULT, but without any device allocation.  (The paper has no
+ * counterpart: it is an interface for callers of this library.)
+ * salt_dot's partial sums live in a workspace the library cudaMalloc's on the
+ * first reducing call on a stream.  Callers that cannot allow that -- code
+ * issuing work while its stream is captured into a CUDA graph, runtimes that
+ * hand out all device memory from a fixed up-front reservation, loops that
+ * cannot afford cudaMalloc's implicit device synchronisation -- use this entry
+ * point instead.  Its scratch is a static device array of 32 KiB + 256 B that
+ * every GPU loading the library holds until process exit; it never calls
+ * cudaMalloc, cudaFree or any allocating routine.
+ *   n      0 <= n <= 2^28 (268435456); larger n returns SALT_ERR_BUDGET
+ *          (the scratch holds one partial per 65536 elements, 4096 in all)
+ *   x, y   device, 16-byte aligned, `dtype` elements
+ *   out    device pointer to one double
+ * Accumulation as salt_dot (F32: compensated Dot2, F64: FMA), partials
+ * combined in FP64 in a fixed order, so the result depends on n only.
+ * The first call on each device looks up the scratch array's device address
+ * (set-up); make that first call before capturing any stream.  Every call
+ * shares the one array and clears its ticket word on `stream` before the
+ * kernel: calls whose work overlaps on the GPU (two streams at once) race on
+ * it, so serialise them.
+ * Errors: SALT_ERR_DTYPE, SALT_ERR_ARG, SALT_ERR_ALIGN, SALT_ERR_BUDGET (all
+ * before any launch), SALT_ERR_CUDA; text via salt_last_error(). */
+salt_status salt_dot_noalloc(int32_t dtype, int64_t n, const void* x, const void* y, double* out,
+                             void* stream);
+
 /* Free every workspace the library holds (call with no library work in
  * flight).  Returns SALT_OK or SALT_ERR_CUDA. */
 salt_status salt_release_workspaces(void);

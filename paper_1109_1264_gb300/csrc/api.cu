@@ -28,6 +28,9 @@ static salt_status set_error(salt_status st, const std::string& msg) {
   t_last_error = msg;
   return st;
 }
+// Lets other translation units report through salt_last_error().
+salt_status report_error(salt_status st, const std::string& msg) { return set_error(st, msg); }
+
 static salt_status cuda_error(cudaError_t e, const char* where) {
   return set_error(SALT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }

@@ -24,7 +24,7 @@ MAX_PROG, MAX_VECS, MAX_SCALS, MAX_STACK, MAX_REDS = 32, 8, 8, 8, 4
 # Symbols that include/salt.h declares (checked by the test suite).
 EXPORTS = ["salt_version", "salt_status_str", "salt_last_error", "salt_check_program", "salt_eval",
            "salt_axpby", "salt_dot", "salt_nrm2", "salt_fill_uniform", "salt_release_workspaces",
-           "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count"]
+           "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_dot_noalloc"]
 
 
 class Insn(ctypes.Structure):
@@ -65,6 +65,7 @@ def _load() -> ctypes.CDLL:
         "salt_tune_get": (i32, [ip, i32, i32, i64, ctypes.POINTER(LaunchCfg)]),
         "salt_tune_clear": (i32, []),
         "salt_launch_count": (i64, []),
+        "salt_dot_noalloc": (i32, [i32, i64, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -188,6 +189,14 @@ def salt_fill_uniform(x, key: int, offset: int = 0, stream=None) -> None:
     _contig([x])
     _check(lib.salt_fill_uniform(_dtype_code(x), x.numel(), int(key) & 0xFFFFFFFFFFFFFFFF, int(offset),
                                  _ptr(x), _stream_ptr(stream)))
+
+
+def salt_dot_noalloc(x, y, out, stream=None) -> None:
+    """out[0] <- sum x_i y_i using only the library's static scratch (no
+    device allocation; n <= 2^28)."""
+    _contig([x, y])
+    dt = _common_dtype([x, y])
+    _check(lib.salt_dot_noalloc(dt, _n_of([x, y]), _ptr(x), _ptr(y), _ptr(out), _stream_ptr(stream)))
 
 
 def salt_release_workspaces() -> None:
