@@ -52,18 +52,24 @@ struct Nrm2F32Plain {
   __device__ __forceinline__ void add(float x) { s = __fmaf_rn(x, x, s); }
 };
 
+// F64: the range of |x| is read from the biased exponent with integer
+// instructions -- on GB300 the FP64 pipe (about 2 instructions per clock per
+// SM) is the scarce resource, and a medium element then costs exactly one
+// FP64 instruction (the FMA).  Medium: 2^-511 <= |x| < 2^486 (biased exponent
+// 512..1508); big: |x| >= 2^486, Inf and NaN (exponent >= 1509); small:
+// |x| < 2^-511, zeros and subnormals (exponent < 512).
 struct Nrm2F64 {
   double sml = 0.0, med = 0.0, big = 0.0;
   __device__ __forceinline__ void add(double x) {
-    const double ax = fabs(x);
-    if (ax > Blue<double>::tbig) {
-      const double t = __dmul_rn(ax, Blue<double>::sbig);
+    const unsigned bexp = ((unsigned)__double2hiint(x) >> 20) & 0x7FFu;
+    if (bexp - 512u < 997u) {
+      med = __fma_rn(x, x, med);
+    } else if (bexp >= 1509u) {
+      const double t = __dmul_rn(fabs(x), Blue<double>::sbig);
       big = __fma_rn(t, t, big);
-    } else if (ax < Blue<double>::tsml) {
-      const double t = __dmul_rn(ax, Blue<double>::ssml);
-      sml = __fma_rn(t, t, sml);
     } else {
-      med = __fma_rn(ax, ax, med);
+      const double t = __dmul_rn(fabs(x), Blue<double>::ssml);
+      sml = __fma_rn(t, t, sml);
     }
   }
 };
