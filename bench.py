@@ -238,6 +238,7 @@ def main():
     ap.add_argument("--cpu-log2", type=int, default=22)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -355,7 +356,10 @@ def main():
     if not args.no_e2e:
         result["e2e"] = e2e_measure(torch, salt, loads, args, world, steps, abytes)
     del loads
+    steps = None
     torch.cuda.empty_cache()
+    if not args.no_batched:
+        result["batched"] = batched_measure(torch, salt)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(1 << args.cpu_log2)
@@ -364,6 +368,61 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096) -> dict:
+    """4096 CG-style updates (r <- r - alpha q; rho = r.r; p <- r + beta p),
+    lengths log-uniform in [64, 2^20], in one persistent graph-replayed launch
+    (autotuned) versus 4096 plain per-call launches on one stream."""
+    from paper_1109_1264_gb300 import inputs
+    from paper_1109_1264_gb300.programs import PROG_CG
+    lens = inputs.loguniform_lengths(0, nitems, 64, 1 << 20)
+    ab = inputs.cg_scalars(0, nitems)
+    out = {}
+    stream = torch.cuda.current_stream()
+    for dt, tdt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+        align = 16 // es
+        offs, o = [], 0
+        for n in lens:
+            offs.append(o)
+            o += -(-int(n) // align) * align
+        bufs = [torch.empty(o, dtype=tdt, device="cuda") for _ in range(3)]
+        for k, buf in enumerate(bufs):
+            salt.salt_fill_uniform(buf, inputs.vector_key(0, 0, k))
+        b = salt.Batch(nitems)
+        for i in range(nitems):
+            n = int(lens[i])
+            b.add(PROG_CG, [buf[offs[i]:offs[i] + n] for buf in bufs], list(ab[i]))
+        red = torch.zeros(nitems, dtype=torch.float64, device="cuda")
+        nbytes = b.info()["bytes"]
+        best_ms = b.autotune(red, reps=3)
+        cfg = b.get_config()
+
+        def timed(fn, k):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(k):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / k
+
+        ms_b = timed(lambda: b.launch(red), reps)
+        ms_p = timed(lambda: b.launch_plain(red), max(3, reps // 4))
+        out[dt] = {"batched_gbs": round(nbytes / (ms_b * 1e-3) / 1e9, 1),
+                   "plain_gbs": round(nbytes / (ms_p * 1e-3) / 1e9, 1),
+                   "ratio": round(ms_p / ms_b, 2), "batched_ms": round(ms_b, 4), "plain_ms": round(ms_p, 4),
+                   "bytes_per_launch": nbytes, "autotune_best_ms": round(best_ms, 4), "config": cfg}
+        b.close()
+        del bufs
+        torch.cuda.empty_cache()
+    out["workload"] = ("4096 CG updates per launch, n log-uniform in [64, 2^20] (sum %d), one graph-replayed "
+                       "persistent launch vs 4096 plain salt_eval calls" % int(lens.sum()))
+    return out
 
 
 def e2e_measure(torch, salt, loads, args, world, steps, abytes):

@@ -276,6 +276,73 @@ salt_status salt_tune_clear(void);
  * (all threads), for accounting in benchmarks. */
 int64_t salt_launch_count(void);
 
+/* ===========================================================================
+ * Batches: thousands of independent, uneven-length expressions and
+ * reductions in ONE persistent launch, replayed as a CUDA graph.  (The paper
+ * evaluates one expression per loop; a batch keeps its per-expression loop --
+ * same compiled programs, same per-element results -- and removes the
+ * per-call launch cost that dominates short vectors: Section 4.3 notes that
+ * the best loop shape for small vectors differs from the one for large ones.)
+ *
+ * Every item is split into tiles of `tile_bytes` per operand; resident blocks
+ * pull tiles from an atomic counter and run the owning item's program on the
+ * tile.  An item's DOT / SUMSQ / norm result is the tile partial sums added
+ * in tile order by the block that finishes the item's last tile, so it
+ * depends only on the item's length and the tile size: the same bits whatever
+ * else is in the batch.  Elementwise results are bit-identical to salt_eval.
+ * Items must not write memory that another item of the batch reads or writes
+ * (checked at launch: SALT_ERR_ALIAS).  A batch object is not thread-safe.
+ *
+ * The batch owns device memory for its item table, tile counters and
+ * partials (allocated on the first launch after items change, freed by
+ * salt_batch_destroy).  The first launch after any change uploads the table
+ * synchronously (it waits for the stream) and builds the graph; launches
+ * with unchanged items and the same red_out replay the graph. */
+typedef struct salt_batch salt_batch;
+
+/* capacity: maximum number of items (1 .. 2^20). */
+salt_status salt_batch_create(salt_batch** out, int32_t capacity);
+salt_status salt_batch_destroy(salt_batch* b);
+
+/* Adds one program item; arguments as salt_eval (device operands, host
+ * program and scalars read during the call).  The program must have a
+ * compiled instantiation (salt_check_program's compiled_out), at most 5
+ * vector operands and 2 scalars.  *red_index_out (may be NULL) receives the
+ * index in the launch's red_out of the item's first DOT/SUMSQ result, or -1.
+ * Errors: as salt_eval, SALT_ERR_BUDGET when full. */
+salt_status salt_batch_add(salt_batch* b, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                           void* const* vecs, int32_t nvecs, const double* scalars, int32_t nscal,
+                           int32_t* red_index_out);
+/* Adds a Euclidean-norm item (as salt_nrm2, SALT_DEFAULT accumulation). */
+salt_status salt_batch_add_nrm2(salt_batch* b, int32_t dtype, int64_t n, const void* x, int32_t* red_index_out);
+/* Removes every item (the device memory is kept for reuse). */
+salt_status salt_batch_clear(salt_batch* b);
+/* Item count, result count (red_out entries) and algorithmic bytes (each
+ * operand element read once, each result element written once); any output
+ * may be NULL. */
+salt_status salt_batch_info(const salt_batch* b, int32_t* nitems, int32_t* nresults, int64_t* bytes);
+
+/* Launch shape: unroll 1/2/4, block 64, 128 or 256,
+ * blocks_per_sm 0 (as many as fit) .. 32, tile_bytes 1 KiB .. 64 MiB
+ * (multiple of 256). */
+salt_status salt_batch_set_config(salt_batch* b, int32_t unroll, int32_t block, int32_t blocks_per_sm,
+                                  int64_t tile_bytes);
+salt_status salt_batch_get_config(const salt_batch* b, int32_t* unroll, int32_t* block, int32_t* blocks_per_sm,
+                                  int64_t* tile_bytes);
+
+/* One persistent launch over all items (a CUDA graph: counter reset + kernel)
+ * on `stream`.  red_out: device array of >= nresults doubles. */
+salt_status salt_batch_launch(salt_batch* b, double* red_out, void* stream);
+/* The same items as individual salt_eval / salt_nrm2 calls on `stream`, in
+ * item order (the plain per-call path, for comparison). */
+salt_status salt_batch_launch_plain(salt_batch* b, double* red_out, void* stream);
+/* Times every launch shape over unroll {1,2,4} x block {128,256} x
+ * tile_bytes {16,32,64,128} KiB (reps launches each, after one warm-up) and
+ * keeps the fastest; *best_ms (may be NULL) receives its time per launch.
+ * The items' programs run (1 + reps) x 24 times: in-place programs update
+ * their operands each time. */
+salt_status salt_batch_autotune(salt_batch* b, double* red_out, int32_t reps, double* best_ms, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,7 @@
 #include "../../include/salt.h"
 #include "fused.cuh"
 #include "host.h"
+#include "internal.h"
 #include "interp.cuh"
 #include "reduce.cuh"
 #include "registry.h"
@@ -171,19 +172,6 @@ static salt_status check_dtype(int32_t dt) {
 }
 
 // ------------------------------------------------------------ execution ---
-struct EvalArgs {
-  const salt_insn* prog;
-  int nprog;
-  int dt;
-  int64_t n;
-  void* const* vecs;
-  int nvecs;
-  const double* scalars;
-  int nscal;
-  double* red_out;
-  cudaStream_t stream;
-};
-
 template <typename T>
 static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, const DevInfo& info) {
   Registry& reg = registry();
@@ -255,7 +243,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, cons
   return SALT_OK;
 }
 
-static salt_status eval_impl(const EvalArgs& a) {
+salt_status validate_eval(const EvalArgs& a, Analysis* an_out) {
   salt_status st = check_dtype(a.dt);
   if (st != SALT_OK) return st;
   if (a.n < 0) return set_error(SALT_ERR_ARG, "n must be >= 0");
@@ -297,6 +285,14 @@ static salt_status eval_impl(const EvalArgs& a) {
       }
     }
   }
+  *an_out = an;
+  return SALT_OK;
+}
+
+salt_status eval_impl(const EvalArgs& a) {
+  Analysis an;
+  salt_status st = validate_eval(a, &an);
+  if (st != SALT_OK) return st;
   int dev = 0;
   DevInfo info;
   st = device_info(&dev, &info);
@@ -435,6 +431,23 @@ salt_status salt_dot(int32_t dtype, int64_t n, const void* x, const void* y, dou
 
 salt_status salt_nrm2(int32_t dtype, int64_t n, const void* x, double* out, int32_t flags,
                       void* stream) {
+  return nrm2_impl(dtype, n, x, out, flags, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace salt {
+
+salt_status current_device(int* dev, int* sms) {
+  DevInfo info;
+  salt_status st = device_info(dev, &info);
+  *sms = st == SALT_OK ? info.sms : 0;
+  return st;
+}
+
+void count_launch() { g_launches.fetch_add(1); }
+
+salt_status nrm2_impl(int32_t dtype, int64_t n, const void* x, double* out, int32_t flags, cudaStream_t stream) {
   salt_status st = check_dtype(dtype);
   if (st != SALT_OK) return st;
   if (flags != SALT_DEFAULT && flags != SALT_PLAIN) return set_error(SALT_ERR_ARG, "unknown flags");
@@ -444,9 +457,12 @@ salt_status salt_nrm2(int32_t dtype, int64_t n, const void* x, double* out, int3
   if (n > 0 && !x) return set_error(SALT_ERR_ARG, "x is NULL");
   if (!aligned(x, 16)) return set_error(SALT_ERR_ALIGN, "x must be 16-byte aligned");
   const int special = (dtype == SALT_F32 && flags == SALT_PLAIN) ? SPECIAL_NRM2_PLAIN : SPECIAL_NRM2;
-  return run_special(special, dtype == SALT_F32 ? DT_F32 : DT_F64, n, x, nullptr, out,
-                     (cudaStream_t)stream);
+  return run_special(special, dtype == SALT_F32 ? DT_F32 : DT_F64, n, x, nullptr, out, stream);
 }
+
+}  // namespace salt
+
+extern "C" {
 
 salt_status salt_fill_uniform(int32_t dtype, int64_t n, uint64_t key, int64_t offset, void* x,
                               void* stream) {

@@ -1,0 +1,282 @@
+// Batched persistent evaluation: thousands of independent, uneven-length
+// expression items in ONE launch.
+//
+// The host lays every item out as a run of fixed-size tiles (tile_bytes per
+// operand) and writes a table of items with the first global tile of each.
+// Resident blocks pull global tile numbers from an atomic counter (no
+// waiting), find the owning item by binary search, and run that item's
+// compiled program on the tile's element range -- the same per-element
+// operations as the single-expression kernels, so elementwise results are
+// bit-identical to them.  Reductions: each tile's block folds its partial sum
+// into partials[tile]; the block that finishes an item's last tile (per-item
+// ticket) adds the item's partials in tile order and writes the result.  The
+// summation order therefore depends only on the item's length and the tile
+// size, never on which block ran which tile or on the other items in the
+// launch.
+#pragma once
+
+#include "fused.cuh"
+#include "reduce.cuh"
+#include "registry.h"
+#include "shapes.h"
+
+namespace salt {
+
+constexpr int kBatchOps = 5;       // operands per item (largest shape: E)
+constexpr int kBatchPartials = 3;  // FP64 partial values per tile
+constexpr int32_t kKindNrm2 = -1;  // item kind: Euclidean norm (else shape id)
+
+struct BatchItem {
+  int32_t kind;       // shape id, or kKindNrm2
+  int32_t dtype;      // DT_F32 / DT_F64
+  int64_t n;          // elements
+  int64_t tile_begin; // first global tile of this item
+  int32_t ntiles;     // >= 1 (an empty item still owns one empty tile)
+  int32_t red_index;  // first result slot in red_out, or -1
+  void* v[kBatchOps]; // canonical operands
+  double sc[2];       // scalars (rounded to float for F32 items)
+};
+
+struct BatchHeader {
+  int32_t nitems;
+  int32_t pad;
+  int64_t total_tiles;
+  int64_t tile_bytes;  // bytes per operand per tile (multiple of 16 * block * unroll)
+};
+
+struct BatchParams {
+  const BatchHeader* hdr;
+  const BatchItem* items;
+  unsigned* counter;  // global tile counter; zero at launch
+  unsigned* tickets;  // per-item tile tickets; zero at launch
+  double* partials;   // kBatchPartials per global tile
+  double* red_out;
+};
+
+// One block evaluates program P on elements [lo, hi) of an item: whole
+// sub-tiles of U vectors per thread (load burst, op burst, store burst), then
+// single vectors, then single elements.
+template <class P, typename T, int U>
+__device__ __forceinline__ void range_eval(T* const* v, const T (&sc)[kMaxScals], int64_t lo, int64_t hi,
+                                           typename AccOf<T>::type (&acc)[kMaxReds]) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  constexpr unsigned LM = P::load_mask(), SMASK = P::store_mask();
+  using Acc = typename AccOf<T>::type;
+  using V = VecT<T, 16>;
+  const int64_t bd = blockDim.x;
+  const int64_t SUB = (int64_t)U * bd * VEC;
+  const int64_t nsub = (hi - lo) / SUB;
+  for (int64_t s = 0; s < nsub; ++s) {
+    const int64_t base = lo + s * SUB + (int64_t)threadIdx.x * VEC;
+    T x[kMaxVecs][U * VEC];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int k = 0; k < kMaxVecs; ++k) {
+        if ((LM >> k) & 1u) {
+          V t;
+          if ((SMASK >> k) & 1u) vload<false>(t, v[k] + base + u * bd * VEC);
+          else vload<true>(t, v[k] + base + u * bd * VEC);
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) x[k][u * VEC + e] = t.e[e];
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) x[k][u * VEC + e] = T(0);
+        }
+      }
+    }
+    exec_chunk<P, T, Acc, U * VEC>(x, sc, acc);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int k = 0; k < kMaxVecs; ++k) {
+        if ((SMASK >> k) & 1u) {
+          V t;
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) t.e[e] = x[k][u * VEC + e];
+          vstore(v[k] + base + u * bd * VEC, t);
+        }
+      }
+    }
+  }
+  const int64_t rlo = lo + nsub * SUB;
+  const int64_t nvr = (hi - rlo) / VEC;
+  for (int64_t j = threadIdx.x; j < nvr; j += bd) {
+    const int64_t off = rlo + j * VEC;
+    T x[kMaxVecs][VEC];
+#pragma unroll
+    for (int k = 0; k < kMaxVecs; ++k) {
+      if ((LM >> k) & 1u) {
+        V t;
+        if ((SMASK >> k) & 1u) vload<false>(t, v[k] + off);
+        else vload<true>(t, v[k] + off);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) x[k][e] = t.e[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) x[k][e] = T(0);
+      }
+    }
+    exec_chunk<P, T, Acc, VEC>(x, sc, acc);
+#pragma unroll
+    for (int k = 0; k < kMaxVecs; ++k) {
+      if ((SMASK >> k) & 1u) {
+        V t;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) t.e[e] = x[k][e];
+        vstore(v[k] + off, t);
+      }
+    }
+  }
+  for (int64_t i = rlo + nvr * VEC + threadIdx.x; i < hi; i += bd) {
+    T x[kMaxVecs][1];
+#pragma unroll
+    for (int k = 0; k < kMaxVecs; ++k) x[k][0] = ((LM >> k) & 1u) ? v[k][i] : T(0);
+    exec_chunk<P, T, Acc, 1>(x, sc, acc);
+#pragma unroll
+    for (int k = 0; k < kMaxVecs; ++k)
+      if ((SMASK >> k) & 1u) v[k][i] = x[k][0];
+  }
+}
+
+// Program item: returns the number of partial values produced (its
+// reductions) in vals.
+template <class P, typename T, int U>
+__device__ __forceinline__ int item_program(const BatchItem& it, int64_t lo, int64_t hi, double (&vals)[kBatchPartials]) {
+  T* v[kMaxVecs];
+#pragma unroll
+  for (int k = 0; k < kMaxVecs; ++k) v[k] = k < kBatchOps ? (T*)it.v[k] : nullptr;
+  T sc[kMaxScals];
+#pragma unroll
+  for (int k = 0; k < kMaxScals; ++k) sc[k] = k < 2 ? (T)it.sc[k] : T(0);
+  typename AccOf<T>::type acc[kMaxReds];
+  range_eval<P, T, U>(v, sc, lo, hi, acc);
+  constexpr int NR = P::nred();
+#pragma unroll
+  for (int r = 0; r < NR && r < kBatchPartials; ++r) vals[r] = acc[r].value();
+  return NR;
+}
+
+template <typename T>
+__device__ __forceinline__ int item_nrm2(const BatchItem& it, int64_t lo, int64_t hi, double (&vals)[kBatchPartials]) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  using V = VecT<T, 16>;
+  const T* x = (const T*)it.v[0];
+  if constexpr (sizeof(T) == 4) {
+    Nrm2F32 acc;
+    for (int64_t i = lo + (int64_t)threadIdx.x * VEC; i < hi; i += (int64_t)blockDim.x * VEC) {
+      if (i + VEC <= hi) {
+        V a;
+        vload<true>(a, x + i);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc.add(a.e[e]);
+      } else {
+        for (int64_t j = i; j < hi; ++j) acc.add(x[j]);
+      }
+    }
+    vals[0] = acc.value();
+    return 1;
+  } else {
+    Nrm2F64 acc;
+    for (int64_t i = lo + (int64_t)threadIdx.x * VEC; i < hi; i += (int64_t)blockDim.x * VEC) {
+      if (i + VEC <= hi) {
+        V a;
+        vload<true>(a, x + i);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) acc.add(a.e[e]);
+      } else {
+        for (int64_t j = i; j < hi; ++j) acc.add(x[j]);
+      }
+    }
+    vals[0] = acc.sml;
+    vals[1] = acc.med;
+    vals[2] = acc.big;
+    return 3;
+  }
+}
+
+template <typename T, int U>
+__device__ __forceinline__ int dispatch_item(const BatchItem& it, int64_t lo, int64_t hi, double (&vals)[kBatchPartials]) {
+  switch (it.kind) {
+#define SALT_BATCH_CASE(name, ...) \
+  case SHAPE_##name:               \
+    return item_program<Prog_##name, T, U>(it, lo, hi, vals);
+    SALT_SHAPE_LIST(SALT_BATCH_CASE)
+#undef SALT_BATCH_CASE
+    default:
+      return item_nrm2<T>(it, lo, hi, vals);
+  }
+}
+
+template <int U>
+__global__ void __launch_bounds__(256) batch_kernel(const BatchParams p) {
+  __shared__ int64_t s_tile;
+  __shared__ int s_item;
+  __shared__ bool s_last;
+  __shared__ double smem[256];
+  const int64_t total = p.hdr->total_tiles;
+  const int nitems = p.hdr->nitems;
+  const int64_t tile_bytes = p.hdr->tile_bytes;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int64_t t = (int64_t)atomicAdd(p.counter, 1u);
+      int item = 0;
+      if (t < total) {
+        int a = 0, b = nitems - 1;  // last item with tile_begin <= t
+        while (a < b) {
+          const int mid = (a + b + 1) >> 1;
+          if (p.items[mid].tile_begin <= t) a = mid;
+          else b = mid - 1;
+        }
+        item = a;
+      }
+      s_tile = t;
+      s_item = item;
+    }
+    __syncthreads();
+    const int64_t tile = s_tile;
+    if (tile >= total) break;
+    const int item = s_item;
+    const BatchItem it = p.items[item];
+    const int64_t tile_elems = tile_bytes / (it.dtype == DT_F32 ? 4 : 8);
+    const int64_t lo = (tile - it.tile_begin) * tile_elems;
+    const int64_t hi = lo + tile_elems < it.n ? lo + tile_elems : it.n;
+    double vals[kBatchPartials] = {0.0, 0.0, 0.0};
+    const int nv = it.dtype == DT_F32 ? dispatch_item<float, U>(it, lo, hi, vals)
+                                      : dispatch_item<double, U>(it, lo, hi, vals);
+    if (nv > 0) {
+      // this tile's partials, then the per-item ticket
+      for (int r = 0; r < nv; ++r) {
+        const double t = block_sum<double>(vals[r], smem);
+        if (threadIdx.x == 0) p.partials[tile * kBatchPartials + r] = t;
+      }
+      if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned k = atomicAdd(&p.tickets[item], 1u);
+        s_last = (k == (unsigned)it.ntiles - 1u);
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        double tot[kBatchPartials] = {0.0, 0.0, 0.0};
+        for (int r = 0; r < nv; ++r) {
+          double a = 0.0;
+          for (int64_t k = threadIdx.x; k < it.ntiles; k += blockDim.x)
+            a += ((volatile double*)p.partials)[(it.tile_begin + k) * kBatchPartials + r];
+          tot[r] = block_sum<double>(a, smem);
+        }
+        if (threadIdx.x == 0) {
+          if (it.kind == kKindNrm2) {
+            p.red_out[it.red_index] = it.dtype == DT_F32 ? __dsqrt_rn(tot[0]) : blue_finish(tot[0], tot[1], tot[2]);
+          } else {
+            for (int r = 0; r < nv; ++r) p.red_out[it.red_index + r] = tot[r];
+          }
+          p.tickets[item] = 0u;
+        }
+      }
+    }
+    __syncthreads();  // s_tile / s_item / s_last are rewritten next iteration
+  }
+}
+
+}  // namespace salt

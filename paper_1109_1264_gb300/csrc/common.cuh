@@ -131,23 +131,27 @@ template <> struct AccOf<float> { using type = AccF32; };
 template <> struct AccOf<double> { using type = AccF64; };
 
 // ---------------------------------------------------------------------------
-// Deterministic block sum: butterfly within each warp, then warp 0 folds the
-// per-warp sums.  The order depends only on blockDim.  Valid in thread 0.
+// Deterministic block sum through shared memory: every thread deposits its
+// value, the part above the largest power of two is folded in, then a
+// halving tree.  The order depends only on blockDim.  It uses no warp
+// shuffles, so the result does not depend on how warps reconverge after the
+// divergent tail loops that precede it (a shuffle-based version lost lane
+// contributions after such a tail in one kernel).  Returned to every thread.
+constexpr int kMaxBlock = 256;
 template <typename R>
-__device__ __forceinline__ R block_sum(R v, R* smem /* >= 32 entries */) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();  // smem may still be read by a previous call
-  if (lane == 0) smem[warp] = v;
+__device__ __forceinline__ R block_sum(R v, R* buf /* >= blockDim.x entries */) {
+  __syncthreads();  // buf may still be read by a previous call
+  buf[threadIdx.x] = v;
   __syncthreads();
-  const int nw = (blockDim.x + 31) >> 5;
-  if (warp == 0) {
-    v = lane < nw ? smem[lane] : R(0);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  unsigned p2 = 1;
+  while (p2 * 2 <= blockDim.x) p2 *= 2;
+  if (threadIdx.x < blockDim.x - p2) buf[threadIdx.x] += buf[threadIdx.x + p2];
+  __syncthreads();
+  for (unsigned s = p2 >> 1; s > 0; s >>= 1) {
+    if (threadIdx.x < s) buf[threadIdx.x] += buf[threadIdx.x + s];
+    __syncthreads();
   }
-  return v;
+  return buf[0];
 }
 
 // Cross-block combination: every block deposits NV partial values; the last

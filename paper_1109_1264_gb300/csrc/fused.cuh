@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(256) fused_kernel(const MapParams<T> p) {
   }
 
   if constexpr (NR > 0) {
-    __shared__ double smem[32];
+    __shared__ double smem[kMaxBlock];
     double vals[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) vals[r] = acc[r].value();

@@ -1,0 +1,43 @@
+// Internal interfaces shared by the C-ABI translation units (not exported).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/salt.h"
+#include "host.h"
+
+namespace salt {
+
+struct EvalArgs {
+  const salt_insn* prog;
+  int nprog;
+  int dt;
+  int64_t n;
+  void* const* vecs;
+  int nvecs;
+  const double* scalars;
+  int nscal;
+  double* red_out;
+  cudaStream_t stream;
+};
+
+// Records `msg` as the calling thread's salt_last_error() and returns `st`.
+salt_status report_error(salt_status st, const std::string& msg);
+
+// Every host-side check of a salt_eval call (dtype, sizes, program, NULL
+// operands, alignment, aliasing).  Fills `an` on success.  No CUDA calls.
+salt_status validate_eval(const EvalArgs& a, Analysis* an);
+
+// salt_eval and salt_nrm2 without the C wrappers.
+salt_status eval_impl(const EvalArgs& a);
+salt_status nrm2_impl(int32_t dtype, int64_t n, const void* x, double* out, int32_t flags, cudaStream_t s);
+
+// SM count of the current device (cached); 0 and an error on failure.
+salt_status current_device(int* dev, int* sms);
+
+// Number of kernel launches issued by the library (all threads).
+void count_launch();
+
+}  // namespace salt

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(256) interp_kernel(const InterpParams<T> p) {
   }
 
   if (p.nred > 0) {
-    __shared__ double smem[32];
+    __shared__ double smem[kMaxBlock];
     double vals[kMaxReds];
 #pragma unroll
     for (int r = 0; r < kMaxReds; ++r) vals[r] = acc[r].value();

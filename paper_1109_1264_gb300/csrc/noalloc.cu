@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kBlock) dot_span_kernel(const T* __restrict__ 
       for (int64_t j = i; j < end; ++j) acc.add_prod(x[j], y[j]);
     }
   }
-  __shared__ double smem[32];
+  __shared__ double smem[kMaxBlock];
   double vals[1] = {acc.value()};
   if (grid_combine<double, 1>(vals, partials, ticket, smem) && threadIdx.x == 0) *out = vals[0];
 }

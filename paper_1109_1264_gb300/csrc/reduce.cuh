@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(256) nrm2_kernel(const NrmParams p) {
           for (int e = 0; e < VEC; ++e) acc.add(a.e[e]);
         },
         [&](T a, T) { acc.add(a); });
-    __shared__ float smem[32];
+    __shared__ float smem[kMaxBlock];
     float vals[1] = {acc.s};
     if (grid_combine<float, 1>(vals, (float*)p.partials, p.ticket, smem) && threadIdx.x == 0)
       *p.out = (double)sqrtf(vals[0]);
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) nrm2_kernel(const NrmParams p) {
           for (int e = 0; e < VEC; ++e) acc.add(a.e[e]);
         },
         [&](T a, T) { acc.add(a); });
-    __shared__ double smem[32];
+    __shared__ double smem[kMaxBlock];
     double vals[1] = {acc.value()};
     if (grid_combine<double, 1>(vals, (double*)p.partials, p.ticket, smem) && threadIdx.x == 0)
       *p.out = __dsqrt_rn(vals[0]);
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256) nrm2_kernel(const NrmParams p) {
           for (int e = 0; e < VEC; ++e) acc.add(a.e[e]);
         },
         [&](T a, T) { acc.add(a); });
-    __shared__ double smem[32];
+    __shared__ double smem[kMaxBlock];
     double vals[3] = {acc.sml, acc.med, acc.big};
     if (grid_combine<double, 3>(vals, (double*)p.partials, p.ticket, smem) && threadIdx.x == 0)
       *p.out = blue_finish(vals[0], vals[1], vals[2]);
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) dot_plain_kernel(const DotParams p) {
         for (int e = 0; e < VEC; ++e) acc.add_prod(a.e[e], b.e[e]);
       },
       [&](float a, float b) { acc.add_prod(a, b); });
-  __shared__ float smem[32];
+  __shared__ float smem[kMaxBlock];
   float vals[1] = {acc.s};
   if (grid_combine<float, 1>(vals, (float*)p.partials, p.ticket, smem) && threadIdx.x == 0)
     *p.out = (double)vals[0];

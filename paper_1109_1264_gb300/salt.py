@@ -231,3 +231,106 @@ def salt_last_error() -> str:
 
 def salt_status_str(status: int) -> str:
     return lib.salt_status_str(status).decode()
+
+
+# ----------------------------------------------------------------- batches --
+
+_BATCH_SIGS = {
+    "salt_batch_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32],
+    "salt_batch_destroy": [ctypes.c_void_p],
+    "salt_batch_add": [ctypes.c_void_p, ctypes.POINTER(Insn), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                       ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                       ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
+    "salt_batch_add_nrm2": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                            ctypes.POINTER(ctypes.c_int32)],
+    "salt_batch_clear": [ctypes.c_void_p],
+    "salt_batch_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                        ctypes.POINTER(ctypes.c_int64)],
+    "salt_batch_set_config": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64],
+    "salt_batch_get_config": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)],
+    "salt_batch_launch": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "salt_batch_launch_plain": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "salt_batch_autotune": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                            ctypes.c_void_p],
+}
+for _name, _args in _BATCH_SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = ctypes.c_int32
+    _f.argtypes = _args
+EXPORTS += list(_BATCH_SIGS)
+
+
+class Batch:
+    """A salt_batch handle.  Methods are the salt_batch_* entry points with
+    torch tensors marshalled to device pointers.  Keeps references to the
+    operand tensors so their memory outlives the batch's launches."""
+
+    def __init__(self, capacity: int):
+        h = ctypes.c_void_p()
+        _check(lib.salt_batch_create(ctypes.byref(h), int(capacity)))
+        self.handle = h
+        self._keep = []
+
+    def close(self):
+        if self.handle:
+            _check(lib.salt_batch_destroy(self.handle))
+            self.handle = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, prog, vecs, scalars=(), n: int | None = None) -> int:
+        _contig(vecs)
+        dt = _common_dtype(vecs)
+        if n is None:
+            n = _n_of(vecs)
+        arr, m = program(prog)
+        ptrs = (ctypes.c_void_p * max(len(vecs), 1))(*[_ptr(v) for v in vecs])
+        sc = (ctypes.c_double * max(len(scalars), 1))(*[float(s) for s in scalars])
+        idx = ctypes.c_int32()
+        _check(lib.salt_batch_add(self.handle, arr, m, dt, int(n), ptrs, len(vecs), sc, len(scalars),
+                                  ctypes.byref(idx)))
+        self._keep.append(list(vecs))
+        return idx.value
+
+    def add_nrm2(self, x) -> int:
+        _contig([x])
+        idx = ctypes.c_int32()
+        _check(lib.salt_batch_add_nrm2(self.handle, _dtype_code(x), x.numel(), _ptr(x), ctypes.byref(idx)))
+        self._keep.append([x])
+        return idx.value
+
+    def clear(self):
+        _check(lib.salt_batch_clear(self.handle))
+        self._keep = []
+
+    def info(self) -> dict:
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(lib.salt_batch_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"items": a.value, "results": b.value, "bytes": c.value}
+
+    def set_config(self, unroll: int, block: int, blocks_per_sm: int, tile_bytes: int):
+        _check(lib.salt_batch_set_config(self.handle, unroll, block, blocks_per_sm, int(tile_bytes)))
+
+    def get_config(self) -> dict:
+        u, b, p, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _check(lib.salt_batch_get_config(self.handle, ctypes.byref(u), ctypes.byref(b), ctypes.byref(p),
+                                         ctypes.byref(t)))
+        return {"unroll": u.value, "block": b.value, "blocks_per_sm": p.value, "tile_bytes": t.value}
+
+    def launch(self, red_out=None, stream=None):
+        _check(lib.salt_batch_launch(self.handle, _ptr(red_out), _stream_ptr(stream)))
+
+    def launch_plain(self, red_out=None, stream=None):
+        _check(lib.salt_batch_launch_plain(self.handle, _ptr(red_out), _stream_ptr(stream)))
+
+    def autotune(self, red_out=None, reps: int = 3, stream=None) -> float:
+        best = ctypes.c_double()
+        _check(lib.salt_batch_autotune(self.handle, _ptr(red_out), int(reps), ctypes.byref(best),
+                                       _stream_ptr(stream)))
+        return best.value
