@@ -239,6 +239,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -360,6 +361,9 @@ def main():
     torch.cuda.empty_cache()
     if not args.no_batched:
         result["batched"] = batched_measure(torch, salt)
+    if not args.no_served:
+        torch.cuda.empty_cache()
+        result["served"] = served_measure(salt)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(1 << args.cpu_log2)
@@ -423,6 +427,43 @@ def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096) -> dict:
     out["workload"] = ("4096 CG updates per launch, n log-uniform in [64, 2^20] (sum %d), one graph-replayed "
                        "persistent launch vs 4096 plain salt_eval calls" % int(lens.sum()))
     return out
+
+
+def served_measure(salt, count: int = 3000, seed: int = 0) -> dict:
+    """Poisson stream of requests over the 5 served shapes (d = a + (b - c),
+    axpby, e, dot, nrm2), n log-uniform in [2^8, 2^24], 70% FP32 / 30% FP64,
+    operands resident in an 8 GiB arena; saturation throughput first (all
+    requests arrive at once), then arrival rates from 10% to 120% of it."""
+    import numpy as np
+
+    from paper_1109_1264_gb300 import inputs
+    ops = np.array([4, 3, 5, 2, 1], dtype=np.int64)  # operands read + written per shape
+    shapes, is64, lens = inputs.request_mix(seed, count)
+    es = np.where(is64, 8, 4)
+    total_bytes = int(np.sum(ops[shapes] * es * lens))
+    srv = salt.Server()
+    try:
+        zeros = np.zeros(count)
+        srv.replay(zeros[:200], shapes[:200], is64[:200].astype(np.int32), lens[:200], seed + 99)  # warm-up
+        lat, _, wall = srv.replay(zeros, shapes, is64.astype(np.int32), lens, seed)
+        sat_rps = count / (wall * 1e-6)
+        sat_gbs = total_bytes / (wall * 1e-6) / 1e9
+        points = []
+        for k, frac in enumerate((0.1, 0.3, 0.5, 0.7, 0.9, 1.2)):
+            rate = frac * sat_rps
+            arr = inputs.poisson_arrivals(seed + 1 + k, count, rate) * 1e6
+            lat, _, wall = srv.replay(arr, shapes, is64.astype(np.int32), lens, seed)
+            points.append({"load": frac, "rate_rps": round(rate, 1), "p50_us": round(float(np.percentile(lat, 50)), 1),
+                           "p99_us": round(float(np.percentile(lat, 99)), 1),
+                           "gbs": round(total_bytes / (wall * 1e-6) / 1e9, 1)})
+        stats = srv.stats()
+    finally:
+        srv.stop()
+    return {"saturation_rps": round(sat_rps, 1), "saturation_gbs": round(sat_gbs, 1),
+            "requests_per_point": count, "bytes_per_point": total_bytes,
+            "points": points, "steps_total": stats["steps"],
+            "workload": "5 shapes uniform, n log-uniform [2^8, 2^24], 70% FP32 / 30% FP64, 8 GiB resident budget, "
+                        "2 streams; latency from arrival to observed completion (includes the on-device input fill)"}
 
 
 def e2e_measure(torch, salt, loads, args, world, steps, abytes):

@@ -343,6 +343,88 @@ salt_status salt_batch_launch_plain(salt_batch* b, double* red_out, void* stream
  * their operands each time. */
 salt_status salt_batch_autotune(salt_batch* b, double* red_out, int32_t reps, double* best_ms, void* stream);
 
+/* ===========================================================================
+ * Serving: continuous batching of expression requests (no counterpart in the
+ * paper, which evaluates one expression per call; each request here is still
+ * one of its fused loops).
+ *
+ * A server owns a device arena of `budget_bytes` for request operands, a
+ * scheduler thread and `streams` CUDA streams.  Submitted requests are
+ * admitted in arrival order while fewer than `max_requests` are resident and
+ * the arena can hold their operand vectors; a request stays resident until
+ * the client releases it.  Whenever a stream is free, the scheduler launches
+ * a step holding every admitted request not yet run (up to `max_batch`):
+ * one batched launch fills the requests' input vectors on the device from
+ * their keys (the counter-based generator of salt_fill_uniform, standing in
+ * for the upload of client data), a second runs their programs (the batch
+ * kernel).  Steps on different streams overlap on the GPU; requests arriving
+ * meanwhile join the next step.  All requests use one tile size, so a
+ * request's results are the same bits alone or in any mix.
+ * Latency = host time at which the scheduler observed the step's completion
+ * event minus the request's submission time. */
+typedef struct salt_server salt_server;
+
+typedef struct {
+  int64_t budget_bytes; /* device arena for request operands (>= 1 MiB)          */
+  int32_t max_requests; /* resident requests at once                              */
+  int32_t max_batch;    /* requests per step (1 .. 65536)                          */
+  int32_t streams;      /* steps in flight (1 .. 8)                                */
+  int32_t tile_bytes;   /* bytes per operand per tile (>= 1024, multiple of 256)   */
+  int32_t unroll;       /* batch kernel unroll: 1, 2, 4                            */
+  int32_t block;        /* batch kernel block: 64, 128, 256                        */
+  int64_t max_n;        /* longest request accepted                                */
+} salt_serve_config;
+
+/* Defaults: 8 GiB budget, 4096 resident requests, 256 per step, 2 streams,
+ * 64 KiB tiles, unroll 2, 256 threads, n <= 2^24. */
+salt_status salt_serve_default_config(salt_serve_config* cfg);
+/* Allocates the arena and per-stream tables on the current device and starts
+ * the scheduler thread.  Errors: SALT_ERR_ARG, SALT_ERR_CUDA. */
+salt_status salt_serve_start(salt_server** out, const salt_serve_config* cfg);
+/* Drains the steps in flight, stops the scheduler, frees everything
+ * (requests not yet complete are dropped). */
+salt_status salt_serve_stop(salt_server* s);
+
+/* Submits a request.  prog/nprog: a program with a compiled instantiation
+ * (<= 5 vector operands, <= 2 scalars); prog == NULL requests the Euclidean
+ * norm of one operand.  keys[k] (nkeys entries, one per operand index) seeds
+ * operand k's contents: element i is value i of the counter-based uniform
+ * stream `keys[k]` (salt_fill_uniform); keys of output-only operands are
+ * ignored.  Scalars are read during the call.  *request_id receives the id.
+ * Errors: SALT_ERR_ARG (n beyond max_n, stopped server), SALT_ERR_PROGRAM,
+ * SALT_ERR_DTYPE, SALT_ERR_BUDGET (operands larger than the whole arena). */
+salt_status salt_serve_submit(salt_server* s, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                              const uint64_t* keys, int32_t nkeys, const double* scalars, int32_t nscal,
+                              int64_t* request_id);
+/* State: 0 waiting, 1 running, 2 done.  When done: *latency_us and the
+ * request's DOT/SUMSQ/norm results in red[0..nred) (host memory); either
+ * pointer may be NULL.  SALT_ERR_NOTFOUND for an unknown (or released) id. */
+salt_status salt_serve_poll(salt_server* s, int64_t id, int32_t* state, double* latency_us, double* red);
+/* Waits (bounded) until the request is done: SALT_ERR_TIMEOUT after
+ * timeout_us microseconds. */
+salt_status salt_serve_wait(salt_server* s, int64_t id, int64_t timeout_us);
+/* Copies operand `operand` (the submit's operand index) of a done request to
+ * host memory (bytes >= n * element size). */
+salt_status salt_serve_read(salt_server* s, int64_t id, int32_t operand, void* host_dst, int64_t bytes);
+/* Frees a done request's operands, or cancels a waiting one.  A running
+ * request cannot be released (SALT_ERR_ARG). */
+salt_status salt_serve_release(salt_server* s, int64_t id);
+/* Completed requests, steps launched, algorithmic bytes of completed
+ * requests, arena bytes in use, requests waiting; any pointer may be NULL. */
+salt_status salt_serve_stats(salt_server* s, int64_t* completed, int64_t* steps, int64_t* bytes,
+                             int64_t* resident_bytes, int32_t* waiting);
+/* Load generator: submits `count` requests at host times t0 + arrival_us[i]
+ * (t0 = the call's start; arrival_us ascending), each the standard served
+ * shape shape[i] -- 0: d = a + (b - c), 1: y = 1.5 x - 0.25 y, 2: e = 1.5 a -
+ * 0.25 b - c o d, 3: dot(x, y), 4: nrm2(x) -- with dtype[i] and n[i], operand
+ * k keyed seed * 0x100000001B3 + i * 16 + k + 1 (mod 2^64); releases each
+ * request as it completes and returns latency_us[i] (measured from its
+ * nominal arrival), its first result red_first[i] (may be NULL; 0 if none)
+ * and *wall_us, the time from t0 to the last completion. */
+salt_status salt_serve_replay(salt_server* s, int32_t count, const double* arrival_us, const int32_t* shape,
+                              const int32_t* dtype, const int64_t* n, uint64_t seed, double* latency_us,
+                              double* red_first, double* wall_us);
+
 #ifdef __cplusplus
 }
 #endif

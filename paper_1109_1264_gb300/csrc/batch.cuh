@@ -25,6 +25,8 @@ namespace salt {
 constexpr int kBatchOps = 5;       // operands per item (largest shape: E)
 constexpr int kBatchPartials = 3;  // FP64 partial values per tile
 constexpr int32_t kKindNrm2 = -1;  // item kind: Euclidean norm (else shape id)
+constexpr int32_t kKindFill = -2;  // item kind: counter-based uniform fill of v[0]
+                                   // with the key stored in the bits of sc[0]
 
 struct BatchItem {
   int32_t kind;       // shape id, or kKindNrm2
@@ -195,6 +197,23 @@ __device__ __forceinline__ int item_nrm2(const BatchItem& it, int64_t lo, int64_
   }
 }
 
+// Fill item: element i of v[0] is value i of the counter-based uniform stream
+// (the same generator as fill_kernel), standing in for an upload.
+template <typename T>
+__device__ __forceinline__ int item_fill(const BatchItem& it, int64_t lo, int64_t hi) {
+  T* x = (T*)it.v[0];
+  const uint64_t key = (uint64_t)__double_as_longlong(it.sc[0]);
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const uint64_t h = splitmix64_at(key, (uint64_t)i);
+    if constexpr (sizeof(T) == 8) {
+      x[i] = __dsub_rn(__dmul_rn(2.0, (double)(h >> 11) * 0x1p-53), 1.0);
+    } else {
+      x[i] = __fsub_rn(__fmul_rn(2.0f, (float)(uint32_t)(h >> 40) * 0x1p-24f), 1.0f);
+    }
+  }
+  return 0;
+}
+
 template <typename T, int U>
 __device__ __forceinline__ int dispatch_item(const BatchItem& it, int64_t lo, int64_t hi, double (&vals)[kBatchPartials]) {
   switch (it.kind) {
@@ -203,6 +222,8 @@ __device__ __forceinline__ int dispatch_item(const BatchItem& it, int64_t lo, in
     return item_program<Prog_##name, T, U>(it, lo, hi, vals);
     SALT_SHAPE_LIST(SALT_BATCH_CASE)
 #undef SALT_BATCH_CASE
+    case kKindFill:
+      return item_fill<T>(it, lo, hi);
     default:
       return item_nrm2<T>(it, lo, hi, vals);
   }

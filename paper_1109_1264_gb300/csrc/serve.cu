@@ -1,0 +1,731 @@
+// Serving loop (include/salt.h, salt_serve_*): continuous batching of
+// expression requests on one GPU.
+//
+// Requests arrive at any time.  A scheduler thread admits them in arrival
+// order while resident slots and the device-memory budget allow (operand
+// vectors live in a device arena until the client releases the request), and
+// launches a step as soon as one of its streams is free: every request
+// admitted since the previous step goes into ONE batched launch pair -- a fill
+// launch that writes the requests' input vectors on the device (standing in
+// for their upload), then the compute launch.  Requests arriving while steps
+// run wait for the next free stream, so up to `streams` steps overlap on the
+// GPU.  Completion is observed by polling each step's event; a request's
+// latency is completion time minus submission time on the host clock.
+//
+// Every request runs with the same tile size, so its reductions use the same
+// partition whatever else is in its step: alone or in a mix, the results are
+// the same bits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/salt.h"
+#include "batch.cuh"
+#include "internal.h"
+#include "registry.h"
+
+using namespace salt;
+
+namespace {
+
+double now_us() {
+  return std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+constexpr size_t kAlign = 256;
+size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// First-fit allocator over [0, size) with coalescing of freed neighbours.
+class Arena {
+ public:
+  void init(size_t size) {
+    free_.clear();
+    free_[0] = size;
+    size_ = size;
+    used_ = 0;
+  }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = round_up(bytes);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        const size_t start = it->first, rem = it->second - bytes;
+        free_.erase(it);
+        if (rem) free_[start + bytes] = rem;
+        used_ += bytes;
+        *off = start;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = round_up(bytes);
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t used() const { return used_; }
+
+ private:
+  std::map<size_t, size_t> free_;
+  size_t size_ = 0, used_ = 0;
+};
+
+enum : int32_t { RS_WAITING = 0, RS_RUNNING = 1, RS_DONE = 2 };
+
+struct Request {
+  int64_t id = 0;
+  int32_t kind = 0;  // shape id or kKindNrm2
+  int32_t dtype = 0;
+  int64_t n = 0;
+  int nvec = 0;
+  uint32_t load_mask = 0;
+  int nred = 0;
+  uint64_t keys[kBatchOps] = {0, 0, 0, 0, 0};
+  int user_of[kBatchOps] = {0, 0, 0, 0, 0};  // canonical operand -> user operand index
+  double sc[2] = {0.0, 0.0};
+  size_t vec_bytes = 0;
+  size_t off[kBatchOps] = {0, 0, 0, 0, 0};
+  bool resident = false;
+  int32_t state = RS_WAITING;
+  double t_submit = 0, t_done = 0;
+  double red[kBatchPartials] = {0, 0, 0};
+  int64_t bytes_alg = 0;  // algorithmic bytes of the compute
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  char* d_mem = nullptr;
+  char* h_mem = nullptr;
+  // device layout
+  BatchHeader* d_hdr[2] = {nullptr, nullptr};  // [0] fill, [1] compute
+  BatchItem* d_items[2] = {nullptr, nullptr};
+  unsigned* d_counters[2] = {nullptr, nullptr};
+  double* d_partials = nullptr;
+  double* d_red = nullptr;
+  // host staging (pinned), mirrors [hdr0 | items0 | hdr1 | items1], then red
+  size_t table_bytes = 0;
+  double* h_red = nullptr;
+  std::vector<Request*> reqs;
+  bool busy = false;
+};
+
+using KernelFn = void (*)(const BatchParams);
+KernelFn kernel_for(int unroll) {
+  switch (unroll) {
+    case 1: return &batch_kernel<1>;
+    case 2: return &batch_kernel<2>;
+    default: return &batch_kernel<4>;
+  }
+}
+
+salt_status fail(salt_status st, const std::string& m) { return report_error(st, m); }
+salt_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(SALT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+}  // namespace
+
+struct salt_server {
+  salt_serve_config cfg{};
+  int device = 0;
+  int sms = 0;
+  int grid = 0;
+  char* arena_base = nullptr;
+  Arena arena;
+  std::vector<Slot> slots;
+  int64_t items_cap = 0, tiles_cap = 0;
+  // shared state
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> waiting;             // submitted, not yet admitted
+  std::deque<Request*> pending;             // admitted (resident), not yet launched
+  std::unordered_map<int64_t, Request*> reqs;
+  std::deque<int64_t> completed;            // completion queue (ids)
+  int64_t next_id = 1;
+  int32_t resident = 0;
+  bool stop = false;
+  std::thread sched;
+  std::string sched_error;
+  // statistics
+  std::atomic<int64_t> n_done{0}, n_steps{0}, bytes_done{0};
+};
+
+namespace {
+
+size_t slot_device_bytes(const salt_server* s, size_t* off_items, size_t* off_counters, size_t* off_partials,
+                         size_t* off_red) {
+  const size_t hdr = 256;
+  const size_t items = round_up(sizeof(BatchItem) * (size_t)s->items_cap);
+  const size_t counters = round_up(sizeof(unsigned) * (size_t)(s->items_cap + 1));
+  const size_t partials = round_up(sizeof(double) * kBatchPartials * (size_t)s->tiles_cap);
+  const size_t red = round_up(sizeof(double) * kBatchPartials * (size_t)s->cfg.max_batch);
+  // [hdr0 items0 hdr1 items1 | counters0 counters1 | partials | red]
+  off_items[0] = hdr;
+  off_items[1] = hdr + items + hdr;
+  off_counters[0] = 2 * (hdr + items);
+  off_counters[1] = off_counters[0] + counters;
+  *off_partials = off_counters[1] + counters;
+  *off_red = *off_partials + partials;
+  return *off_red + red;
+}
+
+// Called with the request's shape/dtype set: lay out its operands in the arena.
+bool arena_take(salt_server* s, Request* r) {
+  int k = 0;
+  for (; k < r->nvec; ++k) {
+    if (!s->arena.alloc(r->vec_bytes, &r->off[k])) break;
+  }
+  if (k == r->nvec) return true;
+  for (int j = 0; j < k; ++j) s->arena.release(r->off[j], r->vec_bytes);
+  return false;
+}
+
+void arena_give(salt_server* s, Request* r) {
+  for (int k = 0; k < r->nvec; ++k) s->arena.release(r->off[k], r->vec_bytes);
+}
+
+int64_t tiles_of(const salt_server* s, int dtype, int64_t n) {
+  const int64_t te = s->cfg.tile_bytes / (dtype == SALT_F32 ? 4 : 8);
+  return n > 0 ? (n + te - 1) / te : 1;
+}
+
+// Builds and launches one step on `slot` from the front of `pending`
+// (scheduler thread, lock not held while launching).
+salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch) {
+  size_t off_items[2], off_counters[2], off_partials, off_red;
+  slot_device_bytes(s, off_items, off_counters, &off_partials, &off_red);
+  // host tables in the pinned staging area
+  BatchHeader* h_hdr[2] = {(BatchHeader*)slot.h_mem, (BatchHeader*)(slot.h_mem + off_items[1] - 256)};
+  BatchItem* h_items[2] = {(BatchItem*)(slot.h_mem + off_items[0]), (BatchItem*)(slot.h_mem + off_items[1])};
+  int nitems[2] = {0, 0};
+  int64_t tiles[2] = {0, 0};
+  int nred = 0;
+  for (Request* r : batch) {
+    char* base = s->arena_base;
+    const int dt = r->dtype == SALT_F32 ? DT_F32 : DT_F64;
+    for (int k = 0; k < r->nvec; ++k) {
+      if (!((r->load_mask >> k) & 1u)) continue;
+      BatchItem& f = h_items[0][nitems[0]++];
+      memset(&f, 0, sizeof f);
+      f.kind = kKindFill;
+      f.dtype = dt;
+      f.n = r->n;
+      f.tile_begin = tiles[0];
+      f.ntiles = (int32_t)tiles_of(s, r->dtype, r->n);
+      f.red_index = -1;
+      f.v[0] = base + r->off[k];
+      uint64_t key = r->keys[k];
+      memcpy(&f.sc[0], &key, sizeof key);
+      tiles[0] += f.ntiles;
+    }
+    BatchItem& c = h_items[1][nitems[1]++];
+    memset(&c, 0, sizeof c);
+    c.kind = r->kind;
+    c.dtype = dt;
+    c.n = r->n;
+    c.tile_begin = tiles[1];
+    c.ntiles = (int32_t)tiles_of(s, r->dtype, r->n);
+    c.red_index = r->nred > 0 ? nred : -1;
+    for (int k = 0; k < r->nvec; ++k) c.v[k] = base + r->off[k];
+    c.sc[0] = r->sc[0];
+    c.sc[1] = r->sc[1];
+    tiles[1] += c.ntiles;
+    nred += r->nred;
+  }
+  for (int t = 0; t < 2; ++t) {
+    memset(h_hdr[t], 0, sizeof(BatchHeader));
+    h_hdr[t]->nitems = nitems[t];
+    h_hdr[t]->total_tiles = tiles[t];
+    h_hdr[t]->tile_bytes = s->cfg.tile_bytes;
+  }
+  cudaError_t e = cudaMemcpyAsync(slot.d_mem, slot.h_mem, slot.table_bytes, cudaMemcpyHostToDevice, slot.stream);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(slot.d_counters[0], 0, off_partials - off_counters[0], slot.stream);
+  KernelFn k = kernel_for(s->cfg.unroll);
+  for (int t = 0; t < 2 && e == cudaSuccess; ++t) {
+    if (nitems[t] == 0) continue;
+    BatchParams p{slot.d_hdr[t], slot.d_items[t], slot.d_counters[t], slot.d_counters[t] + 1, slot.d_partials,
+                  slot.d_red};
+    const int grid = (int)std::min<int64_t>(s->grid, tiles[t]);
+    k<<<grid, s->cfg.block, 0, slot.stream>>>(p);
+    count_launch();
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && nred > 0)
+    e = cudaMemcpyAsync(slot.h_red, slot.d_red, sizeof(double) * nred, cudaMemcpyDeviceToHost, slot.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(slot.done, slot.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "serving step");
+  slot.reqs = batch;
+  slot.busy = true;
+  s->n_steps.fetch_add(1);
+  return SALT_OK;
+}
+
+void complete_slot(salt_server* s, Slot& slot) {
+  const double t = now_us();
+  std::lock_guard<std::mutex> lk(s->mu);
+  int idx = 0;
+  for (Request* r : slot.reqs) {
+    for (int j = 0; j < r->nred; ++j) r->red[j] = slot.h_red[idx + j];
+    idx += r->nred;
+    r->state = RS_DONE;
+    r->t_done = t;
+    s->completed.push_back(r->id);
+    s->n_done.fetch_add(1);
+    s->bytes_done.fetch_add(r->bytes_alg);
+  }
+  slot.reqs.clear();
+  slot.busy = false;
+  s->cv.notify_all();
+}
+
+void scheduler(salt_server* s) {
+  cudaSetDevice(s->device);
+  std::vector<Request*> batch;
+  for (;;) {
+    bool did = false;
+    for (Slot& slot : s->slots) {
+      if (slot.busy) {
+        const cudaError_t q = cudaEventQuery(slot.done);
+        if (q == cudaSuccess) {
+          complete_slot(s, slot);
+          did = true;
+        } else if (q != cudaErrorNotReady) {
+          std::lock_guard<std::mutex> lk(s->mu);
+          s->sched_error = std::string("step failed: ") + cudaGetErrorString(q);
+          s->stop = true;
+          s->cv.notify_all();
+        }
+      }
+    }
+    Slot* free_slot = nullptr;
+    for (Slot& slot : s->slots)
+      if (!slot.busy) {
+        free_slot = &slot;
+        break;
+      }
+    batch.clear();
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      // admission: arrival order, while slots and budget allow
+      while (!s->waiting.empty() && s->resident < s->cfg.max_requests) {
+        Request* r = s->waiting.front();
+        if (!arena_take(s, r)) break;
+        s->waiting.pop_front();
+        r->resident = true;
+        ++s->resident;
+        s->pending.push_back(r);
+      }
+      bool any_busy = false;
+      for (Slot& slot : s->slots) any_busy = any_busy || slot.busy;
+      if (s->stop && !any_busy) break;
+      if (free_slot && !s->pending.empty() && !s->stop) {
+        int64_t tiles = 0, fills = 0;
+        while (!s->pending.empty() && (int32_t)batch.size() < s->cfg.max_batch) {
+          Request* r = s->pending.front();
+          const int64_t t = tiles_of(s, r->dtype, r->n);
+          const int nf = __builtin_popcount(r->load_mask);
+          if (!batch.empty() && (tiles + t > s->tiles_cap || fills + nf > s->items_cap)) break;
+          s->pending.pop_front();
+          r->state = RS_RUNNING;
+          batch.push_back(r);
+          tiles += t;
+          fills += nf;
+        }
+      }
+      if (batch.empty() && !did) {
+        s->cv.wait_for(lk, std::chrono::microseconds(any_busy ? 5 : 200));
+        continue;
+      }
+    }
+    if (!batch.empty()) {
+      salt_status st = launch_step(s, *free_slot, batch);
+      if (st != SALT_OK) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->sched_error = salt_last_error();
+        s->stop = true;
+        s->cv.notify_all();
+      }
+    }
+  }
+}
+
+// Key of operand `slot` of request `item` under `seed` (same recipe as the
+// Python input module's vector_key).
+uint64_t vector_key(uint64_t seed, uint64_t item, uint64_t slot) {
+  return seed * 0x100000001B3ull + item * 16ull + slot + 1ull;
+}
+
+salt_status submit_impl(salt_server* s, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                        const uint64_t* keys, int32_t nkeys, const double* scalars, int32_t nscal,
+                        double t_submit, int64_t* id_out) {
+  if (dtype != SALT_F32 && dtype != SALT_F64) return fail(SALT_ERR_DTYPE, "dtype must be SALT_F32 or SALT_F64");
+  if (n < 0 || n > s->cfg.max_n) return fail(SALT_ERR_ARG, "n outside 0 .. max_n of the server");
+  if (nkeys < 0 || nkeys > kBatchOps || (nkeys > 0 && !keys)) return fail(SALT_ERR_ARG, "bad keys");
+  Request* r = new Request();
+  r->dtype = dtype;
+  r->n = n;
+  const int64_t es = dtype == SALT_F32 ? 4 : 8;
+  if (!prog) {  // Euclidean norm of one operand
+    if (nkeys != 1) {
+      delete r;
+      return fail(SALT_ERR_ARG, "a norm request has exactly one key");
+    }
+    r->kind = kKindNrm2;
+    r->nvec = 1;
+    r->load_mask = 1u;
+    r->nred = 1;
+    r->keys[0] = keys[0];
+    r->bytes_alg = n * es;
+  } else {
+    Analysis an;
+    std::string err;
+    salt_status st = analyse(prog, nprog, nkeys, nscal, &an, &err);
+    if (st != SALT_OK) {
+      delete r;
+      return fail(st, err);
+    }
+    if (an.used_scals && !scalars) {
+      delete r;
+      return fail(SALT_ERR_ARG, "scalars is NULL");
+    }
+    Canonical c;
+    canonicalise(prog, nprog, &c);
+    const int shape = find_shape(c);
+    if (shape < 0 || c.nvec > kBatchOps || c.nscal > 2 || c.nred > kBatchPartials) {
+      delete r;
+      return fail(SALT_ERR_PROGRAM, "program has no compiled instantiation the server can batch");
+    }
+    r->kind = shape;
+    r->nvec = c.nvec;
+    r->load_mask = c.load_mask;
+    r->nred = c.nred;
+    for (int k = 0; k < c.nvec; ++k) {
+      r->user_of[k] = c.vec_user[k];
+      r->keys[k] = keys[c.vec_user[k]];
+    }
+    for (int k = 0; k < c.nscal; ++k) {
+      const double v = scalars[c.scal_user[k]];
+      r->sc[k] = dtype == SALT_F32 ? (double)(float)v : v;
+    }
+    r->bytes_alg = (int64_t)(__builtin_popcount(c.load_mask) + __builtin_popcount(c.store_mask)) * es * n;
+  }
+  r->vec_bytes = round_up((size_t)std::max<int64_t>(n, 1) * es);
+  if ((int64_t)(r->vec_bytes * r->nvec) > s->cfg.budget_bytes) {
+    delete r;
+    return fail(SALT_ERR_BUDGET, "request needs more device memory than the whole budget");
+  }
+  r->t_submit = t_submit;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) {
+    delete r;
+    return fail(SALT_ERR_ARG, s->sched_error.empty() ? "server is stopping" : s->sched_error);
+  }
+  r->id = s->next_id++;
+  s->reqs[r->id] = r;
+  s->waiting.push_back(r);
+  *id_out = r->id;
+  s->cv.notify_all();
+  return SALT_OK;
+}
+
+void release_locked(salt_server* s, Request* r) {
+  if (r->resident) {
+    arena_give(s, r);
+    r->resident = false;
+    --s->resident;
+  }
+  s->reqs.erase(r->id);
+  delete r;
+  s->cv.notify_all();
+}
+
+}  // namespace
+
+extern "C" {
+
+salt_status salt_serve_default_config(salt_serve_config* cfg) {
+  if (!cfg) return fail(SALT_ERR_ARG, "cfg is NULL");
+  cfg->budget_bytes = (int64_t)8 << 30;
+  cfg->max_requests = 4096;
+  cfg->max_batch = 256;
+  cfg->streams = 2;
+  cfg->tile_bytes = 64 * 1024;
+  cfg->unroll = 2;
+  cfg->block = 256;
+  cfg->max_n = (int64_t)1 << 24;
+  return SALT_OK;
+}
+
+salt_status salt_serve_start(salt_server** out, const salt_serve_config* cfg) {
+  if (!out || !cfg) return fail(SALT_ERR_ARG, "out or cfg is NULL");
+  if (cfg->budget_bytes < (1 << 20) || cfg->max_requests < 1 || cfg->max_batch < 1 || cfg->max_batch > 65536 ||
+      cfg->streams < 1 || cfg->streams > 8 || cfg->tile_bytes < 1024 || cfg->tile_bytes % 256 ||
+      (cfg->unroll != 1 && cfg->unroll != 2 && cfg->unroll != 4) ||
+      (cfg->block != 64 && cfg->block != 128 && cfg->block != 256) || cfg->max_n < 1)
+    return fail(SALT_ERR_ARG, "invalid server configuration");
+  int dev = 0, sms = 0;
+  salt_status st = current_device(&dev, &sms);
+  if (st != SALT_OK) return st;
+  salt_server* s = new salt_server();
+  s->cfg = *cfg;
+  s->device = dev;
+  s->sms = sms;
+  int bps = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)kernel_for(cfg->unroll), cfg->block, 0);
+  s->grid = sms * std::max(bps, 1);
+  s->items_cap = (int64_t)cfg->max_batch * kBatchOps;
+  const int64_t per_req_tiles = (cfg->max_n * 8 + cfg->tile_bytes - 1) / cfg->tile_bytes;
+  s->tiles_cap = std::max<int64_t>((int64_t)cfg->max_batch * 4, per_req_tiles * 4);
+  cudaError_t e = cudaMalloc(&s->arena_base, (size_t)cfg->budget_bytes);
+  if (e != cudaSuccess) {
+    delete s;
+    return cuda_fail(e, "cudaMalloc(arena)");
+  }
+  s->arena.init((size_t)cfg->budget_bytes);
+  s->slots.resize((size_t)cfg->streams);
+  size_t off_items[2], off_counters[2], off_partials, off_red;
+  const size_t dbytes = slot_device_bytes(s, off_items, off_counters, &off_partials, &off_red);
+  for (Slot& slot : s->slots) {
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&slot.d_mem, dbytes);
+    slot.table_bytes = off_counters[0];
+    if (e == cudaSuccess) e = cudaHostAlloc(&slot.h_mem, slot.table_bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess)
+      e = cudaHostAlloc(&slot.h_red, sizeof(double) * kBatchPartials * cfg->max_batch, cudaHostAllocDefault);
+    if (e != cudaSuccess) break;
+    for (int t = 0; t < 2; ++t) {
+      slot.d_hdr[t] = (BatchHeader*)(slot.d_mem + off_items[t] - 256);
+      slot.d_items[t] = (BatchItem*)(slot.d_mem + off_items[t]);
+      slot.d_counters[t] = (unsigned*)(slot.d_mem + off_counters[t]);
+    }
+    slot.d_partials = (double*)(slot.d_mem + off_partials);
+    slot.d_red = (double*)(slot.d_mem + off_red);
+  }
+  if (e != cudaSuccess) {
+    for (Slot& slot : s->slots) {
+      if (slot.d_mem) cudaFree(slot.d_mem);
+      if (slot.h_mem) cudaFreeHost(slot.h_mem);
+      if (slot.h_red) cudaFreeHost(slot.h_red);
+      if (slot.done) cudaEventDestroy(slot.done);
+      if (slot.stream) cudaStreamDestroy(slot.stream);
+    }
+    cudaFree(s->arena_base);
+    delete s;
+    return cuda_fail(e, "server resources");
+  }
+  s->sched = std::thread(scheduler, s);
+  *out = s;
+  return SALT_OK;
+}
+
+salt_status salt_serve_submit(salt_server* s, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                              const uint64_t* keys, int32_t nkeys, const double* scalars, int32_t nscal,
+                              int64_t* request_id) {
+  if (!s || !request_id) return fail(SALT_ERR_ARG, "server or request_id is NULL");
+  return submit_impl(s, prog, nprog, dtype, n, keys, nkeys, scalars, nscal, now_us(), request_id);
+}
+
+salt_status salt_serve_poll(salt_server* s, int64_t id, int32_t* state, double* latency_us, double* red) {
+  if (!s) return fail(SALT_ERR_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return fail(SALT_ERR_NOTFOUND, "unknown request id");
+  const Request* r = it->second;
+  if (state) *state = r->state;
+  if (r->state == RS_DONE) {
+    if (latency_us) *latency_us = r->t_done - r->t_submit;
+    if (red)
+      for (int j = 0; j < r->nred; ++j) red[j] = r->red[j];
+  }
+  return SALT_OK;
+}
+
+salt_status salt_serve_wait(salt_server* s, int64_t id, int64_t timeout_us) {
+  if (!s) return fail(SALT_ERR_ARG, "server is NULL");
+  std::unique_lock<std::mutex> lk(s->mu);
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+  for (;;) {
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return fail(SALT_ERR_NOTFOUND, "unknown request id");
+    if (it->second->state == RS_DONE) return SALT_OK;
+    if (s->stop && !s->sched_error.empty()) return fail(SALT_ERR_CUDA, s->sched_error);
+    if (s->cv.wait_until(lk, deadline) == std::cv_status::timeout) {
+      it = s->reqs.find(id);
+      if (it != s->reqs.end() && it->second->state == RS_DONE) return SALT_OK;
+      return fail(SALT_ERR_TIMEOUT, "request not complete within the timeout");
+    }
+  }
+}
+
+salt_status salt_serve_read(salt_server* s, int64_t id, int32_t operand, void* host_dst, int64_t bytes) {
+  if (!s || !host_dst) return fail(SALT_ERR_ARG, "server or host_dst is NULL");
+  char* src = nullptr;
+  int64_t n = 0, es = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return fail(SALT_ERR_NOTFOUND, "unknown request id");
+    Request* r = it->second;
+    if (r->state != RS_DONE) return fail(SALT_ERR_ARG, "request is not complete");
+    int k = -1;
+    for (int j = 0; j < r->nvec; ++j)
+      if ((r->kind == kKindNrm2 ? 0 : r->user_of[j]) == operand) k = j;
+    if (k < 0) return fail(SALT_ERR_ARG, "request has no such operand");
+    es = r->dtype == SALT_F32 ? 4 : 8;
+    n = r->n;
+    if (bytes < n * es) return fail(SALT_ERR_ARG, "host buffer too small");
+    src = s->arena_base + r->off[k];
+  }
+  if (n == 0) return SALT_OK;
+  cudaError_t e = cudaMemcpy(host_dst, src, (size_t)(n * es), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SALT_OK : cuda_fail(e, "cudaMemcpy(read)");
+}
+
+salt_status salt_serve_release(salt_server* s, int64_t id) {
+  if (!s) return fail(SALT_ERR_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return fail(SALT_ERR_NOTFOUND, "unknown request id");
+  Request* r = it->second;
+  if (r->state == RS_RUNNING) return fail(SALT_ERR_ARG, "request is running; wait for it first");
+  if (r->state == RS_WAITING) {
+    auto w = std::find(s->waiting.begin(), s->waiting.end(), r);
+    if (w != s->waiting.end()) s->waiting.erase(w);
+    auto p = std::find(s->pending.begin(), s->pending.end(), r);
+    if (p != s->pending.end()) s->pending.erase(p);
+  }
+  release_locked(s, r);
+  return SALT_OK;
+}
+
+salt_status salt_serve_stats(salt_server* s, int64_t* completed, int64_t* steps, int64_t* bytes,
+                             int64_t* resident_bytes, int32_t* waiting) {
+  if (!s) return fail(SALT_ERR_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (completed) *completed = s->n_done.load();
+  if (steps) *steps = s->n_steps.load();
+  if (bytes) *bytes = s->bytes_done.load();
+  if (resident_bytes) *resident_bytes = (int64_t)s->arena.used();
+  if (waiting) *waiting = (int32_t)(s->waiting.size() + s->pending.size());
+  return SALT_OK;
+}
+
+salt_status salt_serve_stop(salt_server* s) {
+  if (!s) return SALT_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  if (s->sched.joinable()) s->sched.join();
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(s->device);
+  for (Slot& slot : s->slots) {
+    if (slot.stream) cudaStreamSynchronize(slot.stream);
+    if (slot.d_mem) cudaFree(slot.d_mem);
+    if (slot.h_mem) cudaFreeHost(slot.h_mem);
+    if (slot.h_red) cudaFreeHost(slot.h_red);
+    if (slot.done) cudaEventDestroy(slot.done);
+    if (slot.stream) cudaStreamDestroy(slot.stream);
+  }
+  cudaFree(s->arena_base);
+  cudaSetDevice(cur);
+  for (auto& kv : s->reqs) delete kv.second;
+  delete s;
+  return SALT_OK;
+}
+
+salt_status salt_serve_replay(salt_server* s, int32_t count, const double* arrival_us, const int32_t* shape,
+                              const int32_t* dtype, const int64_t* n, uint64_t seed, double* latency_us,
+                              double* red_first, double* wall_us) {
+  if (!s || count < 0 || (count > 0 && (!arrival_us || !shape || !dtype || !n || !latency_us)))
+    return fail(SALT_ERR_ARG, "bad replay arguments");
+  static const salt_insn progs[4][12] = {
+      {{SALT_OP_VEC, 0}, {SALT_OP_VEC, 1}, {SALT_OP_VEC, 2}, {SALT_OP_SUB, 0}, {SALT_OP_ADD, 0}, {SALT_OP_STORE, 3}},
+      {{SALT_OP_SCAL, 0}, {SALT_OP_VEC, 0}, {SALT_OP_SMUL, 0}, {SALT_OP_SCAL, 1}, {SALT_OP_VEC, 1},
+       {SALT_OP_SMUL, 0}, {SALT_OP_ADD, 0}, {SALT_OP_STORE, 1}},
+      {{SALT_OP_SCAL, 0}, {SALT_OP_VEC, 0}, {SALT_OP_SMUL, 0}, {SALT_OP_SCAL, 1}, {SALT_OP_VEC, 1},
+       {SALT_OP_SMUL, 0}, {SALT_OP_ADD, 0}, {SALT_OP_VEC, 2}, {SALT_OP_VEC, 3}, {SALT_OP_MUL, 0},
+       {SALT_OP_SUB, 0}, {SALT_OP_STORE, 4}},
+      {{SALT_OP_VEC, 0}, {SALT_OP_VEC, 1}, {SALT_OP_DOT, 0}}};
+  static const int32_t plen[4] = {6, 8, 12, 3};
+  static const int32_t pvec[5] = {4, 2, 5, 2, 1};
+  const double sc[2] = {1.5, -0.25};
+  std::vector<int64_t> ids((size_t)count, 0);
+  std::unordered_map<int64_t, int32_t> index_of;
+  const double t0 = now_us();
+  int32_t next = 0, done = 0;
+  double last_done = t0;
+  while (done < count) {
+    const double t = now_us() - t0;
+    while (next < count && arrival_us[next] <= t) {
+      const int sh = shape[next];
+      if (sh < 0 || sh > 4) return fail(SALT_ERR_ARG, "shape index outside 0..4");
+      uint64_t keys[kBatchOps];
+      for (int k = 0; k < pvec[sh]; ++k) keys[k] = vector_key(seed, (uint64_t)next, (uint64_t)k);
+      int64_t id = 0;
+      salt_status st = submit_impl(s, sh == 4 ? nullptr : progs[sh], sh == 4 ? 0 : plen[sh], dtype[next], n[next],
+                                   keys, pvec[sh], sc, 2, t0 + arrival_us[next], &id);
+      if (st != SALT_OK) return st;
+      ids[(size_t)next] = id;
+      index_of[id] = next;
+      ++next;
+    }
+    std::vector<int64_t> finished;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->stop && !s->sched_error.empty()) return fail(SALT_ERR_CUDA, s->sched_error);
+      if (s->completed.empty()) {
+        const double wait = next < count ? std::max(0.0, arrival_us[next] - (now_us() - t0)) : 200.0;
+        if (wait > 2.0) s->cv.wait_for(lk, std::chrono::microseconds((int64_t)std::min(wait, 200.0)));
+      }
+      while (!s->completed.empty()) {
+        finished.push_back(s->completed.front());
+        s->completed.pop_front();
+      }
+      for (int64_t id : finished) {
+        auto it = index_of.find(id);
+        auto rq = s->reqs.find(id);
+        if (it == index_of.end() || rq == s->reqs.end()) continue;  // not ours
+        Request* r = rq->second;
+        latency_us[it->second] = r->t_done - r->t_submit;
+        if (red_first) red_first[it->second] = r->nred > 0 ? r->red[0] : 0.0;
+        last_done = std::max(last_done, r->t_done);
+        release_locked(s, r);
+        index_of.erase(it);
+        ++done;
+      }
+    }
+  }
+  if (wall_us) *wall_us = last_done - t0;
+  return SALT_OK;
+}
+
+}  // extern "C"

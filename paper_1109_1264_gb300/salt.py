@@ -334,3 +334,119 @@ class Batch:
         _check(lib.salt_batch_autotune(self.handle, _ptr(red_out), int(reps), ctypes.byref(best),
                                        _stream_ptr(stream)))
         return best.value
+
+
+# ----------------------------------------------------------------- serving --
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("max_requests", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("streams", ctypes.c_int32), ("tile_bytes", ctypes.c_int32), ("unroll", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("max_n", ctypes.c_int64)]
+
+
+_vp, _i32, _i64, _dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
+_SERVE_SIGS = {
+    "salt_serve_default_config": [ctypes.POINTER(ServeConfig)],
+    "salt_serve_start": [ctypes.POINTER(_vp), ctypes.POINTER(ServeConfig)],
+    "salt_serve_stop": [_vp],
+    "salt_serve_submit": [_vp, ctypes.POINTER(Insn), _i32, _i32, _i64, ctypes.POINTER(ctypes.c_uint64), _i32,
+                          _dp, _i32, ctypes.POINTER(_i64)],
+    "salt_serve_poll": [_vp, _i64, ctypes.POINTER(_i32), _dp, _dp],
+    "salt_serve_wait": [_vp, _i64, _i64],
+    "salt_serve_read": [_vp, _i64, _i32, _vp, _i64],
+    "salt_serve_release": [_vp, _i64],
+    "salt_serve_stats": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                         ctypes.POINTER(_i64), ctypes.POINTER(_i32)],
+    "salt_serve_replay": [_vp, _i32, _dp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64),
+                          ctypes.c_uint64, _dp, _dp, _dp],
+}
+for _name, _args in _SERVE_SIGS.items():
+    _f = getattr(lib, _name)
+    _f.restype = ctypes.c_int32
+    _f.argtypes = _args
+EXPORTS += list(_SERVE_SIGS)
+
+SERVED_SHAPES = ("d=a+(b-c)", "axpby", "e", "dot", "nrm2")
+
+
+def serve_default_config() -> ServeConfig:
+    c = ServeConfig()
+    _check(lib.salt_serve_default_config(ctypes.byref(c)))
+    return c
+
+
+class Server:
+    """A salt_server handle (methods = the salt_serve_* entry points)."""
+
+    def __init__(self, cfg: ServeConfig | None = None, **overrides):
+        cfg = cfg or serve_default_config()
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        h = ctypes.c_void_p()
+        _check(lib.salt_serve_start(ctypes.byref(h), ctypes.byref(cfg)))
+        self.handle = h
+        self.cfg = cfg
+
+    def stop(self):
+        if self.handle:
+            _check(lib.salt_serve_stop(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
+
+    def submit(self, prog, dtype: int, n: int, keys, scalars=()) -> int:
+        arr, m = program(prog) if prog is not None else (None, 0)
+        ks = (ctypes.c_uint64 * max(len(keys), 1))(*[int(k) & 0xFFFFFFFFFFFFFFFF for k in keys])
+        sc = (ctypes.c_double * max(len(scalars), 1))(*[float(s) for s in scalars])
+        rid = ctypes.c_int64()
+        _check(lib.salt_serve_submit(self.handle, arr, m, dtype, int(n), ks, len(keys), sc, len(scalars),
+                                     ctypes.byref(rid)))
+        return rid.value
+
+    def poll(self, rid: int):
+        st, lat = ctypes.c_int32(), ctypes.c_double()
+        red = (ctypes.c_double * 4)()
+        _check(lib.salt_serve_poll(self.handle, rid, ctypes.byref(st), ctypes.byref(lat), red))
+        return st.value, lat.value, list(red)
+
+    def wait(self, rid: int, timeout_us: int = 10_000_000):
+        _check(lib.salt_serve_wait(self.handle, rid, int(timeout_us)))
+
+    def read(self, rid: int, operand: int, out):
+        """Copy an operand of a done request into the numpy array ``out``."""
+        _check(lib.salt_serve_read(self.handle, rid, operand, out.ctypes.data, out.nbytes))
+        return out
+
+    def release(self, rid: int):
+        _check(lib.salt_serve_release(self.handle, rid))
+
+    def stats(self) -> dict:
+        c, s, b, r = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        w = ctypes.c_int32()
+        _check(lib.salt_serve_stats(self.handle, ctypes.byref(c), ctypes.byref(s), ctypes.byref(b), ctypes.byref(r),
+                                    ctypes.byref(w)))
+        return {"completed": c.value, "steps": s.value, "bytes": b.value, "resident_bytes": r.value,
+                "waiting": w.value}
+
+    def replay(self, arrival_us, shape, dtype, n, seed: int):
+        """Returns (latency_us array, first results array, wall_us)."""
+        import numpy as np
+        cnt = len(arrival_us)
+        a = np.ascontiguousarray(arrival_us, dtype=np.float64)
+        s = np.ascontiguousarray(shape, dtype=np.int32)
+        d = np.ascontiguousarray(dtype, dtype=np.int32)
+        nn = np.ascontiguousarray(n, dtype=np.int64)
+        lat = np.zeros(cnt, dtype=np.float64)
+        red = np.zeros(cnt, dtype=np.float64)
+        wall = ctypes.c_double()
+        P = ctypes.POINTER
+        _check(lib.salt_serve_replay(self.handle, cnt, a.ctypes.data_as(P(ctypes.c_double)),
+                                     s.ctypes.data_as(P(ctypes.c_int32)), d.ctypes.data_as(P(ctypes.c_int32)),
+                                     nn.ctypes.data_as(P(ctypes.c_int64)), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                     lat.ctypes.data_as(P(ctypes.c_double)), red.ctypes.data_as(P(ctypes.c_double)),
+                                     ctypes.byref(wall)))
+        return lat, red, wall.value

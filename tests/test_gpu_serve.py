@@ -1,0 +1,182 @@
+"""Serving loop (GPU): served results against the oracle, each result the same
+alone and in a mix, admission by the device-memory budget, bounded waits,
+cancellation, and the trace replayer."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+from paper_1109_1264_gb300 import inputs
+from paper_1109_1264_gb300 import programs as P
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = {np.float64: 1e-13, np.float32: 1e-6}
+SHAPES = [(P.PROG_D, 4, 3), (P.PROG_AXPBY, 2, 1), (P.PROG_E, 5, 4), (P.PROG_DOT, 2, None), (None, 1, None)]
+SC = [1.5, -0.25]
+
+
+def assert_bits_equal(got, want, what=""):
+    iu = np.uint32 if got.dtype == np.float32 else np.uint64
+    bad = ~((got.view(iu) == want.view(iu)) | (np.isnan(got) & np.isnan(want)))
+    assert not bad.any(), f"{what}: {int(bad.sum())} elements differ"
+
+
+@pytest.fixture(scope="module")
+def salt(saltlib, cuda_dev):
+    return saltlib
+
+
+def host_inputs(keys, nv, n, dt):
+    return [inputs.hash_uniform(k, n, dt) for k in keys[:nv]]
+
+
+def expected(shape_i, keys, n, dt):
+    prog, nv, out = SHAPES[shape_i]
+    vecs = host_inputs(keys, nv, n, dt)
+    if prog is None:
+        return vecs, None, exact.exact_nrm2(vecs[0]), exact.exact_nrm2(vecs[0])
+    if prog == P.PROG_D:
+        vecs[3] = np.zeros(n, dt)
+    if prog == P.PROG_E:
+        vecs[4] = np.zeros(n, dt)
+    want = [v.copy() for v in vecs]
+    oracle.eval_program(prog, want, SC[:2])
+    if prog == P.PROG_DOT:
+        return want, None, exact.exact_dot(vecs[0], vecs[1]), exact.abs_dot(vecs[0], vecs[1])
+    return want, out, None, None
+
+
+def test_served_results_match_oracle(salt):
+    srv = salt.Server(budget_bytes=1 << 28, max_n=1 << 20)
+    try:
+        reqs = []
+        for dt, code in ((np.float64, salt.F64), (np.float32, salt.F32)):
+            for si, (prog, nv, _) in enumerate(SHAPES):
+                for n in (0, 1, 7, 300, 65536 + 3, (1 << 20)):
+                    keys = [inputs.vector_key(77, len(reqs), k) for k in range(nv)]
+                    rid = srv.submit(prog, code, n, keys, SC if prog is not None else ())
+                    reqs.append((rid, si, dt, n, keys))
+        for rid, si, dt, n, keys in reqs:
+            srv.wait(rid, 20_000_000)
+            state, lat, red = srv.poll(rid)
+            assert state == 2 and lat > 0
+            want, out, ref, scale = expected(si, keys, n, dt)
+            if out is not None:
+                got = srv.read(rid, out, np.empty(n, dt))
+                assert_bits_equal(got, want[out], f"shape {si} n={n}")
+            if ref is not None:
+                assert abs(red[0] - ref) <= TOL[dt] * scale, (si, dt, n, red[0], ref)
+            srv.release(rid)
+        st = srv.stats()
+        assert st["completed"] == len(reqs) and st["resident_bytes"] == 0 and st["waiting"] == 0
+    finally:
+        srv.stop()
+
+
+def test_alone_vs_mix_bit_identical(salt):
+    """>= 200 requests, each run alone (one request per step) and then all
+    submitted at once (steps of many requests on two streams)."""
+    srv = salt.Server(budget_bytes=1 << 30, max_n=1 << 16)
+    try:
+        shapes, is64, lens = inputs.request_mix(5, 240, lo=2 ** 8, hi=2 ** 16)
+        def submit_all():
+            ids = []
+            for i in range(len(lens)):
+                prog, nv, _ = SHAPES[int(shapes[i])]
+                keys = [inputs.vector_key(5, i, k) for k in range(nv)]
+                ids.append(srv.submit(prog, salt.F64 if is64[i] else salt.F32, int(lens[i]), keys,
+                                      SC if prog is not None else ()))
+            return ids
+
+        def collect(ids):
+            res = []
+            for i, rid in enumerate(ids):
+                srv.wait(rid, 20_000_000)
+                _, _, red = srv.poll(rid)
+                prog, nv, out = SHAPES[int(shapes[i])]
+                dt = np.float64 if is64[i] else np.float32
+                vec = srv.read(rid, out, np.empty(int(lens[i]), dt)) if out is not None else None
+                res.append((red[0], vec))
+                srv.release(rid)
+            return res
+
+        alone = []
+        for i in range(len(lens)):  # one at a time: each request is alone in its step
+            prog, nv, _ = SHAPES[int(shapes[i])]
+            keys = [inputs.vector_key(5, i, k) for k in range(nv)]
+            rid = srv.submit(prog, salt.F64 if is64[i] else salt.F32, int(lens[i]), keys,
+                             SC if prog is not None else ())
+            alone += collect_one(srv, rid, shapes[i], is64[i], lens[i])
+        before = srv.stats()["steps"]
+        mix = collect(submit_all())
+        steps = srv.stats()["steps"] - before
+        # Python submits one request every few tens of microseconds while
+        # small steps finish quickly, so steps carry a few requests each.
+        assert steps < 0.6 * len(lens), f"the mix ran in {steps} steps: requests were not batched"
+        for i, ((ra, va), (rm, vm)) in enumerate(zip(alone, mix)):
+            if SHAPES[int(shapes[i])][0] in (P.PROG_DOT, None):
+                assert np.float64(ra).view(np.uint64) == np.float64(rm).view(np.uint64), i
+            if va is not None:
+                assert_bits_equal(vm, va, f"request {i}")
+    finally:
+        srv.stop()
+
+
+def collect_one(srv, rid, shape, is64, n):
+    srv.wait(rid, 20_000_000)
+    _, _, red = srv.poll(rid)
+    prog, nv, out = SHAPES[int(shape)]
+    dt = np.float64 if is64 else np.float32
+    vec = srv.read(rid, out, np.empty(int(n), dt)) if out is not None else None
+    srv.release(rid)
+    return [(red[0], vec)]
+
+
+def test_budget_admission_timeout_and_cancel(salt):
+    srv = salt.Server(budget_bytes=4 << 20, max_n=1 << 20)
+    try:
+        n = 300_000  # 2 FP32 operands = 2.4 MB: two such requests do not fit in 4 MiB
+        keys = [1, 2]
+        a = srv.submit(P.PROG_DOT, salt.F32, n, keys)
+        srv.wait(a, 20_000_000)
+        b = srv.submit(P.PROG_DOT, salt.F32, n, keys)
+        c = srv.submit(P.PROG_DOT, salt.F32, 10, keys)  # small, but queued behind b (arrival order)
+        with pytest.raises(salt.SaltError) as ei:
+            srv.wait(b, 50_000)
+        assert ei.value.status == salt.ERR_TIMEOUT
+        assert srv.poll(b)[0] == 0 and srv.poll(c)[0] == 0
+        srv.release(c)  # cancel a waiting request
+        with pytest.raises(salt.SaltError) as ei:
+            srv.poll(c)
+        assert ei.value.status == salt.ERR_NOTFOUND
+        srv.release(a)  # frees the budget: b is admitted and runs
+        srv.wait(b, 20_000_000)
+        assert srv.poll(b)[2][0] == srv.poll(b)[2][0]
+        srv.release(b)
+        with pytest.raises(salt.SaltError) as ei:
+            srv.submit(P.PROG_DOT, salt.F64, 1 << 20, keys)  # 16 MiB > whole budget
+        assert ei.value.status == salt.ERR_BUDGET
+    finally:
+        srv.stop()
+
+
+def test_replay_poisson_trace(salt):
+    srv = salt.Server(budget_bytes=1 << 30, max_n=1 << 18)
+    try:
+        count = 400
+        shapes, is64, lens = inputs.request_mix(9, count, lo=2 ** 8, hi=2 ** 18)
+        arr = inputs.poisson_arrivals(9, count, 20_000.0) * 1e6  # 20k requests/s, in µs
+        lat, red, wall = srv.replay(arr, shapes, is64.astype(np.int32), lens, seed=9)
+        assert np.all(lat > 0) and wall > 0
+        for i in list(range(0, count, 37)):
+            si = int(shapes[i])
+            if SHAPES[si][0] in (P.PROG_DOT, None):
+                dt = np.float64 if is64[i] else np.float32
+                keys = [inputs.vector_key(9, i, k) for k in range(SHAPES[si][1])]
+                _, _, ref, scale = expected(si, keys, int(lens[i]), dt)
+                assert abs(red[i] - ref) <= TOL[dt] * scale, (i, red[i], ref)
+        assert srv.stats()["resident_bytes"] == 0
+    finally:
+        srv.stop()
