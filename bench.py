@@ -132,6 +132,18 @@ class Workload:
         for k, t in enumerate((self.a, self.b, self.c, self.d, self.y)):
             salt.salt_fill_uniform(t, key=seed * 16 + k + 1)
 
+    def tune(self, salt) -> dict:
+        """Autotunes the launch shape of each op of the step (setup, untimed)."""
+        from paper_1109_1264_gb300.programs import PROG_AXPBY, PROG_DOT, PROG_E
+        got = {}
+        got["e"], _ = salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_E, [self.a, self.b, self.c, self.d, self.out],
+                                         [ALPHA, BETA], reps=2)
+        got["axpby"], _ = salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_AXPBY, [self.a, self.y], [ALPHA, BETA], reps=2)
+        got["dot"], _ = salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_DOT, [self.a, self.b], red_out=self.red[0:1],
+                                           reps=2)
+        got["nrm2"], _ = salt.salt_autotune(salt.KERNEL_NRM2, None, [self.c], red_out=self.red[1:2], reps=2)
+        return got
+
     def ops(self, salt):
         """(name, callable) of the step, in order."""
         from paper_1109_1264_gb300.programs import PROG_E
@@ -240,6 +252,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -261,6 +274,7 @@ def main():
 
     n = 1 << args.log2n
     loads = {dt: Workload(torch, salt, dt, n, seed=rank) for dt in DTYPES}
+    tuned = {dt: loads[dt].tune(salt) for dt in DTYPES} if not args.no_tune else None
     steps = []
     for dt in DTYPES:
         for name, fn in loads[dt].ops(salt):
@@ -344,7 +358,8 @@ def main():
         "data": "synthetic: counter-based uniform[-1,1) (SplitMix64) operands, alpha=1.5, beta=-0.25",
         "config": {"workload": "BLAS-1 sweep top size: e=alpha*a+beta*b-c*d, y=alpha*x+beta*y, dot, nrm2; "
                                "FP32 and FP64; n=2^%d" % args.log2n,
-                   "n": n, "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush needed)"},
+                   "n": n, "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush needed)",
+                   "tuned": tuned},
         "frac_of_measured_hbm": round(value / world / hbm_peak, 4),
         "roofline": roof,
         "per_kernel_ms": {f"{op}_{dt}": round(ms, 4) for (dt, op), ms in per_kernel.items()},
@@ -482,19 +497,48 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
         h2d += 5 * w.n * ES[dt]
         d2h += 2 * w.n * ES[dt] + 16
     stream = torch.cuda.current_stream()
+    # The step is pipelined through the public API: each vector is split into
+    # chunks, and chunk k's uploads, kernels and read-backs go to stream k % 2,
+    # so copies in both directions overlap the kernels of the other stream.
+    nchunks = 8
+    side = [torch.cuda.Stream() for _ in range(2)]
+    dred = {dt: torch.zeros(2 * nchunks, dtype=torch.float64, device="cuda") for dt in loads}
+    for dt in loads:
+        host[dt]["red"] = torch.empty(2 * nchunks, dtype=torch.float64, pin_memory=True)
+        d2h += 16 * nchunks - 16
 
     def step():
+        for s in side:
+            s.wait_stream(stream)
         for dt, w in loads.items():
             hs = host[dt]
-            for k in ("a", "b", "c", "d", "y"):
-                getattr(w, k).copy_(hs[k], non_blocking=True)
-            salt.salt_eval(PROG_E, [w.a, w.b, w.c, w.d, w.out], [ALPHA, BETA])
-            salt.salt_axpby(ALPHA, w.a, BETA, w.y)
-            salt.salt_dot(w.a, w.b, w.red[0:1])
-            salt.salt_nrm2(w.c, w.red[1:2])
-            hs["out"].copy_(w.out, non_blocking=True)
-            hs["y_out"].copy_(w.y, non_blocking=True)
-            hs["red"].copy_(w.red, non_blocking=True)
+            n = w.n
+            bounds = [n * k // nchunks for k in range(nchunks + 1)]
+            bounds = [b - b % 4 for b in bounds[:-1]] + [n]
+            for k in range(nchunks):
+                lo, hi = bounds[k], bounds[k + 1]
+                with torch.cuda.stream(side[k % 2]):
+                    dv = {key: getattr(w, key)[lo:hi] for key in ("a", "b", "c", "d", "y", "out")}
+                    for key in ("a", "b", "c", "d", "y"):
+                        dv[key].copy_(hs[key][lo:hi], non_blocking=True)
+                    salt.salt_eval(PROG_E, [dv["a"], dv["b"], dv["c"], dv["d"], dv["out"]], [ALPHA, BETA])
+                    salt.salt_axpby(ALPHA, dv["a"], BETA, dv["y"])
+                    salt.salt_dot(dv["a"], dv["b"], dred[dt][2 * k:2 * k + 1])
+                    salt.salt_nrm2(dv["c"], dred[dt][2 * k + 1:2 * k + 2])
+                    hs["out"][lo:hi].copy_(dv["out"], non_blocking=True)
+                    hs["y_out"][lo:hi].copy_(dv["y"], non_blocking=True)
+        for s in side:
+            stream.wait_stream(s)
+        for dt in loads:
+            host[dt]["red"].copy_(dred[dt], non_blocking=True)
+
+    def combine():
+        # dot = sum of chunk dots; nrm2 = sqrt(sum of chunk norms squared)
+        out = {}
+        for dt in loads:
+            r = host[dt]["red"].tolist()
+            out[dt] = (sum(r[0::2]), sum(v * v for v in r[1::2]) ** 0.5)
+        return out
 
     k = max(3, min(args.steps, 10))
     for _ in range(3):
@@ -507,11 +551,13 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    combine()
     ms = e0.elapsed_time(e1)
     step_bytes = sum(abytes[(dt, op)] for dt, op, _ in steps)
     return {"value": round(world * step_bytes * k / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
-            "ms_per_step": round(ms / k, 3)}
+            "ms_per_step": round(ms / k, 3),
+            "pipeline": f"{nchunks} chunks per vector over 2 streams (uploads, kernels and read-backs overlap)"}
 
 
 if __name__ == "__main__":

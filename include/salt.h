@@ -272,6 +272,29 @@ salt_status salt_tune_get(const salt_insn* prog, int32_t nprog, int32_t dtype, i
 /* Forget every pinned configuration. */
 salt_status salt_tune_clear(void);
 
+/* Kernel families for salt_autotune. */
+#define SALT_KERNEL_PROGRAM 0    /* the kernel salt_eval picks for `prog`       */
+#define SALT_KERNEL_NRM2 1       /* salt_nrm2, SALT_DEFAULT: vecs = {x}          */
+#define SALT_KERNEL_NRM2_PLAIN 2 /* salt_nrm2, SALT_PLAIN (F32): vecs = {x}      */
+#define SALT_KERNEL_DOT_PLAIN 3  /* salt_dot, SALT_PLAIN (F32): vecs = {x, y}    */
+
+/* Autotuner: runs the call (arguments as salt_eval; for the other families
+ * vecs / red_out as noted above) under every configuration of unroll {1,2,4}
+ * x vec_bytes {16,32} x block {128,256} x blocks_per_sm {as many as fit, 2,
+ * 4}, `reps` timed runs each after one warm-up, on `stream`, and pins the
+ * fastest for (family, dtype, n bucket) in the tuning table.  *best and
+ * *best_ms (either may be NULL) receive it and its time per call.  The call
+ * runs (reps + 1) times per configuration (36 configurations; 12 for the
+ * interpreter, which has no unroll): in-place programs update their operands
+ * each time. */
+salt_status salt_autotune(int32_t kernel, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                          void* const* vecs, int32_t nvecs, const double* scalars, int32_t nscal, double* red_out,
+                          int32_t reps, salt_launch_cfg* best, double* best_ms, void* stream);
+/* Writes the tuning table as text (one line per entry) / merges such a file
+ * into it.  Errors: SALT_ERR_ARG (unreadable, unwritable or malformed). */
+salt_status salt_tune_save(const char* path);
+salt_status salt_tune_load(const char* path);
+
 /* Number of kernel launches this library has issued on the calling process
  * (all threads), for accounting in benchmarks. */
 int64_t salt_launch_count(void);

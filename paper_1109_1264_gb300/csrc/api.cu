@@ -146,13 +146,29 @@ static salt_launch_cfg lookup_cfg(int family, int dt, int64_t n) {
   return it != g_tune.end() ? it->second : default_cfg(family, dt);
 }
 
+// Resident blocks per SM of a kernel at a block size, cached per device (the
+// occupancy query costs microseconds, as much as a small kernel).
+static std::mutex g_occ_mu;
+static std::map<std::tuple<int, const void*, int, size_t>, int> g_occ;
+
 static int occupancy_blocks(const void* kernel, int block, size_t smem) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, kernel, block, smem);
+  {
+    std::lock_guard<std::mutex> lk(g_occ_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
+  }
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, block, smem) != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
-  return nb < 1 ? 1 : nb;
+  nb = nb < 1 ? 1 : nb;
+  std::lock_guard<std::mutex> lk(g_occ_mu);
+  g_occ[key] = nb;
+  return nb;
 }
 
 static int grid_for(int64_t n, int64_t tile_elems, int sms, int bps) {
@@ -542,6 +558,139 @@ salt_status salt_tune_get(const salt_insn* prog, int32_t nprog, int32_t dtype, i
 salt_status salt_tune_clear(void) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune.clear();
+  return SALT_OK;
+}
+
+salt_status salt_autotune(int32_t kernel, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                          void* const* vecs, int32_t nvecs, const double* scalars, int32_t nscal, double* red_out,
+                          int32_t reps, salt_launch_cfg* best_out, double* best_ms, void* stream) {
+  salt_status st = check_dtype(dtype);
+  if (st != SALT_OK) return st;
+  if (reps < 1 || n < 1) return set_error(SALT_ERR_ARG, "reps and n must be >= 1");
+  const cudaStream_t s = (cudaStream_t)stream;
+  int family = 0;
+  switch (kernel) {
+    case SALT_KERNEL_PROGRAM: {
+      Analysis an;
+      EvalArgs a{prog, nprog, dtype, n, vecs, nvecs, scalars, nscal, red_out, s};
+      st = validate_eval(a, &an);
+      if (st != SALT_OK) return st;
+      st = tune_family(prog, nprog, &family);
+      if (st != SALT_OK) return st;
+      break;
+    }
+    case SALT_KERNEL_NRM2: family = 100 + SPECIAL_NRM2; break;
+    case SALT_KERNEL_NRM2_PLAIN: family = 100 + SPECIAL_NRM2_PLAIN; break;
+    case SALT_KERNEL_DOT_PLAIN: family = 100 + SPECIAL_DOT_PLAIN; break;
+    default: return set_error(SALT_ERR_ARG, "unknown kernel family");
+  }
+  if (kernel != SALT_KERNEL_PROGRAM && (!vecs || nvecs < (kernel == SALT_KERNEL_DOT_PLAIN ? 2 : 1) || !red_out))
+    return set_error(SALT_ERR_ARG, "vecs / red_out missing");
+  if ((kernel == SALT_KERNEL_NRM2_PLAIN || kernel == SALT_KERNEL_DOT_PLAIN) && dtype != SALT_F32)
+    return set_error(SALT_ERR_DTYPE, "the plain kernels are F32 only");
+  auto run = [&]() -> salt_status {
+    switch (kernel) {
+      case SALT_KERNEL_PROGRAM: {
+        EvalArgs a{prog, nprog, dtype, n, vecs, nvecs, scalars, nscal, red_out, s};
+        return eval_impl(a);
+      }
+      case SALT_KERNEL_NRM2: return nrm2_impl(dtype, n, vecs[0], red_out, SALT_DEFAULT, s);
+      case SALT_KERNEL_NRM2_PLAIN: return nrm2_impl(dtype, n, vecs[0], red_out, SALT_PLAIN, s);
+      default: return salt_dot(dtype, n, vecs[0], vecs[1], red_out, SALT_PLAIN, stream);
+    }
+  };
+  const int dt = dtype == SALT_F32 ? DT_F32 : DT_F64;
+  const TuneKey key(family, dt, bucket_of(n));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return set_error(SALT_ERR_CUDA, "cudaEventCreate");
+  salt_launch_cfg best = default_cfg(family, dt);
+  float best_t = 1e30f;
+  for (int u : {1, 2, 4}) {
+    if (family == 200 && u != 1) continue;  // the interpreter has no unroll
+    for (int vb : {16, 32}) {
+      for (int blk : {128, 256}) {
+        for (int bps : {0, 2, 4}) {
+          const salt_launch_cfg c{u, vb, blk, bps};
+          {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[key] = c;
+          }
+          st = run();
+          if (st == SALT_OK) cudaEventRecord(e0, s);
+          for (int r = 0; r < reps && st == SALT_OK; ++r) st = run();
+          if (st != SALT_OK) break;
+          cudaEventRecord(e1, s);
+          if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = set_error(SALT_ERR_CUDA, "cudaEventSynchronize");
+            break;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (ms / reps < best_t) {
+            best_t = ms / reps;
+            best = c;
+          }
+        }
+        if (st != SALT_OK) break;
+      }
+      if (st != SALT_OK) break;
+    }
+    if (st != SALT_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (st == SALT_OK) g_tune[key] = best;
+    else g_tune.erase(key);
+  }
+  if (st != SALT_OK) return st;
+  if (best_out) *best_out = best;
+  if (best_ms) *best_ms = best_t;
+  return SALT_OK;
+}
+
+salt_status salt_tune_save(const char* path) {
+  if (!path) return set_error(SALT_ERR_ARG, "path is NULL");
+  FILE* f = fopen(path, "w");
+  if (!f) return set_error(SALT_ERR_ARG, std::string("cannot write ") + path);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  fprintf(f, "# salt tuning table: family dtype log2n_bucket unroll vec_bytes block blocks_per_sm\n");
+  for (const auto& kv : g_tune)
+    fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+            kv.second.unroll, kv.second.vec_bytes, kv.second.block, kv.second.blocks_per_sm);
+  fclose(f);
+  return SALT_OK;
+}
+
+salt_status salt_tune_load(const char* path) {
+  if (!path) return set_error(SALT_ERR_ARG, "path is NULL");
+  FILE* f = fopen(path, "r");
+  if (!f) return set_error(SALT_ERR_ARG, std::string("cannot read ") + path);
+  char line[256];
+  std::map<TuneKey, salt_launch_cfg> add;
+  while (fgets(line, sizeof line, f)) {
+    if (line[0] == '#' || line[0] == '\n') continue;
+    int fam, dt, b;
+    salt_launch_cfg c;
+    if (sscanf(line, "%d %d %d %d %d %d %d", &fam, &dt, &b, &c.unroll, &c.vec_bytes, &c.block,
+               &c.blocks_per_sm) != 7) {
+      fclose(f);
+      return set_error(SALT_ERR_ARG, std::string("malformed tuning line: ") + line);
+    }
+    salt_launch_cfg chk = c;
+    if (chk.blocks_per_sm == 0) chk.blocks_per_sm = 1;  // 0 = as many as fit
+    if (!cfg_valid(chk) || (dt != DT_F32 && dt != DT_F64) || b < 0 || b > 62 ||
+        !((fam >= 0 && fam < NUM_SHAPES) || (fam >= 100 && fam < 100 + NUM_SPECIAL) || fam == 200)) {
+      fclose(f);
+      return set_error(SALT_ERR_ARG, std::string("invalid tuning line: ") + line);
+    }
+    add[TuneKey(fam, dt, b)] = c;
+  }
+  fclose(f);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& kv : add) g_tune[kv.first] = kv.second;
   return SALT_OK;
 }
 

@@ -450,3 +450,42 @@ class Server:
                                      lat.ctypes.data_as(P(ctypes.c_double)), red.ctypes.data_as(P(ctypes.c_double)),
                                      ctypes.byref(wall)))
         return lat, red, wall.value
+
+
+# ------------------------------------------------------------ autotuning --
+
+KERNEL_PROGRAM, KERNEL_NRM2, KERNEL_NRM2_PLAIN, KERNEL_DOT_PLAIN = 0, 1, 2, 3
+lib.salt_autotune.restype = ctypes.c_int32
+lib.salt_autotune.argtypes = [ctypes.c_int32, ctypes.POINTER(Insn), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                              ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                              ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(LaunchCfg),
+                              ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+for _name in ("salt_tune_save", "salt_tune_load"):
+    getattr(lib, _name).restype = ctypes.c_int32
+    getattr(lib, _name).argtypes = [ctypes.c_char_p]
+EXPORTS += ["salt_autotune", "salt_tune_save", "salt_tune_load"]
+
+
+def salt_autotune(kernel: int, prog, vecs, scalars=(), red_out=None, reps: int = 3, stream=None):
+    """Tunes the launch shape of one call (see include/salt.h); returns
+    (configuration dict, milliseconds per call)."""
+    _contig(vecs)
+    dt = _common_dtype(vecs)
+    n = _n_of(vecs)
+    arr, m = program(prog) if prog is not None else (None, 0)
+    ptrs = (ctypes.c_void_p * max(len(vecs), 1))(*[_ptr(v) for v in vecs])
+    sc = (ctypes.c_double * max(len(scalars), 1))(*[float(s) for s in scalars])
+    cfg = LaunchCfg()
+    ms = ctypes.c_double()
+    _check(lib.salt_autotune(kernel, arr, m, dt, int(n), ptrs, len(vecs), sc, len(scalars), _ptr(red_out),
+                             int(reps), ctypes.byref(cfg), ctypes.byref(ms), _stream_ptr(stream)))
+    return ({"unroll": cfg.unroll, "vec_bytes": cfg.vec_bytes, "block": cfg.block,
+             "blocks_per_sm": cfg.blocks_per_sm}, ms.value)
+
+
+def salt_tune_save(path: str) -> None:
+    _check(lib.salt_tune_save(path.encode()))
+
+
+def salt_tune_load(path: str) -> None:
+    _check(lib.salt_tune_load(path.encode()))

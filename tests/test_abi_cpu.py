@@ -137,3 +137,34 @@ def test_tune_table(saltlib):
             saltlib.salt_tune_set(D, saltlib.F32, 1 << 20, *bad)
     saltlib.salt_tune_clear()
     assert saltlib.salt_tune_get(D, saltlib.F32, 1 << 20) == default
+
+
+def test_tune_save_load_roundtrip(saltlib, tmp_path):
+    s = saltlib
+    s.salt_tune_clear()
+    s.salt_tune_set(D, s.F64, 1 << 24, 4, 32, 128, 2)
+    s.salt_tune_set(CG, s.F32, 1000, 1, 16, 64, 8)
+    path = str(tmp_path / "tune.txt")
+    s.salt_tune_save(path)
+    s.salt_tune_clear()
+    assert s.salt_tune_get(D, s.F64, 1 << 24)["block"] == 256
+    s.salt_tune_load(path)
+    assert s.salt_tune_get(D, s.F64, 1 << 24) == {"unroll": 4, "vec_bytes": 32, "block": 128, "blocks_per_sm": 2}
+    assert s.salt_tune_get(CG, s.F32, 1000) == {"unroll": 1, "vec_bytes": 16, "block": 64, "blocks_per_sm": 8}
+    bad = tmp_path / "bad.txt"
+    bad.write_text("0 0 20 3 16 128 2\n")
+    with pytest.raises(s.SaltError):
+        s.salt_tune_load(str(bad))
+    with pytest.raises(s.SaltError):
+        s.salt_tune_load(str(tmp_path / "missing.txt"))
+    s.salt_tune_clear()
+
+
+def test_autotune_argument_errors(saltlib):
+    import ctypes
+    s = saltlib
+    p = (ctypes.c_void_p * 1)(BASE)
+    assert s.lib.salt_autotune(9, None, 0, 0, 100, p, 1, None, 0, BASE, 3, None, None, None) == s.ERR_ARG
+    assert s.lib.salt_autotune(s.KERNEL_NRM2_PLAIN, None, 0, 1, 100, p, 1, None, 0, BASE, 3, None, None,
+                               None) == s.ERR_DTYPE
+    assert s.lib.salt_autotune(s.KERNEL_NRM2, None, 0, 0, 100, p, 1, None, 0, BASE, 0, None, None, None) == s.ERR_ARG
