@@ -216,8 +216,7 @@ def run_reference(args, rank: int, world: int):
             "warmup": args.warmup, "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"BLAS-1 sweep top size, sampled at n=2^{args.cpu_log2} on the host CPU",
-                       "n": n_sample},
+            "config": workload_config(args.log2n, world),
             "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -225,6 +224,27 @@ def run_reference(args, rank: int, world: int):
 
 
 # ---------------------------------------------------------------- GPU arm --
+def workload_config(log2n: int, world: int) -> dict:
+    return {"workload": "BLAS-1 sweep top size: e=alpha*a+beta*b-c*d, y=alpha*x+beta*y, dot, nrm2; "
+                        "FP32 and FP64; n=2^%d" % log2n,
+            "n": 1 << log2n, "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush needed)"}
+
+
+def max_over_ranks(torch, dist, ms: float, world: int, device: str) -> float:
+    """The slowest rank's time: every rank is an independent replica of the
+    step, so the whole job ends when the slowest one does."""
+    if world <= 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(step_bytes: int, steps: int, world: int, max_ms: float) -> float:
+    """Algorithmic bytes all ranks moved / the max-over-ranks time (weak scaling)."""
+    return world * step_bytes * steps / (max_ms * 1e-3) / 1e9
+
+
 def traffic_for(kernel: str, n: int):
     """DRAM bytes per launch from a committed ncu capture, if it was taken on
     the current kernel sources (scaled from the captured size to n)."""
@@ -253,6 +273,9 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--batched-items", type=int, default=4096)
+    ap.add_argument("--batched-fixed", action="store_true", help="skip the batch autotuner (profiling runs)")
+    ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling runs)")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -271,6 +294,12 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     from paper_1109_1264_gb300 import salt
+
+    if args.only_batched:
+        if rank == 0:
+            print(json.dumps({"batched": batched_measure(torch, salt, nitems=args.batched_items,
+                                                         fixed=args.batched_fixed)}), flush=True)
+        return
 
     n = 1 << args.log2n
     loads = {dt: Workload(torch, salt, dt, n, seed=rank) for dt in DTYPES}
@@ -311,17 +340,14 @@ def main():
     launches = salt.salt_launch_count() - launches0
     clk = clocks.stop()
     total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = tt.item()
+    total_ms = max_over_ranks(torch, dist, total_ms, world, "cuda")
 
     per_kernel = {}
     for i, (dt, name, _) in enumerate(steps):
         per_kernel[(dt, name)] = sum(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)) / args.steps
 
     ms_per_step = total_ms / args.steps
-    value = world * step_bytes * args.steps / (total_ms * 1e-3) / 1e9
+    value = whole_job_gbs(step_bytes, args.steps, world, total_ms)
     hbm_peak, peak_kind, sm_max = load_peaks()
     alu_peak = f64_alu_peak_gops(sm_max)
 
@@ -356,10 +382,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic: counter-based uniform[-1,1) (SplitMix64) operands, alpha=1.5, beta=-0.25",
-        "config": {"workload": "BLAS-1 sweep top size: e=alpha*a+beta*b-c*d, y=alpha*x+beta*y, dot, nrm2; "
-                               "FP32 and FP64; n=2^%d" % args.log2n,
-                   "n": n, "parallelism": f"replicas x{world}", "l2": "inputs larger than L2 (no flush needed)",
-                   "tuned": tuned},
+        "config": dict(workload_config(args.log2n, world), tuned=tuned),
         "frac_of_measured_hbm": round(value / world / hbm_peak, 4),
         "roofline": roof,
         "per_kernel_ms": {f"{op}_{dt}": round(ms, 4) for (dt, op), ms in per_kernel.items()},
@@ -375,7 +398,7 @@ def main():
     steps = None
     torch.cuda.empty_cache()
     if not args.no_batched:
-        result["batched"] = batched_measure(torch, salt)
+        result["batched"] = batched_measure(torch, salt, nitems=args.batched_items, fixed=args.batched_fixed)
     if not args.no_served:
         torch.cuda.empty_cache()
         result["served"] = served_measure(salt)
@@ -389,7 +412,7 @@ def main():
         dist.destroy_process_group()
 
 
-def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096) -> dict:
+def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096, fixed: bool = False) -> dict:
     """4096 CG-style updates (r <- r - alpha q; rho = r.r; p <- r + beta p),
     lengths log-uniform in [64, 2^20], in one persistent graph-replayed launch
     (autotuned) versus 4096 plain per-call launches on one stream."""
@@ -414,7 +437,11 @@ def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096) -> dict:
             b.add(PROG_CG, [buf[offs[i]:offs[i] + n] for buf in bufs], list(ab[i]))
         red = torch.zeros(nitems, dtype=torch.float64, device="cuda")
         nbytes = b.info()["bytes"]
-        best_ms = b.autotune(red, reps=3)
+        if fixed:  # the shape the autotuner picks on GB300 (for profiling runs)
+            b.set_config(4, 128, 0, 32768 if dt == "f32" else 131072)
+            best_ms = float("nan")
+        else:
+            best_ms = b.autotune(red, reps=3)
         cfg = b.get_config()
 
         def timed(fn, k):

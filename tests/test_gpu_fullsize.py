@@ -1,0 +1,102 @@
+"""Full-size parity (GPU): the BLAS-1 sweep's top size, n = 2^28 (+7 for the
+elementwise ops, so the tail runs too), in the launch configuration the
+benchmark times (autotuned first, as bench.py does).
+
+Elementwise outputs are checked bit for bit on a sample of elements that the
+oracle recomputes one by one from the counter-based inputs (its value at
+index i depends on element i only).  Reductions use integer-valued data whose
+sums are exact at this size, so the GPU result must equal the closed form."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1109_1264_gb300 import inputs
+from paper_1109_1264_gb300 import programs as P
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+N = (1 << 28) + 7
+ALPHA, BETA = 1.5, -0.25
+
+
+def gather_inputs(key, idx, dt):
+    h = inputs.splitmix64(key, idx.astype(np.uint64))
+    if dt == np.float64:
+        return 2.0 * ((h >> np.uint64(11)).astype(np.float64) * 2.0 ** -53) - 1.0
+    return (2.0 * ((h >> np.uint64(40)).astype(np.float64) * 2.0 ** -24) - 1.0).astype(np.float32)
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_elementwise_full_size_sampled(saltlib, cuda_dev, dt):
+    s = saltlib
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    keys = [101, 102, 103, 104, 105]
+    a, b, c, d, y = (torch.empty(N, dtype=tdt, device=cuda_dev) for _ in range(5))
+    out = torch.empty(N, dtype=tdt, device=cuda_dev)
+    for t, k in zip((a, b, c, d, y), keys):
+        s.salt_fill_uniform(t, key=k)
+    s.salt_tune_clear()
+    try:
+        s.salt_autotune(s.KERNEL_PROGRAM, P.PROG_E, [a, b, c, d, out], [ALPHA, BETA], reps=1)
+        s.salt_autotune(s.KERNEL_PROGRAM, P.PROG_AXPBY, [a, y], [ALPHA, BETA], reps=1)
+        # the autotuner ran axpby in place: start y afresh
+        s.salt_fill_uniform(y, key=keys[4])
+        s.salt_eval(P.PROG_E, [a, b, c, d, out], [ALPHA, BETA])
+        s.salt_axpby(ALPHA, a, BETA, y)
+        torch.cuda.synchronize()
+    finally:
+        s.salt_tune_clear()
+    rng = np.random.default_rng(3)
+    idx = np.unique(np.concatenate([np.arange(4096), np.arange(N - 4096, N), rng.integers(0, N, 200_000)]))
+    ins = [gather_inputs(k, idx, dt) for k in keys]
+    want_e = [ins[0].copy(), ins[1].copy(), ins[2].copy(), ins[3].copy(), np.zeros(len(idx), dt)]
+    oracle.eval_program(oracle.PROG_E, want_e, [ALPHA, BETA])
+    want_y = [ins[0].copy(), ins[4].copy()]
+    oracle.eval_program(oracle.PROG_AXPBY, want_y, [ALPHA, BETA])
+    tidx = torch.from_numpy(idx.astype(np.int64)).to(cuda_dev)
+    got_e = out[tidx].cpu().numpy()
+    got_y = y[tidx].cpu().numpy()
+    iu = np.uint32 if dt == np.float32 else np.uint64
+    assert np.array_equal(got_e.view(iu), want_e[4].view(iu))
+    assert np.array_equal(got_y.view(iu), want_y[1].view(iu))
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_reductions_full_size_closed_form(saltlib, cuda_dev, dt):
+    """x_i = (i mod 1024) - 512, y_i = ((7 i) mod 512) - 256, n = 2^28: every
+    product and partial sum is an integer below 2^53, so the compensated FP32
+    and the FP64 paths must return the exact integer, and the norm the
+    correctly rounded square root of the exact sum of squares."""
+    s = saltlib
+    n = 1 << 28
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    i = torch.arange(n, device=cuda_dev, dtype=torch.int64)
+    x = ((i % 1024) - 512).to(tdt)
+    yv = (((7 * i) % 512) - 256).to(tdt)
+    del i
+    outv = torch.zeros(3, dtype=torch.float64, device=cuda_dev)
+    s.salt_tune_clear()
+    try:
+        s.salt_autotune(s.KERNEL_PROGRAM, P.PROG_DOT, [x, yv], red_out=outv[0:1], reps=1)
+        s.salt_autotune(s.KERNEL_NRM2, None, [x], red_out=outv[1:2], reps=1)
+        s.salt_dot(x, yv, outv[0:1])
+        s.salt_nrm2(x, outv[1:2])
+        s.salt_dot(x, x, outv[2:3])
+        torch.cuda.synchronize()
+    finally:
+        s.salt_tune_clear()
+    got_dot, got_nrm, got_sq = outv.cpu().tolist()
+    # exact closed forms from one period (the data repeat every 1024 / 512 elements)
+    j = np.arange(1024, dtype=np.int64)
+    xs = j - 512
+    per_x2 = int(np.sum(xs * xs))
+    sumsq = per_x2 * (n // 1024)
+    # dot: period lcm(1024, 512 * ...) -- compute on one period of 1024 of i, since 7 i mod 512 has period 512
+    ys = ((7 * j) % 512) - 256
+    dot = int(np.sum(xs * ys)) * (n // 1024)
+    assert got_dot == dot, (got_dot, dot)
+    assert got_sq == sumsq, (got_sq, sumsq)
+    assert got_nrm == math.sqrt(sumsq), (got_nrm, math.sqrt(sumsq))
