@@ -276,6 +276,7 @@ def main():
     ap.add_argument("--batched-items", type=int, default=4096)
     ap.add_argument("--batched-fixed", action="store_true", help="skip the batch autotuner (profiling runs)")
     ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling runs)")
+    ap.add_argument("--sweep", action="store_true", help="the paper's four-op size sweep instead of the step")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -294,6 +295,11 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     from paper_1109_1264_gb300 import salt
+
+    if args.sweep:
+        if rank == 0:
+            print(json.dumps(sweep_measure(torch, salt)), flush=True)
+        return
 
     if args.only_batched:
         if rank == 0:
@@ -466,9 +472,73 @@ def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096, fixed: bool
         b.close()
         del bufs
         torch.cuda.empty_cache()
-    out["workload"] = ("4096 CG updates per launch, n log-uniform in [64, 2^20] (sum %d), one graph-replayed "
-                       "persistent launch vs 4096 plain salt_eval calls" % int(lens.sum()))
+    out["workload"] = ("%d CG updates per launch, n log-uniform in [64, 2^20] (sum %d), one graph-replayed "
+                       "persistent launch vs %d plain salt_eval calls" % (nitems, int(lens.sum()), nitems))
     return out
+
+
+def sweep_measure(torch, salt, reps: int = 15, max_log2: int = 28) -> dict:
+    """The paper's benchmark set (Section 5) as a size sweep on the GPU: xDOT,
+    xSCAL (x = a x), xAXPY (y = a x + y) and the out-of-place scaling y = a x
+    that BLAS must express as xCOPY + xSCAL -- fused (one pass, 2 x es bytes
+    per element) versus the two calls (copy, then in-place scale: 4 x es).
+    L2 is flushed (a 256 MiB write) before every timed call; median of reps.
+    torch's own kernels (torch.dot = cuBLAS dot, mul_, add_, copy_+mul_) are
+    timed the same way as context."""
+    import numpy as np
+
+    from paper_1109_1264_gb300.programs import PROG_DOT, PROG_SCALE
+    scal = [("SCAL", 0), ("VEC", 0), ("SMUL", 0), ("STORE", 0)]
+    axpy = [("SCAL", 0), ("VEC", 0), ("SMUL", 0), ("VEC", 1), ("ADD", 0), ("STORE", 1)]
+    copy = [("VEC", 0), ("STORE", 1)]
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sizes = sorted({1 << k for k in range(10, max_log2 + 1)} | {(1 << k) + 7 for k in range(10, max_log2 + 1, 2)})
+    out = {}
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    for dt, tdt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+        rows = []
+        xb = torch.empty(1 << max_log2, dtype=tdt, device="cuda")
+        yb = torch.empty(1 << max_log2, dtype=tdt, device="cuda")
+        salt.salt_fill_uniform(xb, 11)
+        salt.salt_fill_uniform(yb, 12)
+        red = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for n in sizes:
+            if n > (1 << max_log2):
+                continue
+            x, y = xb[:n], yb[:n]
+            r = {"n": n}
+            ms = timed(lambda: salt.salt_eval(PROG_DOT, [x, y], red_out=red))
+            r["dot"] = round(2 * es * n / (ms * 1e-3) / 1e9, 1)
+            ms = timed(lambda: salt.salt_eval(scal, [x], [0.999]))
+            r["scal"] = round(2 * es * n / (ms * 1e-3) / 1e9, 1)
+            ms = timed(lambda: salt.salt_eval(axpy, [x, y], [1e-3]))
+            r["axpy"] = round(3 * es * n / (ms * 1e-3) / 1e9, 1)
+            ms_f = timed(lambda: salt.salt_eval(PROG_SCALE, [x, y], [1.5]))
+            ms_2 = timed(lambda: (salt.salt_eval(copy, [x, y]), salt.salt_eval(scal, [y], [1.5])))
+            # GB/s of the operation itself (2 x es bytes per element) under both schedules
+            r["copy_scal_fused"] = round(2 * es * n / (ms_f * 1e-3) / 1e9, 1)
+            r["copy_scal_two_calls"] = round(2 * es * n / (ms_2 * 1e-3) / 1e9, 1)
+            r["torch_dot"] = round(2 * es * n / (timed(lambda: torch.dot(x, y)) * 1e-3) / 1e9, 1)
+            r["torch_axpy"] = round(3 * es * n / (timed(lambda: y.add_(x, alpha=1e-3)) * 1e-3) / 1e9, 1)
+            r["torch_copy_scal"] = round(2 * es * n / (timed(lambda: y.copy_(x).mul_(1.5)) * 1e-3) / 1e9, 1)
+            rows.append(r)
+        out[dt] = rows
+        del xb, yb
+    return {"sweep": out, "note": "GB/s of algorithmic bytes; L2 flushed before each timed call; median of %d" % reps}
 
 
 def served_measure(salt, count: int = 3000, seed: int = 0) -> dict:
@@ -501,7 +571,17 @@ def served_measure(salt, count: int = 3000, seed: int = 0) -> dict:
         stats = srv.stats()
     finally:
         srv.stop()
+    # The same stream without batching: one request per step (per-request fill
+    # and compute launches), all requests arriving at once.
+    srv1 = salt.Server(max_batch=1)
+    try:
+        srv1.replay(zeros[:200], shapes[:200], is64[:200].astype(np.int32), lens[:200], seed + 99)
+        _, _, wall1 = srv1.replay(zeros, shapes, is64.astype(np.int32), lens, seed)
+    finally:
+        srv1.stop()
+    unbatched_gbs = total_bytes / (wall1 * 1e-6) / 1e9
     return {"saturation_rps": round(sat_rps, 1), "saturation_gbs": round(sat_gbs, 1),
+            "unbatched_saturation_gbs": round(unbatched_gbs, 1), "batched_vs_unbatched": round(sat_gbs / unbatched_gbs, 2),
             "requests_per_point": count, "bytes_per_point": total_bytes,
             "points": points, "steps_total": stats["steps"],
             "workload": "5 shapes uniform, n log-uniform [2^8, 2^24], 70% FP32 / 30% FP64, 8 GiB resident budget, "
