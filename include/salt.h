@@ -241,6 +241,26 @@ salt_status salt_fill_uniform(int32_t dtype, int64_t n, uint64_t key, int64_t of
 salt_status salt_dot_noalloc(int32_t dtype, int64_t n, const void* x, const void* y, double* out,
                              void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Run-time compilation of programs without a compile-time instantiation.
+ * The paper's expression templates generate each expression's loop at
+ * compile time (Section 2); with SALT_JIT_ON, salt_eval does the same at run
+ * time for any program that has no compiled instantiation: the program is
+ * written out as the template arguments of the same fused kernel, compiled
+ * by NVRTC for the current GPU on the first call per (program, dtype, launch
+ * shape) -- tens to hundreds of milliseconds, so make that call before any
+ * stream capture -- and cached for the process.  Results are bit-identical to
+ * the interpreter's.  SALT_JIT_OFF (the default): such programs run on the
+ * interpreter kernel.  salt_set_jit returns SALT_ERR_ARG for another mode;
+ * salt_eval returns SALT_ERR_CUDA with NVRTC's log if compilation fails or
+ * NVRTC cannot be loaded. */
+#define SALT_JIT_OFF 0
+#define SALT_JIT_ON 1
+salt_status salt_set_jit(int32_t mode);
+/* Current mode, kernels compiled so far and their total compile time (ms);
+ * any pointer may be NULL. */
+salt_status salt_jit_stats(int32_t* mode, int64_t* kernels, double* compile_ms);
+
 /* Free every workspace the library holds (call with no library work in
  * flight).  Returns SALT_OK or SALT_ERR_CUDA. */
 salt_status salt_release_workspaces(void);

@@ -23,7 +23,9 @@ LIB = os.path.join(HERE, "libsalt.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-fmad=false", "-lineinfo", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
-              "-I", CSRC, "-I", INCLUDE]
+              "-I", CSRC, "-I", INCLUDE, "-I", BUILD]
+# Device headers that the run-time compiler (csrc/jit.cu) needs, embedded as strings.
+JIT_HEADERS = ["prog.cuh", "common.cuh", "fused.cuh"]
 
 
 def nvcc() -> str:
@@ -49,10 +51,29 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+def write_jit_sources() -> None:
+    """_build/jit_sources.inc: the fused-kernel headers as C++ raw strings."""
+    lines = ["// Generated by build.py from csrc/: do not edit.",
+             f"static const int kJitHeaderCount = {len(JIT_HEADERS)};",
+             "static const char* const kJitHeaderNames[] = {" + ", ".join(f'"{h}"' for h in JIT_HEADERS) + "};",
+             "static const char* const kJitHeaderSources[] = {"]
+    for h in JIT_HEADERS:
+        text = open(os.path.join(CSRC, h)).read()
+        assert ')SALTJIT"' not in text
+        lines.append('R"SALTJIT(' + text + ')SALTJIT",')
+    lines.append("};")
+    path = os.path.join(BUILD, "jit_sources.inc")
+    new = "\n".join(lines) + "\n"
+    if not os.path.exists(path) or open(path).read() != new:
+        with open(path, "w") as f:
+            f.write(new)
+
+
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    write_jit_sources()
     cc = nvcc()
     srcs = _sources()
 
@@ -72,7 +93,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".tmp"
-    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -225,6 +225,35 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, cons
     return SALT_OK;
   }
 
+  if (jit_mode() == SALT_JIT_ON) {
+    // The fused kernel instantiated for this program at run time.  Launch
+    // shape: the tuned defaults of the compiled shapes (32-byte vectors when
+    // every operand allows, unroll 4 for F32 and 2 for F64, 256 threads).
+    const int unroll = sizeof(T) == 4 ? 4 : 2;
+    const int vb = all32 ? 32 : 16;
+    const void* k = nullptr;
+    salt_status st = jit_kernel(c, sizeof(T) == 4, unroll, vb, &k);
+    if (st != SALT_OK) return st;
+    const int block = 256;
+    int bps = occupancy_blocks(k, block, 0);
+    if (bps > kMaxBlocksPerSM) bps = kMaxBlocksPerSM;
+    const int64_t vec = vb / (int64_t)sizeof(T);
+    const int grid = grid_for(a.n, (int64_t)unroll * block * vec, info.sms, bps);
+    MapParams<T> p;
+    memset(&p, 0, sizeof p);
+    for (int j = 0; j < c.nvec; ++j) p.v[j] = (T*)a.vecs[c.vec_user[j]];
+    for (int j = 0; j < c.nscal; ++j) p.sc[j] = (T)a.scalars[c.scal_user[j]];
+    p.n = a.n;
+    p.red_out = a.red_out;
+    p.partials = ws.partials;
+    p.ticket = ws.ticket;
+    void* args[] = {&p};
+    cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(block), args, 0, a.stream);
+    g_launches.fetch_add(1);
+    if (e != cudaSuccess) return cuda_error(e, "JIT kernel launch");
+    return SALT_OK;
+  }
+
   // Generic interpreter.
   InterpParams<T> p;
   memset(&p, 0, sizeof p);

@@ -3,8 +3,18 @@
 // Section 3), reduction accumulators and deterministic block combination.
 #pragma once
 
+#ifdef __CUDACC_RTC__
+// Compiled at run time by NVRTC (csrc/jit.cu): no system headers there.
+typedef long long int64_t;
+typedef unsigned long long uint64_t;
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef unsigned char uint8_t;
+typedef decltype(sizeof(0)) size_t;
+#else
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 #include "prog.cuh"
 

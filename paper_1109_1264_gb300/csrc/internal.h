@@ -40,4 +40,10 @@ salt_status current_device(int* dev, int* sms);
 // Number of kernel launches issued by the library (all threads).
 void count_launch();
 
+// Run-time compiled fused kernels (csrc/jit.cu): the current mode
+// (SALT_JIT_OFF / SALT_JIT_ON) and the kernel for a canonical program
+// (compiled and cached on first use).
+int32_t jit_mode();
+salt_status jit_kernel(const Canonical& c, int is_f32, int unroll, int vec_bytes, const void** kernel_out);
+
 }  // namespace salt

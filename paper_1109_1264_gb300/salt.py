@@ -489,3 +489,24 @@ def salt_tune_save(path: str) -> None:
 
 def salt_tune_load(path: str) -> None:
     _check(lib.salt_tune_load(path.encode()))
+
+
+# --------------------------------------------------------- run-time compile --
+
+JIT_OFF, JIT_ON = 0, 1
+lib.salt_set_jit.restype = ctypes.c_int32
+lib.salt_set_jit.argtypes = [ctypes.c_int32]
+lib.salt_jit_stats.restype = ctypes.c_int32
+lib.salt_jit_stats.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                               ctypes.POINTER(ctypes.c_double)]
+EXPORTS += ["salt_set_jit", "salt_jit_stats"]
+
+
+def salt_set_jit(mode: int) -> None:
+    _check(lib.salt_set_jit(int(mode)))
+
+
+def salt_jit_stats() -> dict:
+    m, k, t = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double()
+    _check(lib.salt_jit_stats(ctypes.byref(m), ctypes.byref(k), ctypes.byref(t)))
+    return {"mode": m.value, "kernels": k.value, "compile_ms": t.value}

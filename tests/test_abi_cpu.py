@@ -168,3 +168,13 @@ def test_autotune_argument_errors(saltlib):
     assert s.lib.salt_autotune(s.KERNEL_NRM2_PLAIN, None, 0, 1, 100, p, 1, None, 0, BASE, 3, None, None,
                                None) == s.ERR_DTYPE
     assert s.lib.salt_autotune(s.KERNEL_NRM2, None, 0, 0, 100, p, 1, None, 0, BASE, 0, None, None, None) == s.ERR_ARG
+
+
+def test_jit_mode_switch(saltlib):
+    s = saltlib
+    assert s.salt_jit_stats()["mode"] == s.JIT_OFF
+    with pytest.raises(s.SaltError):
+        s.salt_set_jit(5)
+    s.salt_set_jit(s.JIT_ON)
+    assert s.salt_jit_stats()["mode"] == s.JIT_ON
+    s.salt_set_jit(s.JIT_OFF)

@@ -1,0 +1,90 @@
+"""Run-time compiled fused kernels (GPU): programs without a compile-time
+instantiation, compiled by NVRTC, must match the oracle bit for bit, be
+cached, and beat the interpreter."""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+import oracle_pins
+from test_gpu_parity import assert_bits_equal, check_reductions, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture
+def jit(saltlib, cuda_dev):
+    saltlib.salt_set_jit(saltlib.JIT_ON)
+    yield saltlib
+    saltlib.salt_set_jit(saltlib.JIT_OFF)
+
+
+def test_jit_random_programs_match_oracle(jit):
+    s = jit
+    rng = random.Random(23)
+    nrng = np.random.default_rng(23)
+    before = s.salt_jit_stats()["kernels"]
+    ran = 0
+    for t in range(24):
+        dt = np.float64 if t % 2 == 0 else np.float32
+        nvecs, nscal = rng.randint(1, 6), rng.randint(0, 3)
+        while True:
+            prog = oracle_pins.random_program(rng, nvecs, nscal)
+            if len(prog) <= s.MAX_PROG and sum(o in ("DOT", "SUMSQ") for o, _ in prog) <= s.MAX_REDS:
+                break
+        _, compiled = s.salt_check_program(prog, nvecs, nscal)
+        ran += not compiled
+        n = rng.choice([1, 17, 1023, 70001, 300007])
+        vecs = [nrng.uniform(-1, 1, n).astype(dt) for _ in range(nvecs)]
+        scalars = list(nrng.uniform(-2, 2, nscal))
+        got, red = run_gpu(s, prog, vecs, scalars, dt)
+        want, _ = run_oracle(prog, vecs, scalars)
+        for k, (g, w) in enumerate(zip(got, want)):
+            assert_bits_equal(g, w, f"jit prog {prog} n={n} operand {k}")
+        check_reductions(prog, vecs, scalars, red, dt, f"jit prog {prog}")
+    assert ran > 10 and s.salt_jit_stats()["kernels"] > before
+
+
+def test_jit_cache_and_speed_over_interpreter(jit, cuda_dev):
+    """A 6-operand expression that no compiled shape covers:
+    f = (a - b) o (c + d) - 2.5 e, plus sum f^2."""
+    s = jit
+    prog = [("VEC", 0), ("VEC", 1), ("SUB", 0), ("VEC", 2), ("VEC", 3), ("ADD", 0), ("MUL", 0),
+            ("SCAL", 0), ("VEC", 4), ("SMUL", 0), ("SUB", 0), ("STORE", 5), ("VEC", 5), ("SUMSQ", 0)]
+    assert s.salt_check_program(prog, 6, 1) == (1, False)
+    n = 1 << 25
+    x = [torch.empty(n, dtype=torch.float32, device=cuda_dev) for _ in range(6)]
+    for k, t in enumerate(x):
+        s.salt_fill_uniform(t, 500 + k)
+    red = torch.zeros(1, dtype=torch.float64, device=cuda_dev)
+    stream = torch.cuda.current_stream()
+
+    def timed():
+        s.salt_eval(prog, x, [2.5], red_out=red)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            s.salt_eval(prog, x, [2.5], red_out=red)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 5
+
+    k0 = s.salt_jit_stats()["kernels"]
+    t_jit = timed()
+    k1 = s.salt_jit_stats()["kernels"]
+    assert k1 - k0 <= 1  # compiled at most once, then cached
+    out_jit = x[5].clone()
+    r_jit = red.item()
+    s.salt_set_jit(s.JIT_OFF)
+    t_int = timed()
+    assert s.salt_jit_stats()["kernels"] == k1
+    assert_bits_equal(x[5].cpu().numpy(), out_jit.cpu().numpy(), "jit vs interpreter")
+    ref = exact.exact_sumsq(out_jit.cpu().numpy())
+    assert abs(r_jit - ref) <= 1e-6 * ref and abs(red.item() - ref) <= 1e-6 * ref
+    gbs = lambda ms: 6 * 4 * n / (ms * 1e-3) / 1e9  # algorithmic: 5 reads + 1 write of 4 B
+    print(f"jit {t_jit:.3f} ms ({gbs(t_jit):.0f} GB/s), interpreter {t_int:.3f} ms ({gbs(t_int):.0f} GB/s)")
+    assert t_jit < t_int
