@@ -20,9 +20,14 @@
  * once.
  *
  * Conventions for every entry point below:
- *  - Vectors are dense, contiguous, caller-owned DEVICE memory of the
- *    call's dtype, each 16-byte aligned (cudaMalloc / torch allocations are).
- *    The library never frees or retains them.
+ *  - Vectors are dense, contiguous (salt_eval_strided: strided),
+ *    caller-owned DEVICE memory of the call's dtype, aligned at least to the
+ *    element size.  When every operand of a call is 16-byte aligned and
+ *    contiguous (cudaMalloc / torch allocations are) the kernels use 128- or
+ *    256-bit accesses; otherwise element accesses (the paper's scalar
+ *    single_op path, Section 4.2, for the whole range).  Batches and the
+ *    plain-mode reductions need 16-byte alignment.  The library never frees
+ *    or retains the vectors.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *    asynchronous on that stream; results are valid once the caller has
  *    synchronised with it.
@@ -59,7 +64,7 @@ typedef enum {
   SALT_ERR_ARG = 1,      /* bad size, count, NULL pointer, bad flag          */
   SALT_ERR_PROGRAM = 2,  /* malformed or ill-typed program                    */
   SALT_ERR_DTYPE = 3,    /* unknown dtype, or operands of different dtypes    */
-  SALT_ERR_ALIGN = 4,    /* a vector pointer is not 16-byte aligned           */
+  SALT_ERR_ALIGN = 4,    /* a pointer is not aligned as the call requires      */
   SALT_ERR_ALIAS = 5,    /* an output overlaps another operand's memory       */
   SALT_ERR_BUDGET = 6,   /* request larger than a budget or capacity          */
   SALT_ERR_TIMEOUT = 7,  /* a bounded host wait ran out                       */
@@ -163,6 +168,16 @@ salt_status salt_check_program(const salt_insn* prog, int32_t nprog, int32_t nve
 salt_status salt_eval(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
                       void* const* vecs, int32_t nvecs, const double* scalars, int32_t nscal,
                       double* red_out, void* stream);
+
+/* salt_eval with strided operands (BLAS incx semantics, positive strides):
+ * element i of operand k is vecs[k][i * strides[k]]; strides is a host array
+ * of nvecs element strides, each >= 1 for the operands the program names
+ * (SALT_ERR_ARG otherwise).  Elements between the strided positions are never
+ * read or written.  Aliasing is judged on the whole address range an operand
+ * spans, ((n - 1) * stride + 1) elements.  Otherwise as salt_eval. */
+salt_status salt_eval_strided(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                              void* const* vecs, const int64_t* strides, int32_t nvecs, const double* scalars,
+                              int32_t nscal, double* red_out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * salt_axpby -- y <- alpha*x + beta*y (Section 5's xAXPY generalised; xSCAL

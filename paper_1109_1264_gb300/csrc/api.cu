@@ -45,6 +45,7 @@ Registry& registry() {
     register_f64_vb16(r);
     register_f64_vb32(r);
     register_misc(r);
+    register_elementwise(r);
   });
   return r;
 }
@@ -193,14 +194,56 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, cons
   Registry& reg = registry();
   const int shape = find_shape(c);
   const int dt = sizeof(T) == 4 ? DT_F32 : DT_F64;
-  // 32-byte vectors need 32-byte aligned operands.
-  bool all32 = true;
-  for (int k = 0; k < c.nvec; ++k) all32 = all32 && aligned(a.vecs[c.vec_user[k]], 32);
+  // 32-byte vectors need 32-byte aligned operands; operands that are not
+  // 16-byte aligned or not contiguous take the element-access kernels.
+  bool all32 = true, elementwise = false;
+  for (int k = 0; k < c.nvec; ++k) {
+    all32 = all32 && aligned(a.vecs[c.vec_user[k]], 32);
+    elementwise = elementwise || !aligned(a.vecs[c.vec_user[k]], 16) ||
+                  (a.strides && a.strides[c.vec_user[k]] != 1);
+  }
 
   Workspace ws;
   if (c.nred > 0) {
     salt_status st = workspace(dev, info, a.stream, &ws);
     if (st != SALT_OK) return st;
+  }
+
+  if (elementwise && (shape >= 0 || jit_mode() == SALT_JIT_ON)) {
+    MapParams<T> p;
+    memset(&p, 0, sizeof p);
+    for (int k = 0; k < c.nvec; ++k) {
+      p.v[k] = (T*)a.vecs[c.vec_user[k]];
+      p.stride[k] = a.strides ? a.strides[c.vec_user[k]] : 1;
+    }
+    for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
+    p.n = a.n;
+    p.red_out = a.red_out;
+    p.partials = ws.partials;
+    p.ticket = ws.ticket;
+    const void* kern = nullptr;
+    const KernelEntry* ke = nullptr;
+    if (shape >= 0) {
+      ke = &reg.strided[shape][dt];
+      kern = ke->kernel;
+    } else {
+      salt_status st = jit_kernel(c, sizeof(T) == 4, kElemUnroll, 0, &kern);
+      if (st != SALT_OK) return st;
+    }
+    const int block = 256;
+    int bps = occupancy_blocks(kern, block, 0);
+    if (bps > kMaxBlocksPerSM) bps = kMaxBlocksPerSM;
+    const int grid = grid_for(a.n, (int64_t)kElemUnroll * block, info.sms, bps);
+    cudaError_t e;
+    if (ke) {
+      e = ke->launch(&p, grid, block, 0, a.stream);
+    } else {
+      void* args[] = {&p};
+      e = cudaLaunchKernel(kern, dim3(grid), dim3(block), args, 0, a.stream);
+    }
+    g_launches.fetch_add(1);
+    if (e != cudaSuccess) return cuda_error(e, "element-access kernel launch");
+    return SALT_OK;
   }
 
   if (shape >= 0) {
@@ -264,6 +307,8 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, cons
   p.nred = c.nred;
   p.load_mask = c.load_mask;
   p.store_mask = c.store_mask;
+  p.elementwise = elementwise ? 1 : 0;
+  for (int k = 0; k < c.nvec; ++k) p.stride[k] = a.strides ? a.strides[c.vec_user[k]] : 1;
   for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]];
   for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
   p.n = a.n;
@@ -308,22 +353,32 @@ salt_status validate_eval(const EvalArgs& a, Analysis* an_out) {
       snprintf(b, sizeof b, "vector operand %d is NULL", k);
       return set_error(SALT_ERR_ARG, b);
     }
-    if (!aligned(a.vecs[k], 16)) {
+    if (!aligned(a.vecs[k], es)) {
       char b[96];
-      snprintf(b, sizeof b, "vector operand %d is not 16-byte aligned", k);
+      snprintf(b, sizeof b, "vector operand %d is not aligned to its element size", k);
       return set_error(SALT_ERR_ALIGN, b);
+    }
+    if (a.strides && a.strides[k] < 1) {
+      char b[96];
+      snprintf(b, sizeof b, "stride of vector operand %d must be >= 1", k);
+      return set_error(SALT_ERR_ARG, b);
     }
   }
   // An output may share memory with an input only through the same operand
-  // index (exact in-place update).
-  const uintptr_t bytes = (uintptr_t)a.n * es;
+  // index (exact in-place update).  Strided operands are judged by the whole
+  // address range they span.
+  auto extent = [&](int k) -> uintptr_t {
+    const int64_t s = a.strides ? a.strides[k] : 1;
+    return a.n > 0 ? (uintptr_t)(((a.n - 1) * s + 1) * (int64_t)es) : 0;
+  };
   for (int i = 0; i < a.nvecs; ++i) {
     if (!((an.used_vecs >> i) & 1u)) continue;
     for (int j = i + 1; j < a.nvecs; ++j) {
       if (!((an.used_vecs >> j) & 1u)) continue;
       if (!(((an.stored_vecs >> i) | (an.stored_vecs >> j)) & 1u)) continue;
       const uintptr_t pi = (uintptr_t)a.vecs[i], pj = (uintptr_t)a.vecs[j];
-      if (bytes > 0 && pi < pj + bytes && pj < pi + bytes) {
+      const uintptr_t bi = extent(i), bj = extent(j);
+      if (bi > 0 && bj > 0 && pi < pj + bj && pj < pi + bi) {
         char b[128];
         snprintf(b, sizeof b, "operands %d and %d overlap and one of them is stored", i, j);
         return set_error(SALT_ERR_ALIAS, b);
@@ -368,6 +423,16 @@ static salt_status run_special(int special, int dt, int64_t n, const void* x, co
   Workspace ws;
   st = workspace(dev, info, s, &ws);
   if (st != SALT_OK) return st;
+  if (special == SPECIAL_NRM2 && !aligned(x, 16)) {  // element accesses
+    const KernelEntry& ke = registry().nrm2_elem[dt];
+    int bps = occupancy_blocks(ke.kernel, 256, 0);
+    if (bps > kMaxBlocksPerSM) bps = kMaxBlocksPerSM;
+    const int grid = grid_for(n, 256, info.sms, bps);
+    NrmParams p{x, n, out, ws.partials, ws.ticket};
+    cudaError_t e = ke.launch(&p, grid, 256, 0, s);
+    g_launches.fetch_add(1);
+    return e == cudaSuccess ? SALT_OK : cuda_error(e, "norm kernel launch");
+  }
   salt_launch_cfg cfg = lookup_cfg(100 + special, dt, n);
   if (cfg.vec_bytes == 32 && !(aligned(x, 32) && (!y || aligned(y, 32)))) cfg.vec_bytes = 16;
   const KernelEntry& ke = registry().special[special][dt][unroll_index(cfg.unroll)][vb_index(cfg.vec_bytes)];
@@ -436,6 +501,14 @@ salt_status salt_eval(const salt_insn* prog, int32_t nprog, int32_t dtype, int64
   return eval_impl(a);
 }
 
+salt_status salt_eval_strided(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                              void* const* vecs, const int64_t* strides, int32_t nvecs, const double* scalars,
+                              int32_t nscal, double* red_out, void* stream) {
+  if (!strides && nvecs > 0) return set_error(SALT_ERR_ARG, "strides is NULL");
+  EvalArgs a{prog, nprog, dtype, n, vecs, nvecs, scalars, nscal, red_out, (cudaStream_t)stream, strides};
+  return eval_impl(a);
+}
+
 salt_status salt_axpby(int32_t dtype, int64_t n, double alpha, const void* x, double beta, void* y,
                        void* stream) {
   static const salt_insn prog[] = {{SALT_OP_SCAL, 0}, {SALT_OP_VEC, 0}, {SALT_OP_SMUL, 0},
@@ -465,9 +538,13 @@ salt_status salt_dot(int32_t dtype, int64_t n, const void* x, const void* y, dou
   if (!out) return set_error(SALT_ERR_ARG, "out is NULL");
   if (!aligned(out, 8)) return set_error(SALT_ERR_ALIGN, "out must be 8-byte aligned");
   if (n > 0 && (!x || !y)) return set_error(SALT_ERR_ARG, "x or y is NULL");
-  if (!aligned(x, 16) || !aligned(y, 16)) return set_error(SALT_ERR_ALIGN, "x and y must be 16-byte aligned");
-  if (dtype == SALT_F32 && flags == SALT_PLAIN)
+  const size_t es = dtype == SALT_F32 ? 4 : 8;
+  if (!aligned(x, es) || !aligned(y, es)) return set_error(SALT_ERR_ALIGN, "x and y must be element-aligned");
+  if (dtype == SALT_F32 && flags == SALT_PLAIN) {
+    if (!aligned(x, 16) || !aligned(y, 16))
+      return set_error(SALT_ERR_ALIGN, "SALT_PLAIN needs 16-byte aligned x and y");
     return run_special(SPECIAL_DOT_PLAIN, DT_F32, n, x, y, out, (cudaStream_t)stream);
+  }
   static const salt_insn prog[] = {{SALT_OP_VEC, 0}, {SALT_OP_VEC, 1}, {SALT_OP_DOT, 0}};
   void* vecs[2] = {const_cast<void*>(x), const_cast<void*>(y)};
   EvalArgs a{prog, 3, dtype, n, vecs, 2, nullptr, 0, out, (cudaStream_t)stream};
@@ -500,7 +577,8 @@ salt_status nrm2_impl(int32_t dtype, int64_t n, const void* x, double* out, int3
   if (!out) return set_error(SALT_ERR_ARG, "out is NULL");
   if (!aligned(out, 8)) return set_error(SALT_ERR_ALIGN, "out must be 8-byte aligned");
   if (n > 0 && !x) return set_error(SALT_ERR_ARG, "x is NULL");
-  if (!aligned(x, 16)) return set_error(SALT_ERR_ALIGN, "x must be 16-byte aligned");
+  if (!aligned(x, dtype == SALT_F32 ? 4 : 8)) return set_error(SALT_ERR_ALIGN, "x must be element-aligned");
+  if (flags == SALT_PLAIN && !aligned(x, 16)) return set_error(SALT_ERR_ALIGN, "SALT_PLAIN needs a 16-byte aligned x");
   const int special = (dtype == SALT_F32 && flags == SALT_PLAIN) ? SPECIAL_NRM2_PLAIN : SPECIAL_NRM2;
   return run_special(special, dtype == SALT_F32 ? DT_F32 : DT_F64, n, x, nullptr, out, stream);
 }

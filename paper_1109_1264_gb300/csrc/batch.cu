@@ -305,8 +305,10 @@ salt_status salt_batch_add(salt_batch* b, const salt_insn* prog, int32_t nprog, 
   if (shape < 0) return fail(SALT_ERR_PROGRAM, "program has no compiled instantiation, so it cannot be batched");
   if (c.nvec > kBatchOps || c.nscal > 2 || c.nred > kBatchPartials)
     return fail(SALT_ERR_PROGRAM, "program exceeds the batch item limits");
-  for (int k = 0; k < c.nvec && n > 0; ++k)
+  for (int k = 0; k < c.nvec && n > 0; ++k) {
     if (!vecs[c.vec_user[k]]) return fail(SALT_ERR_ARG, "operand is NULL");
+    if ((uintptr_t)vecs[c.vec_user[k]] % 16) return fail(SALT_ERR_ALIGN, "batch operands must be 16-byte aligned");
+  }
   HostItem it;
   it.prog.assign(prog, prog + nprog);
   it.vecs.assign(vecs, vecs + nvecs);

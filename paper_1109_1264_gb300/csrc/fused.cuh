@@ -21,6 +21,7 @@ struct MapParams {
   double* red_out;      // device, one double per reduction
   void* partials;       // workspace: gridDim.x * NR values
   unsigned* ticket;     // workspace: zero between launches
+  int64_t stride[kMaxVecs];  // element strides (strided_kernel only)
 };
 
 // Per-element evaluation of program P: node I at compile-time stack depth.
@@ -173,6 +174,66 @@ __global__ void __launch_bounds__(256) fused_kernel(const MapParams<T> p) {
       if ((SMASK >> s) & 1u) p.v[s][i] = x[s][0];
   }
 
+  if constexpr (NR > 0) {
+    __shared__ double smem[kMaxBlock];
+    double vals[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) vals[r] = acc[r].value();
+    if (grid_combine<double, NR>(vals, (double*)p.partials, p.ticket, smem) && threadIdx.x == 0) {
+#pragma unroll
+      for (int r = 0; r < NR; ++r) p.red_out[r] = vals[r];
+    }
+  }
+}
+
+// Element-wise access variant for operands that are not 16-byte aligned or
+// not contiguous: element i of operand k is v[k][i * stride[k]].  Each thread
+// takes U elements per pass, U * blockDim apart within a block's stretch, so
+// unit-stride operands still coalesce; the load burst / operation / store
+// burst shape is kept, and out-of-range elements are neither loaded, stored
+// nor reduced.
+template <class P, typename T, int U>
+__global__ void __launch_bounds__(256) strided_kernel(const MapParams<T> p) {
+  constexpr unsigned LM = P::load_mask(), SMASK = P::store_mask();
+  constexpr int NR = P::nred();
+  using Acc = typename AccOf<T>::type;
+  T sc[kMaxScals];
+#pragma unroll
+  for (int k = 0; k < kMaxScals; ++k) sc[k] = p.sc[k];
+  Acc acc[kMaxReds];
+  const int64_t n = p.n;
+  const int64_t bd = blockDim.x;
+  const int64_t span = (int64_t)U * bd;
+  for (int64_t base = (int64_t)blockIdx.x * span; base < n; base += (int64_t)gridDim.x * span) {
+    T x[kMaxVecs][U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * bd + threadIdx.x;
+#pragma unroll
+      for (int s = 0; s < kMaxVecs; ++s)
+        x[s][u] = (((LM >> s) & 1u) && i < n) ? p.v[s][i * p.stride[s]] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * bd + threadIdx.x;
+      if (i < n) {
+        T v[kMaxVecs];
+#pragma unroll
+        for (int s = 0; s < kMaxVecs; ++s) v[s] = x[s][u];
+        exec_elem<P>(v, sc, acc);
+#pragma unroll
+        for (int s = 0; s < kMaxVecs; ++s)
+          if ((SMASK >> s) & 1u) x[s][u] = v[s];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = base + u * bd + threadIdx.x;
+#pragma unroll
+      for (int s = 0; s < kMaxVecs; ++s)
+        if (((SMASK >> s) & 1u) && i < n) p.v[s][i * p.stride[s]] = x[s][u];
+    }
+  }
   if constexpr (NR > 0) {
     __shared__ double smem[kMaxBlock];
     double vals[NR];

@@ -21,6 +21,7 @@ struct EvalArgs {
   int nscal;
   double* red_out;
   cudaStream_t stream;
+  const int64_t* strides = nullptr;  // per operand, in elements; NULL: all 1
 };
 
 // Records `msg` as the calling thread's salt_last_error() and returns `st`.

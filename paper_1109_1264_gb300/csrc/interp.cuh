@@ -34,6 +34,8 @@ struct InterpParams {
   uint32_t load_mask, store_mask;
   int32_t len, nred;
   RegInsn code[kMaxRegCode];
+  int32_t elementwise;        // 1: operands unaligned or strided, element accesses only
+  int64_t stride[kMaxVecs];   // element strides (used when elementwise)
 };
 
 template <typename T, class Acc>
@@ -68,13 +70,14 @@ __global__ void __launch_bounds__(256) interp_kernel(const InterpParams<T> p) {
     for (int s = 0; s < kMaxVecs; ++s) {
       if ((p.load_mask >> s) & 1u) {
         T* r = row(s);
-        if (cnt == VEC) {
+        if (cnt == VEC && !p.elementwise) {
           V t;
           if ((p.store_mask >> s) & 1u) vload<false>(t, p.v[s] + base);
           else vload<true>(t, p.v[s] + base);
           *reinterpret_cast<V*>(r) = t;
         } else {
-          for (int e = 0; e < VEC; ++e) r[e] = e < cnt ? p.v[s][base + e] : T(0);
+          const int64_t st = p.elementwise ? p.stride[s] : 1;
+          for (int e = 0; e < VEC; ++e) r[e] = e < cnt ? p.v[s][(base + e) * st] : T(0);
         }
       }
     }
@@ -128,10 +131,11 @@ __global__ void __launch_bounds__(256) interp_kernel(const InterpParams<T> p) {
     for (int s = 0; s < kMaxVecs; ++s) {
       if ((p.store_mask >> s) & 1u) {
         const T* r = row(s);
-        if (cnt == VEC) {
+        if (cnt == VEC && !p.elementwise) {
           vstore(p.v[s] + base, *reinterpret_cast<const V*>(r));
         } else {
-          for (int e = 0; e < cnt; ++e) p.v[s][base + e] = r[e];
+          const int64_t st = p.elementwise ? p.stride[s] : 1;
+          for (int e = 0; e < cnt; ++e) p.v[s][(base + e) * st] = r[e];
         }
       }
     }

@@ -96,10 +96,11 @@ salt_status jit_kernel(const Canonical& c, int is_f32, int unroll, int vec_bytes
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  std::string name = "salt::fused_kernel<salt::Prog<";
+  // vec_bytes == 0: the element-access kernel (unaligned or strided operands)
+  std::string name = vec_bytes ? "salt::fused_kernel<salt::Prog<" : "salt::strided_kernel<salt::Prog<";
   for (int i = 0; i < c.len; ++i) name += (i ? "," : "") + std::to_string(c.code[i]);
-  name += ">," + std::string(is_f32 ? "float" : "double") + "," + std::to_string(unroll) + "," +
-          std::to_string(vec_bytes) + ">";
+  name += ">," + std::string(is_f32 ? "float" : "double") + "," + std::to_string(unroll);
+  name += vec_bytes ? "," + std::to_string(vec_bytes) + ">" : ">";
   const std::string key = std::to_string(dev) + "|" + name;
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_cache.find(key);

@@ -182,6 +182,29 @@ __global__ void __launch_bounds__(256) nrm2_kernel(const NrmParams p) {
   }
 }
 
+// Norm of an operand that is not 16-byte aligned: element loads (consecutive
+// threads, consecutive elements), same accumulators and combination as
+// nrm2_kernel.
+template <typename T>
+__global__ void __launch_bounds__(256) nrm2_elem_kernel(const NrmParams p) {
+  const T* x = (const T*)p.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  __shared__ double smem[kMaxBlock];
+  if constexpr (sizeof(T) == 4) {
+    Nrm2F32 acc;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) acc.add(x[i]);
+    double vals[1] = {acc.value()};
+    if (grid_combine<double, 1>(vals, (double*)p.partials, p.ticket, smem) && threadIdx.x == 0)
+      *p.out = __dsqrt_rn(vals[0]);
+  } else {
+    Nrm2F64 acc;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.n; i += stride) acc.add(x[i]);
+    double vals[3] = {acc.sml, acc.med, acc.big};
+    if (grid_combine<double, 3>(vals, (double*)p.partials, p.ticket, smem) && threadIdx.x == 0)
+      *p.out = blue_finish(vals[0], vals[1], vals[2]);
+  }
+}
+
 struct DotParams {
   const void* x;
   const void* y;

@@ -22,11 +22,16 @@ enum : int { DT_F32 = 0, DT_F64 = 1 };
 // Special (non-program) kernels.
 enum SpecialId : int { SPECIAL_NRM2 = 0, SPECIAL_NRM2_PLAIN, SPECIAL_DOT_PLAIN, NUM_SPECIAL };
 
+// Unroll of the element-access kernels (operands unaligned or strided).
+constexpr int kElemUnroll = 4;
+
 struct Registry {
   KernelEntry fused[NUM_SHAPES][2][kNumUnroll][kNumVB];
   KernelEntry special[NUM_SPECIAL][2][kNumUnroll][kNumVB];
   KernelEntry interp[2][kNumVB];
   KernelEntry fill[2];
+  KernelEntry strided[NUM_SHAPES][2];  // strided_kernel<P, T, kElemUnroll>
+  KernelEntry nrm2_elem[2];            // nrm2_elem_kernel<T>
 };
 
 Registry& registry();
@@ -37,6 +42,7 @@ void register_f32_vb32(Registry&);
 void register_f64_vb16(Registry&);
 void register_f64_vb32(Registry&);
 void register_misc(Registry&);
+void register_elementwise(Registry&);
 
 inline int unroll_index(int u) { return u == 1 ? 0 : u == 2 ? 1 : u == 4 ? 2 : -1; }
 inline int vb_index(int vb) { return vb == 16 ? 0 : vb == 32 ? 1 : -1; }

@@ -24,7 +24,8 @@ MAX_PROG, MAX_VECS, MAX_SCALS, MAX_STACK, MAX_REDS = 32, 8, 8, 8, 4
 # Symbols that include/salt.h declares (checked by the test suite).
 EXPORTS = ["salt_version", "salt_status_str", "salt_last_error", "salt_check_program", "salt_eval",
            "salt_axpby", "salt_dot", "salt_nrm2", "salt_fill_uniform", "salt_release_workspaces",
-           "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_dot_noalloc"]
+           "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_dot_noalloc",
+           "salt_eval_strided"]
 
 
 class Insn(ctypes.Structure):
@@ -66,6 +67,8 @@ def _load() -> ctypes.CDLL:
         "salt_tune_clear": (i32, []),
         "salt_launch_count": (i64, []),
         "salt_dot_noalloc": (i32, [i32, i64, vp, vp, vp, vp]),
+        "salt_eval_strided": (i32, [ip, i32, i32, i64, ctypes.POINTER(vp), ctypes.POINTER(i64), i32, dp, i32, vp,
+                                    vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -150,16 +153,26 @@ def salt_check_program(prog, nvecs: int, nscal: int) -> tuple[int, bool]:
 def salt_eval(prog, vecs, scalars=(), red_out=None, n: int | None = None, stream=None) -> None:
     """Run ``prog`` over the torch CUDA tensors ``vecs`` (all float32 or all
     float64, same length).  DOT/SUMSQ results go to ``red_out`` (a float64 CUDA
-    tensor with one entry per reduction)."""
-    _contig(vecs)
+    tensor with one entry per reduction).  1-D views with a positive stride
+    are passed to salt_eval_strided."""
     dt = _common_dtype(vecs)
     if n is None:
         n = _n_of(vecs)
     arr, m = program(prog)
     ptrs = (ctypes.c_void_p * max(len(vecs), 1))(*[_ptr(v) for v in vecs])
     sc = (ctypes.c_double * max(len(scalars), 1))(*[float(s) for s in scalars])
-    _check(lib.salt_eval(arr, m, dt, int(n), ptrs, len(vecs), sc, len(scalars), _ptr(red_out),
-                         _stream_ptr(stream)))
+    if all(v is None or v.is_contiguous() for v in vecs):
+        _check(lib.salt_eval(arr, m, dt, int(n), ptrs, len(vecs), sc, len(scalars), _ptr(red_out),
+                             _stream_ptr(stream)))
+        return
+    strides = []
+    for v in vecs:
+        if v is not None and (v.dim() != 1 or v.stride(0) < 1):
+            raise SaltError(ERR_ARG, "SALT_ERR_ARG", "operands must be 1-D with a positive stride")
+        strides.append(1 if v is None else int(v.stride(0)))
+    st = (ctypes.c_int64 * max(len(vecs), 1))(*strides)
+    _check(lib.salt_eval_strided(arr, m, dt, int(n), ptrs, st, len(vecs), sc, len(scalars), _ptr(red_out),
+                                 _stream_ptr(stream)))
 
 
 def salt_axpby(alpha: float, x, beta: float, y, stream=None) -> None:

@@ -83,7 +83,8 @@ def test_eval_argument_errors(saltlib):
     ok = [BASE, BASE + 2 ** 20, BASE + 2 ** 21, BASE + 2 ** 22]
     assert _raw_eval(saltlib, D, 2, 10, ok) == saltlib.ERR_DTYPE
     assert _raw_eval(saltlib, D, 0, -1, ok) == saltlib.ERR_ARG
-    assert _raw_eval(saltlib, D, 0, 10, [ok[0], ok[1] + 8, ok[2], ok[3]]) == saltlib.ERR_ALIGN
+    assert _raw_eval(saltlib, D, 0, 10, [ok[0], ok[1] + 2, ok[2], ok[3]]) == saltlib.ERR_ALIGN
+    assert _raw_eval(saltlib, D, 1, 10, [ok[0], ok[1] + 4, ok[2], ok[3]]) == saltlib.ERR_ALIGN
     assert _raw_eval(saltlib, D, 0, 10, [ok[0], None, ok[2], ok[3]]) == saltlib.ERR_ARG
     # output overlapping an input through a different operand index
     assert _raw_eval(saltlib, D, 1, 100, [ok[0], ok[1], ok[2], ok[0] + 16]) == saltlib.ERR_ALIAS
@@ -115,10 +116,11 @@ def test_dot_nrm2_argument_errors(saltlib):
     L = saltlib.lib
     assert L.salt_dot(0, 10, BASE, BASE, BASE, 7, None) == saltlib.ERR_ARG
     assert L.salt_dot(3, 10, BASE, BASE, BASE, 0, None) == saltlib.ERR_DTYPE
-    assert L.salt_dot(0, 10, BASE + 4, BASE, BASE, 0, None) == saltlib.ERR_ALIGN
+    assert L.salt_dot(0, 10, BASE + 2, BASE, BASE, 0, None) == saltlib.ERR_ALIGN
+    assert L.salt_dot(0, 10, BASE + 4, BASE, BASE, 1, None) == saltlib.ERR_ALIGN  # plain mode needs 16 B
     assert L.salt_dot(0, 10, BASE, BASE, None, 0, None) == saltlib.ERR_ARG
     assert L.salt_nrm2(1, -3, BASE, BASE, 0, None) == saltlib.ERR_ARG
-    assert L.salt_nrm2(1, 10, BASE + 8, BASE, 0, None) == saltlib.ERR_ALIGN
+    assert L.salt_nrm2(1, 10, BASE + 4, BASE, 0, None) == saltlib.ERR_ALIGN
     assert L.salt_axpby(0, 10, 1.0, BASE, 1.0, BASE + 16, None) == saltlib.ERR_ALIAS
     assert L.salt_fill_uniform(0, -1, 1, 0, BASE, None) == saltlib.ERR_ARG
 
@@ -178,3 +180,17 @@ def test_jit_mode_switch(saltlib):
     s.salt_set_jit(s.JIT_ON)
     assert s.salt_jit_stats()["mode"] == s.JIT_ON
     s.salt_set_jit(s.JIT_OFF)
+
+
+def test_strided_argument_errors(saltlib):
+    s = saltlib
+    arr, m = s.program(D)
+    p = (ctypes.c_void_p * 4)(BASE, BASE + 2 ** 20, BASE + 2 ** 21, BASE + 2 ** 22)
+    sc = (ctypes.c_double * 1)(0.0)
+    bad = (ctypes.c_int64 * 4)(1, 0, 1, 1)
+    assert s.lib.salt_eval_strided(arr, m, 0, 10, p, bad, 4, sc, 0, None, None) == s.ERR_ARG
+    assert s.lib.salt_eval_strided(arr, m, 0, 10, p, None, 4, sc, 0, None, None) == s.ERR_ARG
+    # a strided output spanning another operand's memory
+    st = (ctypes.c_int64 * 4)(1, 1, 1, 100000)
+    q = (ctypes.c_void_p * 4)(BASE, BASE + 2 ** 20, BASE + 2 ** 21, BASE + 2 ** 20 - 4096)
+    assert s.lib.salt_eval_strided(arr, m, 0, 10, q, st, 4, sc, 0, None, None) == s.ERR_ALIAS
