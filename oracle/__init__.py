@@ -16,8 +16,12 @@ this package imports nothing from the product.
   judged against, because a sequential FP64 sum is itself off by up to
   ``gamma_n * sum|x_i y_i|``.
 
-Programs are lists of ``(name, arg)`` pairs with names ``VEC, SCAL, ADD,
-SUB, MUL, SMUL, NEG, STORE, DOT, SUMSQ`` (arg used by VEC, SCAL, STORE).
+Programs are lists of ``(name, arg)`` pairs with names ``VEC, SCAL, DSCAL,
+ADD, SUB, MUL, DIV, SMUL, NEG, STORE, DOT, SUMSQ`` (arg used by VEC, SCAL,
+DSCAL, STORE).  ADD, SUB, MUL, DIV and NEG act elementwise on vectors or on
+two scalars (a loop-invariant scalar node, Section 4.2 init/load_once);
+DSCAL is a scalar that the product reads from device memory -- here it is
+simply passed in by value.
 """
 from __future__ import annotations
 
@@ -33,7 +37,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 # The oracle's own node numbering (matches the enum in oracle.c).
 _CODES = {"VEC": 1, "SCAL": 2, "ADD": 3, "SUB": 4, "MUL": 5, "SMUL": 6,
-          "NEG": 7, "STORE": 8, "DOT": 9, "SUMSQ": 10}
+          "NEG": 7, "STORE": 8, "DOT": 9, "SUMSQ": 10, "DIV": 11, "DSCAL": 12}
 
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
 
@@ -57,7 +61,7 @@ def _load(path: str = _LIB) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.restype = ctypes.c_int
         f.argtypes = [i32p, i32p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(vp),
-                      ctypes.c_int32, dp, ctypes.c_int32, dp]
+                      ctypes.c_int32, dp, ctypes.c_int32, dp, ctypes.c_int32, dp]
     for name in ("oracle_dot_f64", "oracle_dot_f32"):
         f = getattr(lib, name)
         f.restype = ctypes.c_double
@@ -92,9 +96,10 @@ def _dtype_of(vecs):
     return dt
 
 
-def eval_program(prog, vecs, scalars=(), n=None, path: str = _LIB):
+def eval_program(prog, vecs, scalars=(), n=None, path: str = _LIB, dscalars=()):
     """Evaluate ``prog`` node by node.  ``vecs`` are C-contiguous numpy
-    arrays (all float32 or all float64) that STORE overwrites in place.
+    arrays (all float32 or all float64) that STORE overwrites in place;
+    ``scalars`` feed SCAL nodes and ``dscalars`` DSCAL nodes.
     Returns the list of reduction results (DOT/SUMSQ, in program order)."""
     dt = _dtype_of(vecs)
     for v in vecs:
@@ -106,10 +111,12 @@ def eval_program(prog, vecs, scalars=(), n=None, path: str = _LIB):
     args = (ctypes.c_int32 * max(len(prog), 1))(*[int(a) for _, a in prog])
     ptrs = (ctypes.c_void_p * max(len(vecs), 1))(*[v.ctypes.data for v in vecs])
     sc = (ctypes.c_double * max(len(scalars), 1))(*[float(s) for s in scalars])
+    dsc = (ctypes.c_double * max(len(dscalars), 1))(*[float(s) for s in dscalars])
     nred = sum(1 for o, _ in prog if o in ("DOT", "SUMSQ"))
     red = (ctypes.c_double * max(nred, 1))()
     fn = lib(path).oracle_eval_f64 if dt == np.float64 else lib(path).oracle_eval_f32
-    rc = fn(ops, args, len(prog), int(n), ptrs, len(vecs), sc, len(scalars), red)
+    rc = fn(ops, args, len(prog), int(n), ptrs, len(vecs), sc, len(scalars), dsc, len(dscalars),
+            red)
     if rc == 1:
         raise OracleProgramError("invalid program")
     if rc != 0:

@@ -127,9 +127,12 @@ def round_to(fr: Fraction, dtype) -> float:
     return d
 
 
-def exact_program(prog, vecs, scalars, dtype):
+def exact_program(prog, vecs, scalars, dtype, dscalars=()):
     """Per-element evaluation of a postfix program with exact rational
-    arithmetic and one rounding per node to ``dtype`` (finite values only).
+    arithmetic and one rounding per node to ``dtype`` (finite values only;
+    every DIV denominator nonzero).  Scalar nodes (two scalar operands) are
+    rounded like vector nodes; SCAL and DSCAL values are rounded to
+    ``dtype`` once.
 
     Returns (stored vectors as lists of floats keyed by slot, reductions as
     Fractions, and per reduction the exact sum of |terms|, the scale of
@@ -138,8 +141,10 @@ def exact_program(prog, vecs, scalars, dtype):
     cur = [[float(t) for t in v] for v in vecs]
     if dtype == np.float32:
         sc = [float(np.float32(s)) for s in scalars]
+        dsc = [float(np.float32(s)) for s in dscalars]
     else:
         sc = [float(s) for s in scalars]
+        dsc = [float(s) for s in dscalars]
     # reductions: accumulate exactly over elements in order of appearance
     nred = sum(1 for o, _ in prog if o in ("DOT", "SUMSQ"))
     red_exact = [Fraction(0)] * nred
@@ -152,19 +157,29 @@ def exact_program(prog, vecs, scalars, dtype):
                 stack.append(("v", cur[k][i]))
             elif op == "SCAL":
                 stack.append(("s", sc[k]))
-            elif op in ("ADD", "SUB", "MUL"):
-                b = stack.pop()[1]
-                a = stack.pop()[1]
+            elif op == "DSCAL":
+                stack.append(("s", dsc[k]))
+            elif op in ("ADD", "SUB", "MUL", "DIV"):
+                kb, b = stack.pop()
+                ka, a = stack.pop()
                 fa, fb = Fraction(a), Fraction(b)
-                ex = fa + fb if op == "ADD" else (fa - fb if op == "SUB" else fa * fb)
-                stack.append(("v", round_to(ex, dtype)))
+                if op == "ADD":
+                    ex = fa + fb
+                elif op == "SUB":
+                    ex = fa - fb
+                elif op == "MUL":
+                    ex = fa * fb
+                else:
+                    ex = fa / fb
+                kind = "s" if (ka, kb) == ("s", "s") else "v"
+                stack.append((kind, round_to(ex, dtype)))
             elif op == "SMUL":
                 v = stack.pop()[1]
                 s = stack.pop()[1]
                 stack.append(("v", round_to(Fraction(s) * Fraction(v), dtype)))
             elif op == "NEG":
-                v = stack.pop()[1]
-                stack.append(("v", -v))
+                kv, v = stack.pop()
+                stack.append((kv, -v))
             elif op == "STORE":
                 cur[k][i] = stack.pop()[1]
             elif op == "DOT":

@@ -21,6 +21,12 @@
  *    says expression templates fuse away).
  *  - Section 4.2 (Listing 2): the tail elements get the same scalar operation
  *    as the vector body, so the result is a function of the element only.
+ *  - Section 4.2: init / load_once compute, once per loop, what does not
+ *    depend on the element (the TemporaryStorage).  Scalar subexpressions --
+ *    ADD, SUB, MUL, DIV, NEG of two scalars, scalar operands given by value
+ *    (SCAL) or living in device memory (DSCAL, here passed in by value) --
+ *    are such loop invariants; each is one operation rounded to the
+ *    program's dtype, like a vector node.
  *  - Section 2 (lazy evaluation in dot product and norm) and Section 5
  *    (xDOT, xSCAL, xAXPY): reductions are plain sums of elementwise products,
  *    accumulated here sequentially in index order in FP64.
@@ -47,7 +53,9 @@ enum {
   OR_NEG = 7,   /* -v                               */
   OR_STORE = 8, /* assign top of stack to vector k  */
   OR_DOT = 9,   /* sum_i a_i * b_i                  */
-  OR_SUMSQ = 10 /* sum_i a_i * a_i                  */
+  OR_SUMSQ = 10, /* sum_i a_i * a_i                  */
+  OR_DIV = 11,   /* a / b (elementwise, or two scalars) */
+  OR_DSCAL = 12  /* push device-resident scalar k    */
 };
 
 /* Error codes of oracle_eval_*: 0 success. */
@@ -69,7 +77,7 @@ static void free_stack64(item64* st, int sp) {
 
 int oracle_eval_f64(const int32_t* ops, const int32_t* args, int32_t nprog, int64_t n,
                     double* const* vecs, int32_t nvecs, const double* scal, int32_t nscal,
-                    double* red) {
+                    const double* dscal, int32_t ndscal, double* red) {
   item64 st[OR_MAX_STACK];
   int sp = 0, nred = 0;
   size_t bytes = (size_t)(n > 0 ? n : 1) * sizeof(double);
@@ -84,7 +92,20 @@ int oracle_eval_f64(const int32_t* ops, const int32_t* args, int32_t nprog, int6
     } else if (op == OR_SCAL) {
       if (k < 0 || k >= nscal || sp >= OR_MAX_STACK) goto bad;
       st[sp].is_vec = 0; st[sp].v = NULL; st[sp].s = scal[k]; ++sp;
-    } else if (op == OR_ADD || op == OR_SUB || op == OR_MUL) {
+    } else if (op == OR_DSCAL) {
+      if (k < 0 || k >= ndscal || sp >= OR_MAX_STACK) goto bad;
+      st[sp].is_vec = 0; st[sp].v = NULL; st[sp].s = dscal[k]; ++sp;
+    } else if ((op == OR_ADD || op == OR_SUB || op == OR_MUL || op == OR_DIV) && sp >= 2 &&
+               !st[sp - 2].is_vec && !st[sp - 1].is_vec) {
+      /* scalar node: one FP64 operation */
+      double a = st[sp - 2].s, b = st[sp - 1].s, r;
+      if (op == OR_ADD) r = a + b;
+      else if (op == OR_SUB) r = a - b;
+      else if (op == OR_MUL) r = a * b;
+      else r = a / b;
+      --sp;
+      st[sp - 1].s = r;
+    } else if (op == OR_ADD || op == OR_SUB || op == OR_MUL || op == OR_DIV) {
       if (sp < 2 || !st[sp - 2].is_vec || !st[sp - 1].is_vec) goto bad;
       double* a = st[sp - 2].v;
       double* b = st[sp - 1].v;
@@ -93,6 +114,7 @@ int oracle_eval_f64(const int32_t* ops, const int32_t* args, int32_t nprog, int6
       if (op == OR_ADD) for (int64_t i = 0; i < n; ++i) t[i] = a[i] + b[i];
       if (op == OR_SUB) for (int64_t i = 0; i < n; ++i) t[i] = a[i] - b[i];
       if (op == OR_MUL) for (int64_t i = 0; i < n; ++i) t[i] = a[i] * b[i];
+      if (op == OR_DIV) for (int64_t i = 0; i < n; ++i) t[i] = a[i] / b[i];
       free(a); free(b);
       sp -= 2;
       st[sp].is_vec = 1; st[sp].v = t; ++sp;
@@ -107,7 +129,11 @@ int oracle_eval_f64(const int32_t* ops, const int32_t* args, int32_t nprog, int6
       sp -= 2;
       st[sp].is_vec = 1; st[sp].v = t; ++sp;
     } else if (op == OR_NEG) {
-      if (sp < 1 || !st[sp - 1].is_vec) goto bad;
+      if (sp < 1) goto bad;
+      if (!st[sp - 1].is_vec) {
+        st[sp - 1].s = -st[sp - 1].s;
+        continue;
+      }
       double* v = st[sp - 1].v;
       for (int64_t i = 0; i < n; ++i) v[i] = -v[i];
     } else if (op == OR_STORE) {
@@ -161,7 +187,7 @@ static void free_stack32(item32* st, int sp) {
 
 int oracle_eval_f32(const int32_t* ops, const int32_t* args, int32_t nprog, int64_t n,
                     float* const* vecs, int32_t nvecs, const double* scal, int32_t nscal,
-                    double* red) {
+                    const double* dscal, int32_t ndscal, double* red) {
   item32 st[OR_MAX_STACK];
   int sp = 0, nred = 0;
   size_t bytes = (size_t)(n > 0 ? n : 1) * sizeof(float);
@@ -176,7 +202,20 @@ int oracle_eval_f32(const int32_t* ops, const int32_t* args, int32_t nprog, int6
     } else if (op == OR_SCAL) {
       if (k < 0 || k >= nscal || sp >= OR_MAX_STACK) goto bad;
       st[sp].is_vec = 0; st[sp].v = NULL; st[sp].s = (float)scal[k]; ++sp;
-    } else if (op == OR_ADD || op == OR_SUB || op == OR_MUL) {
+    } else if (op == OR_DSCAL) {
+      if (k < 0 || k >= ndscal || sp >= OR_MAX_STACK) goto bad;
+      st[sp].is_vec = 0; st[sp].v = NULL; st[sp].s = (float)dscal[k]; ++sp;
+    } else if ((op == OR_ADD || op == OR_SUB || op == OR_MUL || op == OR_DIV) && sp >= 2 &&
+               !st[sp - 2].is_vec && !st[sp - 1].is_vec) {
+      /* scalar node: one FP32 operation */
+      float a = st[sp - 2].s, b = st[sp - 1].s, r;
+      if (op == OR_ADD) r = a + b;
+      else if (op == OR_SUB) r = a - b;
+      else if (op == OR_MUL) r = a * b;
+      else r = a / b;
+      --sp;
+      st[sp - 1].s = r;
+    } else if (op == OR_ADD || op == OR_SUB || op == OR_MUL || op == OR_DIV) {
       if (sp < 2 || !st[sp - 2].is_vec || !st[sp - 1].is_vec) goto bad;
       float* a = st[sp - 2].v;
       float* b = st[sp - 1].v;
@@ -185,6 +224,7 @@ int oracle_eval_f32(const int32_t* ops, const int32_t* args, int32_t nprog, int6
       if (op == OR_ADD) for (int64_t i = 0; i < n; ++i) t[i] = a[i] + b[i];
       if (op == OR_SUB) for (int64_t i = 0; i < n; ++i) t[i] = a[i] - b[i];
       if (op == OR_MUL) for (int64_t i = 0; i < n; ++i) t[i] = a[i] * b[i];
+      if (op == OR_DIV) for (int64_t i = 0; i < n; ++i) t[i] = a[i] / b[i];
       free(a); free(b);
       sp -= 2;
       st[sp].is_vec = 1; st[sp].v = t; ++sp;
@@ -199,7 +239,11 @@ int oracle_eval_f32(const int32_t* ops, const int32_t* args, int32_t nprog, int6
       sp -= 2;
       st[sp].is_vec = 1; st[sp].v = t; ++sp;
     } else if (op == OR_NEG) {
-      if (sp < 1 || !st[sp - 1].is_vec) goto bad;
+      if (sp < 1) goto bad;
+      if (!st[sp - 1].is_vec) {
+        st[sp - 1].s = -st[sp - 1].s;
+        continue;
+      }
       float* v = st[sp - 1].v;
       for (int64_t i = 0; i < n; ++i) v[i] = -v[i];
     } else if (op == OR_STORE) {

@@ -84,9 +84,12 @@ def check_e_and_axpby_exact(path):
         assert np.array_equal(x, a), "x must be left untouched"
 
 
-def random_program(rng: random.Random, nvecs: int, nscal: int, max_len: int = 20):
-    """A random well-typed postfix program over nvecs vectors / nscal scalars.
-    Keeps stack depth <= 6, ends with an empty stack and has >= 1 output."""
+def random_program(rng: random.Random, nvecs: int, nscal: int, max_len: int = 20,
+                   ndscal: int = 0, ext: bool = False):
+    """A random well-typed postfix program over nvecs vectors / nscal scalars
+    (and ndscal device scalars).  With ``ext`` it also draws elementwise DIV
+    and scalar-typed ADD/SUB/MUL/DIV/NEG nodes.  Keeps stack depth <= 6,
+    ends with an empty stack and has >= 1 output."""
     prog = []
     stack = []  # 'v' or 's'
     outputs = 0
@@ -99,8 +102,16 @@ def random_program(rng: random.Random, nvecs: int, nscal: int, max_len: int = 20
             choices += ["VEC"] * 3
             if nscal:
                 choices += ["SCAL"]
+            if ndscal:
+                choices += ["DSCAL"]
         if len(stack) >= 2 and stack[-1] == "v" and stack[-2] == "v":
             choices += ["ADD", "SUB", "MUL", "DOT"]
+            if ext:
+                choices += ["DIV"]
+        if ext and len(stack) >= 2 and stack[-1] == "s" and stack[-2] == "s":
+            choices += ["S_ADD", "S_SUB", "S_MUL", "S_DIV"]
+        if ext and stack and stack[-1] == "s":
+            choices += ["S_NEG"]
         if len(stack) >= 2 and stack[-1] == "v" and stack[-2] == "s":
             choices += ["SMUL"] * 3
         if stack and stack[-1] == "v":
@@ -113,8 +124,14 @@ def random_program(rng: random.Random, nvecs: int, nscal: int, max_len: int = 20
             prog.append(("VEC", rng.randrange(nvecs))); stack.append("v")
         elif op == "SCAL":
             prog.append(("SCAL", rng.randrange(nscal))); stack.append("s")
-        elif op in ("ADD", "SUB", "MUL"):
+        elif op == "DSCAL":
+            prog.append(("DSCAL", rng.randrange(ndscal))); stack.append("s")
+        elif op in ("ADD", "SUB", "MUL", "DIV"):
             prog.append((op, 0)); stack.pop()
+        elif op in ("S_ADD", "S_SUB", "S_MUL", "S_DIV"):
+            prog.append((op[2:], 0)); stack.pop()
+        elif op == "S_NEG":
+            prog.append(("NEG", 0))
         elif op == "SMUL":
             prog.append((op, 0)); stack.pop(); stack.pop(); stack.append("v")
         elif op == "NEG":
@@ -135,10 +152,10 @@ def random_program(rng: random.Random, nvecs: int, nscal: int, max_len: int = 20
             return prog
 
 
-def _check_against_exact(prog, vecs, scalars, dt, path):
+def _check_against_exact(prog, vecs, scalars, dt, path, dscalars=()):
     ours = [v.copy() for v in vecs]
-    red = oracle.eval_program(prog, ours, scalars, path=path)
-    want, red_exact, red_abs = exact.exact_program(prog, vecs, scalars, dt)
+    red = oracle.eval_program(prog, ours, scalars, path=path, dscalars=dscalars)
+    want, red_exact, red_abs = exact.exact_program(prog, vecs, scalars, dt, dscalars)
     for k, (got, w) in enumerate(zip(ours, want)):
         assert _eq_bits_or_nan(got.astype(np.float64), np.array(w, dtype=np.float64)), (prog, k)
     # Reductions: a sequential FP64 sum obeys |err| <= gamma_n sum|terms|
@@ -165,6 +182,155 @@ def check_brute_force_random_programs(path, count=60):
         vecs = [nrng.uniform(-1, 1, n).astype(dt) for _ in range(nvecs)]
         scalars = list(nrng.uniform(-2, 2, nscal))
         _check_against_exact(prog, vecs, scalars, dt, path)
+
+
+def _finite_exact(prog, vecs, scalars, dt, dscalars):
+    """True when exact evaluation stays finite (no zero denominator, no
+    overflow), i.e. when the rational reference is defined."""
+    try:
+        want, _, _ = exact.exact_program(prog, vecs, scalars, dt, dscalars)
+    except (ZeroDivisionError, OverflowError):
+        return False
+    return all(math.isfinite(t) for w in want for t in w)
+
+
+def check_brute_force_extended_programs(path, count=80):
+    """Random programs with elementwise DIV, scalar-typed nodes and device
+    scalars, on tiny n, against exact rational arithmetic with one rounding
+    per node (scalar nodes included: Section 4.2 init/load_once values are
+    computed once, in the program's dtype)."""
+    rng = random.Random(11)
+    nrng = np.random.default_rng(11)
+    checked = 0
+    for t in range(count):
+        dt = np.float64 if t % 2 == 0 else np.float32
+        nvecs = rng.randint(1, 5)
+        nscal = rng.randint(0, 3)
+        ndscal = rng.randint(1, 3)
+        prog = random_program(rng, nvecs, nscal, ndscal=ndscal, ext=True)
+        n = rng.choice([0, 1, 3, 8, 17, 33, 64])
+        # magnitudes in [0.5, 2): quotients of inputs stay in range
+        vecs = [(nrng.uniform(0.5, 2.0, n) * nrng.choice([-1.0, 1.0], n)).astype(dt)
+                for _ in range(nvecs)]
+        scalars = list(nrng.uniform(0.5, 2.0, nscal) * nrng.choice([-1.0, 1.0], nscal))
+        dscalars = list(nrng.uniform(0.5, 2.0, ndscal) * nrng.choice([-1.0, 1.0], ndscal))
+        if not _finite_exact(prog, vecs, scalars, dt, dscalars):
+            continue
+        _check_against_exact(prog, vecs, scalars, dt, path, dscalars)
+        checked += 1
+    assert checked >= count // 2, checked
+
+
+def check_div_exact(path):
+    """a / b with a = q * b for small integers q and b: the quotient is q
+    exactly (both operands and q representable, IEEE division correctly
+    rounded); and 1 / 3 is the correctly rounded third in each precision."""
+    rng = np.random.default_rng(12)
+    for dt in (np.float64, np.float32):
+        n = 333
+        q = rng.integers(-1000, 1000, n)
+        b = rng.integers(1, 1000, n) * rng.choice([-1, 1], n)
+        a = (q * b).astype(dt)
+        out = np.zeros(n, dtype=dt)
+        oracle.eval_program([("VEC", 0), ("VEC", 1), ("DIV", 0), ("STORE", 2)],
+                            [a, b.astype(dt), out], path=path)
+        assert np.array_equal(out.astype(np.int64), q), dt
+        ones = np.ones(4, dtype=dt)
+        threes = np.full(4, 3.0, dtype=dt)
+        oracle.eval_program([("VEC", 0), ("VEC", 1), ("DIV", 0), ("STORE", 2)],
+                            [ones, threes, out[:4]], path=path)
+        assert np.all(out[:4] == exact.round_to(Fraction(1, 3), dt)), dt
+
+
+def check_scalar_nodes(path):
+    """Scalar-typed nodes are one operation each, in the program's dtype,
+    with operands in postfix order: (s0 - s1), (s0 / s1), -(s0), (s0 * s1)
+    scaled onto a vector of ones; in FP32 the scalar node result is rounded
+    to float: 1 + 2^-24 rounds to 1 (ties to even), so the product with
+    1 + 2^-23 is 1 + 2^-23, where an unrounded FP64 scalar would give
+    1 + 2^-22."""
+    for dt in (np.float64, np.float32):
+        ones = np.ones(5, dtype=dt)
+        out = np.zeros(5, dtype=dt)
+        cases = [("SUB", 3.0, 1.0, 2.0), ("DIV", 1.0, 4.0, 0.25), ("MUL", -3.0, 0.5, -1.5),
+                 ("ADD", 1.25, 2.0, 3.25)]
+        for op, s0, s1, want in cases:
+            oracle.eval_program([("SCAL", 0), ("SCAL", 1), (op, 0), ("VEC", 0), ("SMUL", 0), ("STORE", 1)],
+                                [ones, out], [s0, s1], path=path)
+            assert np.all(out == want), (dt, op, out)
+            oracle.eval_program([("DSCAL", 0), ("DSCAL", 1), (op, 0), ("VEC", 0), ("SMUL", 0), ("STORE", 1)],
+                                [ones, out], dscalars=[s0, s1], path=path)
+            assert np.all(out == want), (dt, op, "dscal", out)
+        oracle.eval_program([("DSCAL", 1), ("NEG", 0), ("VEC", 0), ("SMUL", 0), ("STORE", 1)],
+                            [ones, out], dscalars=[7.0, 2.5], path=path)
+        assert np.all(out == -2.5), (dt, out)
+    v = np.full(3, 1.0 + 2.0 ** -23, dtype=np.float32)
+    out = np.zeros(3, dtype=np.float32)
+    oracle.eval_program([("SCAL", 0), ("SCAL", 1), ("ADD", 0), ("VEC", 0), ("SMUL", 0), ("STORE", 1)],
+                        [v, out], [1.0, 2.0 ** -24], path=path)
+    assert np.all(out == np.float32(1.0 + 2.0 ** -23)), out
+    # a device scalar is rounded to float once: 1 + 2^-24 + 2^-40 -> 1 + 2^-23
+    oracle.eval_program([("DSCAL", 0), ("VEC", 0), ("SMUL", 0), ("STORE", 1)],
+                        [np.ones(3, dtype=np.float32), out], dscalars=[1.0 + 2.0 ** -24 + 2.0 ** -40], path=path)
+    assert np.all(out == np.float32(1.0 + 2.0 ** -23)), out
+
+
+# Conjugate gradients (Hestenes-Stiefel) as three fused programs whose
+# scalars alpha = rho / (p.q) and beta = rho' / rho are scalar subtrees over
+# device-resident reduction results.  Slots: 0 d (diagonal of A), 1 p, 2 q,
+# 3 x, 4 r.
+CG_Q_PQ = [("VEC", 0), ("VEC", 1), ("MUL", 0), ("STORE", 2), ("VEC", 1), ("VEC", 2), ("DOT", 0)]
+CG_XR_RHO = [("VEC", 3), ("DSCAL", 0), ("DSCAL", 1), ("DIV", 0), ("VEC", 1), ("SMUL", 0), ("ADD", 0),
+             ("STORE", 3),
+             ("VEC", 4), ("DSCAL", 0), ("DSCAL", 1), ("DIV", 0), ("VEC", 2), ("SMUL", 0), ("SUB", 0),
+             ("STORE", 4),
+             ("VEC", 4), ("SUMSQ", 0)]
+CG_P = [("VEC", 4), ("DSCAL", 0), ("DSCAL", 1), ("DIV", 0), ("VEC", 1), ("SMUL", 0), ("ADD", 0),
+        ("STORE", 1)]
+
+
+def cg_diagonal(evalp, d, b, iters):
+    """Runs ``iters`` CG iterations for diag(d) x = b from x = 0 with the
+    three programs above through ``evalp(prog, vecs, dscalars)``; returns x
+    and the residual norms sqrt(rho_k)."""
+    dt = d.dtype
+    n = d.shape[0]
+    p, q, x, r = b.copy(), np.zeros(n, dt), np.zeros(n, dt), b.copy()
+    vecs = [d, p, q, x, r]
+    rho = evalp([("VEC", 4), ("SUMSQ", 0)], vecs, [])[0]
+    hist = [math.sqrt(rho)]
+    for _ in range(iters):
+        pq = evalp(CG_Q_PQ, vecs, [])[0]
+        rho_new = evalp(CG_XR_RHO, vecs, [rho, pq])[0]
+        evalp(CG_P, vecs, [rho_new, rho])
+        rho = rho_new
+        hist.append(math.sqrt(rho))
+    return x, hist
+
+
+def check_cg_distinct_eigenvalues(path):
+    """CG on an SPD matrix with k distinct eigenvalues reaches the solution
+    in at most k iterations in exact arithmetic (Hestenes and Stiefel 1952;
+    Nocedal and Wright, Numerical Optimization, Thm. 5.4).  A diagonal A
+    with k = 4 distinct entries in [1, 8]: after 4 iterations x equals b / d
+    to a few ulps of the condition number, while after 3 it does not."""
+    rng = np.random.default_rng(13)
+
+    def evalp(prog, vecs, ds):
+        return oracle.eval_program(prog, vecs, dscalars=ds, path=path)
+
+    for dt, tol in ((np.float64, 1e-13), (np.float32, 2e-6)):
+        n = 1001
+        d = rng.choice([1.0, 2.0, 5.0, 8.0], n).astype(dt)
+        b = rng.uniform(-1, 1, n).astype(dt)
+        xs = b.astype(np.float64) / d.astype(np.float64)
+        x3, _ = cg_diagonal(evalp, d, b, 3)
+        x4, hist = cg_diagonal(evalp, d, b, 4)
+        err3 = np.linalg.norm(x3 - xs) / np.linalg.norm(xs)
+        err4 = np.linalg.norm(x4 - xs) / np.linalg.norm(xs)
+        assert err4 < tol, (dt, err4)
+        assert err3 > 1e-3, (dt, err3)
+        assert hist[-1] < tol * hist[0], (dt, hist)
 
 
 def check_tail_lengths(path):
@@ -225,11 +391,15 @@ def check_invalid_programs(path):
         [("VEC", 0), ("VEC", 0)],  # leftover stack
         [("VEC", 5), ("STORE", 0)],  # vector index out of range
         [("SCAL", 0), ("STORE", 0)],  # storing a scalar
+        [("VEC", 0), ("SCAL", 0), ("ADD", 0), ("STORE", 0)],  # vector + scalar
+        [("SCAL", 0), ("VEC", 0), ("DIV", 0), ("STORE", 0)],  # scalar / vector
+        [("DSCAL", 2), ("VEC", 0), ("SMUL", 0), ("STORE", 0)],  # device scalar out of range
+        [("DSCAL", 0), ("SUMSQ", 0)],  # reduction of a scalar
     ]
     for prog in bad:
         v = [np.zeros(4), np.zeros(4)]
         try:
-            oracle.eval_program(prog, v, [1.0], path=path)
+            oracle.eval_program(prog, v, [1.0], path=path, dscalars=[1.0, 2.0])
         except oracle.OracleProgramError:
             continue
         raise AssertionError(f"accepted invalid program {prog}")
@@ -300,6 +470,10 @@ ALL_CHECKS = [
     check_d_integer_identity,
     check_e_and_axpby_exact,
     check_brute_force_random_programs,
+    check_brute_force_extended_programs,
+    check_div_exact,
+    check_scalar_nodes,
+    check_cg_distinct_eigenvalues,
     check_tail_lengths,
     check_cg_store_then_load,
     check_special_values,

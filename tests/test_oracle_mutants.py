@@ -39,6 +39,15 @@ MUTANTS = [
     ("nrm2_f64_scale_sign", "return ldexp(sqrt(acc), e);", 0, "return ldexp(sqrt(acc), -e);"),
     ("nrm2_f64_no_scaling", "double t = ldexp(x[i], -e);", 0, "double t = x[i]; e = 0;"),
     ("nrm2_f32_no_sqrt", "  return sqrt(acc);\n}", 0, "  return acc;\n}"),
+    ("f64_div_swapped", "t[i] = a[i] / b[i];", 0, "t[i] = b[i] / a[i];"),
+    ("f32_div_is_mul", "t[i] = a[i] / b[i];", 1, "t[i] = a[i] * b[i];"),
+    ("f64_scalar_sub_swapped", "else if (op == OR_SUB) r = a - b;", 0, "else if (op == OR_SUB) r = b - a;"),
+    ("f32_scalar_div_inverted", "else r = a / b;", 1, "else r = b / a;"),
+    ("f32_scalar_add_wrong_operand", "if (op == OR_ADD) r = a + b;", 1, "if (op == OR_ADD) r = a + a;"),
+    ("f64_dscal_wrong_index", "st[sp].s = dscal[k];", 0, "st[sp].s = dscal[0];"),
+    ("f32_dscal_reads_scal", "st[sp].s = (float)dscal[k];", 0, "st[sp].s = (float)scal[k];"),
+    ("f64_scalar_neg_noop", "st[sp - 1].s = -st[sp - 1].s;", 0, "st[sp - 1].s = st[sp - 1].s;"),
+    ("f32_scalar_neg_noop", "st[sp - 1].s = -st[sp - 1].s;", 1, "st[sp - 1].s = st[sp - 1].s;"),
 ]
 
 
