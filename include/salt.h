@@ -79,19 +79,30 @@ typedef enum {
  *            STORE k earlier in the program it reads the stored value)
  *   SCAL k   push scalar operand k (a loop constant: the paper's
  *            load_once/TemporaryStorage, Section 4.2)
+ *   DSCAL k  push device scalar k: the double at dscalars[k] in device
+ *            memory (salt_eval_ex), read when the kernel starts
  *   ADD      pop b, pop a, push a + b        (ExprAdd, Figure 1)
  *   SUB      pop b, pop a, push a - b        (ExprSub, Figure 1)
  *   MUL      pop b, pop a, push a * b        (elementwise product)
+ *   DIV      pop b, pop a, push a / b        (elementwise quotient)
  *   SMUL     pop v (vector), pop s (scalar), push s * v   (xSCAL / xAXPY)
  *   NEG      pop a, push -a
  *   STORE k  pop a, assign it to vector k   (Store root, Figure 1)
  *   DOT      pop b, pop a, accumulate sum_i a_i * b_i into the next result
  *   SUMSQ    pop a, accumulate sum_i a_i * a_i into the next result
- * Every node computes in the program's dtype, round-to-nearest-even, with no
- * fused multiply-add, in exactly this order: elementwise results are
- * bit-identical to evaluating the tree one node at a time.  Scalars are given
- * as double and rounded once to float for an F32 program.  Reductions: see
- * salt_dot. */
+ * ADD, SUB, MUL, DIV and NEG take two vectors (one vector for NEG) or two
+ * scalars (one scalar): a scalar subexpression such as (DSCAL0 DSCAL1 DIV)
+ * does not depend on the element, so, like the paper's init / load_once
+ * values (Section 4.2), it is computed once per launch -- on the host when
+ * it reads only SCAL operands, else by the kernel before its loop -- and
+ * equal subexpressions are computed once.  The scalar slots after this
+ * hoisting (SCAL operands plus distinct subexpressions) must not exceed
+ * SALT_MAX_SCALS.
+ * Every node, scalar nodes included, computes in the program's dtype,
+ * round-to-nearest-even, with no fused multiply-add, in exactly this order:
+ * elementwise results are bit-identical to evaluating the tree one node at a
+ * time.  Scalars (SCAL and DSCAL) are doubles, rounded once to float for an
+ * F32 program.  Reductions: see salt_dot. */
 typedef enum {
   SALT_OP_VEC = 0,
   SALT_OP_SCAL = 1,
@@ -102,12 +113,14 @@ typedef enum {
   SALT_OP_NEG = 6,
   SALT_OP_STORE = 7,
   SALT_OP_DOT = 8,
-  SALT_OP_SUMSQ = 9
+  SALT_OP_SUMSQ = 9,
+  SALT_OP_DIV = 10,
+  SALT_OP_DSCAL = 11
 } salt_opcode;
 
 typedef struct {
   uint8_t op;  /* salt_opcode                                   */
-  uint8_t arg; /* operand index for VEC / SCAL / STORE, else 0  */
+  uint8_t arg; /* operand index for VEC / SCAL / DSCAL / STORE, else 0 */
 } salt_insn;
 
 #define SALT_MAX_PROG 32  /* instructions per program       */
@@ -115,6 +128,7 @@ typedef struct {
 #define SALT_MAX_SCALS 8  /* scalar operands per program    */
 #define SALT_MAX_STACK 8  /* evaluation stack depth         */
 #define SALT_MAX_REDS 4   /* DOT / SUMSQ results per program */
+#define SALT_MAX_DSCALS 8 /* device scalars per program     */
 
 /* Reduction flags. */
 #define SALT_DEFAULT 0
@@ -133,16 +147,20 @@ const char* salt_last_error(void);
 
 /* ---------------------------------------------------------------------------
  * salt_check_program -- host-only validation and typing of a program
- * (no GPU needed).  Checks opcodes, operand indices against nvecs / nscal,
- * operand types (ADD/SUB/MUL/DOT take two vectors, SMUL a scalar below a
- * vector, NEG/STORE/SUMSQ a vector), stack depth <= SALT_MAX_STACK, an empty
- * stack at the end, at least one STORE or reduction, <= SALT_MAX_REDS
- * reductions.
+ * (no GPU needed).  Checks opcodes, operand indices against nvecs / nscal
+ * (DSCAL indices against SALT_MAX_DSCALS; salt_eval_ex checks them against
+ * its ndscal), operand types (ADD/SUB/MUL/DIV take two vectors or two
+ * scalars, NEG one of either, DOT two vectors, SMUL a scalar below a vector,
+ * STORE/SUMSQ a vector), stack depth <= SALT_MAX_STACK, an empty stack at
+ * the end, at least one STORE or reduction, <= SALT_MAX_REDS reductions, and
+ * <= SALT_MAX_SCALS scalar slots after hoisting.
  * Outputs (any may be NULL):
  *   nred_out      number of DOT/SUMSQ results,
- *   compiled_out  1 if the program has a compile-time instantiation (the
+ *   compiled_out  1 if the program (after hoisting its scalar
+ *                 subexpressions) has a compile-time instantiation (the
  *                 fast path; the paper's expression templates, Section 2),
- *                 0 if it runs on the generic interpreter kernel.
+ *                 0 if it runs on the generic interpreter kernel (or, with
+ *                 SALT_JIT_ON, a run-time compiled one).
  * Returns SALT_OK or SALT_ERR_PROGRAM / SALT_ERR_ARG. */
 salt_status salt_check_program(const salt_insn* prog, int32_t nprog, int32_t nvecs,
                                int32_t nscal, int32_t* nred_out, int32_t* compiled_out);
@@ -178,6 +196,41 @@ salt_status salt_eval(const salt_insn* prog, int32_t nprog, int32_t dtype, int64
 salt_status salt_eval_strided(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
                               void* const* vecs, const int64_t* strides, int32_t nvecs, const double* scalars,
                               int32_t nscal, double* red_out, void* stream);
+
+/* salt_eval with DEVICE-RESIDENT scalars (and optional strides): the DSCAL k
+ * nodes of `prog` read the double at dscalars[k], a host array of ndscal
+ * (<= SALT_MAX_DSCALS) device pointers, each 8-byte aligned.  The value is
+ * read when the kernel starts, in stream order, so a reduction result that
+ * an earlier call on the same stream wrote (a DOT / SUMSQ red_out) can
+ * steer this call without the host reading it: e.g. conjugate gradients'
+ * alpha = rho / (p . q) as  DSCAL0 DSCAL1 DIV  (Hestenes and Stiefel 1952).
+ * A device scalar must not lie in memory the same call writes (a stored
+ * vector or red_out): SALT_ERR_ALIAS.  strides may be NULL (contiguous) or
+ * as salt_eval_strided.  Not part of the paper, whose scalars are host
+ * values; with ndscal == 0 this is salt_eval / salt_eval_strided.
+ * Errors as salt_eval. */
+salt_status salt_eval_ex(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                         void* const* vecs, const int64_t* strides, int32_t nvecs, const double* scalars,
+                         int32_t nscal, const double* const* dscalars, int32_t ndscal, double* red_out,
+                         void* stream);
+
+/* salt_explain -- host only (no GPU): the program the kernels evaluate for
+ * `prog`, after its scalar subexpressions are hoisted, with the values of
+ * the scalar slots.  Not part of the paper; an inspection aid.
+ *   dtype              SALT_F32 or SALT_F64 (the precision of scalar nodes)
+ *   scalars, nscal     by-value scalars, as for salt_eval
+ *   dvals, ndscal      host values standing in for the device scalars
+ *   out, nout          receives the hoisted program (<= nprog insns; SCAL k
+ *                      with k >= nscal names a hoisted subexpression)
+ *   slots, nslots      receives the slot values (<= SALT_MAX_SCALS): the
+ *                      nscal user scalars, then each hoisted subexpression
+ *                      computed on the host, one operation per node in dtype
+ *   compiled_out       (may be NULL) as salt_check_program
+ * For a program without DSCAL these are exactly the program and scalars
+ * salt_eval launches.  Errors: as salt_check_program, SALT_ERR_DTYPE. */
+salt_status salt_explain(const salt_insn* prog, int32_t nprog, int32_t dtype, int32_t nvecs, const double* scalars,
+                         int32_t nscal, const double* dvals, int32_t ndscal, salt_insn* out, int32_t* nout,
+                         double* slots, int32_t* nslots, int32_t* compiled_out);
 
 /* ---------------------------------------------------------------------------
  * salt_axpby -- y <- alpha*x + beta*y (Section 5's xAXPY generalised; xSCAL

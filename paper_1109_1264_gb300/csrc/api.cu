@@ -190,7 +190,8 @@ static salt_status check_dtype(int32_t dt) {
 
 // ------------------------------------------------------------ execution ---
 template <typename T>
-static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, const DevInfo& info) {
+static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarCode* scode, int dev,
+                            const DevInfo& info) {
   Registry& reg = registry();
   const int shape = find_shape(c);
   const int dt = sizeof(T) == 4 ? DT_F32 : DT_F64;
@@ -217,6 +218,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, cons
       p.stride[k] = a.strides ? a.strides[c.vec_user[k]] : 1;
     }
     for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
+    if (scode) p.scode = *scode;
     p.n = a.n;
     p.red_out = a.red_out;
     p.partials = ws.partials;
@@ -227,7 +229,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, cons
       ke = &reg.strided[shape][dt];
       kern = ke->kernel;
     } else {
-      salt_status st = jit_kernel(c, sizeof(T) == 4, kElemUnroll, 0, &kern);
+      salt_status st = jit_kernel(c, sizeof(T) == 4, kElemUnroll, 0, false, &kern);
       if (st != SALT_OK) return st;
     }
     const int block = 256;
@@ -249,7 +251,9 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, cons
   if (shape >= 0) {
     salt_launch_cfg cfg = lookup_cfg(shape, dt, a.n);
     if (cfg.vec_bytes == 32 && !all32) cfg.vec_bytes = 16;
-    const KernelEntry& ke = reg.fused[shape][dt][unroll_index(cfg.unroll)][vb_index(cfg.vec_bytes)];
+    if (scode) cfg.unroll = kDsUnroll<T>;  // one unroll per device-scalar instantiation
+    const KernelEntry& ke = scode ? reg.fused_ds[shape][dt][vb_index(cfg.vec_bytes)]
+                                  : reg.fused[shape][dt][unroll_index(cfg.unroll)][vb_index(cfg.vec_bytes)];
     int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy_blocks(ke.kernel, cfg.block, 0);
     if (bps > kMaxBlocksPerSM) bps = kMaxBlocksPerSM;
     const int64_t vec = cfg.vec_bytes / (int64_t)sizeof(T);
@@ -258,6 +262,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, cons
     memset(&p, 0, sizeof p);
     for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]];
     for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
+    if (scode) p.scode = *scode;
     p.n = a.n;
     p.red_out = a.red_out;
     p.partials = ws.partials;
@@ -275,7 +280,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, cons
     const int unroll = sizeof(T) == 4 ? 4 : 2;
     const int vb = all32 ? 32 : 16;
     const void* k = nullptr;
-    salt_status st = jit_kernel(c, sizeof(T) == 4, unroll, vb, &k);
+    salt_status st = jit_kernel(c, sizeof(T) == 4, unroll, vb, scode != nullptr, &k);
     if (st != SALT_OK) return st;
     const int block = 256;
     int bps = occupancy_blocks(k, block, 0);
@@ -286,6 +291,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, cons
     memset(&p, 0, sizeof p);
     for (int j = 0; j < c.nvec; ++j) p.v[j] = (T*)a.vecs[c.vec_user[j]];
     for (int j = 0; j < c.nscal; ++j) p.sc[j] = (T)a.scalars[c.scal_user[j]];
+    if (scode) p.scode = *scode;
     p.n = a.n;
     p.red_out = a.red_out;
     p.partials = ws.partials;
@@ -311,6 +317,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, int dev, cons
   for (int k = 0; k < c.nvec; ++k) p.stride[k] = a.strides ? a.strides[c.vec_user[k]] : 1;
   for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]];
   for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
+  if (scode) p.scode = *scode;
   p.n = a.n;
   p.red_out = a.red_out;
   p.partials = ws.partials;
@@ -339,10 +346,23 @@ salt_status validate_eval(const EvalArgs& a, Analysis* an_out) {
   if (a.n < 0) return set_error(SALT_ERR_ARG, "n must be >= 0");
   Analysis an;
   std::string err;
-  st = analyse(a.prog, a.nprog, a.nvecs, a.nscal, &an, &err);
+  st = analyse(a.prog, a.nprog, a.nvecs, a.nscal, &an, &err, a.ndscal);
   if (st != SALT_OK) return set_error(st, err);
   if (an.used_vecs && !a.vecs) return set_error(SALT_ERR_ARG, "vecs is NULL");
   if (an.used_scals && !a.scalars) return set_error(SALT_ERR_ARG, "scalars is NULL");
+  if (an.used_dscals && !a.dscal) return set_error(SALT_ERR_ARG, "dscalars is NULL");
+  for (int k = 0; k < a.ndscal; ++k) {
+    if (!((an.used_dscals >> k) & 1u)) continue;
+    char b[128];
+    if (!a.dscal[k]) {
+      snprintf(b, sizeof b, "device scalar %d is NULL", k);
+      return set_error(SALT_ERR_ARG, b);
+    }
+    if (!aligned(a.dscal[k], 8)) {
+      snprintf(b, sizeof b, "device scalar %d is not 8-byte aligned", k);
+      return set_error(SALT_ERR_ALIGN, b);
+    }
+  }
   if (an.nred > 0 && !a.red_out) return set_error(SALT_ERR_ARG, "red_out is NULL but the program reduces");
   if (a.red_out && !aligned(a.red_out, 8)) return set_error(SALT_ERR_ALIGN, "red_out must be 8-byte aligned");
   const size_t es = a.dt == SALT_F32 ? 4 : 8;
@@ -385,6 +405,25 @@ salt_status validate_eval(const EvalArgs& a, Analysis* an_out) {
       }
     }
   }
+  // A device scalar is read when each block starts, while other blocks may
+  // already be storing vectors or the last block writing red_out: it must
+  // not lie in memory this call writes.
+  for (int k = 0; k < a.ndscal; ++k) {
+    if (!((an.used_dscals >> k) & 1u)) continue;
+    const uintptr_t q = (uintptr_t)a.dscal[k];
+    bool hit = a.red_out && an.nred > 0 && q + 8 > (uintptr_t)a.red_out &&
+               q < (uintptr_t)a.red_out + 8 * (uintptr_t)an.nred;
+    for (int i = 0; i < a.nvecs && !hit; ++i) {
+      if (!((an.stored_vecs >> i) & 1u)) continue;
+      const uintptr_t pi = (uintptr_t)a.vecs[i], bi = extent(i);
+      hit = bi > 0 && q + 8 > pi && q < pi + bi;
+    }
+    if (hit) {
+      char b[128];
+      snprintf(b, sizeof b, "device scalar %d lies in memory that the call writes", k);
+      return set_error(SALT_ERR_ALIAS, b);
+    }
+  }
   *an_out = an;
   return SALT_OK;
 }
@@ -397,6 +436,12 @@ salt_status eval_impl(const EvalArgs& a) {
   DevInfo info;
   st = device_info(&dev, &info);
   if (st != SALT_OK) return st;
+  Hoisted h;
+  if (an.scalar_nodes) {
+    std::string err;
+    st = hoist_scalars(a.prog, a.nprog, a.nscal, &h, &err);
+    if (st != SALT_OK) return set_error(st, err);
+  }
   if (a.n == 0) {
     if (an.nred > 0) {
       cudaError_t e = cudaMemsetAsync(a.red_out, 0, sizeof(double) * an.nred, a.stream);
@@ -404,9 +449,58 @@ salt_status eval_impl(const EvalArgs& a) {
     }
     return SALT_OK;
   }
+  if (!an.scalar_nodes) {
+    Canonical c;
+    canonicalise(a.prog, a.nprog, &c);
+    return a.dt == SALT_F32 ? run_eval<float>(a, c, nullptr, dev, info)
+                            : run_eval<double>(a, c, nullptr, dev, info);
+  }
+  // Scalar subexpressions: each became one scalar slot, computed here when
+  // it reads only by-value scalars, else at kernel start on the device.
+  double sc2[kMaxScals] = {};
+  for (int k = 0; k < a.nscal; ++k) sc2[k] = a.scalars ? a.scalars[k] : 0.0;
+  if (!h.device) {
+    for (int j = 0; j < h.nhoist; ++j)
+      sc2[a.nscal + j] = a.dt == SALT_F32 ? host_scalar_value_f32(a.prog, h, j, sc2)
+                                          : host_scalar_value_f64(a.prog, h, j, sc2);
+  }
+  EvalArgs a2 = a;
+  a2.prog = h.prog;
+  a2.nprog = h.nprog;
+  a2.scalars = sc2;
+  a2.nscal = h.nscal;
   Canonical c;
-  canonicalise(a.prog, a.nprog, &c);
-  return a.dt == SALT_F32 ? run_eval<float>(a, c, dev, info) : run_eval<double>(a, c, dev, info);
+  canonicalise(h.prog, h.nprog, &c);
+  ScalarCode code;
+  if (h.device && !build_scalar_code(a.prog, h, c, a.nscal, sc2, a.dscal, &code))
+    return set_error(SALT_ERR_PROGRAM, "scalar subexpressions too long for the device scalar code");
+  const ScalarCode* pc = h.device ? &code : nullptr;
+  return a.dt == SALT_F32 ? run_eval<float>(a2, c, pc, dev, info) : run_eval<double>(a2, c, pc, dev, info);
+}
+
+// Canonical form of a program after hoisting its scalar subexpressions (the
+// form that selects the kernel).  Call after analyse() succeeded.
+static salt_status canonical_hoisted(const salt_insn* prog, int nprog, int nscal, const Analysis& an,
+                                     Canonical* c) {
+  if (!an.scalar_nodes) {
+    canonicalise(prog, nprog, c);
+    return SALT_OK;
+  }
+  Hoisted h;
+  std::string err;
+  salt_status st = hoist_scalars(prog, nprog, nscal, &h, &err);
+  if (st != SALT_OK) return set_error(st, err);
+  canonicalise(h.prog, h.nprog, c);
+  return SALT_OK;
+}
+
+// Scalar operands a program names (highest SCAL index + 1), for calls that
+// take no nscal.
+static int scal_count(const salt_insn* prog, int nprog) {
+  int n = 0;
+  for (int pc = 0; prog && pc < nprog && pc < kMaxProg; ++pc)
+    if (prog[pc].op == OP_SCAL && prog[pc].arg + 1 > n) n = prog[pc].arg + 1;
+  return n > kMaxScals ? kMaxScals : n;
 }
 
 // Reductions with their own kernels (nrm2, plain F32 dot).
@@ -483,14 +577,13 @@ salt_status salt_check_program(const salt_insn* prog, int32_t nprog, int32_t nve
                                int32_t* nred_out, int32_t* compiled_out) {
   Analysis an;
   std::string err;
-  salt_status st = analyse(prog, nprog, nvecs, nscal, &an, &err);
+  salt_status st = analyse(prog, nprog, nvecs, nscal, &an, &err, kMaxDscals);
   if (st != SALT_OK) return set_error(st, err);
+  Canonical c;
+  st = canonical_hoisted(prog, nprog, nscal, an, &c);
+  if (st != SALT_OK) return st;
   if (nred_out) *nred_out = an.nred;
-  if (compiled_out) {
-    Canonical c;
-    canonicalise(prog, nprog, &c);
-    *compiled_out = find_shape(c) >= 0 ? 1 : 0;
-  }
+  if (compiled_out) *compiled_out = find_shape(c) >= 0 ? 1 : 0;
   return SALT_OK;
 }
 
@@ -506,6 +599,54 @@ salt_status salt_eval_strided(const salt_insn* prog, int32_t nprog, int32_t dtyp
                               int32_t nscal, double* red_out, void* stream) {
   if (!strides && nvecs > 0) return set_error(SALT_ERR_ARG, "strides is NULL");
   EvalArgs a{prog, nprog, dtype, n, vecs, nvecs, scalars, nscal, red_out, (cudaStream_t)stream, strides};
+  return eval_impl(a);
+}
+
+salt_status salt_explain(const salt_insn* prog, int32_t nprog, int32_t dtype, int32_t nvecs, const double* scalars,
+                         int32_t nscal, const double* dvals, int32_t ndscal, salt_insn* out, int32_t* nout,
+                         double* slots, int32_t* nslots, int32_t* compiled_out) {
+  salt_status st = check_dtype(dtype);
+  if (st != SALT_OK) return st;
+  Analysis an;
+  std::string err;
+  st = analyse(prog, nprog, nvecs, nscal, &an, &err, ndscal);
+  if (st != SALT_OK) return set_error(st, err);
+  if (an.used_scals && !scalars) return set_error(SALT_ERR_ARG, "scalars is NULL");
+  if (an.used_dscals && !dvals) return set_error(SALT_ERR_ARG, "dvals is NULL");
+  if (!out || !nout || !slots || !nslots) return set_error(SALT_ERR_ARG, "an output pointer is NULL");
+  Hoisted h;
+  if (an.scalar_nodes) {
+    st = hoist_scalars(prog, nprog, nscal, &h, &err);
+    if (st != SALT_OK) return set_error(st, err);
+  } else {
+    for (int pc = 0; pc < nprog; ++pc) h.prog[pc] = prog[pc];
+    h.nprog = nprog;
+    h.nscal = nscal;
+  }
+  double sc2[kMaxScals] = {};
+  for (int k = 0; k < nscal; ++k) sc2[k] = scalars ? scalars[k] : 0.0;
+  for (int j = 0; j < h.nhoist; ++j)
+    sc2[nscal + j] = dtype == SALT_F32 ? host_scalar_value_f32(prog, h, j, sc2, dvals)
+                                       : host_scalar_value_f64(prog, h, j, sc2, dvals);
+  for (int pc = 0; pc < h.nprog; ++pc) out[pc] = h.prog[pc];
+  *nout = h.nprog;
+  for (int k = 0; k < h.nscal; ++k) slots[k] = sc2[k];
+  *nslots = h.nscal;
+  if (compiled_out) {
+    Canonical c;
+    canonicalise(h.prog, h.nprog, &c);
+    *compiled_out = find_shape(c) >= 0 ? 1 : 0;
+  }
+  return SALT_OK;
+}
+
+salt_status salt_eval_ex(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                         void* const* vecs, const int64_t* strides, int32_t nvecs, const double* scalars,
+                         int32_t nscal, const double* const* dscalars, int32_t ndscal, double* red_out,
+                         void* stream) {
+  EvalArgs a{prog, nprog, dtype, n, vecs, nvecs, scalars, nscal, red_out, (cudaStream_t)stream, strides};
+  a.dscal = dscalars;
+  a.ndscal = ndscal;
   return eval_impl(a);
 }
 
@@ -625,13 +766,14 @@ salt_status salt_release_workspaces(void) {
   return st;
 }
 
-static salt_status tune_family(const salt_insn* prog, int32_t nprog, int* family) {
+static salt_status tune_family(const salt_insn* prog, int32_t nprog, int32_t nscal, int* family) {
   Analysis an;
   std::string err;
-  salt_status st = analyse(prog, nprog, kMaxVecs, kMaxScals, &an, &err);
+  salt_status st = analyse(prog, nprog, kMaxVecs, nscal, &an, &err, kMaxDscals);
   if (st != SALT_OK) return set_error(st, err);
   Canonical c;
-  canonicalise(prog, nprog, &c);
+  st = canonical_hoisted(prog, nprog, nscal, an, &c);
+  if (st != SALT_OK) return st;
   const int s = find_shape(c);
   *family = s >= 0 ? s : 200;
   return SALT_OK;
@@ -643,7 +785,7 @@ salt_status salt_tune_set(const salt_insn* prog, int32_t nprog, int32_t dtype, i
   if (st != SALT_OK) return st;
   if (!cfg || !cfg_valid(*cfg)) return set_error(SALT_ERR_ARG, "invalid launch configuration");
   int fam = 0;
-  st = tune_family(prog, nprog, &fam);
+  st = tune_family(prog, nprog, scal_count(prog, nprog), &fam);
   if (st != SALT_OK) return st;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[TuneKey(fam, dtype == SALT_F32 ? DT_F32 : DT_F64, bucket_of(n))] = *cfg;
@@ -656,7 +798,7 @@ salt_status salt_tune_get(const salt_insn* prog, int32_t nprog, int32_t dtype, i
   if (st != SALT_OK) return st;
   if (!cfg) return set_error(SALT_ERR_ARG, "cfg is NULL");
   int fam = 0;
-  st = tune_family(prog, nprog, &fam);
+  st = tune_family(prog, nprog, scal_count(prog, nprog), &fam);
   if (st != SALT_OK) return st;
   *cfg = lookup_cfg(fam, dtype == SALT_F32 ? DT_F32 : DT_F64, n);
   return SALT_OK;
@@ -682,7 +824,7 @@ salt_status salt_autotune(int32_t kernel, const salt_insn* prog, int32_t nprog, 
       EvalArgs a{prog, nprog, dtype, n, vecs, nvecs, scalars, nscal, red_out, s};
       st = validate_eval(a, &an);
       if (st != SALT_OK) return st;
-      st = tune_family(prog, nprog, &family);
+      st = tune_family(prog, nprog, nscal, &family);
       if (st != SALT_OK) return st;
       break;
     }

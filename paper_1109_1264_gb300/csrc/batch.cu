@@ -299,6 +299,23 @@ salt_status salt_batch_add(salt_batch* b, const salt_insn* prog, int32_t nprog, 
   a.red_out = dummy_red;
   salt_status st = validate_eval(a, &an);
   if (st != SALT_OK) return st;
+  // Scalar subexpressions (by-value scalars only: a batch takes no device
+  // scalars) are computed here; the item carries the hoisted program.
+  Hoisted h;
+  double sc2[kMaxScals] = {};
+  if (an.scalar_nodes) {
+    std::string err;
+    st = hoist_scalars(prog, nprog, nscal, &h, &err);
+    if (st != SALT_OK) return fail(st, err);
+    for (int k = 0; k < nscal; ++k) sc2[k] = scalars[k];
+    for (int j = 0; j < h.nhoist; ++j)
+      sc2[nscal + j] = dtype == SALT_F32 ? host_scalar_value_f32(prog, h, j, sc2)
+                                         : host_scalar_value_f64(prog, h, j, sc2);
+    prog = h.prog;
+    nprog = h.nprog;
+    nscal = h.nscal;
+    scalars = sc2;
+  }
   Canonical c;
   canonicalise(prog, nprog, &c);
   const int shape = find_shape(c);

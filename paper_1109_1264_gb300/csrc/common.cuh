@@ -29,12 +29,82 @@ template <> struct Arith<float> {
   static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
 };
 template <> struct Arith<double> {
   static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
 };
+
+// ---------------------------------------------------------------------------
+// Scalar subexpressions (the paper's init / load_once values, Section 4.2:
+// computed once per loop, not per element).  The host replaces every scalar
+// subtree of a program by one scalar slot.  When the subtree reads a scalar
+// that lives in device memory, its value is computed on the device at kernel
+// start by this small stack code, one operation per node in T, and written
+// to the slot; otherwise the host computes it the same way before launch.
+enum : uint8_t { S_SC = 0, S_DS, S_ADD, S_SUB, S_MUL, S_DIV, S_NEG, S_OUT };
+constexpr int kMaxScalarCode = 48;
+struct ScalarCode {
+  int32_t len;                   // instructions; 0: every slot is passed by value
+  uint8_t code[kMaxScalarCode];  // op * 16 + arg
+  double cval[kMaxScals];        // S_SC k pushes cval[k] rounded to T
+  const double* ds[kMaxDscals];  // S_DS k pushes *ds[k] rounded to T
+};
+
+// Runs `c` in one thread with its stack and slots in shared memory (no
+// local memory); S_OUT k pops into sc[k].  The host validated the code, so
+// the stack stays within kMaxStack; the bound checks only keep a malformed
+// code inside the arrays.
+template <typename T>
+__device__ __forceinline__ void run_scalar_code(const ScalarCode& c, T* st, T* sc) {
+  int sp = 0;
+  for (int pc = 0; pc < c.len && pc < kMaxScalarCode; ++pc) {
+    const int op = c.code[pc] >> 4, k = c.code[pc] & 15;
+    if (op == S_SC || op == S_DS) {
+      if (sp > kMaxStack || k >= kMaxScals) return;
+      st[sp++] = op == S_SC ? (T)c.cval[k] : (T)(*c.ds[k]);
+    } else if (op == S_NEG) {
+      if (sp < 1) return;
+      st[sp - 1] = -st[sp - 1];
+    } else if (op == S_OUT) {
+      if (sp < 1 || k >= kMaxScals) return;
+      sc[k] = st[--sp];
+    } else {
+      if (sp < 2) return;
+      const T a = st[sp - 2], b = st[sp - 1];
+      st[sp - 2] = op == S_ADD ? Arith<T>::add(a, b)
+                 : op == S_SUB ? Arith<T>::sub(a, b)
+                 : op == S_MUL ? Arith<T>::mul(a, b)
+                               : Arith<T>::div(a, b);
+      --sp;
+    }
+  }
+}
+
+// The scalar slots of a launch: the by-value slots `psc`, with the slots
+// that `c` computes overwritten (thread 0 evaluates, the block shares the
+// values through shared memory).  Uniform branch when len == 0.
+template <typename T>
+__device__ __forceinline__ void load_scalars(const T (&psc)[kMaxScals], const ScalarCode& c,
+                                             T (&sc)[kMaxScals]) {
+#pragma unroll
+  for (int k = 0; k < kMaxScals; ++k) sc[k] = psc[k];
+  if (c.len > 0) {
+    __shared__ T s_sc[kMaxScals];
+    __shared__ T s_st[kMaxStack + 1];
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < kMaxScals; ++k) s_sc[k] = psc[k];
+      run_scalar_code<T>(c, s_st, s_sc);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kMaxScals; ++k) sc[k] = s_sc[k];
+  }
+}
 
 // ---------------------------------------------------------------------------
 // The vectorizer: VB-byte vectors of T (VB = 16 or 32).  32-byte accesses are

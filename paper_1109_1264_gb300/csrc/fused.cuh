@@ -22,6 +22,7 @@ struct MapParams {
   void* partials;       // workspace: gridDim.x * NR values
   unsigned* ticket;     // workspace: zero between launches
   int64_t stride[kMaxVecs];  // element strides (strided_kernel only)
+  ScalarCode scode;          // scalar slots computed on the device (len 0: none)
 };
 
 // Per-element evaluation of program P: node I at compile-time stack depth.
@@ -40,6 +41,8 @@ __device__ __forceinline__ void exec_node(T (&st)[kMaxStack + 1], T (&v)[kMaxVec
       st[d - 2] = Arith<T>::sub(st[d - 2], st[d - 1]);
     } else if constexpr (op == OP_MUL || op == OP_SMUL) {
       st[d - 2] = Arith<T>::mul(st[d - 2], st[d - 1]);
+    } else if constexpr (op == OP_DIV) {
+      st[d - 2] = Arith<T>::div(st[d - 2], st[d - 1]);
     } else if constexpr (op == OP_NEG) {
       st[d - 1] = -st[d - 1];
     } else if constexpr (op == OP_STORE) {
@@ -76,7 +79,11 @@ __device__ __forceinline__ void exec_chunk(T (&x)[kMaxVecs][NE], const T (&sc)[k
   }
 }
 
-template <class P, typename T, int U, int VB>
+// DS: some scalar slots are computed on the device from p.scode at kernel
+// start.  A separate instantiation, because scalars that may come from
+// shared memory occupy registers for the whole loop, while by-value
+// scalars are re-read from the constant bank at each use.
+template <class P, typename T, int U, int VB, bool DS = false>
 __global__ void __launch_bounds__(256) fused_kernel(const MapParams<T> p) {
   constexpr int VEC = VB / (int)sizeof(T);
   constexpr unsigned LM = P::load_mask(), SMASK = P::store_mask();
@@ -85,8 +92,12 @@ __global__ void __launch_bounds__(256) fused_kernel(const MapParams<T> p) {
   using V = VecT<T, VB>;
 
   T sc[kMaxScals];
+  if constexpr (DS) {
+    load_scalars<T>(p.sc, p.scode, sc);
+  } else {
 #pragma unroll
-  for (int k = 0; k < kMaxScals; ++k) sc[k] = p.sc[k];
+    for (int k = 0; k < kMaxScals; ++k) sc[k] = p.sc[k];
+  }
   Acc acc[kMaxReds];
 
   const int64_t n = p.n;
@@ -198,8 +209,7 @@ __global__ void __launch_bounds__(256) strided_kernel(const MapParams<T> p) {
   constexpr int NR = P::nred();
   using Acc = typename AccOf<T>::type;
   T sc[kMaxScals];
-#pragma unroll
-  for (int k = 0; k < kMaxScals; ++k) sc[k] = p.sc[k];
+  load_scalars<T>(p.sc, p.scode, sc);
   Acc acc[kMaxReds];
   const int64_t n = p.n;
   const int64_t bd = blockDim.x;

@@ -2,16 +2,18 @@
 #include "host.h"
 
 #include <cstdio>
+#include <cstring>
 
 namespace salt {
 
 static const char* op_name(int op) {
-  static const char* names[] = {"VEC", "SCAL", "ADD", "SUB", "MUL", "SMUL", "NEG", "STORE", "DOT", "SUMSQ"};
-  return op >= 0 && op < 10 ? names[op] : "?";
+  static const char* names[] = {"VEC",   "SCAL", "ADD",   "SUB", "MUL", "SMUL",
+                                "NEG",   "STORE", "DOT",  "SUMSQ", "DIV", "DSCAL"};
+  return op >= 0 && op < 12 ? names[op] : "?";
 }
 
 salt_status analyse(const salt_insn* prog, int nprog, int nvecs, int nscal, Analysis* out,
-                    std::string* err) {
+                    std::string* err, int ndscal) {
   char buf[160];
   auto fail = [&](salt_status st, const char* msg) {
     if (err) *err = msg;
@@ -22,7 +24,8 @@ salt_status analyse(const salt_insn* prog, int nprog, int nvecs, int nscal, Anal
     snprintf(buf, sizeof buf, "program length %d outside 1..%d", nprog, kMaxProg);
     return fail(SALT_ERR_ARG, buf);
   }
-  if (nvecs < 0 || nvecs > kMaxVecs || nscal < 0 || nscal > kMaxScals)
+  if (nvecs < 0 || nvecs > kMaxVecs || nscal < 0 || nscal > kMaxScals || ndscal < 0 ||
+      ndscal > kMaxDscals)
     return fail(SALT_ERR_ARG, "operand counts outside 0..8");
   Analysis a;
   char stack[kMaxProg + 1];  // 'v' vector, 's' scalar
@@ -44,19 +47,27 @@ salt_status analyse(const salt_insn* prog, int nprog, int nvecs, int nscal, Anal
         a.used_scals |= 1u << arg;
         stack[sp++] = 's';
         break;
+      case OP_DSCAL:
+        if (arg >= ndscal) return bad("device scalar index out of range");
+        a.used_dscals |= 1u << arg;
+        a.scalar_nodes = true;
+        stack[sp++] = 's';
+        break;
       case OP_ADD:
       case OP_SUB:
       case OP_MUL:
+      case OP_DIV:
+        if (sp < 2) return bad("needs two operands");
+        if (stack[sp - 1] != stack[sp - 2]) return bad("operands must be two vectors or two scalars");
+        if (stack[sp - 1] == 's') a.scalar_nodes = true;
+        --sp;  // the result keeps the operands' type
+        break;
       case OP_DOT:
         if (sp < 2) return bad("needs two operands");
         if (stack[sp - 1] != 'v' || stack[sp - 2] != 'v') return bad("operands must be vectors");
         sp -= 2;
-        if (op == OP_DOT) {
-          ++a.nred;
-          ++outputs;
-        } else {
-          stack[sp++] = 'v';
-        }
+        ++a.nred;
+        ++outputs;
         break;
       case OP_SMUL:
         if (sp < 2) return bad("needs two operands");
@@ -67,7 +78,7 @@ salt_status analyse(const salt_insn* prog, int nprog, int nvecs, int nscal, Anal
         break;
       case OP_NEG:
         if (sp < 1) return bad("needs an operand");
-        if (stack[sp - 1] != 'v') return bad("operand must be a vector");
+        if (stack[sp - 1] == 's') a.scalar_nodes = true;
         break;
       case OP_STORE:
       case OP_SUMSQ:
@@ -173,9 +184,10 @@ bool lower(const Canonical& c, RegInsn* code, int* len) {
       case OP_SCAL: st[sp++] = {true, arg}; break;
       case OP_ADD:
       case OP_SUB:
-      case OP_MUL: {
+      case OP_MUL:
+      case OP_DIV: {
         const Ent b = st[--sp], a = st[--sp];
-        const uint8_t io = op == OP_ADD ? I_ADD : op == OP_SUB ? I_SUB : I_MUL;
+        const uint8_t io = op == OP_ADD ? I_ADD : op == OP_SUB ? I_SUB : op == OP_MUL ? I_MUL : I_DIV;
         if (!emit(io, 8 + sp, a.reg, b.reg)) return false;
         st[sp] = {false, 8 + sp};
         ++sp;
@@ -221,6 +233,147 @@ bool lower(const Canonical& c, RegInsn* code, int* len) {
     }
   }
   *len = n;
+  return true;
+}
+
+// ------------------------------------------------- scalar subexpressions --
+
+salt_status hoist_scalars(const salt_insn* prog, int nprog, int nscal, Hoisted* h, std::string* err) {
+  Hoisted r;
+  // Per stack entry, the tokens of its subtree (bit pc).  A scalar subtree
+  // need not be contiguous: a statement (VEC k SUMSQ, VEC k STORE j) may sit
+  // between its tokens, above its partial values on the stack.
+  uint32_t st[kMaxProg + 1];
+  int sp = 0;
+  uint32_t skip = 0;       // tokens of hoisted occurrences
+  int slot_at[kMaxProg];   // hoisted slot whose subtree has its root at pc, or -1
+  for (int pc = 0; pc < nprog; ++pc) slot_at[pc] = -1;
+  auto same = [&](uint32_t ma, uint32_t mb) {  // equal token sequences
+    int i = 0, j = 0;
+    for (;;) {
+      while (i < nprog && !((ma >> i) & 1u)) ++i;
+      while (j < nprog && !((mb >> j) & 1u)) ++j;
+      if (i >= nprog || j >= nprog) return i >= nprog && j >= nprog;
+      if (prog[i].op != prog[j].op || prog[i].arg != prog[j].arg) return false;
+      ++i;
+      ++j;
+    }
+  };
+  for (int pc = 0; pc < nprog; ++pc) {
+    const uint32_t bit = 1u << pc;
+    switch (prog[pc].op) {
+      case OP_VEC:
+      case OP_SCAL:
+      case OP_DSCAL: st[sp++] = bit; break;
+      case OP_NEG: st[sp - 1] |= bit; break;
+      case OP_STORE:
+      case OP_SUMSQ: --sp; break;
+      case OP_DOT: sp -= 2; break;
+      case OP_SMUL: {
+        const uint32_t mv = st[--sp], ms = st[--sp];
+        int root = -1;  // last token of the scalar operand
+        for (int t = 0; t < nprog; ++t)
+          if ((ms >> t) & 1u) root = t;
+        const bool bare = (ms & (ms - 1)) == 0 && prog[root].op == OP_SCAL;
+        if (!bare) {
+          int j = -1;
+          for (int q = 0; q < r.nhoist && j < 0; ++q)
+            if (same(r.mask[q], ms)) j = q;
+          if (j < 0) {
+            if (nscal + r.nhoist >= kMaxScals) {
+              if (err) *err = "more than 8 scalar slots after hoisting the scalar subexpressions";
+              return SALT_ERR_PROGRAM;
+            }
+            j = r.nhoist++;
+            r.mask[j] = ms;
+            for (int t = 0; t < nprog; ++t)
+              if (((ms >> t) & 1u) && prog[t].op == OP_DSCAL) r.device = true;
+          }
+          skip |= ms;
+          slot_at[root] = j;
+        }
+        st[sp++] = ms | mv | bit;
+        break;
+      }
+      default: {  // ADD SUB MUL DIV, on two vectors or two scalars
+        const uint32_t mb = st[--sp];
+        st[sp - 1] |= mb | bit;
+        break;
+      }
+    }
+  }
+  for (int pc = 0; pc < nprog; ++pc) {
+    if (slot_at[pc] >= 0) {
+      r.prog[r.nprog++] = salt_insn{(uint8_t)OP_SCAL, (uint8_t)(nscal + slot_at[pc])};
+    } else if (!((skip >> pc) & 1u)) {
+      r.prog[r.nprog++] = prog[pc];
+    }
+  }
+  r.nscal = nscal + r.nhoist;
+  *h = r;
+  return SALT_OK;
+}
+
+template <typename T>
+static double host_scalar_value(const salt_insn* prog, const Hoisted& h, int j, const double* scalars,
+                                const double* dvals) {
+  T st[kMaxProg + 1];
+  int sp = 0;
+  for (int pc = 0; pc < kMaxProg; ++pc) {
+    if (!((h.mask[j] >> pc) & 1u)) continue;
+    const int op = prog[pc].op;
+    if (op == OP_SCAL) {
+      st[sp++] = (T)scalars[prog[pc].arg];
+    } else if (op == OP_DSCAL) {
+      st[sp++] = (T)(dvals ? dvals[prog[pc].arg] : 0.0);
+    } else if (op == OP_NEG) {
+      st[sp - 1] = -st[sp - 1];
+    } else {
+      const T a = st[sp - 2], b = st[sp - 1];
+      T v;
+      if (op == OP_ADD) v = a + b;
+      else if (op == OP_SUB) v = a - b;
+      else if (op == OP_MUL) v = a * b;
+      else v = a / b;
+      st[sp - 2] = v;
+      --sp;
+    }
+  }
+  return (double)st[0];
+}
+
+double host_scalar_value_f32(const salt_insn* prog, const Hoisted& h, int j, const double* scalars,
+                             const double* dvals) {
+  return host_scalar_value<float>(prog, h, j, scalars, dvals);
+}
+double host_scalar_value_f64(const salt_insn* prog, const Hoisted& h, int j, const double* scalars,
+                             const double* dvals) {
+  return host_scalar_value<double>(prog, h, j, scalars, dvals);
+}
+
+bool build_scalar_code(const salt_insn* prog, const Hoisted& h, const Canonical& c, int user_nscal,
+                       const double* scalars, const double* const* dscal, ScalarCode* out) {
+  ScalarCode sc;
+  memset(&sc, 0, sizeof sc);
+  for (int k = 0; k < user_nscal && k < kMaxScals; ++k) sc.cval[k] = scalars ? scalars[k] : 0.0;
+  for (int k = 0; k < kMaxDscals; ++k) sc.ds[k] = dscal ? dscal[k] : nullptr;
+  int n = 0;
+  for (int k = 0; k < c.nscal; ++k) {
+    const int j = c.scal_user[k] - user_nscal;
+    if (j < 0) continue;  // a user scalar, passed by value
+    for (int pc = 0; pc < kMaxProg; ++pc) {
+      if (!((h.mask[j] >> pc) & 1u)) continue;
+      const int op = prog[pc].op, arg = prog[pc].arg;
+      const int sop = op == OP_SCAL ? S_SC : op == OP_DSCAL ? S_DS : op == OP_ADD ? S_ADD
+                    : op == OP_SUB ? S_SUB : op == OP_MUL ? S_MUL : op == OP_DIV ? S_DIV : S_NEG;
+      if (n >= kMaxScalarCode) return false;
+      sc.code[n++] = (uint8_t)(sop * 16 + (sop == S_SC || sop == S_DS ? arg : 0));
+    }
+    if (n >= kMaxScalarCode) return false;
+    sc.code[n++] = (uint8_t)(S_OUT * 16 + k);
+  }
+  sc.len = n;
+  *out = sc;
   return true;
 }
 

@@ -7,9 +7,9 @@
 
 namespace salt {
 
-template <class P, typename T, int U, int VB>
+template <class P, typename T, int U, int VB, bool DS = false>
 cudaError_t launch_fused(const void* prm, int grid, int block, size_t smem, cudaStream_t s) {
-  fused_kernel<P, T, U, VB><<<grid, block, smem, s>>>(*static_cast<const MapParams<T>*>(prm));
+  fused_kernel<P, T, U, VB, DS><<<grid, block, smem, s>>>(*static_cast<const MapParams<T>*>(prm));
   return cudaGetLastError();
 }
 
@@ -35,6 +35,13 @@ void register_unroll(Registry& r) {
                                        (const void*)&fused_kernel<Prog_##name, T, U, VB>};
   SALT_SHAPE_LIST(SALT_REG_ENTRY)
 #undef SALT_REG_ENTRY
+  if constexpr (U == kDsUnroll<T>) {
+#define SALT_REG_DS(name, ...)                                                       \
+  r.fused_ds[SHAPE_##name][dt][vi] = {&launch_fused<Prog_##name, T, U, VB, true>,   \
+                                      (const void*)&fused_kernel<Prog_##name, T, U, VB, true>};
+    SALT_SHAPE_LIST(SALT_REG_DS)
+#undef SALT_REG_DS
+  }
   r.special[SPECIAL_NRM2][dt][ui][vi] = {&launch_nrm2<T, U, VB, false>,
                                          (const void*)&nrm2_kernel<T, U, VB, false>};
   if constexpr (dt == DT_F32) {

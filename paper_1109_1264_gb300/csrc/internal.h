@@ -22,6 +22,8 @@ struct EvalArgs {
   double* red_out;
   cudaStream_t stream;
   const int64_t* strides = nullptr;  // per operand, in elements; NULL: all 1
+  const double* const* dscal = nullptr;  // device scalars (DSCAL k reads *dscal[k])
+  int ndscal = 0;
 };
 
 // Records `msg` as the calling thread's salt_last_error() and returns `st`.
@@ -45,6 +47,9 @@ void count_launch();
 // (SALT_JIT_OFF / SALT_JIT_ON) and the kernel for a canonical program
 // (compiled and cached on first use).
 int32_t jit_mode();
-salt_status jit_kernel(const Canonical& c, int is_f32, int unroll, int vec_bytes, const void** kernel_out);
+// ds: the variant that computes scalar slots on the device (fused kernel
+// only; the element-access kernel always can).
+salt_status jit_kernel(const Canonical& c, int is_f32, int unroll, int vec_bytes, bool ds,
+                       const void** kernel_out);
 
 }  // namespace salt

@@ -15,7 +15,7 @@
 
 namespace salt {
 
-enum : uint8_t { I_ADD = 0, I_SUB, I_MUL, I_SMUL, I_NEG, I_COPY, I_DOT, I_SUMSQ };
+enum : uint8_t { I_ADD = 0, I_SUB, I_MUL, I_SMUL, I_NEG, I_COPY, I_DOT, I_SUMSQ, I_DIV };
 constexpr int kMaxRegCode = 64;
 constexpr int kRegs = 16;
 
@@ -36,6 +36,7 @@ struct InterpParams {
   RegInsn code[kMaxRegCode];
   int32_t elementwise;        // 1: operands unaligned or strided, element accesses only
   int64_t stride[kMaxVecs];   // element strides (used when elementwise)
+  ScalarCode scode;           // scalar slots computed on the device (len 0: none)
 };
 
 template <typename T, class Acc>
@@ -57,6 +58,19 @@ __global__ void __launch_bounds__(256) interp_kernel(const InterpParams<T> p) {
   T* R = reinterpret_cast<T*>(smem_raw);
   const int64_t bd = blockDim.x;
   auto row = [&](int r) -> T* { return R + ((int64_t)r * bd + threadIdx.x) * VEC; };
+
+  // Scalar slots, shared by the block (dynamic slot numbers read shared
+  // memory, not local memory).
+  __shared__ T ssc[kMaxScals];
+  {
+    T sc[kMaxScals];
+    load_scalars<T>(p.sc, p.scode, sc);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < kMaxScals; ++k) ssc[k] = sc[k];
+    }
+    __syncthreads();
+  }
 
   Acc acc[kMaxReds];
   const int64_t n = p.n;
@@ -102,8 +116,13 @@ __global__ void __launch_bounds__(256) interp_kernel(const InterpParams<T> p) {
 #pragma unroll
           for (int e = 0; e < VEC; ++e) d[e] = Arith<T>::mul(a[e], b[e]);
         } break;
+        case I_DIV: {
+          const T* b = row(in.b);
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) d[e] = Arith<T>::div(a[e], b[e]);
+        } break;
         case I_SMUL: {
-          const T s = p.sc[in.b];
+          const T s = ssc[in.b];
 #pragma unroll
           for (int e = 0; e < VEC; ++e) d[e] = Arith<T>::mul(s, a[e]);
         } break;

@@ -91,7 +91,8 @@ NvrtcApi& api() {
 
 int32_t jit_mode() { return g_mode.load(); }
 
-salt_status jit_kernel(const Canonical& c, int is_f32, int unroll, int vec_bytes, const void** kernel_out) {
+salt_status jit_kernel(const Canonical& c, int is_f32, int unroll, int vec_bytes, bool ds,
+                       const void** kernel_out) {
   int dev = 0, major = 0, minor = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
@@ -100,7 +101,7 @@ salt_status jit_kernel(const Canonical& c, int is_f32, int unroll, int vec_bytes
   std::string name = vec_bytes ? "salt::fused_kernel<salt::Prog<" : "salt::strided_kernel<salt::Prog<";
   for (int i = 0; i < c.len; ++i) name += (i ? "," : "") + std::to_string(c.code[i]);
   name += ">," + std::string(is_f32 ? "float" : "double") + "," + std::to_string(unroll);
-  name += vec_bytes ? "," + std::to_string(vec_bytes) + ">" : ">";
+  name += vec_bytes ? "," + std::to_string(vec_bytes) + (ds ? ",true>" : ">") : ">";
   const std::string key = std::to_string(dev) + "|" + name;
   std::lock_guard<std::mutex> lk(g_mu);
   auto it = g_cache.find(key);

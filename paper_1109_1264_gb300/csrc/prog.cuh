@@ -22,7 +22,9 @@ enum : int {
   OP_NEG = 6,
   OP_STORE = 7,
   OP_DOT = 8,
-  OP_SUMSQ = 9
+  OP_SUMSQ = 9,
+  OP_DIV = 10,   // elementwise a / b (two scalars: a scalar node, hoisted)
+  OP_DSCAL = 11  // scalar read from device memory (hoisted, never in a kernel program)
 };
 
 constexpr int kMaxProg = 32;
@@ -30,16 +32,17 @@ constexpr int kMaxVecs = 8;
 constexpr int kMaxScals = 8;
 constexpr int kMaxStack = 8;
 constexpr int kMaxReds = 4;
+constexpr int kMaxDscals = 8;
 
 __host__ __device__ constexpr int pack(int op, int arg) { return op * 16 + arg; }
 
 // Stack effect of one opcode.
 __host__ __device__ constexpr int stack_delta(int op) {
-  return op == OP_VEC || op == OP_SCAL ? 1
+  return op == OP_VEC || op == OP_SCAL || op == OP_DSCAL ? 1
        : op == OP_NEG ? 0
        : op == OP_STORE || op == OP_SUMSQ ? -1
        : op == OP_DOT ? -2
-       : -1;  // ADD SUB MUL SMUL
+       : -1;  // ADD SUB MUL DIV SMUL
 }
 
 template <int... C>

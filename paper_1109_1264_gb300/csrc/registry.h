@@ -25,8 +25,13 @@ enum SpecialId : int { SPECIAL_NRM2 = 0, SPECIAL_NRM2_PLAIN, SPECIAL_DOT_PLAIN, 
 // Unroll of the element-access kernels (operands unaligned or strided).
 constexpr int kElemUnroll = 4;
 
+// Unroll of the fused kernels that compute scalar slots on the device (one
+// instantiation per shape, dtype and width; the tuned F32 / F64 defaults).
+template <typename T> constexpr int kDsUnroll = sizeof(T) == 4 ? 4 : 2;
+
 struct Registry {
   KernelEntry fused[NUM_SHAPES][2][kNumUnroll][kNumVB];
+  KernelEntry fused_ds[NUM_SHAPES][2][kNumVB];  // device scalar slots, unroll kDsUnroll
   KernelEntry special[NUM_SPECIAL][2][kNumUnroll][kNumVB];
   KernelEntry interp[2][kNumVB];
   KernelEntry fill[2];

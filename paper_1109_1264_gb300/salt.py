@@ -18,14 +18,14 @@ F32, F64 = 0, 1
 OK, ERR_ARG, ERR_PROGRAM, ERR_DTYPE, ERR_ALIGN, ERR_ALIAS, ERR_BUDGET, ERR_TIMEOUT, ERR_CUDA, ERR_NOTFOUND = range(10)
 DEFAULT, PLAIN = 0, 1
 OPS = {"VEC": 0, "SCAL": 1, "ADD": 2, "SUB": 3, "MUL": 4, "SMUL": 5, "NEG": 6, "STORE": 7,
-       "DOT": 8, "SUMSQ": 9}
-MAX_PROG, MAX_VECS, MAX_SCALS, MAX_STACK, MAX_REDS = 32, 8, 8, 8, 4
+       "DOT": 8, "SUMSQ": 9, "DIV": 10, "DSCAL": 11}
+MAX_PROG, MAX_VECS, MAX_SCALS, MAX_STACK, MAX_REDS, MAX_DSCALS = 32, 8, 8, 8, 4, 8
 
 # Symbols that include/salt.h declares (checked by the test suite).
 EXPORTS = ["salt_version", "salt_status_str", "salt_last_error", "salt_check_program", "salt_eval",
            "salt_axpby", "salt_dot", "salt_nrm2", "salt_fill_uniform", "salt_release_workspaces",
            "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_dot_noalloc",
-           "salt_eval_strided"]
+           "salt_eval_strided", "salt_eval_ex", "salt_explain"]
 
 
 class Insn(ctypes.Structure):
@@ -69,6 +69,10 @@ def _load() -> ctypes.CDLL:
         "salt_dot_noalloc": (i32, [i32, i64, vp, vp, vp, vp]),
         "salt_eval_strided": (i32, [ip, i32, i32, i64, ctypes.POINTER(vp), ctypes.POINTER(i64), i32, dp, i32, vp,
                                     vp]),
+        "salt_eval_ex": (i32, [ip, i32, i32, i64, ctypes.POINTER(vp), ctypes.POINTER(i64), i32, dp, i32,
+                               ctypes.POINTER(vp), i32, vp, vp]),
+        "salt_explain": (i32, [ip, i32, i32, i32, dp, i32, dp, i32, ip, ctypes.POINTER(i32), dp,
+                               ctypes.POINTER(i32), ctypes.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -150,17 +154,55 @@ def salt_check_program(prog, nvecs: int, nscal: int) -> tuple[int, bool]:
     return nred.value, bool(comp.value)
 
 
-def salt_eval(prog, vecs, scalars=(), red_out=None, n: int | None = None, stream=None) -> None:
+def _dscal_ptr(d) -> int | None:
+    """A device scalar: a float64 CUDA tensor view (its first element) or a
+    raw device address."""
+    if d is None or isinstance(d, int):
+        return d
+    import torch
+    if d.dtype != torch.float64 or not d.is_cuda:
+        raise SaltError(ERR_DTYPE, "SALT_ERR_DTYPE", "device scalars are float64 CUDA tensors")
+    return int(d.data_ptr())
+
+
+def salt_explain(prog, nvecs: int, scalars=(), dtype: int = F64, dvals=()):
+    """Host only: (hoisted program as [(name, arg)], slot values, compiled)
+    -- what the kernels evaluate for ``prog``."""
+    names = {v: k for k, v in OPS.items()}
+    arr, m = program(prog)
+    sc = (ctypes.c_double * max(len(scalars), 1))(*[float(x) for x in scalars])
+    dv = (ctypes.c_double * max(len(dvals), 1))(*[float(x) for x in dvals])
+    out = (Insn * max(m, 1))()
+    nout, nslots, comp = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    slots = (ctypes.c_double * MAX_SCALS)()
+    _check(lib.salt_explain(arr, m, dtype, nvecs, sc, len(scalars), dv, len(dvals), out, ctypes.byref(nout),
+                            slots, ctypes.byref(nslots), ctypes.byref(comp)))
+    hp = [(names[out[i].op], out[i].arg) for i in range(nout.value)]
+    return hp, [slots[i] for i in range(nslots.value)], bool(comp.value)
+
+
+def salt_eval(prog, vecs, scalars=(), red_out=None, n: int | None = None, stream=None,
+              dscalars=None) -> None:
     """Run ``prog`` over the torch CUDA tensors ``vecs`` (all float32 or all
     float64, same length).  DOT/SUMSQ results go to ``red_out`` (a float64 CUDA
     tensor with one entry per reduction).  1-D views with a positive stride
-    are passed to salt_eval_strided."""
+    are passed to salt_eval_strided.  ``dscalars`` (device scalars for DSCAL
+    nodes: float64 CUDA tensor views, e.g. ``red[0:1]``) route the call to
+    salt_eval_ex."""
     dt = _common_dtype(vecs)
     if n is None:
         n = _n_of(vecs)
     arr, m = program(prog)
     ptrs = (ctypes.c_void_p * max(len(vecs), 1))(*[_ptr(v) for v in vecs])
     sc = (ctypes.c_double * max(len(scalars), 1))(*[float(s) for s in scalars])
+    if dscalars is not None:
+        strides = None
+        if not all(v is None or v.is_contiguous() for v in vecs):
+            strides = (ctypes.c_int64 * max(len(vecs), 1))(*[1 if v is None else int(v.stride(0)) for v in vecs])
+        ds = (ctypes.c_void_p * max(len(dscalars), 1))(*[_dscal_ptr(d) for d in dscalars])
+        _check(lib.salt_eval_ex(arr, m, dt, int(n), ptrs, strides, len(vecs), sc, len(scalars), ds,
+                                len(dscalars), _ptr(red_out), _stream_ptr(stream)))
+        return
     if all(v is None or v.is_contiguous() for v in vecs):
         _check(lib.salt_eval(arr, m, dt, int(n), ptrs, len(vecs), sc, len(scalars), _ptr(red_out),
                              _stream_ptr(stream)))

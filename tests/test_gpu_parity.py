@@ -92,7 +92,7 @@ def test_named_programs_bit_exact(salt, name, dt):
         check_reductions(prog, vecs, scalars, red, dt, f"{name} n={n}")
 
 
-def reduction_operands(prog, vecs_np, scalars):
+def reduction_operands(prog, vecs_np, scalars, dscalars=()):
     """The operand vectors of every DOT / SUMSQ of ``prog``, materialised by
     the oracle: each reduction is rewritten into STOREs to fresh operands
     (same stack effect), so the oracle's node-by-node evaluation produces
@@ -111,12 +111,12 @@ def reduction_operands(prog, vecs_np, scalars):
         else:
             rewritten.append((op, arg))
     vs = [v.copy() for v in vecs_np] + [np.zeros_like(vecs_np[0]) for _ in range(extra)]
-    oracle.eval_program(rewritten, vs, scalars)
+    oracle.eval_program(rewritten, vs, scalars, dscalars=dscalars)
     return [(vs[a], vs[b]) for a, b in pairs]
 
 
-def check_reductions(prog, vecs_np, scalars, red, dt, what=""):
-    for k, (a, b) in enumerate(reduction_operands(prog, vecs_np, scalars)):
+def check_reductions(prog, vecs_np, scalars, red, dt, what="", dscalars=()):
+    for k, (a, b) in enumerate(reduction_operands(prog, vecs_np, scalars, dscalars)):
         ref = exact.exact_dot(a, b)
         scale = exact.abs_dot(a, b)
         assert abs(red[k] - ref) <= TOL[dt] * scale, (what, k, red[k], ref, scale)

@@ -1,0 +1,198 @@
+"""Scalar subexpressions, elementwise DIV and device-resident scalars on the
+GPU, against the oracle: elementwise results bit-identical (scalar nodes are
+one operation each in the program's dtype, computed once per launch),
+reductions within tolerance, and conjugate gradients driven entirely by
+device scalars (alpha = rho / (p.q), beta = rho' / rho) with no host read
+between its steps."""
+import math
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle_pins import CG_P, CG_Q_PQ, CG_XR_RHO, cg_diagonal, random_program
+from test_gpu_parity import TOL, assert_bits_equal, check_reductions
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TDT = {np.float32: torch.float32, np.float64: torch.float64}
+AXPY_DS = [("DSCAL", 0), ("DSCAL", 1), ("DIV", 0), ("VEC", 0), ("SMUL", 0), ("VEC", 1), ("ADD", 0),
+           ("STORE", 1)]
+
+
+def _signed(rng, n, dt):
+    """Magnitudes in [0.5, 2) with random signs: quotients stay in range."""
+    return (rng.uniform(0.5, 2.0, n) * rng.choice([-1.0, 1.0], n)).astype(dt)
+
+
+def _run(s, prog, vecs, scalars, dscalars, dev, views=None):
+    tv = [torch.from_numpy(v.copy()).to(dev) for v in vecs] if views is None else views
+    nred = sum(1 for o, _ in prog if o in ("DOT", "SUMSQ"))
+    red = torch.full((max(nred, 1),), float("nan"), dtype=torch.float64, device=dev)
+    ds = torch.tensor(list(dscalars) or [0.0], dtype=torch.float64, device=dev)
+    s.salt_eval(prog, tv, scalars, red_out=red if nred else None,
+                dscalars=[ds[k:k + 1] for k in range(len(dscalars))] if dscalars else None)
+    torch.cuda.synchronize()
+    return [t.cpu().numpy() for t in tv], red.cpu().numpy()[:nred]
+
+
+def _check(prog, vecs, scalars, dscalars, got, red, dt, what):
+    want = [v.copy() for v in vecs]
+    oracle.eval_program(prog, want, scalars, dscalars=dscalars)
+    for k, (g, w) in enumerate(zip(got, want)):
+        assert_bits_equal(g, w, f"{what} operand {k}")
+    if red.size and all(np.all(np.isfinite(w)) for w in want):
+        check_reductions(prog, vecs, scalars, red, dt, what, dscalars=dscalars)
+
+
+@pytest.mark.parametrize("jit", [False, True], ids=["interp", "jit"])
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_random_extended_programs(saltlib, cuda_dev, dt, jit):
+    """Random programs with DIV, scalar-typed nodes and device scalars."""
+    s = saltlib
+    rng = random.Random(31 + jit)
+    nrng = np.random.default_rng(31)
+    s.salt_set_jit(s.JIT_ON if jit else s.JIT_OFF)
+    try:
+        done = 0
+        while done < 24:
+            nv, ns, nd = rng.randint(1, 5), rng.randint(0, 2), rng.randint(1, 3)
+            prog = random_program(rng, nv, ns, max_len=12, ndscal=nd, ext=True)
+            try:
+                s.salt_check_program(prog, nv, ns)
+            except s.SaltError:
+                continue  # beyond the library's size limits
+            for n in (1, 7, 1000, 70001):
+                vecs = [_signed(nrng, n, dt) for _ in range(nv)]
+                scalars = list(nrng.uniform(0.5, 2.0, ns))
+                dscalars = list(nrng.uniform(-2.0, 2.0, nd))
+                got, red = _run(s, prog, vecs, scalars, dscalars, cuda_dev)
+                _check(prog, vecs, scalars, dscalars, got, red, dt, f"{prog} n={n}")
+            done += 1
+    finally:
+        s.salt_set_jit(s.JIT_OFF)
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_hoisted_subexpressions_on_compiled_shapes(saltlib, cuda_dev, dt):
+    """Programs whose scalar subtrees hoist to a slot run on the compiled
+    kernels: the slot computed at kernel start (device scalars) or on the
+    host (by-value scalars) gives the oracle's bits, including the FP32
+    rounding of each scalar node."""
+    s = saltlib
+    nrng = np.random.default_rng(32)
+    folded = [("SCAL", 0), ("SCAL", 1), ("MUL", 0), ("NEG", 0), ("VEC", 0), ("SMUL", 0), ("VEC", 1),
+              ("ADD", 0), ("STORE", 1)]
+    e_ds = [("DSCAL", 0), ("VEC", 0), ("SMUL", 0), ("DSCAL", 1), ("DSCAL", 2), ("SUB", 0), ("VEC", 1),
+            ("SMUL", 0), ("ADD", 0), ("VEC", 2), ("VEC", 3), ("MUL", 0), ("SUB", 0), ("STORE", 4)]
+    cases = [(AXPY_DS, 2, (), (3.0, 7.0)),
+             (AXPY_DS, 2, (), (1.0 + 2.0 ** -24 + 2.0 ** -40, 1.0 + 2.0 ** -23)),
+             (folded, 2, (1.0 / 3.0, -2.5), ()),
+             (folded, 2, (1.0, 1.0 + 2.0 ** -24), ()),
+             (e_ds, 5, (), (1.5, 0.75, 1.0))]
+    for prog, nv, scalars, dscalars in cases:
+        assert s.salt_check_program(prog, nv, len(scalars))[1], prog
+        for n in (1, 5, 4096 + 7, (1 << 20) + 3):
+            vecs = [nrng.uniform(-1, 1, n).astype(dt) for _ in range(nv)]
+            got, red = _run(s, prog, vecs, scalars, dscalars, cuda_dev)
+            _check(prog, vecs, scalars, dscalars, got, red, dt, f"{prog} n={n}")
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_device_scalars_with_strided_operands(saltlib, cuda_dev, dt):
+    s = saltlib
+    nrng = np.random.default_rng(33)
+    for n in (3, 999, 65537):
+        vecs = [nrng.uniform(-1, 1, n).astype(dt) for _ in range(2)]
+        bufs = [torch.full((2 * n + 1,), 7.0, dtype=TDT[dt], device=cuda_dev) for _ in range(2)]
+        for b, v in zip(bufs, vecs):
+            b[0:2 * n:2] = torch.from_numpy(v).to(cuda_dev)
+        views = [b[0:2 * n:2] for b in bufs]
+        got, _ = _run(s, AXPY_DS, vecs, (), (2.0, -3.0), cuda_dev, views=views)
+        _check(AXPY_DS, vecs, (), (2.0, -3.0), got, np.zeros(0), dt, f"strided n={n}")
+        assert torch.all(bufs[1][1::2] == 7.0)
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_device_scalar_follows_stream_order(saltlib, cuda_dev, dt):
+    """A DOT result written by one call steers the next call on the same
+    stream with no synchronisation between them."""
+    s = saltlib
+    nrng = np.random.default_rng(34)
+    n = (1 << 22) + 5
+    x, y = (nrng.uniform(-1, 1, n).astype(dt) for _ in range(2))
+    tx, ty = (torch.from_numpy(v).to(cuda_dev) for v in (x, y))
+    red = torch.zeros(2, dtype=torch.float64, device=cuda_dev)
+    s.salt_eval([("VEC", 0), ("VEC", 1), ("DOT", 0)], [tx, ty], red_out=red[0:1])
+    prog = [("DSCAL", 0), ("VEC", 0), ("SMUL", 0), ("VEC", 1), ("ADD", 0), ("STORE", 1)]
+    s.salt_eval(prog, [tx, ty], dscalars=[red[0:1]])
+    torch.cuda.synchronize()
+    d = float(red[0].cpu())
+    want = [x.copy(), y.copy()]
+    oracle.eval_program(prog, want, dscalars=[d])
+    assert_bits_equal(ty.cpu().numpy(), want[1], "y")
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_cg_diagonal_device_scalars(saltlib, cuda_dev, dt):
+    """CG for diag(d) x = b with every scalar on the device: three calls per
+    iteration, reduction results feeding DSCAL nodes, one synchronisation at
+    the end.  Four distinct eigenvalues: converged after four iterations,
+    and close to the oracle's CG iterate (the two differ only through the
+    rounding of their reductions)."""
+    s = saltlib
+    rng = np.random.default_rng(35)
+    for n in (1001, (1 << 20) + 3):
+        d = rng.choice([1.0, 2.0, 5.0, 8.0], n).astype(dt)
+        b = rng.uniform(-1, 1, n).astype(dt)
+        iters = 4
+        tv = [torch.from_numpy(v.copy()).to(cuda_dev) for v in (d, b, np.zeros(n, dt), np.zeros(n, dt), b)]
+        red = torch.zeros(1 + 2 * iters, dtype=torch.float64, device=cuda_dev)
+        s.salt_eval([("VEC", 4), ("SUMSQ", 0)], tv, red_out=red[0:1])
+        rho = 0
+        for i in range(iters):
+            pq, rho_new = 1 + 2 * i, 2 + 2 * i
+            s.salt_eval(CG_Q_PQ, tv, red_out=red[pq:pq + 1])
+            s.salt_eval(CG_XR_RHO, tv, red_out=red[rho_new:rho_new + 1],
+                        dscalars=[red[rho:rho + 1], red[pq:pq + 1]])
+            s.salt_eval(CG_P, tv, dscalars=[red[rho_new:rho_new + 1], red[rho:rho + 1]])
+            rho = rho_new
+        torch.cuda.synchronize()
+        x = tv[3].cpu().numpy().astype(np.float64)
+        xs = b.astype(np.float64) / d.astype(np.float64)
+        err = np.linalg.norm(x - xs) / np.linalg.norm(xs)
+        assert err < (1e-13 if dt == np.float64 else 2e-6), (n, err)
+        res = red.cpu().numpy()
+        assert math.sqrt(res[2 * iters]) < (1e-13 if dt == np.float64 else 2e-6) * math.sqrt(res[0])
+
+        def evalp(prog, vecs, ds):
+            return oracle.eval_program(prog, vecs, dscalars=ds)
+
+        xo, _ = cg_diagonal(evalp, d, b, iters)
+        rel = np.linalg.norm(x - xo) / np.linalg.norm(xo)
+        assert rel < (1e-12 if dt == np.float64 else 1e-5), (n, rel)
+
+
+def test_batch_folds_by_value_scalar_subexpressions(saltlib, cuda_dev):
+    """A batch item whose scalars are a subexpression of by-value scalars runs
+    on the batch kernel with the folded value: the same bits as salt_eval."""
+    s = saltlib
+    nrng = np.random.default_rng(36)
+    folded = [("SCAL", 0), ("SCAL", 1), ("DIV", 0), ("VEC", 0), ("SMUL", 0), ("VEC", 1), ("ADD", 0),
+              ("STORE", 1)]
+    n = 10007
+    for dt in (np.float32, np.float64):
+        x, y = (nrng.uniform(-1, 1, n).astype(dt) for _ in range(2))
+        tx, ty = (torch.from_numpy(v).to(cuda_dev) for v in (x, y))
+        b = s.Batch(capacity=4)
+        try:
+            b.add(folded, [tx, ty], [1.0, 3.0])
+            b.launch(torch.zeros(1, dtype=torch.float64, device=cuda_dev))
+            torch.cuda.synchronize()
+        finally:
+            b.close()
+        want = [x.copy(), y.copy()]
+        oracle.eval_program(folded, want, [1.0, 3.0])
+        assert_bits_equal(ty.cpu().numpy(), want[1], f"batch {dt.__name__}")
