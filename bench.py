@@ -277,6 +277,8 @@ def main():
     ap.add_argument("--batched-fixed", action="store_true", help="skip the batch autotuner (profiling runs)")
     ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling runs)")
     ap.add_argument("--sweep", action="store_true", help="the paper's four-op size sweep instead of the step")
+    ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--cg-log2", type=int, default=28)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -408,6 +410,9 @@ def main():
     if not args.no_served:
         torch.cuda.empty_cache()
         result["served"] = served_measure(salt)
+    if not args.no_cg:
+        torch.cuda.empty_cache()
+        result["cg"] = cg_measure(torch, salt, log2n=args.cg_log2)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(1 << args.cpu_log2)
@@ -539,6 +544,90 @@ def sweep_measure(torch, salt, reps: int = 15, max_log2: int = 28) -> dict:
         out[dt] = rows
         del xb, yb
     return {"sweep": out, "note": "GB/s of algorithmic bytes; L2 flushed before each timed call; median of %d" % reps}
+
+
+def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> dict:
+    """Conjugate gradients for diag(d) x = b with every scalar on the device
+    (alpha = rho / p.q and beta = rho' / rho as DSCAL quotients), d in [1, 8):
+    salt_cg_diag (two fused passes per iteration: 11 vector passes) against
+    the same iteration as six single-operation calls of this library (run-time
+    compiled where no compiled shape exists: 15 vector passes, 6 launches).
+    Operands (>= 1 GiB each) exceed L2.  GB/s counts the fused schedule's
+    algorithmic bytes for both, so the ratio is the speed-up."""
+    import numpy as np
+
+    n = 1 << log2n
+    stream = torch.cuda.current_stream()
+    out = {}
+    for dt, tdt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+        d, b, x, r, p, q = (torch.empty(n, dtype=tdt, device="cuda") for _ in range(6))
+        salt.salt_fill_uniform(d, 21)
+        d.add_(1.0).mul_(3.5).add_(1.0)
+        salt.salt_fill_uniform(b, 22)
+        rho = torch.zeros(2 * iters + 1, dtype=torch.float64, device="cuda")
+        rho_u = torch.zeros(2 * iters + 1, dtype=torch.float64, device="cuda")
+        vecs = [d, p, q, x, r, b]
+        r0 = [("VEC", 5), ("VEC", 0), ("VEC", 3), ("MUL", 0), ("SUB", 0), ("STORE", 4), ("VEC", 4), ("SUMSQ", 0)]
+        quot = [("DSCAL", 0), ("DSCAL", 1), ("DIV", 0)]
+        p_upd = [("SCAL", 0), ("VEC", 4), ("SMUL", 0)] + quot + [("VEC", 1), ("SMUL", 0), ("ADD", 0), ("STORE", 1)]
+        q_mul = [("VEC", 0), ("VEC", 1), ("MUL", 0), ("STORE", 2)]
+        pq_dot = [("VEC", 1), ("VEC", 2), ("DOT", 0)]
+        x_upd = quot + [("VEC", 1), ("SMUL", 0), ("VEC", 3), ("ADD", 0), ("STORE", 3)]
+        r_upd = quot + [("NEG", 0), ("VEC", 2), ("SMUL", 0), ("VEC", 4), ("ADD", 0), ("STORE", 4)]
+        rr = [("VEC", 4), ("SUMSQ", 0)]
+
+        def fused():
+            salt.salt_cg_diag(d, b, x, r, p, q, iters, rho)
+
+        def unfused():
+            salt.salt_eval(r0, vecs, red_out=rho_u[0:1])
+            for k in range(iters):
+                pq = rho_u[2 * k + 1:2 * k + 2]
+                if k == 0:
+                    salt.salt_eval([("VEC", 4), ("STORE", 1)], vecs)
+                else:
+                    salt.salt_eval(p_upd, vecs, [1.0], dscalars=[rho_u[2 * k:2 * k + 1], rho_u[2 * k - 2:2 * k - 1]])
+                salt.salt_eval(q_mul, vecs)
+                salt.salt_eval(pq_dot, vecs, red_out=pq)
+                ds = [rho_u[2 * k:2 * k + 1], pq]
+                salt.salt_eval(x_upd, vecs, dscalars=ds)
+                salt.salt_eval(r_upd, vecs, dscalars=ds)
+                salt.salt_eval(rr, vecs, red_out=rho_u[2 * k + 2:2 * k + 3])
+
+        def timed(fn):
+            ts = []
+            for _ in range(reps + 1):
+                x.zero_()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return float(np.median(ts[1:]))  # first run: warm-up (and JIT compilation)
+
+        salt.salt_set_jit(salt.JIT_ON)
+        try:
+            ms_u = timed(unfused)
+        finally:
+            salt.salt_set_jit(salt.JIT_OFF)
+        ms_f = timed(fused)
+        passes = 4 + 4 + 6 + 11 * (iters - 1)
+        abytes = passes * es * n
+        h_f, h_u = rho.cpu().numpy(), rho_u.cpu().numpy()
+        out[dt] = {"n": n, "iters": iters, "ms_fused": round(ms_f, 3), "ms_unfused": round(ms_u, 3),
+                   "ms_per_iter_fused": round(ms_f / iters, 4),
+                   "gbs_fused": round(abytes / (ms_f * 1e-3) / 1e9, 1),
+                   "gbs_unfused_same_bytes": round(abytes / (ms_u * 1e-3) / 1e9, 1),
+                   "speedup": round(ms_u / ms_f, 3),
+                   "launches_fused": 1 + 2 * iters, "launches_unfused": 1 + 6 * iters,
+                   "rel_residual": float(np.sqrt(h_f[-1] / h_f[0])),
+                   "rho_rel_diff_fused_vs_unfused": float(abs(h_f[-1] - h_u[-1]) / h_f[-1])}
+        del d, b, x, r, p, q, vecs
+        torch.cuda.empty_cache()
+    return out
 
 
 def served_measure(salt, count: int = 3000, seed: int = 0) -> dict:

@@ -214,6 +214,30 @@ salt_status salt_eval_ex(const salt_insn* prog, int32_t nprog, int32_t dtype, in
                          int32_t nscal, const double* const* dscalars, int32_t ndscal, double* red_out,
                          void* stream);
 
+/* salt_cg_diag -- `iters` conjugate-gradient iterations (Hestenes and
+ * Stiefel 1952) for diag(d) x = b, with every scalar kept on the device: two
+ * fused launches per iteration on `stream` and no host synchronisation.
+ *   pass 1  p = r + beta p;  q = d o p;  pq = p . q     (iteration 0: p = r)
+ *   pass 2  x = x + alpha p;  r = r - alpha q;  rho' = r . r
+ * with beta = rho_k / rho_{k-1} and alpha = rho_k / pq read as DSCAL
+ * quotients (salt_eval_ex) from the previous launches' results.  A start
+ * launch computes r = b - d o x and rho_0 = r . r.
+ *   d, b        inputs, n elements (d > 0 for an SPD operator)
+ *   x           in: the initial guess; out: the iterate
+ *   r, p, q     work vectors of n elements (out: residual, direction, d o p)
+ *   rho         device array of >= 2 * iters + 1 doubles: rho[0] = rho_0,
+ *               rho[2k+1] = (p . q) of iteration k, rho[2k+2] = rho_{k+1}
+ *               (the squared residual norms: the convergence history)
+ * All vectors are distinct and 16-byte aligned for the vector kernels
+ * (otherwise the element-access kernels run).  There is no stopping test:
+ * once a residual is exactly zero the next quotients are 0 / 0 (NaN), so
+ * choose `iters` from the rho history of a shorter run.  The same
+ * computation is available piecewise through salt_eval_ex; this is not
+ * part of the paper.  Every call is validated before the first launch.
+ * Errors as salt_eval. */
+salt_status salt_cg_diag(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r, void* p,
+                         void* q, int32_t iters, double* rho, void* stream);
+
 /* salt_explain -- host only (no GPU): the program the kernels evaluate for
  * `prog`, after its scalar subexpressions are hoisted, with the values of
  * the scalar slots.  Not part of the paper; an inspection aid.

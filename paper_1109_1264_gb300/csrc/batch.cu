@@ -319,7 +319,8 @@ salt_status salt_batch_add(salt_batch* b, const salt_insn* prog, int32_t nprog, 
   Canonical c;
   canonicalise(prog, nprog, &c);
   const int shape = find_shape(c);
-  if (shape < 0) return fail(SALT_ERR_PROGRAM, "program has no compiled instantiation, so it cannot be batched");
+  if (shape < 0 || shape >= NUM_BATCH_SHAPES)
+    return fail(SALT_ERR_PROGRAM, "program has no instantiation in the batch kernel, so it cannot be batched");
   if (c.nvec > kBatchOps || c.nscal > 2 || c.nred > kBatchPartials)
     return fail(SALT_ERR_PROGRAM, "program exceeds the batch item limits");
   for (int k = 0; k < c.nvec && n > 0; ++k) {

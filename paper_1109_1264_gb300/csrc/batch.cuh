@@ -220,7 +220,7 @@ __device__ __forceinline__ int dispatch_item(const BatchItem& it, int64_t lo, in
 #define SALT_BATCH_CASE(name, ...) \
   case SHAPE_##name:               \
     return item_program<Prog_##name, T, U>(it, lo, hi, vals);
-    SALT_SHAPE_LIST(SALT_BATCH_CASE)
+    SALT_BATCH_SHAPE_LIST(SALT_BATCH_CASE)
 #undef SALT_BATCH_CASE
     case kKindFill:
       return item_fill<T>(it, lo, hi);

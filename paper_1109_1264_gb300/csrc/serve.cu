@@ -416,7 +416,7 @@ salt_status submit_impl(salt_server* s, const salt_insn* prog, int32_t nprog, in
     Canonical c;
     canonicalise(prog, nprog, &c);
     const int shape = find_shape(c);
-    if (shape < 0 || c.nvec > kBatchOps || c.nscal > 2 || c.nred > kBatchPartials) {
+    if (shape < 0 || shape >= NUM_BATCH_SHAPES || c.nvec > kBatchOps || c.nscal > 2 || c.nred > kBatchPartials) {
       delete r;
       return fail(SALT_ERR_PROGRAM, "program has no compiled instantiation the server can batch");
     }

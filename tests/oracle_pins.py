@@ -308,6 +308,33 @@ def cg_diagonal(evalp, d, b, iters):
     return x, hist
 
 
+# The same iteration as two passes (the search-direction update fused into
+# the next matrix-vector product), started from any x; slot 5 holds b.
+CG_R0 = [("VEC", 5), ("VEC", 0), ("VEC", 3), ("MUL", 0), ("SUB", 0), ("STORE", 4), ("VEC", 4), ("SUMSQ", 0)]
+CG_P0 = [("VEC", 4), ("STORE", 1), ("VEC", 0), ("VEC", 1), ("MUL", 0), ("STORE", 2), ("VEC", 1), ("VEC", 2),
+         ("DOT", 0)]
+CG_PQ = [("VEC", 4), ("DSCAL", 0), ("DSCAL", 1), ("DIV", 0), ("VEC", 1), ("SMUL", 0), ("ADD", 0), ("STORE", 1),
+         ("VEC", 0), ("VEC", 1), ("MUL", 0), ("STORE", 2), ("VEC", 1), ("VEC", 2), ("DOT", 0)]
+
+
+def cg_diagonal_two_pass(evalp, d, b, x0, iters):
+    """CG from x0 with two programs per iteration; returns x and the history
+    [rho_0, pq_0, rho_1, pq_1, ..., rho_iters]."""
+    n = d.shape[0]
+    dt = d.dtype
+    p, q, r = np.zeros(n, dt), np.zeros(n, dt), np.zeros(n, dt)
+    x = x0.copy()
+    vecs = [d, p, q, x, r, b]
+    hist = [evalp(CG_R0, vecs, [])[0]]
+    for k in range(iters):
+        if k == 0:
+            hist.append(evalp(CG_P0, vecs, [])[0])
+        else:
+            hist.append(evalp(CG_PQ, vecs, [hist[2 * k], hist[2 * k - 2]])[0])
+        hist.append(evalp(CG_XR_RHO, vecs, [hist[2 * k], hist[2 * k + 1]])[0])
+    return x, hist
+
+
 def check_cg_distinct_eigenvalues(path):
     """CG on an SPD matrix with k distinct eigenvalues reaches the solution
     in at most k iterations in exact arithmetic (Hestenes and Stiefel 1952;
@@ -331,6 +358,14 @@ def check_cg_distinct_eigenvalues(path):
         assert err4 < tol, (dt, err4)
         assert err3 > 1e-3, (dt, err3)
         assert hist[-1] < tol * hist[0], (dt, hist)
+        # the two-pass form performs the same operations: the same bits
+        x2, h2 = cg_diagonal_two_pass(evalp, d, b, np.zeros(n, dt), 4)
+        assert np.array_equal(x2, x4), dt
+        assert [math.sqrt(v) for v in h2[0::2]] == hist, dt
+        # from a nonzero start it converges to the same solution
+        x0 = rng.uniform(-3, 3, n).astype(dt)
+        x5, _ = cg_diagonal_two_pass(evalp, d, b, x0, 4)
+        assert np.linalg.norm(x5 - xs) / np.linalg.norm(xs) < 10 * tol, dt
 
 
 def check_tail_lengths(path):

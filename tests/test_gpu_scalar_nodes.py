@@ -11,7 +11,9 @@ import numpy as np
 import pytest
 
 import oracle
-from oracle_pins import CG_P, CG_Q_PQ, CG_XR_RHO, cg_diagonal, random_program
+from oracle_pins import (CG_P, CG_P0, CG_PQ, CG_Q_PQ, CG_R0, CG_XR_RHO, cg_diagonal, cg_diagonal_two_pass,
+                         random_program)
+from oracle import exact
 from test_gpu_parity import TOL, assert_bits_equal, check_reductions
 
 pytestmark = pytest.mark.gpu
@@ -196,3 +198,50 @@ def test_batch_folds_by_value_scalar_subexpressions(saltlib, cuda_dev):
         want = [x.copy(), y.copy()]
         oracle.eval_program(folded, want, [1.0, 3.0])
         assert_bits_equal(ty.cpu().numpy(), want[1], f"batch {dt.__name__}")
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_cg_diag_entry_point(saltlib, cuda_dev, dt):
+    """salt_cg_diag: (1) replaying the oracle's two-pass CG with the GPU's own
+    reduction results as the device scalars reproduces every vector bit for
+    bit, and each GPU reduction is within tolerance of the exact value of
+    its (bit-identical) operands; (2) from x0 != 0 it converges to b / d in
+    four iterations (four distinct eigenvalues) and agrees with the
+    oracle's own CG."""
+    s = saltlib
+    rng = np.random.default_rng(37)
+    for n in (999, (1 << 20) + 5):
+        d = rng.choice([1.0, 2.0, 5.0, 8.0], n).astype(dt)
+        b = rng.uniform(-1, 1, n).astype(dt)
+        x0 = rng.uniform(-3, 3, n).astype(dt)
+        iters = 4
+        td, tb, tx = (torch.from_numpy(v.copy()).to(cuda_dev) for v in (d, b, x0))
+        tr, tp, tq = (torch.zeros(n, dtype=TDT[dt], device=cuda_dev) for _ in range(3))
+        rho = torch.full((2 * iters + 1,), float("nan"), dtype=torch.float64, device=cuda_dev)
+        s.salt_cg_diag(td, tb, tx, tr, tp, tq, iters, rho)
+        torch.cuda.synchronize()
+        g = rho.cpu().numpy().tolist()
+        # (1) replay
+        p, q, r, x = np.zeros(n, dt), np.zeros(n, dt), np.zeros(n, dt), x0.copy()
+        vecs = [d, p, q, x, r, b]
+        steps = [(CG_R0, [])]
+        for k in range(iters):
+            steps.append((CG_P0, []) if k == 0 else (CG_PQ, [g[2 * k], g[2 * k - 2]]))
+            steps.append((CG_XR_RHO, [g[2 * k], g[2 * k + 1]]))
+        for j, (prog, ds) in enumerate(steps):
+            oracle.eval_program(prog, vecs, dscalars=ds)
+            a, c = (r, r) if prog in (CG_R0, CG_XR_RHO) else (p, q)
+            ref = exact.exact_dot(a, c)
+            assert abs(g[j] - ref) <= TOL[dt] * exact.abs_dot(a, c), (n, j, g[j], ref)
+        for name, want, got in (("x", x, tx), ("r", r, tr), ("p", p, tp), ("q", q, tq)):
+            assert_bits_equal(got.cpu().numpy(), want, f"cg n={n} {name}")
+        # (2) convergence and agreement with the oracle's own iterate
+        xs = b.astype(np.float64) / d.astype(np.float64)
+        xg = x.astype(np.float64)
+        tol = 1e-12 if dt == np.float64 else 2e-5
+        assert np.linalg.norm(xg - xs) / np.linalg.norm(xs) < tol
+        # The oracle's own iterate differs through its reductions only: a
+        # sequential FP64 sum is off by up to gamma_n relative (about 1e-10
+        # at n = 2^20; a few 1e-13 typically), which perturbs alpha and beta.
+        xo, _ = cg_diagonal_two_pass(lambda pr, vs, ds: oracle.eval_program(pr, vs, dscalars=ds), d, b, x0, iters)
+        assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < (1e-10 if dt == np.float64 else 1e-5)

@@ -7,7 +7,7 @@ import random
 
 import pytest
 
-from oracle_pins import CG_P, CG_Q_PQ, CG_XR_RHO, random_program
+from oracle_pins import CG_P, CG_P0, CG_PQ, CG_Q_PQ, CG_R0, CG_XR_RHO, random_program
 
 BASE = 0x7F0000000000  # fake device addresses: the host rejects before any use
 
@@ -22,8 +22,11 @@ def test_hoisted_programs_keep_compiled_shapes(saltlib):
     folded = [("SCAL", 0), ("SCAL", 1), ("MUL", 0), ("NEG", 0), ("VEC", 0), ("SMUL", 0), ("VEC", 1),
               ("ADD", 0), ("STORE", 1)]
     assert s.salt_check_program(folded, 2, 2) == (0, True)
-    # the two equal quotients of the CG update share one slot: 4 vectors, 1 scalar
-    assert s.salt_check_program(CG_XR_RHO, 5, 0) == (1, False)
+    # the two equal quotients of the CG update share one slot: 4 vectors, 1
+    # scalar, the compiled second pass of a CG iteration
+    assert s.salt_check_program(CG_XR_RHO, 5, 0) == (1, True)
+    for prog in (CG_R0, CG_P0, CG_PQ):
+        assert s.salt_check_program(prog, 6, 0) == (1, True), prog
     assert s.salt_check_program(CG_Q_PQ, 5, 0) == (1, False)
     assert s.salt_check_program(CG_P, 5, 0) == (0, False)
     # elementwise division has no compiled instantiation
@@ -157,7 +160,7 @@ def test_hoisting_preserves_the_oracle_result(saltlib):
 def test_explain_shows_the_cse_and_folding(saltlib):
     s = saltlib
     hp, slots, comp = s.salt_explain(CG_XR_RHO, 5, (), s.F64, (6.0, 4.0))
-    assert slots == [1.5] and not comp
+    assert slots == [1.5] and comp
     assert hp == [("VEC", 3), ("SCAL", 0), ("VEC", 1), ("SMUL", 0), ("ADD", 0), ("STORE", 3),
                   ("VEC", 4), ("SCAL", 0), ("VEC", 2), ("SMUL", 0), ("SUB", 0), ("STORE", 4),
                   ("VEC", 4), ("SUMSQ", 0)]
