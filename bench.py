@@ -278,6 +278,12 @@ def main():
     ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling runs)")
     ap.add_argument("--sweep", action="store_true", help="the paper's four-op size sweep instead of the step")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--tune-save", default=None, help="write the autotuned launch table to this file")
+    ap.add_argument("--tune-load", default=None,
+                    help="profiling runs: load a saved launch table instead of autotuning")
+    ap.add_argument("--only-cg", action="store_true", help="run only the CG leg (profiling runs)")
+    ap.add_argument("--fixed-e-cfg", default=None,
+                    help="profiling runs: skip the autotuner and launch e with U,VB,BLOCK,BLOCKS_PER_SM")
     ap.add_argument("--cg-log2", type=int, default=28)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
@@ -303,6 +309,11 @@ def main():
             print(json.dumps(sweep_measure(torch, salt)), flush=True)
         return
 
+    if args.only_cg:
+        if rank == 0:
+            print(json.dumps({"cg": cg_measure(torch, salt, log2n=args.cg_log2)}), flush=True)
+        return
+
     if args.only_batched:
         if rank == 0:
             print(json.dumps({"batched": batched_measure(torch, salt, nitems=args.batched_items,
@@ -311,7 +322,21 @@ def main():
 
     n = 1 << args.log2n
     loads = {dt: Workload(torch, salt, dt, n, seed=rank) for dt in DTYPES}
-    tuned = {dt: loads[dt].tune(salt) for dt in DTYPES} if not args.no_tune else None
+    if args.fixed_e_cfg:
+        from paper_1109_1264_gb300.programs import PROG_E
+        u, vb, blk, bps = (int(v) for v in args.fixed_e_cfg.split(","))
+        for code in (salt.F32, salt.F64):
+            salt.salt_tune_set(PROG_E, code, n, u, vb, blk, bps)
+        tuned = {"e": {"unroll": u, "vec_bytes": vb, "block": blk, "blocks_per_sm": bps}, "others": "defaults"}
+    elif args.tune_load:
+        salt.salt_tune_load(args.tune_load)
+        tuned = {"loaded": os.path.basename(args.tune_load)}
+    elif not args.no_tune:
+        tuned = {dt: loads[dt].tune(salt) for dt in DTYPES}
+        if args.tune_save:
+            salt.salt_tune_save(args.tune_save)
+    else:
+        tuned = None
     steps = []
     for dt in DTYPES:
         for name, fn in loads[dt].ops(salt):
@@ -334,6 +359,8 @@ def main():
     time.sleep(0.3)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(steps) + 1)] for _ in range(args.steps)]
     launches0 = salt.salt_launch_count()
+    # for ncu launch lists: library launches before the timed steps (-s)
+    print(f"library launches before the timed steps: {launches0}", file=sys.stderr, flush=True)
     barrier()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)

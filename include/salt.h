@@ -364,8 +364,9 @@ salt_status salt_release_workspaces(void);
  * dtype and size bucket).
  *   unroll        vector accesses per operand per thread per tile (1, 2, 4)
  *   vec_bytes     bytes per vector access (16 or 32)
- *   block         threads per block (64..1024, multiple of 32)
- *   blocks_per_sm resident blocks per SM the grid is sized for (1..32)
+ *   block         threads per block (64..256, multiple of 32)
+ *   blocks_per_sm resident blocks per SM the grid is sized for (1..32; 0:
+ *                 as many as fit, from the occupancy calculator)
  * salt_tune_set pins a configuration for (program, dtype, n bucket) where the
  * bucket is floor(log2(max(n,1))); salt_tune_get reports the configuration a
  * call would use.  Returns SALT_ERR_ARG for an invalid configuration or

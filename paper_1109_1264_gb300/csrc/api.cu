@@ -126,7 +126,7 @@ static int bucket_of(int64_t n) {
 
 static bool cfg_valid(const salt_launch_cfg& c) {
   return unroll_index(c.unroll) >= 0 && vb_index(c.vec_bytes) >= 0 && c.block >= 64 &&
-         c.block <= 256 && c.block % 32 == 0 && c.blocks_per_sm >= 1 &&
+         c.block <= 256 && c.block % 32 == 0 && c.blocks_per_sm >= 0 &&
          c.blocks_per_sm <= kMaxBlocksPerSM && c.block * c.blocks_per_sm <= 2048;
 }
 

@@ -134,7 +134,10 @@ def test_tune_table(saltlib):
                                                                     "blocks_per_sm": 8}
     assert saltlib.salt_tune_get(D, saltlib.F32, 1 << 21) == default  # other bucket
     assert saltlib.salt_tune_get(D, saltlib.F64, 1 << 20) == default  # other dtype
-    for bad in ((3, 16, 128, 4), (2, 8, 128, 4), (2, 16, 100, 4), (2, 16, 512, 4), (2, 16, 256, 9)):
+    saltlib.salt_tune_set(D, saltlib.F32, 1 << 22, 2, 32, 256, 0)  # 0: as many blocks as fit
+    assert saltlib.salt_tune_get(D, saltlib.F32, 1 << 22)["blocks_per_sm"] == 0
+    for bad in ((3, 16, 128, 4), (2, 8, 128, 4), (2, 16, 100, 4), (2, 16, 512, 4), (2, 16, 256, 9),
+                (2, 16, 256, -1)):
         with pytest.raises(saltlib.SaltError):
             saltlib.salt_tune_set(D, saltlib.F32, 1 << 20, *bad)
     saltlib.salt_tune_clear()
