@@ -100,3 +100,38 @@ def test_reductions_full_size_closed_form(saltlib, cuda_dev, dt):
     assert got_dot == dot, (got_dot, dot)
     assert got_sq == sumsq, (got_sq, sumsq)
     assert got_nrm == math.sqrt(sumsq), (got_nrm, math.sqrt(sumsq))
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_cg_passes_full_size_sampled(saltlib, cuda_dev, dt):
+    """The two CG passes of salt_cg_diag at the bench's size (n = 2^28 + 5),
+    on the compiled device-scalar kernels, with device scalars uploaded from
+    the host: sampled elements of p, q, x and r bit-identical to the oracle
+    recomputing them from the counter-based inputs."""
+    from oracle_pins import CG_PQ, CG_XR_RHO
+    s = saltlib
+    n = (1 << 28) + 5
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    keys = {"d": 121, "p": 122, "x": 123, "r": 124}
+    t = {k: torch.empty(n, dtype=tdt, device=cuda_dev) for k in ("d", "p", "q", "x", "r")}
+    for k, key in keys.items():
+        s.salt_fill_uniform(t[k], key=key)
+    t["q"].zero_()
+    ds = torch.tensor([0.75, 1.0 / 3.0, 2.5], dtype=torch.float64, device=cuda_dev)
+    red = torch.zeros(2, dtype=torch.float64, device=cuda_dev)
+    vecs = [t["d"], t["p"], t["q"], t["x"], t["r"], t["r"]]  # slot 5 (b) is not used by these passes
+    s.salt_eval(CG_PQ, vecs, red_out=red[0:1], dscalars=[ds[0:1], ds[1:2]])
+    s.salt_eval(CG_XR_RHO, vecs, red_out=red[1:2], dscalars=[ds[0:1], ds[2:3]])
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    idx = np.unique(np.concatenate([np.arange(4096), np.arange(n - 4096, n), rng.integers(0, n, 200_000)]))
+    ins = {k: gather_inputs(key, idx, dt) for k, key in keys.items()}
+    m = len(idx)
+    want = [ins["d"], ins["p"].copy(), np.zeros(m, dt), ins["x"].copy(), ins["r"].copy(), np.zeros(m, dt)]
+    oracle.eval_program(CG_PQ, want, dscalars=[0.75, 1.0 / 3.0])
+    oracle.eval_program(CG_XR_RHO, want, dscalars=[0.75, 2.5])
+    tidx = torch.from_numpy(idx.astype(np.int64)).to(cuda_dev)
+    iu = np.uint32 if dt == np.float32 else np.uint64
+    for name, slot in (("p", 1), ("q", 2), ("x", 3), ("r", 4)):
+        got = t[name][tidx].cpu().numpy()
+        assert np.array_equal(got.view(iu), want[slot].view(iu)), name
