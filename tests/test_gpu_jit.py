@@ -9,6 +9,7 @@ import pytest
 import oracle
 from oracle import exact
 import oracle_pins
+from paper_1109_1264_gb300 import inputs
 from test_gpu_parity import assert_bits_equal, check_reductions, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
@@ -83,7 +84,11 @@ def test_jit_cache_and_speed_over_interpreter(jit, cuda_dev):
     t_int = timed()
     assert s.salt_jit_stats()["kernels"] == k1
     assert_bits_equal(x[5].cpu().numpy(), out_jit.cpu().numpy(), "jit vs interpreter")
-    ref = exact.exact_sumsq(out_jit.cpu().numpy())
+    # the oracle from the host's copy of the counter-based inputs
+    want = [inputs.hash_uniform(500 + k, n, np.float32) for k in range(6)]
+    oracle.eval_program(prog, want, [2.5])
+    assert_bits_equal(out_jit.cpu().numpy(), want[5], "jit vs oracle")
+    ref = exact.exact_sumsq(want[5])
     assert abs(r_jit - ref) <= 1e-6 * ref and abs(red.item() - ref) <= 1e-6 * ref
     gbs = lambda ms: 6 * 4 * n / (ms * 1e-3) / 1e9  # algorithmic: 5 reads + 1 write of 4 B
     print(f"jit {t_jit:.3f} ms ({gbs(t_jit):.0f} GB/s), interpreter {t_int:.3f} ms ({gbs(t_int):.0f} GB/s)")
