@@ -229,35 +229,53 @@ __device__ __forceinline__ int dispatch_item(const BatchItem& it, int64_t lo, in
   }
 }
 
+// Index of the item that owns global tile t: the last item whose
+// tile_begin <= t.  Warp 0 searches 32 ways at a time (one probe per lane, a
+// ballot picks the sub-range), so 4096 items take 3 dependent loads instead
+// of 12.  Called by all 32 lanes of warp 0, converged.
+__device__ __forceinline__ int find_item(const BatchItem* items, int nitems, int64_t t) {
+  const int lane = threadIdx.x & 31;
+  int a = 0, b = nitems - 1;  // items[a].tile_begin <= t always holds
+  while (a < b) {
+    const int step = (b - a + 32) / 32;  // ceil((b - a + 1) / 32)
+    const int k = a + lane * step;
+    const bool ok = k <= b && items[k].tile_begin <= t;
+    const unsigned m = __ballot_sync(0xffffffffu, ok);
+    const int hi = 31 - __clz((int)m);  // bit 0 is set: k = a satisfies ok
+    a += hi * step;
+    const int nb = a + step - 1;
+    b = nb < b ? nb : b;
+  }
+  return a;
+}
+
 template <int U>
 __global__ void __launch_bounds__(256) batch_kernel(const BatchParams p) {
   __shared__ int64_t s_tile;
   __shared__ int s_item;
   __shared__ bool s_last;
-  __shared__ double smem[256];
+  __shared__ double smem[kMaxBlock];
   const int64_t total = p.hdr->total_tiles;
   const int nitems = p.hdr->nitems;
   const int64_t tile_bytes = p.hdr->tile_bytes;
+  // Tile numbers come from an atomic counter (no waiting).  Thread 0 asks
+  // for the next one when a tile starts and hands it over when the tile
+  // ends, so the atomic's latency hides behind the tile's work; warp 0 then
+  // finds its item.
+  if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(p.counter, 1u);
+  __syncthreads();
   for (;;) {
-    if (threadIdx.x == 0) {
-      const int64_t t = (int64_t)atomicAdd(p.counter, 1u);
-      int item = 0;
-      if (t < total) {
-        int a = 0, b = nitems - 1;  // last item with tile_begin <= t
-        while (a < b) {
-          const int mid = (a + b + 1) >> 1;
-          if (p.items[mid].tile_begin <= t) a = mid;
-          else b = mid - 1;
-        }
-        item = a;
-      }
-      s_tile = t;
-      s_item = item;
+    if (threadIdx.x < 32) {
+      const int64_t t = s_tile;
+      const int item = t < total ? find_item(p.items, nitems, t) : 0;
+      if (threadIdx.x == 0) s_item = item;
     }
     __syncthreads();
     const int64_t tile = s_tile;
     if (tile >= total) break;
     const int item = s_item;
+    unsigned next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(p.counter, 1u);
     const BatchItem it = p.items[item];
     const int64_t tile_elems = tile_bytes / (it.dtype == DT_F32 ? 4 : 8);
     const int64_t lo = (tile - it.tile_begin) * tile_elems;
@@ -296,7 +314,9 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchParams p) {
         }
       }
     }
-    __syncthreads();  // s_tile / s_item / s_last are rewritten next iteration
+    __syncthreads();  // every thread has read s_tile / s_item / s_last of this tile
+    if (threadIdx.x == 0) s_tile = (int64_t)next;
+    __syncthreads();
   }
 }
 
