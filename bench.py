@@ -55,13 +55,21 @@ def f64_alu_peak_gops(sm_mhz: float) -> float:
     return 2 * 152 * sm_mhz * 1e6 / 1e9
 
 
-def source_hash() -> str:
+# The sources that define each profiled kernel (its template, the headers it
+# instantiates and the file that instantiates it); a traffic figure is used
+# only while these are unchanged since the capture.
+KERNEL_SOURCES = {
+    "e_f64": ["prog.cuh", "common.cuh", "fused.cuh", "reduce.cuh", "shapes.h", "registry.h", "inst.cuh",
+              "inst_f64_vb16.cu", "inst_f64_vb32.cu"],
+}
+
+
+def source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1109_1264_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in sorted(KERNEL_SOURCES.get(kernel, [])):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
@@ -255,7 +263,7 @@ def traffic_for(kernel: str, n: int):
     except Exception:
         return None
     ent = t.get(kernel)
-    if not ent or ent.get("source_hash") != source_hash():
+    if not ent or kernel not in KERNEL_SOURCES or ent.get("source_hash") != source_hash(kernel):
         return None
     return int(ent["dram_bytes_per_launch"] * n / ent["n"])
 
