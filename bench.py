@@ -290,6 +290,7 @@ def main():
     ap.add_argument("--tune-load", default=None,
                     help="profiling runs: load a saved launch table instead of autotuning")
     ap.add_argument("--only-cg", action="store_true", help="run only the CG leg (profiling runs)")
+    ap.add_argument("--only-served", action="store_true", help="run only the served leg (profiling runs)")
     ap.add_argument("--fixed-e-cfg", default=None,
                     help="profiling runs: skip the autotuner and launch e with U,VB,BLOCK,BLOCKS_PER_SM")
     ap.add_argument("--cg-log2", type=int, default=28)
@@ -315,6 +316,11 @@ def main():
     if args.sweep:
         if rank == 0:
             print(json.dumps(sweep_measure(torch, salt)), flush=True)
+        return
+
+    if args.only_served:
+        if rank == 0:
+            print(json.dumps({"served": served_measure(salt)}), flush=True)
         return
 
     if args.only_cg:
@@ -667,49 +673,70 @@ def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> 
 
 def served_measure(salt, count: int = 3000, seed: int = 0) -> dict:
     """Poisson stream of requests over the 5 served shapes (d = a + (b - c),
-    axpby, e, dot, nrm2), n log-uniform in [2^8, 2^24], 70% FP32 / 30% FP64,
-    operands resident in an 8 GiB arena; saturation throughput first (all
-    requests arrive at once), then arrival rates from 10% to 120% of it."""
+    axpby, e, dot, nrm2), n log-uniform in [2^8, 2^24], 70% FP32 / 30% FP64.
+    Inputs come from a resident store of counter-filled vectors (8 GiB: four
+    FP32 and two FP64 vectors of 2^28 elements, each request reading slices
+    at hashed offsets); outputs and axpby's read-and-written y live in the
+    server's 8 GiB arena.  Saturation throughput first (all requests arrive
+    at once), then arrival rates from 10% to 120% of it; then the same stream
+    served one request per step, and with every input generated per request
+    on the device (standing in for an upload) instead of the store."""
     import numpy as np
+    import torch
 
     from paper_1109_1264_gb300 import inputs
     ops = np.array([4, 3, 5, 2, 1], dtype=np.int64)  # operands read + written per shape
     shapes, is64, lens = inputs.request_mix(seed, count)
     es = np.where(is64, 8, 4)
     total_bytes = int(np.sum(ops[shapes] * es * lens))
+    slen = 1 << 28
+    store = ([torch.empty(slen, dtype=torch.float32, device="cuda") for _ in range(4)],
+             [torch.empty(slen, dtype=torch.float64, device="cuda") for _ in range(2)])
+    for j, t in enumerate(store[0] + store[1]):
+        salt.salt_fill_uniform(t, inputs.vector_key(seed + 1000, j, 0))
+    torch.cuda.synchronize()
+    zeros = np.zeros(count)
+    d32 = is64.astype(np.int32)
+
+    def saturation(srv, use_store):
+        st = store if use_store else None
+        srv.replay(zeros[:200], shapes[:200], d32[:200], lens[:200], seed + 99, store=st)  # warm-up
+        s0 = srv.stats()["steps"]
+        lat, _, wall = srv.replay(zeros, shapes, d32, lens, seed, store=st)
+        return lat, wall, srv.stats()["steps"] - s0
+
     srv = salt.Server()
     try:
-        zeros = np.zeros(count)
-        srv.replay(zeros[:200], shapes[:200], is64[:200].astype(np.int32), lens[:200], seed + 99)  # warm-up
-        lat, _, wall = srv.replay(zeros, shapes, is64.astype(np.int32), lens, seed)
+        _, wall, steps = saturation(srv, True)
         sat_rps = count / (wall * 1e-6)
         sat_gbs = total_bytes / (wall * 1e-6) / 1e9
         points = []
         for k, frac in enumerate((0.1, 0.3, 0.5, 0.7, 0.9, 1.2)):
             rate = frac * sat_rps
             arr = inputs.poisson_arrivals(seed + 1 + k, count, rate) * 1e6
-            lat, _, wall = srv.replay(arr, shapes, is64.astype(np.int32), lens, seed)
+            lat, _, wall_k = srv.replay(arr, shapes, d32, lens, seed, store=store)
             points.append({"load": frac, "rate_rps": round(rate, 1), "p50_us": round(float(np.percentile(lat, 50)), 1),
                            "p99_us": round(float(np.percentile(lat, 99)), 1),
-                           "gbs": round(total_bytes / (wall * 1e-6) / 1e9, 1)})
-        stats = srv.stats()
+                           "gbs": round(total_bytes / (wall_k * 1e-6) / 1e9, 1)})
+        _, wall_f, steps_f = saturation(srv, False)
     finally:
         srv.stop()
-    # The same stream without batching: one request per step (per-request fill
-    # and compute launches), all requests arriving at once.
     srv1 = salt.Server(max_batch=1)
     try:
-        srv1.replay(zeros[:200], shapes[:200], is64[:200].astype(np.int32), lens[:200], seed + 99)
-        _, _, wall1 = srv1.replay(zeros, shapes, is64.astype(np.int32), lens, seed)
+        _, wall1, _ = saturation(srv1, True)
     finally:
         srv1.stop()
+    del store
+    torch.cuda.empty_cache()
     unbatched_gbs = total_bytes / (wall1 * 1e-6) / 1e9
-    return {"saturation_rps": round(sat_rps, 1), "saturation_gbs": round(sat_gbs, 1),
+    return {"saturation_rps": round(sat_rps, 1), "saturation_gbs": round(sat_gbs, 1), "saturation_steps": steps,
             "unbatched_saturation_gbs": round(unbatched_gbs, 1), "batched_vs_unbatched": round(sat_gbs / unbatched_gbs, 2),
-            "requests_per_point": count, "bytes_per_point": total_bytes,
-            "points": points, "steps_total": stats["steps"],
-            "workload": "5 shapes uniform, n log-uniform [2^8, 2^24], 70% FP32 / 30% FP64, 8 GiB resident budget, "
-                        "2 streams; latency from arrival to observed completion (includes the on-device input fill)"}
+            "fill_per_request_saturation_gbs": round(total_bytes / (wall_f * 1e-6) / 1e9, 1),
+            "fill_per_request_steps": steps_f,
+            "requests_per_point": count, "bytes_per_point": total_bytes, "points": points,
+            "workload": "5 shapes uniform, n log-uniform [2^8, 2^24], 70% FP32 / 30% FP64; inputs from an 8 GiB "
+                        "resident store of counter-filled vectors (slices at hashed offsets), outputs in an 8 GiB "
+                        "arena, 2 streams; latency from arrival to observed completion"}
 
 
 def e2e_measure(torch, salt, loads, args, world, steps, abytes):

@@ -532,6 +532,19 @@ salt_status salt_serve_stop(salt_server* s);
 salt_status salt_serve_submit(salt_server* s, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
                               const uint64_t* keys, int32_t nkeys, const double* scalars, int32_t nscal,
                               int64_t* request_id);
+/* salt_serve_submit with caller-owned operands: ptrs (nops entries, may be
+ * NULL) gives, per operand index, a DEVICE pointer to n elements of the
+ * request's dtype, 16-byte aligned (SALT_ERR_ALIGN otherwise), that the
+ * request reads (and, if stored, writes) in place: no arena space, no fill.
+ * Operands whose pointer is NULL are server-owned and keyed by keys[k] as in
+ * salt_serve_submit (keys may be NULL if every operand has a pointer).  The
+ * caller keeps caller-owned memory valid and unmodified until the request
+ * is done; two requests in flight must not write memory another one reads
+ * or writes (not checked).  salt_serve_read copies caller-owned operands
+ * too. */
+salt_status salt_serve_submit_ex(salt_server* s, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                                 const void* const* ptrs, const uint64_t* keys, int32_t nops,
+                                 const double* scalars, int32_t nscal, int64_t* request_id);
 /* State: 0 waiting, 1 running, 2 done.  When done: *latency_us and the
  * request's DOT/SUMSQ/norm results in red[0..nred) (host memory); either
  * pointer may be NULL.  SALT_ERR_NOTFOUND for an unknown (or released) id. */
@@ -560,6 +573,21 @@ salt_status salt_serve_stats(salt_server* s, int64_t* completed, int64_t* steps,
 salt_status salt_serve_replay(salt_server* s, int32_t count, const double* arrival_us, const int32_t* shape,
                               const int32_t* dtype, const int64_t* n, uint64_t seed, double* latency_us,
                               double* red_first, double* wall_us);
+/* salt_serve_replay over a RESIDENT STORE: the input operands that a shape
+ * only reads come from caller-owned device vectors (salt_serve_submit_ex)
+ * instead of a per-request fill: operand k of request i reads elements
+ * [o, o + n[i]) of store vector (5 i + k) mod nstore of its dtype, with
+ *   h = (key * 0x9E3779B97F4A7C15 mod 2^64) >> 11,
+ *   o = (h mod (len - n[i] + 1)), rounded down to a multiple of 4,
+ * key the operand's key above.  Stored operands (d, y, e) stay server-owned
+ * (y, read and written, is filled from its key).  store_f32 / store_f64:
+ * nstore_f32 / nstore_f64 device vectors of len_f32 / len_f64 elements,
+ * 16-byte aligned; every n[i] <= the length of its dtype's vectors. */
+salt_status salt_serve_replay_store(salt_server* s, int32_t count, const double* arrival_us, const int32_t* shape,
+                                    const int32_t* dtype, const int64_t* n, uint64_t seed,
+                                    const void* const* store_f32, int32_t nstore_f32, int64_t len_f32,
+                                    const void* const* store_f64, int32_t nstore_f64, int64_t len_f64,
+                                    double* latency_us, double* red_first, double* wall_us);
 
 #ifdef __cplusplus
 }

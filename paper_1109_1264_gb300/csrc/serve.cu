@@ -108,6 +108,7 @@ struct Request {
   double sc[2] = {0.0, 0.0};
   size_t vec_bytes = 0;
   size_t off[kBatchOps] = {0, 0, 0, 0, 0};
+  char* ext[kBatchOps] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // caller-owned operand, or NULL
   bool resident = false;
   int32_t state = RS_WAITING;
   double t_submit = 0, t_done = 0;
@@ -194,18 +195,26 @@ size_t slot_device_bytes(const salt_server* s, size_t* off_items, size_t* off_co
 }
 
 // Called with the request's shape/dtype set: lay out its operands in the arena.
+// Caller-owned operands take no arena space.
 bool arena_take(salt_server* s, Request* r) {
   int k = 0;
   for (; k < r->nvec; ++k) {
+    if (r->ext[k]) continue;
     if (!s->arena.alloc(r->vec_bytes, &r->off[k])) break;
   }
   if (k == r->nvec) return true;
-  for (int j = 0; j < k; ++j) s->arena.release(r->off[j], r->vec_bytes);
+  for (int j = 0; j < k; ++j)
+    if (!r->ext[j]) s->arena.release(r->off[j], r->vec_bytes);
   return false;
 }
 
 void arena_give(salt_server* s, Request* r) {
-  for (int k = 0; k < r->nvec; ++k) s->arena.release(r->off[k], r->vec_bytes);
+  for (int k = 0; k < r->nvec; ++k)
+    if (!r->ext[k]) s->arena.release(r->off[k], r->vec_bytes);
+}
+
+char* operand_ptr(const salt_server* s, const Request* r, int k) {
+  return r->ext[k] ? r->ext[k] : s->arena_base + r->off[k];
 }
 
 int64_t tiles_of(const salt_server* s, int dtype, int64_t n) {
@@ -225,10 +234,9 @@ salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch
   int64_t tiles[2] = {0, 0};
   int nred = 0;
   for (Request* r : batch) {
-    char* base = s->arena_base;
     const int dt = r->dtype == SALT_F32 ? DT_F32 : DT_F64;
     for (int k = 0; k < r->nvec; ++k) {
-      if (!((r->load_mask >> k) & 1u)) continue;
+      if (!((r->load_mask >> k) & 1u) || r->ext[k]) continue;  // caller-owned inputs are already there
       BatchItem& f = h_items[0][nitems[0]++];
       memset(&f, 0, sizeof f);
       f.kind = kKindFill;
@@ -237,7 +245,7 @@ salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch
       f.tile_begin = tiles[0];
       f.ntiles = (int32_t)tiles_of(s, r->dtype, r->n);
       f.red_index = -1;
-      f.v[0] = base + r->off[k];
+      f.v[0] = operand_ptr(s, r, k);
       uint64_t key = r->keys[k];
       memcpy(&f.sc[0], &key, sizeof key);
       tiles[0] += f.ntiles;
@@ -250,7 +258,7 @@ salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch
     c.tile_begin = tiles[1];
     c.ntiles = (int32_t)tiles_of(s, r->dtype, r->n);
     c.red_index = r->nred > 0 ? nred : -1;
-    for (int k = 0; k < r->nvec; ++k) c.v[k] = base + r->off[k];
+    for (int k = 0; k < r->nvec; ++k) c.v[k] = operand_ptr(s, r, k);
     c.sc[0] = r->sc[0];
     c.sc[1] = r->sc[1];
     tiles[1] += c.ntiles;
@@ -348,7 +356,8 @@ void scheduler(salt_server* s) {
         while (!s->pending.empty() && (int32_t)batch.size() < s->cfg.max_batch) {
           Request* r = s->pending.front();
           const int64_t t = tiles_of(s, r->dtype, r->n);
-          const int nf = __builtin_popcount(r->load_mask);
+          int nf = 0;
+          for (int k = 0; k < r->nvec; ++k) nf += ((r->load_mask >> k) & 1u) && !r->ext[k];
           if (!batch.empty() && (tiles + t > s->tiles_cap || fills + nf > s->items_cap)) break;
           s->pending.pop_front();
           r->state = RS_RUNNING;
@@ -380,12 +389,25 @@ uint64_t vector_key(uint64_t seed, uint64_t item, uint64_t slot) {
   return seed * 0x100000001B3ull + item * 16ull + slot + 1ull;
 }
 
+// Store vector and element offset of input operand k of replayed request i
+// (salt_serve_replay_store): vector (5 i + k) mod count, offset a multiple of
+// 4 elements (16-byte aligned) in [0, len - n], spread by a multiplicative
+// hash of the operand's key.
+int32_t store_vector(int64_t i, int k, int32_t count) { return (int32_t)(((uint64_t)i * 5u + (uint64_t)k) % (uint64_t)count); }
+int64_t store_offset(uint64_t seed, uint64_t i, uint64_t k, int64_t n, int64_t len) {
+  const uint64_t h = (vector_key(seed, i, k) * 0x9E3779B97F4A7C15ull) >> 11;
+  const int64_t o = (int64_t)(h % (uint64_t)(len - n + 1));
+  return o - o % 4;
+}
+
 salt_status submit_impl(salt_server* s, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
-                        const uint64_t* keys, int32_t nkeys, const double* scalars, int32_t nscal,
-                        double t_submit, int64_t* id_out) {
+                        const void* const* ptrs, const uint64_t* keys, int32_t nkeys, const double* scalars,
+                        int32_t nscal, double t_submit, int64_t* id_out) {
   if (dtype != SALT_F32 && dtype != SALT_F64) return fail(SALT_ERR_DTYPE, "dtype must be SALT_F32 or SALT_F64");
   if (n < 0 || n > s->cfg.max_n) return fail(SALT_ERR_ARG, "n outside 0 .. max_n of the server");
-  if (nkeys < 0 || nkeys > kBatchOps || (nkeys > 0 && !keys)) return fail(SALT_ERR_ARG, "bad keys");
+  if (nkeys < 0 || nkeys > kBatchOps || (nkeys > 0 && !keys && !ptrs)) return fail(SALT_ERR_ARG, "bad keys");
+  for (int k = 0; ptrs && k < nkeys; ++k)
+    if (ptrs[k] && (uintptr_t)ptrs[k] % 16) return fail(SALT_ERR_ALIGN, "caller-owned operands must be 16-byte aligned");
   Request* r = new Request();
   r->dtype = dtype;
   r->n = n;
@@ -399,7 +421,8 @@ salt_status submit_impl(salt_server* s, const salt_insn* prog, int32_t nprog, in
     r->nvec = 1;
     r->load_mask = 1u;
     r->nred = 1;
-    r->keys[0] = keys[0];
+    r->keys[0] = keys ? keys[0] : 0;
+    r->ext[0] = ptrs ? (char*)ptrs[0] : nullptr;
     r->bytes_alg = n * es;
   } else {
     Analysis an;
@@ -426,7 +449,12 @@ salt_status submit_impl(salt_server* s, const salt_insn* prog, int32_t nprog, in
     r->nred = c.nred;
     for (int k = 0; k < c.nvec; ++k) {
       r->user_of[k] = c.vec_user[k];
-      r->keys[k] = keys[c.vec_user[k]];
+      r->ext[k] = ptrs ? (char*)ptrs[c.vec_user[k]] : nullptr;
+      if (!r->ext[k] && !keys) {
+        delete r;
+        return fail(SALT_ERR_ARG, "an operand has neither a pointer nor a key");
+      }
+      r->keys[k] = r->ext[k] ? 0 : keys[c.vec_user[k]];
     }
     for (int k = 0; k < c.nscal; ++k) {
       const double v = scalars[c.scal_user[k]];
@@ -435,7 +463,9 @@ salt_status submit_impl(salt_server* s, const salt_insn* prog, int32_t nprog, in
     r->bytes_alg = (int64_t)(__builtin_popcount(c.load_mask) + __builtin_popcount(c.store_mask)) * es * n;
   }
   r->vec_bytes = round_up((size_t)std::max<int64_t>(n, 1) * es);
-  if ((int64_t)(r->vec_bytes * r->nvec) > s->cfg.budget_bytes) {
+  int owned = 0;
+  for (int k = 0; k < r->nvec; ++k) owned += r->ext[k] == nullptr;
+  if ((int64_t)(r->vec_bytes * owned) > s->cfg.budget_bytes) {
     delete r;
     return fail(SALT_ERR_BUDGET, "request needs more device memory than the whole budget");
   }
@@ -548,7 +578,14 @@ salt_status salt_serve_submit(salt_server* s, const salt_insn* prog, int32_t npr
                               const uint64_t* keys, int32_t nkeys, const double* scalars, int32_t nscal,
                               int64_t* request_id) {
   if (!s || !request_id) return fail(SALT_ERR_ARG, "server or request_id is NULL");
-  return submit_impl(s, prog, nprog, dtype, n, keys, nkeys, scalars, nscal, now_us(), request_id);
+  return submit_impl(s, prog, nprog, dtype, n, nullptr, keys, nkeys, scalars, nscal, now_us(), request_id);
+}
+
+salt_status salt_serve_submit_ex(salt_server* s, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
+                                 const void* const* ptrs, const uint64_t* keys, int32_t nops,
+                                 const double* scalars, int32_t nscal, int64_t* request_id) {
+  if (!s || !request_id) return fail(SALT_ERR_ARG, "server or request_id is NULL");
+  return submit_impl(s, prog, nprog, dtype, n, ptrs, keys, nops, scalars, nscal, now_us(), request_id);
 }
 
 salt_status salt_serve_poll(salt_server* s, int64_t id, int32_t* state, double* latency_us, double* red) {
@@ -600,7 +637,7 @@ salt_status salt_serve_read(salt_server* s, int64_t id, int32_t operand, void* h
     es = r->dtype == SALT_F32 ? 4 : 8;
     n = r->n;
     if (bytes < n * es) return fail(SALT_ERR_ARG, "host buffer too small");
-    src = s->arena_base + r->off[k];
+    src = operand_ptr(s, r, k);
   }
   if (n == 0) return SALT_OK;
   cudaError_t e = cudaMemcpy(host_dst, src, (size_t)(n * es), cudaMemcpyDeviceToHost);
@@ -662,21 +699,35 @@ salt_status salt_serve_stop(salt_server* s) {
   return SALT_OK;
 }
 
-salt_status salt_serve_replay(salt_server* s, int32_t count, const double* arrival_us, const int32_t* shape,
-                              const int32_t* dtype, const int64_t* n, uint64_t seed, double* latency_us,
-                              double* red_first, double* wall_us) {
+}  // extern "C"
+
+namespace {
+
+// Standard served shapes of the load generator and, per shape, the operands
+// it stores (those never come from a caller's store).
+const salt_insn kReplayProgs[4][12] = {
+    {{SALT_OP_VEC, 0}, {SALT_OP_VEC, 1}, {SALT_OP_VEC, 2}, {SALT_OP_SUB, 0}, {SALT_OP_ADD, 0}, {SALT_OP_STORE, 3}},
+    {{SALT_OP_SCAL, 0}, {SALT_OP_VEC, 0}, {SALT_OP_SMUL, 0}, {SALT_OP_SCAL, 1}, {SALT_OP_VEC, 1},
+     {SALT_OP_SMUL, 0}, {SALT_OP_ADD, 0}, {SALT_OP_STORE, 1}},
+    {{SALT_OP_SCAL, 0}, {SALT_OP_VEC, 0}, {SALT_OP_SMUL, 0}, {SALT_OP_SCAL, 1}, {SALT_OP_VEC, 1},
+     {SALT_OP_SMUL, 0}, {SALT_OP_ADD, 0}, {SALT_OP_VEC, 2}, {SALT_OP_VEC, 3}, {SALT_OP_MUL, 0},
+     {SALT_OP_SUB, 0}, {SALT_OP_STORE, 4}},
+    {{SALT_OP_VEC, 0}, {SALT_OP_VEC, 1}, {SALT_OP_DOT, 0}}};
+const int32_t kReplayLen[4] = {6, 8, 12, 3};
+const int32_t kReplayVecs[5] = {4, 2, 5, 2, 1};
+const int32_t kReplayStored[5] = {3, 1, 4, -1, -1};  // stored operand per shape, or -1
+
+struct ReplayStore {
+  const void* const* vec[2] = {nullptr, nullptr};  // [F32, F64] store vectors
+  int32_t count[2] = {0, 0};
+  int64_t len[2] = {0, 0};
+};
+
+salt_status replay_impl(salt_server* s, int32_t count, const double* arrival_us, const int32_t* shape,
+                        const int32_t* dtype, const int64_t* n, uint64_t seed, const ReplayStore* store,
+                        double* latency_us, double* red_first, double* wall_us) {
   if (!s || count < 0 || (count > 0 && (!arrival_us || !shape || !dtype || !n || !latency_us)))
     return fail(SALT_ERR_ARG, "bad replay arguments");
-  static const salt_insn progs[4][12] = {
-      {{SALT_OP_VEC, 0}, {SALT_OP_VEC, 1}, {SALT_OP_VEC, 2}, {SALT_OP_SUB, 0}, {SALT_OP_ADD, 0}, {SALT_OP_STORE, 3}},
-      {{SALT_OP_SCAL, 0}, {SALT_OP_VEC, 0}, {SALT_OP_SMUL, 0}, {SALT_OP_SCAL, 1}, {SALT_OP_VEC, 1},
-       {SALT_OP_SMUL, 0}, {SALT_OP_ADD, 0}, {SALT_OP_STORE, 1}},
-      {{SALT_OP_SCAL, 0}, {SALT_OP_VEC, 0}, {SALT_OP_SMUL, 0}, {SALT_OP_SCAL, 1}, {SALT_OP_VEC, 1},
-       {SALT_OP_SMUL, 0}, {SALT_OP_ADD, 0}, {SALT_OP_VEC, 2}, {SALT_OP_VEC, 3}, {SALT_OP_MUL, 0},
-       {SALT_OP_SUB, 0}, {SALT_OP_STORE, 4}},
-      {{SALT_OP_VEC, 0}, {SALT_OP_VEC, 1}, {SALT_OP_DOT, 0}}};
-  static const int32_t plen[4] = {6, 8, 12, 3};
-  static const int32_t pvec[5] = {4, 2, 5, 2, 1};
   const double sc[2] = {1.5, -0.25};
   std::vector<int64_t> ids((size_t)count, 0);
   std::unordered_map<int64_t, int32_t> index_of;
@@ -689,10 +740,21 @@ salt_status salt_serve_replay(salt_server* s, int32_t count, const double* arriv
       const int sh = shape[next];
       if (sh < 0 || sh > 4) return fail(SALT_ERR_ARG, "shape index outside 0..4");
       uint64_t keys[kBatchOps];
-      for (int k = 0; k < pvec[sh]; ++k) keys[k] = vector_key(seed, (uint64_t)next, (uint64_t)k);
+      const void* ptrs[kBatchOps] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+      for (int k = 0; k < kReplayVecs[sh]; ++k) {
+        keys[k] = vector_key(seed, (uint64_t)next, (uint64_t)k);
+        if (store && k != kReplayStored[sh]) {
+          const int t2 = dtype[next] == SALT_F64 ? 1 : 0;
+          const int64_t len = store->len[t2], nn = n[next];
+          if (store->count[t2] < 1 || nn > len) return fail(SALT_ERR_ARG, "store has no vector long enough");
+          ptrs[k] = (const char*)store->vec[t2][store_vector(next, k, store->count[t2])] +
+                    store_offset(seed, (uint64_t)next, (uint64_t)k, nn, len) * (dtype[next] == SALT_F64 ? 8 : 4);
+        }
+      }
       int64_t id = 0;
-      salt_status st = submit_impl(s, sh == 4 ? nullptr : progs[sh], sh == 4 ? 0 : plen[sh], dtype[next], n[next],
-                                   keys, pvec[sh], sc, 2, t0 + arrival_us[next], &id);
+      salt_status st = submit_impl(s, sh == 4 ? nullptr : kReplayProgs[sh], sh == 4 ? 0 : kReplayLen[sh],
+                                   dtype[next], n[next], store ? ptrs : nullptr, keys, kReplayVecs[sh], sc, 2,
+                                   t0 + arrival_us[next], &id);
       if (st != SALT_OK) return st;
       ids[(size_t)next] = id;
       index_of[id] = next;
@@ -726,6 +788,37 @@ salt_status salt_serve_replay(salt_server* s, int32_t count, const double* arriv
   }
   if (wall_us) *wall_us = last_done - t0;
   return SALT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+salt_status salt_serve_replay(salt_server* s, int32_t count, const double* arrival_us, const int32_t* shape,
+                              const int32_t* dtype, const int64_t* n, uint64_t seed, double* latency_us,
+                              double* red_first, double* wall_us) {
+  return replay_impl(s, count, arrival_us, shape, dtype, n, seed, nullptr, latency_us, red_first, wall_us);
+}
+
+salt_status salt_serve_replay_store(salt_server* s, int32_t count, const double* arrival_us, const int32_t* shape,
+                                    const int32_t* dtype, const int64_t* n, uint64_t seed,
+                                    const void* const* store_f32, int32_t nstore_f32, int64_t len_f32,
+                                    const void* const* store_f64, int32_t nstore_f64, int64_t len_f64,
+                                    double* latency_us, double* red_first, double* wall_us) {
+  if (nstore_f32 < 0 || nstore_f64 < 0 || (nstore_f32 > 0 && !store_f32) || (nstore_f64 > 0 && !store_f64))
+    return fail(SALT_ERR_ARG, "bad store");
+  for (int i = 0; i < nstore_f32; ++i)
+    if (!store_f32[i] || (uintptr_t)store_f32[i] % 16) return fail(SALT_ERR_ALIGN, "store vectors must be 16-byte aligned");
+  for (int i = 0; i < nstore_f64; ++i)
+    if (!store_f64[i] || (uintptr_t)store_f64[i] % 16) return fail(SALT_ERR_ALIGN, "store vectors must be 16-byte aligned");
+  ReplayStore st;
+  st.vec[0] = store_f32;
+  st.vec[1] = store_f64;
+  st.count[0] = nstore_f32;
+  st.count[1] = nstore_f64;
+  st.len[0] = len_f32;
+  st.len[1] = len_f64;
+  return replay_impl(s, count, arrival_us, shape, dtype, n, seed, &st, latency_us, red_first, wall_us);
 }
 
 }  // extern "C"

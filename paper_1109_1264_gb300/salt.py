@@ -426,6 +426,11 @@ _SERVE_SIGS = {
                          ctypes.POINTER(_i64), ctypes.POINTER(_i32)],
     "salt_serve_replay": [_vp, _i32, _dp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64),
                           ctypes.c_uint64, _dp, _dp, _dp],
+    "salt_serve_submit_ex": [_vp, ctypes.POINTER(Insn), _i32, _i32, _i64, ctypes.POINTER(_vp),
+                             ctypes.POINTER(ctypes.c_uint64), _i32, _dp, _i32, ctypes.POINTER(_i64)],
+    "salt_serve_replay_store": [_vp, _i32, _dp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64),
+                                ctypes.c_uint64, ctypes.POINTER(_vp), _i32, _i64, ctypes.POINTER(_vp), _i32, _i64,
+                                _dp, _dp, _dp],
 }
 for _name, _args in _SERVE_SIGS.items():
     _f = getattr(lib, _name)
@@ -465,13 +470,20 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, prog, dtype: int, n: int, keys, scalars=()) -> int:
+    def submit(self, prog, dtype: int, n: int, keys, scalars=(), ptrs=None) -> int:
+        """``ptrs`` (optional, one per operand): caller-owned device tensors
+        or None (server-owned, filled from the key) -> salt_serve_submit_ex."""
         arr, m = program(prog) if prog is not None else (None, 0)
         ks = (ctypes.c_uint64 * max(len(keys), 1))(*[int(k) & 0xFFFFFFFFFFFFFFFF for k in keys])
         sc = (ctypes.c_double * max(len(scalars), 1))(*[float(s) for s in scalars])
         rid = ctypes.c_int64()
-        _check(lib.salt_serve_submit(self.handle, arr, m, dtype, int(n), ks, len(keys), sc, len(scalars),
-                                     ctypes.byref(rid)))
+        if ptrs is None:
+            _check(lib.salt_serve_submit(self.handle, arr, m, dtype, int(n), ks, len(keys), sc, len(scalars),
+                                         ctypes.byref(rid)))
+        else:
+            ps = (ctypes.c_void_p * max(len(ptrs), 1))(*[None if p is None else _ptr(p) for p in ptrs])
+            _check(lib.salt_serve_submit_ex(self.handle, arr, m, dtype, int(n), ps, ks, len(ptrs), sc,
+                                            len(scalars), ctypes.byref(rid)))
         return rid.value
 
     def poll(self, rid: int):
@@ -499,8 +511,10 @@ class Server:
         return {"completed": c.value, "steps": s.value, "bytes": b.value, "resident_bytes": r.value,
                 "waiting": w.value}
 
-    def replay(self, arrival_us, shape, dtype, n, seed: int):
-        """Returns (latency_us array, first results array, wall_us)."""
+    def replay(self, arrival_us, shape, dtype, n, seed: int, store=None):
+        """Returns (latency_us array, first results array, wall_us).  ``store``
+        = (list of float32 CUDA tensors, list of float64 CUDA tensors): the
+        resident store of salt_serve_replay_store."""
         import numpy as np
         cnt = len(arrival_us)
         a = np.ascontiguousarray(arrival_us, dtype=np.float64)
@@ -511,11 +525,19 @@ class Server:
         red = np.zeros(cnt, dtype=np.float64)
         wall = ctypes.c_double()
         P = ctypes.POINTER
-        _check(lib.salt_serve_replay(self.handle, cnt, a.ctypes.data_as(P(ctypes.c_double)),
-                                     s.ctypes.data_as(P(ctypes.c_int32)), d.ctypes.data_as(P(ctypes.c_int32)),
-                                     nn.ctypes.data_as(P(ctypes.c_int64)), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                                     lat.ctypes.data_as(P(ctypes.c_double)), red.ctypes.data_as(P(ctypes.c_double)),
-                                     ctypes.byref(wall)))
+        head = (self.handle, cnt, a.ctypes.data_as(P(ctypes.c_double)), s.ctypes.data_as(P(ctypes.c_int32)),
+                d.ctypes.data_as(P(ctypes.c_int32)), nn.ctypes.data_as(P(ctypes.c_int64)),
+                int(seed) & 0xFFFFFFFFFFFFFFFF)
+        tail = (lat.ctypes.data_as(P(ctypes.c_double)), red.ctypes.data_as(P(ctypes.c_double)), ctypes.byref(wall))
+        if store is None:
+            _check(lib.salt_serve_replay(*head, *tail))
+        else:
+            v32, v64 = store
+            p32 = (ctypes.c_void_p * max(len(v32), 1))(*[_ptr(t) for t in v32])
+            p64 = (ctypes.c_void_p * max(len(v64), 1))(*[_ptr(t) for t in v64])
+            l32 = min((t.numel() for t in v32), default=0)
+            l64 = min((t.numel() for t in v64), default=0)
+            _check(lib.salt_serve_replay_store(*head, p32, len(v32), l32, p64, len(v64), l64, *tail))
         return lat, red, wall.value
 
 

@@ -180,3 +180,94 @@ def test_replay_poisson_trace(salt):
         assert srv.stats()["resident_bytes"] == 0
     finally:
         srv.stop()
+
+
+M64 = (1 << 64) - 1
+
+
+def store_place(seed, i, k, n, length, count):
+    """Store vector and offset of input operand k of replayed request i
+    (the formula salt_serve_replay_store documents)."""
+    key = (seed * 0x100000001B3 + i * 16 + k + 1) & M64
+    h = ((key * 0x9E3779B97F4A7C15) & M64) >> 11
+    o = h % (length - n + 1)
+    return (i * 5 + k) % count, o - o % 4
+
+
+def test_caller_owned_operands(salt, cuda_dev):
+    """Inputs in caller-owned device memory (no fill), the output server-owned
+    or caller-owned: the same bits as the oracle."""
+    srv = salt.Server(budget_bytes=1 << 28, max_n=1 << 20)
+    try:
+        for dt, code, tdt in ((np.float32, salt.F32, torch.float32), (np.float64, salt.F64, torch.float64)):
+            for n in (1, 1000, (1 << 20) - 3):
+                keys = [inputs.vector_key(31, n, k) for k in range(5)]
+                host = [inputs.hash_uniform(k, n, dt) for k in keys]
+                dev = [torch.from_numpy(h).to(cuda_dev) for h in host]
+                out_dev = torch.zeros(n, dtype=tdt, device=cuda_dev)
+                want = [h.copy() for h in host[:4]] + [np.zeros(n, dt)]
+                oracle.eval_program(P.PROG_E, want, SC)
+                # inputs caller-owned, output server-owned
+                a = srv.submit(P.PROG_E, code, n, keys, SC, ptrs=dev[:4] + [None])
+                # everything caller-owned (keys unused)
+                b = srv.submit(P.PROG_E, code, n, keys, SC, ptrs=dev[:4] + [out_dev])
+                # dot with caller-owned inputs
+                c = srv.submit(P.PROG_DOT, code, n, keys[:2], ptrs=dev[:2])
+                for rid in (a, b, c):
+                    srv.wait(rid, 20_000_000)
+                assert_bits_equal(srv.read(a, 4, np.empty(n, dt)), want[4], f"server-owned out n={n}")
+                assert_bits_equal(out_dev.cpu().numpy(), want[4], f"caller-owned out n={n}")
+                assert_bits_equal(srv.read(b, 0, np.empty(n, dt)), host[0], "read of a caller-owned operand")
+                red = srv.poll(c)[2][0]
+                ref = exact.exact_dot(host[0], host[1])
+                assert abs(red - ref) <= TOL[dt] * exact.abs_dot(host[0], host[1])
+                for rid in (a, b, c):
+                    srv.release(rid)
+        assert srv.stats()["resident_bytes"] == 0
+        with pytest.raises(salt.SaltError) as ei:
+            x = torch.zeros(64, dtype=torch.float32, device=cuda_dev)
+            srv.submit(P.PROG_DOT, salt.F32, 10, [1, 2], ptrs=[x[1:], x])  # 4-byte offset
+        assert ei.value.status == salt.ERR_ALIGN
+    finally:
+        srv.stop()
+
+
+def test_replay_resident_store(salt, cuda_dev):
+    """The load generator reading inputs from a resident store: dot and norm
+    results against the exact values of the store slices they read."""
+    srv = salt.Server(budget_bytes=1 << 30, max_n=1 << 18)
+    try:
+        length = (1 << 20) + 8
+        skeys = {np.float32: [901, 902, 903], np.float64: [911, 912]}
+        store = {dt: [torch.empty(length, dtype=torch.float32 if dt == np.float32 else torch.float64,
+                                  device=cuda_dev) for _ in skeys[dt]] for dt in skeys}
+        for dt in skeys:
+            for t, k in zip(store[dt], skeys[dt]):
+                salt.salt_fill_uniform(t, k)
+        count = 400
+        shapes, is64, lens = inputs.request_mix(13, count, lo=2 ** 8, hi=2 ** 18)
+        arr = inputs.poisson_arrivals(13, count, 20_000.0) * 1e6
+        lat, red, wall = srv.replay(arr, shapes, is64.astype(np.int32), lens, seed=13,
+                                    store=(store[np.float32], store[np.float64]))
+        assert np.all(lat > 0) and wall > 0
+        checked = 0
+        for i in range(count):
+            si = int(shapes[i])
+            if SHAPES[si][0] not in (P.PROG_DOT, None):
+                continue
+            dt = np.float64 if is64[i] else np.float32
+            n = int(lens[i])
+            vecs = []
+            for k in range(SHAPES[si][1]):
+                j, o = store_place(13, i, k, n, length, len(skeys[dt]))
+                vecs.append(inputs.hash_uniform(skeys[dt][j], n, dt, offset=o))
+            if si == 4:
+                ref, scale = exact.exact_nrm2(vecs[0]), exact.exact_nrm2(vecs[0])
+            else:
+                ref, scale = exact.exact_dot(vecs[0], vecs[1]), exact.abs_dot(vecs[0], vecs[1])
+            assert abs(red[i] - ref) <= TOL[dt] * scale, (i, red[i], ref)
+            checked += 1
+        assert checked > 100
+        assert srv.stats()["resident_bytes"] == 0
+    finally:
+        srv.stop()
