@@ -286,6 +286,7 @@ def main():
     ap.add_argument("--only-batched", action="store_true", help="run only the batched leg (profiling runs)")
     ap.add_argument("--sweep", action="store_true", help="the paper's four-op size sweep instead of the step")
     ap.add_argument("--no-cg", action="store_true")
+    ap.add_argument("--e2e-chunks", type=int, default=16, help="chunks per vector in the end-to-end pipeline")
     ap.add_argument("--tune-save", default=None, help="write the autotuned launch table to this file")
     ap.add_argument("--tune-load", default=None,
                     help="profiling runs: load a saved launch table instead of autotuning")
@@ -756,39 +757,57 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
         d2h += 2 * w.n * ES[dt] + 16
     stream = torch.cuda.current_stream()
     # The step is pipelined through the public API: each vector is split into
-    # chunks, and chunk k's uploads, kernels and read-backs go to stream k % 2,
-    # so copies in both directions overlap the kernels of the other stream.
-    nchunks = 8
-    side = [torch.cuda.Stream() for _ in range(2)]
+    # chunks; one stream uploads every chunk back to back (the host->device
+    # engine never waits on a read-back), a second runs each chunk's ops as
+    # soon as its upload has landed, a third reads the chunk's results back.
+    nchunks = args.e2e_chunks
+    up, comp, down = (torch.cuda.Stream() for _ in range(3))
     dred = {dt: torch.zeros(2 * nchunks, dtype=torch.float64, device="cuda") for dt in loads}
     for dt in loads:
         host[dt]["red"] = torch.empty(2 * nchunks, dtype=torch.float64, pin_memory=True)
         d2h += 16 * nchunks - 16
 
     def step():
-        for s in side:
+        for s in (up, comp, down):
             s.wait_stream(stream)
+        work = []
         for dt, w in loads.items():
-            hs = host[dt]
             n = w.n
             bounds = [n * k // nchunks for k in range(nchunks + 1)]
             bounds = [b - b % 4 for b in bounds[:-1]] + [n]
             for k in range(nchunks):
-                lo, hi = bounds[k], bounds[k + 1]
-                with torch.cuda.stream(side[k % 2]):
-                    dv = {key: getattr(w, key)[lo:hi] for key in ("a", "b", "c", "d", "y", "out")}
-                    for key in ("a", "b", "c", "d", "y"):
-                        dv[key].copy_(hs[key][lo:hi], non_blocking=True)
-                    salt.salt_eval(PROG_E, [dv["a"], dv["b"], dv["c"], dv["d"], dv["out"]], [ALPHA, BETA])
-                    salt.salt_axpby(ALPHA, dv["a"], BETA, dv["y"])
-                    salt.salt_dot(dv["a"], dv["b"], dred[dt][2 * k:2 * k + 1])
-                    salt.salt_nrm2(dv["c"], dred[dt][2 * k + 1:2 * k + 2])
-                    hs["out"][lo:hi].copy_(dv["out"], non_blocking=True)
-                    hs["y_out"][lo:hi].copy_(dv["y"], non_blocking=True)
-        for s in side:
+                work.append((dt, w, k, bounds[k], bounds[k + 1]))
+        landed = []
+        with torch.cuda.stream(up):
+            for dt, w, k, lo, hi in work:
+                hs = host[dt]
+                for key in ("a", "b", "c", "d", "y"):
+                    getattr(w, key)[lo:hi].copy_(hs[key][lo:hi], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(up)
+                landed.append(ev)
+        done = []
+        with torch.cuda.stream(comp):
+            for (dt, w, k, lo, hi), ev in zip(work, landed):
+                comp.wait_event(ev)
+                dv = {key: getattr(w, key)[lo:hi] for key in ("a", "b", "c", "d", "y", "out")}
+                salt.salt_eval(PROG_E, [dv["a"], dv["b"], dv["c"], dv["d"], dv["out"]], [ALPHA, BETA], stream=comp)
+                salt.salt_axpby(ALPHA, dv["a"], BETA, dv["y"], stream=comp)
+                salt.salt_dot(dv["a"], dv["b"], dred[dt][2 * k:2 * k + 1], stream=comp)
+                salt.salt_nrm2(dv["c"], dred[dt][2 * k + 1:2 * k + 2], stream=comp)
+                ev2 = torch.cuda.Event()
+                ev2.record(comp)
+                done.append(ev2)
+        with torch.cuda.stream(down):
+            for (dt, w, k, lo, hi), ev in zip(work, done):
+                down.wait_event(ev)
+                hs = host[dt]
+                hs["out"][lo:hi].copy_(w.out[lo:hi], non_blocking=True)
+                hs["y_out"][lo:hi].copy_(w.y[lo:hi], non_blocking=True)
+            for dt in loads:
+                host[dt]["red"].copy_(dred[dt], non_blocking=True)
+        for s in (up, comp, down):
             stream.wait_stream(s)
-        for dt in loads:
-            host[dt]["red"].copy_(dred[dt], non_blocking=True)
 
     def combine():
         # dot = sum of chunk dots; nrm2 = sqrt(sum of chunk norms squared)
@@ -815,7 +834,7 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
     return {"value": round(world * step_bytes * k / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
             "ms_per_step": round(ms / k, 3),
-            "pipeline": f"{nchunks} chunks per vector over 2 streams (uploads, kernels and read-backs overlap)"}
+            "pipeline": f"{nchunks} chunks per vector; upload, compute and read-back streams overlap"}
 
 
 if __name__ == "__main__":
