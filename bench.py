@@ -457,7 +457,11 @@ def main():
         result["cg"] = cg_measure(torch, salt, log2n=args.cg_log2)
 
     if rank == 0 and world == 1 and not args.no_cpu:
+        # The CPU-oracle leg: the oracle timed on the host, and the oracle's
+        # exact references judging the GPU reductions' precision.
         result["cpu_baseline"] = cpu_baseline(1 << args.cpu_log2)
+        torch.cuda.empty_cache()
+        result["cpu_baseline"]["precision_vs_exact"] = precision_measure(torch, salt)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -670,6 +674,45 @@ def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> 
         del d, b, x, r, p, q, vecs
         torch.cuda.empty_cache()
     return out
+
+
+def precision_measure(torch, salt, log2n: int = 26) -> dict:
+    """The precision comparison of the dot product and norm: FP32 inputs of
+    random sign and magnitudes 10^U(-3, 3), n = 2^26.  Errors of the
+    compensated FP32 path (the default), the plain FP32 path (FP32
+    accumulation and combination) and the FP64 path on the widened data,
+    relative to the exactly rounded value, beside the CPU oracle's own
+    sequential FP64 sum.  Part of the CPU-oracle leg (it uses the oracle's
+    exact references)."""
+    import numpy as np
+
+    from oracle import exact
+    import oracle as orc
+    from paper_1109_1264_gb300 import inputs
+    n = 1 << log2n
+    x, y = inputs.logmag_vectors(0, n, 2, np.float32)
+    ref, scale, nref = exact.exact_dot(x, y), exact.abs_dot(x, y), exact.exact_nrm2(x)
+    tx, ty = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
+    salt.salt_dot(tx, ty, out[0:1])
+    salt.salt_dot(tx, ty, out[1:2], plain=True)
+    salt.salt_dot(tx.double(), ty.double(), out[2:3])
+    salt.salt_nrm2(tx, out[3:4])
+    salt.salt_nrm2(tx, out[4:5], plain=True)
+    salt.salt_nrm2(tx.double(), out[5:6])
+    comp, plain, wide, nc, npl, nw = out.cpu().tolist()
+    odot, onrm = orc.dot(x, y), orc.nrm2(x)
+
+    def rel(v, r, sc):
+        return float(abs(v - r) / sc)
+
+    return {"n": n, "data": "FP32, random sign x 10^U(-3,3), numpy default_rng(0)",
+            "error_measure": "|got - exact| / sum|x_i y_i| (dot), / exact (nrm2)",
+            "dot": {"compensated_f32": rel(comp, ref, scale), "plain_f32": rel(plain, ref, scale),
+                    "f64_widened": rel(wide, ref, scale), "cpu_oracle_sequential_f64": rel(odot, ref, scale),
+                    "relative_to_value_compensated_f32": float(abs(comp - ref) / abs(ref))},
+            "nrm2": {"compensated_f32": rel(nc, nref, nref), "plain_f32": rel(npl, nref, nref),
+                     "f64_widened": rel(nw, nref, nref), "cpu_oracle": rel(onrm, nref, nref)}}
 
 
 def served_measure(salt, count: int = 3000, seed: int = 0) -> dict:
