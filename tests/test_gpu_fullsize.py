@@ -51,6 +51,7 @@ def test_elementwise_full_size_sampled(saltlib, cuda_dev, dt):
         s.salt_tune_clear()
     rng = np.random.default_rng(3)
     idx = np.unique(np.concatenate([np.arange(4096), np.arange(N - 4096, N), rng.integers(0, N, 200_000)]))
+    assert idx.min() >= 0 and idx.max() < N
     ins = [gather_inputs(k, idx, dt) for k in keys]
     want_e = [ins[0].copy(), ins[1].copy(), ins[2].copy(), ins[3].copy(), np.zeros(len(idx), dt)]
     oracle.eval_program(oracle.PROG_E, want_e, [ALPHA, BETA])
@@ -125,6 +126,7 @@ def test_cg_passes_full_size_sampled(saltlib, cuda_dev, dt):
     torch.cuda.synchronize()
     rng = np.random.default_rng(4)
     idx = np.unique(np.concatenate([np.arange(4096), np.arange(n - 4096, n), rng.integers(0, n, 200_000)]))
+    assert idx.min() >= 0 and idx.max() < n
     ins = {k: gather_inputs(key, idx, dt) for k, key in keys.items()}
     m = len(idx)
     want = [ins["d"], ins["p"].copy(), np.zeros(m, dt), ins["x"].copy(), ins["r"].copy(), np.zeros(m, dt)]
@@ -135,3 +137,65 @@ def test_cg_passes_full_size_sampled(saltlib, cuda_dev, dt):
     for name, slot in (("p", 1), ("q", 2), ("x", 3), ("r", 4)):
         got = t[name][tidx].cpu().numpy()
         assert np.array_equal(got.view(iu), want[slot].view(iu)), name
+
+
+BIG = (1 << 31) + 13  # more elements than a 32-bit index can address
+
+
+def test_elementwise_beyond_2e31_elements_sampled(saltlib, cuda_dev):
+    """axpby and e over n = 2^31 + 13 FP32 elements (every index computation
+    must be 64-bit): sampled elements, including both sides of 2^31 and the
+    tail, bit-identical to the oracle on the counter-based inputs."""
+    s = saltlib
+    keys = [131, 132, 133, 134, 135]
+    a, b, c, d, y, out = (torch.empty(BIG, dtype=torch.float32, device=cuda_dev) for _ in range(6))
+    for t, k in zip((a, b, c, d, y), keys):
+        s.salt_fill_uniform(t, key=k)
+    s.salt_axpby(ALPHA, a, BETA, y)
+    s.salt_eval(P.PROG_E, [a, b, c, d, out], [ALPHA, BETA])
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    idx = np.unique(np.concatenate([np.arange(4096), np.arange((1 << 31) - 4096, BIG),
+                                    rng.integers(0, BIG, 100_000)]))
+    assert idx.min() >= 0 and idx.max() < BIG  # checked on the host before any device gather
+    ins = [gather_inputs(k, idx, np.float32) for k in keys]
+    want_y = [ins[0].copy(), ins[4].copy()]
+    oracle.eval_program(oracle.PROG_AXPBY, want_y, [ALPHA, BETA])
+    want_e = [ins[0].copy(), ins[1].copy(), ins[2].copy(), ins[3].copy(), np.zeros(len(idx), np.float32)]
+    oracle.eval_program(oracle.PROG_E, want_e, [ALPHA, BETA])
+    tidx = torch.from_numpy(idx.astype(np.int64)).to(cuda_dev)
+    assert np.array_equal(y[tidx].cpu().numpy().view(np.uint32), want_y[1].view(np.uint32))
+    assert np.array_equal(out[tidx].cpu().numpy().view(np.uint32), want_e[4].view(np.uint32))
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_reductions_beyond_2e31_elements(saltlib, cuda_dev, dt):
+    """dot and nrm2 over n = 2^31 + 13 integer-valued elements: the FP64 path
+    returns the exact integer (every partial sum is below 2^53), the
+    compensated FP32 path is within 1e-6 of it."""
+    s = saltlib
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    i = torch.arange(BIG, device=cuda_dev, dtype=torch.int64)
+    x = ((i % 1024) - 512).to(tdt)
+    yv = (((7 * i) % 512) - 256).to(tdt)
+    del i
+    torch.cuda.empty_cache()
+    outv = torch.zeros(3, dtype=torch.float64, device=cuda_dev)
+    s.salt_dot(x, yv, outv[0:1])
+    s.salt_nrm2(x, outv[1:2])
+    s.salt_dot(x, x, outv[2:3])
+    torch.cuda.synchronize()
+    got_dot, got_nrm, got_sq = outv.cpu().tolist()
+    j = np.arange(BIG % 1024, dtype=np.int64)  # the partial period at the end
+    full = BIG // 1024
+    xs_all = np.arange(1024, dtype=np.int64) - 512
+    ys_all = ((7 * np.arange(1024, dtype=np.int64)) % 512) - 256
+    sumsq = int(np.sum(xs_all * xs_all)) * full + int(np.sum((j - 512) ** 2))
+    dot = int(np.sum(xs_all * ys_all)) * full + int(np.sum((j - 512) * (((7 * j) % 512) - 256)))
+    absdot = int(np.sum(np.abs(xs_all * ys_all))) * full + int(np.sum(np.abs((j - 512) * (((7 * j) % 512) - 256))))
+    if dt == np.float64:
+        assert got_dot == dot and got_sq == sumsq, (got_dot, dot, got_sq, sumsq)
+        assert got_nrm == math.sqrt(sumsq)
+    else:
+        assert abs(got_dot - dot) <= 1e-6 * absdot, (got_dot, dot)
+        assert abs(got_sq - sumsq) <= 1e-6 * sumsq and abs(got_nrm - math.sqrt(sumsq)) <= 1e-6 * math.sqrt(sumsq)
