@@ -326,7 +326,9 @@ def main():
 
     if args.only_cg:
         if rank == 0:
-            print(json.dumps({"cg": cg_measure(torch, salt, log2n=args.cg_log2)}), flush=True)
+            cg = cg_measure(torch, salt, log2n=args.cg_log2)
+            cg["per_iteration_latency"] = cg_latency_measure(torch, salt)
+            print(json.dumps({"cg": cg}), flush=True)
         return
 
     if args.only_batched:
@@ -455,6 +457,7 @@ def main():
     if not args.no_cg:
         torch.cuda.empty_cache()
         result["cg"] = cg_measure(torch, salt, log2n=args.cg_log2)
+        result["cg"]["per_iteration_latency"] = cg_latency_measure(torch, salt)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         # The CPU-oracle leg: the oracle timed on the host, and the oracle's
@@ -713,6 +716,44 @@ def precision_measure(torch, salt, log2n: int = 26) -> dict:
                     "relative_to_value_compensated_f32": float(abs(comp - ref) / abs(ref))},
             "nrm2": {"compensated_f32": rel(nc, nref, nref), "plain_f32": rel(npl, nref, nref),
                      "f64_widened": rel(nw, nref, nref), "cpu_oracle": rel(onrm, nref, nref)}}
+
+
+def cg_latency_measure(torch, salt, sizes=(1 << 14, 1 << 17, 1 << 20, 1 << 24), iters: int = 100,
+                       reps: int = 3) -> dict:
+    """Microseconds per CG iteration, launch-per-pass (salt_cg_diag: two fused
+    launches per iteration) against one cooperative launch with grid
+    barriers (salt_cg_diag_persistent), for sizes where launches matter."""
+    import numpy as np
+
+    stream = torch.cuda.current_stream()
+    out = {}
+    for dt, tdt in (("f32", torch.float32), ("f64", torch.float64)):
+        rows = []
+        for n in sizes:
+            d, b, x, r, p, q = (torch.empty(n, dtype=tdt, device="cuda") for _ in range(6))
+            salt.salt_fill_uniform(d, 31)
+            d.add_(1.0).mul_(3.5).add_(1.0)
+            salt.salt_fill_uniform(b, 32)
+            rho = torch.zeros(2 * iters + 1, dtype=torch.float64, device="cuda")
+            row = {"n": n}
+            for label, pers in (("launch_per_pass_us", False), ("persistent_us", True)):
+                ts = []
+                for _ in range(reps + 1):
+                    x.zero_()
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    salt.salt_cg_diag(d, b, x, r, p, q, iters, rho, persistent=pers)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                row[label] = round(float(np.median(ts[1:])) * 1e3 / iters, 2)
+            row["speedup"] = round(row["launch_per_pass_us"] / row["persistent_us"], 2)
+            rows.append(row)
+            del d, b, x, r, p, q
+        out[dt] = rows
+    return {"iters": iters, "rows": out}
 
 
 def served_measure(salt, count: int = 3000, seed: int = 0) -> dict:

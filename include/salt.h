@@ -238,6 +238,20 @@ salt_status salt_eval_ex(const salt_insn* prog, int32_t nprog, int32_t dtype, in
 salt_status salt_cg_diag(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r, void* p,
                          void* q, int32_t iters, double* rho, void* stream);
 
+/* salt_cg_diag in ONE cooperative launch: the blocks stay resident for all
+ * iterations and meet at a grid-wide barrier after each reduction (two per
+ * iteration), instead of two kernel launches per iteration -- for small n,
+ * where launches dominate.  Same arguments, per-element operations and
+ * scalar nodes as salt_cg_diag; the reductions use the same accumulators
+ * but another partition of the elements, so rho and the iterates agree with
+ * salt_cg_diag to the reductions' tolerance, not bit for bit.  The launch
+ * uses at most one block per 1024 elements and never more blocks than can
+ * be resident (cudaLaunchCooperativeKernel; SALT_ERR_CUDA if the device
+ * cannot).  Barrier waits are bounded (a few seconds): a launch that cannot
+ * progress ends with NaN in rho[0] instead of hanging.  Not in the paper. */
+salt_status salt_cg_diag_persistent(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r,
+                                    void* p, void* q, int32_t iters, double* rho, void* stream);
+
 /* salt_explain -- host only (no GPU): the program the kernels evaluate for
  * `prog`, after its scalar subexpressions are hoisted, with the values of
  * the scalar slots.  Not part of the paper; an inspection aid.

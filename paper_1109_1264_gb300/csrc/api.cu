@@ -546,6 +546,64 @@ static salt_status run_special(int special, int dt, int64_t n, const void* x, co
   return e == cudaSuccess ? SALT_OK : cuda_error(e, "reduction kernel launch");
 }
 
+// ------------------------------------------------- conjugate gradients ---
+// CG for diag(d) x = b as programs over operand slots 0 d, 1 p, 2 q, 3 x,
+// 4 r, 5 b (the start, the first pass of iteration 0, the first pass of
+// iteration k, the second pass).
+const salt_insn kCgR0[8] = {{SALT_OP_VEC, 5}, {SALT_OP_VEC, 0}, {SALT_OP_VEC, 3}, {SALT_OP_MUL, 0},
+                            {SALT_OP_SUB, 0}, {SALT_OP_STORE, 4}, {SALT_OP_VEC, 4}, {SALT_OP_SUMSQ, 0}};
+const salt_insn kCgP0[9] = {{SALT_OP_VEC, 4}, {SALT_OP_STORE, 1}, {SALT_OP_VEC, 0}, {SALT_OP_VEC, 1},
+                            {SALT_OP_MUL, 0}, {SALT_OP_STORE, 2}, {SALT_OP_VEC, 1}, {SALT_OP_VEC, 2},
+                            {SALT_OP_DOT, 0}};
+// beta = DSCAL0 / DSCAL1 = rho_k / rho_{k-1}
+const salt_insn kCgPQ[15] = {{SALT_OP_VEC, 4}, {SALT_OP_DSCAL, 0}, {SALT_OP_DSCAL, 1}, {SALT_OP_DIV, 0},
+                             {SALT_OP_VEC, 1}, {SALT_OP_SMUL, 0},  {SALT_OP_ADD, 0},    {SALT_OP_STORE, 1},
+                             {SALT_OP_VEC, 0}, {SALT_OP_VEC, 1},   {SALT_OP_MUL, 0},    {SALT_OP_STORE, 2},
+                             {SALT_OP_VEC, 1}, {SALT_OP_VEC, 2},   {SALT_OP_DOT, 0}};
+// alpha = DSCAL0 / DSCAL1 = rho_k / (p . q)
+const salt_insn kCgXR[18] = {{SALT_OP_VEC, 3}, {SALT_OP_DSCAL, 0}, {SALT_OP_DSCAL, 1}, {SALT_OP_DIV, 0},
+                             {SALT_OP_VEC, 1}, {SALT_OP_SMUL, 0},  {SALT_OP_ADD, 0},    {SALT_OP_STORE, 3},
+                             {SALT_OP_VEC, 4}, {SALT_OP_DSCAL, 0}, {SALT_OP_DSCAL, 1},  {SALT_OP_DIV, 0},
+                             {SALT_OP_VEC, 2}, {SALT_OP_SMUL, 0},  {SALT_OP_SUB, 0},    {SALT_OP_STORE, 4},
+                             {SALT_OP_VEC, 4}, {SALT_OP_SUMSQ, 0}};
+
+salt_status cg_call(const salt_insn* prog, int len, int32_t dtype, int64_t n, void* const* vecs, double* red,
+                    const double* ds0, const double* ds1, cudaStream_t s, bool check_only) {
+  const double* ds[2] = {ds0, ds1};
+  EvalArgs a{prog, len, dtype, n, vecs, 6, nullptr, 0, red, s};
+  a.dscal = ds;
+  a.ndscal = ds0 ? 2 : 0;
+  if (check_only) {
+    Analysis an;
+    return validate_eval(a, &an);
+  }
+  return eval_impl(a);
+}
+
+salt_status cg_validate(int32_t dtype, int64_t n, void* const* vecs, int32_t iters, double* rho, cudaStream_t s) {
+  if (iters < 0) return set_error(SALT_ERR_ARG, "iters must be >= 0");
+  if (!rho) return set_error(SALT_ERR_ARG, "rho is NULL");
+  salt_status st = cg_call(kCgR0, 8, dtype, n, vecs, rho, nullptr, nullptr, s, true);
+  if (st == SALT_OK) st = cg_call(kCgP0, 9, dtype, n, vecs, rho + 1, nullptr, nullptr, s, true);
+  if (st == SALT_OK && iters > 1) st = cg_call(kCgPQ, 15, dtype, n, vecs, rho + 3, rho + 2, rho, s, true);
+  if (st == SALT_OK && iters > 0) st = cg_call(kCgXR, 18, dtype, n, vecs, rho + 2, rho, rho + 1, s, true);
+  return st;
+}
+
+salt_status stream_workspace(cudaStream_t s, double** partials, unsigned** words, int* capacity_blocks) {
+  int dev = 0;
+  DevInfo info;
+  salt_status st = device_info(&dev, &info);
+  if (st != SALT_OK) return st;
+  Workspace ws;
+  st = workspace(dev, info, s, &ws);
+  if (st != SALT_OK) return st;
+  *partials = ws.partials;
+  *words = ws.ticket;
+  *capacity_blocks = ws.capacity_blocks * kPartialsPerBlock;
+  return SALT_OK;
+}
+
 }  // namespace salt
 
 using namespace salt;
@@ -652,51 +710,18 @@ salt_status salt_eval_ex(const salt_insn* prog, int32_t nprog, int32_t dtype, in
 
 salt_status salt_cg_diag(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r, void* p,
                          void* q, int32_t iters, double* rho, void* stream) {
-  // Operand slots: 0 d, 1 p, 2 q, 3 x, 4 r, 5 b.
-  static const salt_insn kR0[] = {{SALT_OP_VEC, 5}, {SALT_OP_VEC, 0}, {SALT_OP_VEC, 3}, {SALT_OP_MUL, 0},
-                                  {SALT_OP_SUB, 0}, {SALT_OP_STORE, 4}, {SALT_OP_VEC, 4}, {SALT_OP_SUMSQ, 0}};
-  static const salt_insn kP0[] = {{SALT_OP_VEC, 4}, {SALT_OP_STORE, 1}, {SALT_OP_VEC, 0}, {SALT_OP_VEC, 1},
-                                  {SALT_OP_MUL, 0}, {SALT_OP_STORE, 2}, {SALT_OP_VEC, 1}, {SALT_OP_VEC, 2},
-                                  {SALT_OP_DOT, 0}};
-  // beta = DSCAL0 / DSCAL1 = rho_k / rho_{k-1}
-  static const salt_insn kPQ[] = {{SALT_OP_VEC, 4}, {SALT_OP_DSCAL, 0}, {SALT_OP_DSCAL, 1}, {SALT_OP_DIV, 0},
-                                  {SALT_OP_VEC, 1}, {SALT_OP_SMUL, 0},  {SALT_OP_ADD, 0},    {SALT_OP_STORE, 1},
-                                  {SALT_OP_VEC, 0}, {SALT_OP_VEC, 1},   {SALT_OP_MUL, 0},    {SALT_OP_STORE, 2},
-                                  {SALT_OP_VEC, 1}, {SALT_OP_VEC, 2},   {SALT_OP_DOT, 0}};
-  // alpha = DSCAL0 / DSCAL1 = rho_k / (p . q)
-  static const salt_insn kXR[] = {{SALT_OP_VEC, 3}, {SALT_OP_DSCAL, 0}, {SALT_OP_DSCAL, 1}, {SALT_OP_DIV, 0},
-                                  {SALT_OP_VEC, 1}, {SALT_OP_SMUL, 0},  {SALT_OP_ADD, 0},    {SALT_OP_STORE, 3},
-                                  {SALT_OP_VEC, 4}, {SALT_OP_DSCAL, 0}, {SALT_OP_DSCAL, 1},  {SALT_OP_DIV, 0},
-                                  {SALT_OP_VEC, 2}, {SALT_OP_SMUL, 0},  {SALT_OP_SUB, 0},    {SALT_OP_STORE, 4},
-                                  {SALT_OP_VEC, 4}, {SALT_OP_SUMSQ, 0}};
-  if (iters < 0) return set_error(SALT_ERR_ARG, "iters must be >= 0");
-  if (!rho) return set_error(SALT_ERR_ARG, "rho is NULL");
   void* vecs[6] = {const_cast<void*>(d), p, q, x, r, const_cast<void*>(b)};
   const cudaStream_t s = (cudaStream_t)stream;
-  auto call = [&](const salt_insn* prog, int len, double* red, const double* ds0, const double* ds1,
-                  bool check_only) -> salt_status {
-    const double* ds[2] = {ds0, ds1};
-    EvalArgs a{prog, len, dtype, n, vecs, 6, nullptr, 0, red, s};
-    a.dscal = ds;
-    a.ndscal = ds0 ? 2 : 0;
-    if (check_only) {
-      Analysis an;
-      return validate_eval(a, &an);
-    }
-    return eval_impl(a);
-  };
   // Every call is checked before the first launch (the later iterations
   // differ only in which entries of rho they name).
-  salt_status st = call(kR0, 8, rho, nullptr, nullptr, true);
-  if (st == SALT_OK) st = call(kP0, 9, rho + 1, nullptr, nullptr, true);
-  if (st == SALT_OK && iters > 1) st = call(kPQ, 15, rho + 3, rho + 2, rho, true);
-  if (st == SALT_OK && iters > 0) st = call(kXR, 18, rho + 2, rho, rho + 1, true);
+  salt_status st = cg_validate(dtype, n, vecs, iters, rho, s);
   if (st != SALT_OK) return st;
-  st = call(kR0, 8, rho, nullptr, nullptr, false);
+  st = cg_call(kCgR0, 8, dtype, n, vecs, rho, nullptr, nullptr, s, false);
   for (int k = 0; k < iters && st == SALT_OK; ++k) {
     double* pq = rho + 2 * k + 1;
-    st = k == 0 ? call(kP0, 9, pq, nullptr, nullptr, false) : call(kPQ, 15, pq, rho + 2 * k, rho + 2 * k - 2, false);
-    if (st == SALT_OK) st = call(kXR, 18, rho + 2 * k + 2, rho + 2 * k, pq, false);
+    st = k == 0 ? cg_call(kCgP0, 9, dtype, n, vecs, pq, nullptr, nullptr, s, false)
+                : cg_call(kCgPQ, 15, dtype, n, vecs, pq, rho + 2 * k, rho + 2 * k - 2, s, false);
+    if (st == SALT_OK) st = cg_call(kCgXR, 18, dtype, n, vecs, rho + 2 * k + 2, rho + 2 * k, pq, s, false);
   }
   return st;
 }

@@ -1,0 +1,300 @@
+// Conjugate gradients for diag(d) x = b in ONE cooperative launch
+// (salt_cg_diag_persistent): every block stays resident for all iterations
+// and the blocks meet at a grid-wide barrier after each reduction, so an
+// iteration costs two barriers instead of two kernel launches.
+//
+// Per element the operations are those of salt_cg_diag's programs, in the
+// same order and precision (r = b - d*x; p = r + beta*p; q = d*p;
+// x = x + alpha*p; r = r - alpha*q), and alpha = rho / (p.q), beta =
+// rho' / rho are the same one-division-in-T scalar nodes.  The reductions
+// are the library's accumulators (compensated FP32, FP64 FMA) combined per
+// block by the shared-memory tree and across blocks in block order, which
+// every block does for itself, so all blocks hold the same scalars.
+//
+// Barrier: a monotonic arrival counter (zeroed before the launch); barrier
+// m is passed when the counter reaches m * gridDim.x.  Waits are bounded:
+// after kMaxSpins polls a block records a timeout in the status word, writes
+// NaN into rho[0] (block 0) and returns, and every other block returns at
+// its next barrier, so a launch that cannot make progress ends instead of
+// hanging.  The cooperative launch guarantees that all blocks are resident.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+
+#include "../../include/salt.h"
+#include "common.cuh"
+#include "internal.h"
+
+namespace salt {
+
+namespace {
+
+constexpr unsigned kMaxSpins = 1u << 26;  // polls of >= 32 ns and an L2 round trip: seconds
+constexpr int kCgBlock = 256;
+
+template <typename T>
+struct CgParams {
+  const T* d;
+  const T* b;
+  T* x;
+  T* r;
+  T* p;
+  T* q;
+  int64_t n;
+  int32_t iters;
+  double* rho;        // history: rho[0], then (p.q, rho') per iteration
+  double* partials;   // 2 * gridDim.x values
+  unsigned long long* counter;  // barrier arrivals, zero at launch
+  unsigned* status;             // 0, or 1 after a barrier timeout
+};
+
+// Returns false if the barrier timed out (here or in another block).
+__device__ bool grid_barrier(unsigned long long* counter, unsigned* status, unsigned long long target) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(counter, 1ull);
+    unsigned spins = 0;
+    for (;;) {
+      if (*(volatile unsigned*)status != 0u) {
+        ok = 0;
+        break;
+      }
+      if (*(volatile unsigned long long*)counter >= target) break;
+      if (++spins > kMaxSpins) {
+        atomicExch(status, 1u);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Block sum of each block's value, written to partials[slot * G + block];
+// after the barrier every block adds the G partials in block order.
+template <typename T>
+__device__ bool grid_sum(double v, double* partials, int slot, unsigned long long* counter, unsigned* status,
+                         unsigned long long target, double* smem, double* out) {
+  const double bs = block_sum<double>(v, smem);
+  if (threadIdx.x == 0) partials[(size_t)slot * gridDim.x + blockIdx.x] = bs;
+  if (!grid_barrier(counter, status, target)) return false;
+  const volatile double* part = (const volatile double*)partials + (size_t)slot * gridDim.x;
+  if (gridDim.x <= 32) {
+    // few blocks: one thread adds them in block order (no tree, one barrier)
+    __shared__ double s_tot;
+    if (threadIdx.x == 0) {
+      double a = 0.0;
+      for (unsigned k = 0; k < gridDim.x; ++k) a += part[k];
+      s_tot = a;
+    }
+    __syncthreads();
+    *out = s_tot;
+    return true;
+  }
+  double a = 0.0;
+  for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) a += part[k];
+  // the same fixed-order tree in every block: identical totals
+  *out = block_sum<double>(a, smem);
+  return true;
+}
+
+// W consecutive elements of one operand: one 16-byte access when W > 1.
+template <typename T, int W>
+__device__ __forceinline__ void load_w(T (&v)[W], const T* src) {
+  if constexpr (W == 1) {
+    v[0] = *src;
+  } else {
+    VecT<T, 16> t;
+    vload<false>(t, src);
+#pragma unroll
+    for (int e = 0; e < W; ++e) v[e] = t.e[e];
+  }
+}
+template <typename T, int W>
+__device__ __forceinline__ void store_w(T* dst, const T (&v)[W]) {
+  if constexpr (W == 1) {
+    *dst = v[0];
+  } else {
+    VecT<T, 16> t;
+#pragma unroll
+    for (int e = 0; e < W; ++e) t.e[e] = v[e];
+    vstore(dst, t);
+  }
+}
+
+// The three element passes on elements [j, j + W).
+template <typename T, int W, class Acc>
+__device__ __forceinline__ void start_w(const CgParams<T>& p, int64_t j, Acc& acc) {
+  T b[W], d[W], x[W], r[W];
+  load_w<T, W>(b, p.b + j);
+  load_w<T, W>(d, p.d + j);
+  load_w<T, W>(x, p.x + j);
+#pragma unroll
+  for (int e = 0; e < W; ++e) {
+    r[e] = Arith<T>::sub(b[e], Arith<T>::mul(d[e], x[e]));
+    acc.add_prod(r[e], r[e]);
+  }
+  store_w<T, W>(p.r + j, r);
+}
+
+template <typename T, int W, class Acc>
+__device__ __forceinline__ void pass1_w(const CgParams<T>& p, int64_t j, bool first, T beta, Acc& acc) {
+  T r[W], pv[W], d[W], q[W];
+  load_w<T, W>(r, p.r + j);
+  load_w<T, W>(d, p.d + j);
+  if (!first) load_w<T, W>(pv, p.p + j);
+#pragma unroll
+  for (int e = 0; e < W; ++e) {
+    pv[e] = first ? r[e] : Arith<T>::add(r[e], Arith<T>::mul(beta, pv[e]));
+    q[e] = Arith<T>::mul(d[e], pv[e]);
+    acc.add_prod(pv[e], q[e]);
+  }
+  store_w<T, W>(p.p + j, pv);
+  store_w<T, W>(p.q + j, q);
+}
+
+template <typename T, int W, class Acc>
+__device__ __forceinline__ void pass2_w(const CgParams<T>& p, int64_t j, T alpha, Acc& acc) {
+  T x[W], pv[W], r[W], q[W];
+  load_w<T, W>(x, p.x + j);
+  load_w<T, W>(pv, p.p + j);
+  load_w<T, W>(r, p.r + j);
+  load_w<T, W>(q, p.q + j);
+#pragma unroll
+  for (int e = 0; e < W; ++e) {
+    x[e] = Arith<T>::add(x[e], Arith<T>::mul(alpha, pv[e]));
+    r[e] = Arith<T>::sub(r[e], Arith<T>::mul(alpha, q[e]));
+    acc.add_prod(r[e], r[e]);
+  }
+  store_w<T, W>(p.x + j, x);
+  store_w<T, W>(p.r + j, r);
+}
+
+// Every element of the thread, the same ones in every pass: 16-byte groups
+// of W when `vec` (all operands 16-byte aligned), then single elements.
+#define SALT_CG_EACH(CALL)                                                    \
+  {                                                                           \
+    int64_t done = 0;                                                         \
+    if (vec) {                                                                \
+      const int64_t nv = n / VW;                                              \
+      for (int64_t j = gid; j < nv; j += stride) CALL(VW, j * VW);            \
+      done = nv * VW;                                                         \
+    }                                                                         \
+    for (int64_t i = done + gid; i < n; i += stride) CALL(1, i);              \
+  }
+
+template <typename T>
+__global__ void __launch_bounds__(kCgBlock) cg_persistent_kernel(const CgParams<T> p, int vec) {
+  using Acc = typename AccOf<T>::type;
+  constexpr int VW = 16 / (int)sizeof(T);
+  __shared__ double smem[kMaxBlock];
+  const int64_t n = p.n;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const unsigned long long G = gridDim.x;
+  unsigned long long target = 0;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+
+  // start: r = b - d*x, rho_0 = r.r
+  Acc acc;
+#define SALT_CG_START(W, J) start_w<T, W>(p, J, acc)
+  SALT_CG_EACH(SALT_CG_START)
+#undef SALT_CG_START
+  double rho = 0.0, rho_prev = 0.0, pq = 0.0;
+  target += G;
+  if (!grid_sum<T>(acc.value(), p.partials, 0, p.counter, p.status, target, smem, &rho)) {
+    if (lead) p.rho[0] = NAN;
+    return;
+  }
+  if (lead) p.rho[0] = rho;
+
+  for (int k = 0; k < p.iters; ++k) {
+    // pass 1: p = r (k = 0) or r + beta p; q = d*p; pq = p.q
+    const bool first = k == 0;
+    const T beta = first ? T(0) : Arith<T>::div((T)rho, (T)rho_prev);
+    Acc a1;
+#define SALT_CG_PASS1(W, J) pass1_w<T, W>(p, J, first, beta, a1)
+    SALT_CG_EACH(SALT_CG_PASS1)
+#undef SALT_CG_PASS1
+    target += G;
+    if (!grid_sum<T>(a1.value(), p.partials, 1, p.counter, p.status, target, smem, &pq)) {
+      if (lead) p.rho[0] = NAN;
+      return;
+    }
+    if (lead) p.rho[2 * k + 1] = pq;
+    // pass 2: x = x + alpha p; r = r - alpha q; rho' = r.r
+    const T alpha = Arith<T>::div((T)rho, (T)pq);
+    Acc a2;
+#define SALT_CG_PASS2(W, J) pass2_w<T, W>(p, J, alpha, a2)
+    SALT_CG_EACH(SALT_CG_PASS2)
+#undef SALT_CG_PASS2
+    double rho_next = 0.0;
+    target += G;
+    if (!grid_sum<T>(a2.value(), p.partials, 0, p.counter, p.status, target, smem, &rho_next)) {
+      if (lead) p.rho[0] = NAN;
+      return;
+    }
+    if (lead) p.rho[2 * k + 2] = rho_next;
+    rho_prev = rho;
+    rho = rho_next;
+  }
+}
+#undef SALT_CG_EACH
+
+template <typename T>
+salt_status launch_cg(int64_t n, void* const* v, int32_t iters, double* rho, cudaStream_t s) {
+  double* partials = nullptr;
+  unsigned* words = nullptr;
+  int cap = 0;
+  salt_status st = stream_workspace(s, &partials, &words, &cap);
+  if (st != SALT_OK) return st;
+  int dev = 0, sms = 0;
+  st = current_device(&dev, &sms);
+  if (st != SALT_OK) return st;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_persistent_kernel<T>, kCgBlock, 0);
+  if (e != cudaSuccess || per_sm < 1) return report_error(SALT_ERR_CUDA, "occupancy of the CG kernel");
+  // one block per 4 tiles of the block's width, at most all resident blocks
+  int64_t want = (n + 4 * kCgBlock - 1) / (4 * kCgBlock);
+  int64_t cap_blocks = (int64_t)sms * per_sm;
+  if (cap_blocks > cap / 2) cap_blocks = cap / 2;  // two partial slots per block
+  const int grid = (int)(want < 1 ? 1 : (want < cap_blocks ? want : cap_blocks));
+  // words[0] is the reduction ticket; words[1] = status, words[2..3] = the
+  // 64-bit barrier counter (8-byte aligned: the slot is 256-byte aligned)
+  e = cudaMemsetAsync(words + 1, 0, 3 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return report_error(SALT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  CgParams<T> prm{(const T*)v[0], (const T*)v[5], (T*)v[3], (T*)v[4], (T*)v[1], (T*)v[2],
+                  n, iters, rho, partials, (unsigned long long*)(words + 2), words + 1};
+  int vec = 1;
+  for (int k = 0; k < 6; ++k) vec = vec && ((uintptr_t)v[k] % 16 == 0);
+  void* args[] = {&prm, &vec};
+  e = cudaLaunchCooperativeKernel((const void*)cg_persistent_kernel<T>, dim3(grid), dim3(kCgBlock), args, 0, s);
+  count_launch();
+  if (e != cudaSuccess)
+    return report_error(SALT_ERR_CUDA, std::string("cooperative CG launch: ") + cudaGetErrorString(e));
+  return SALT_OK;
+}
+
+}  // namespace
+
+}  // namespace salt
+
+using namespace salt;
+
+extern "C" salt_status salt_cg_diag_persistent(int32_t dtype, int64_t n, const void* d, const void* b, void* x,
+                                               void* r, void* p, void* q, int32_t iters, double* rho,
+                                               void* stream) {
+  void* vecs[6] = {const_cast<void*>(d), p, q, x, r, const_cast<void*>(b)};
+  const cudaStream_t s = (cudaStream_t)stream;
+  salt_status st = cg_validate(dtype, n, vecs, iters, rho, s);
+  if (st != SALT_OK) return st;
+  return dtype == SALT_F32 ? launch_cg<float>(n, vecs, iters, rho, s) : launch_cg<double>(n, vecs, iters, rho, s);
+}

@@ -37,6 +37,19 @@ salt_status validate_eval(const EvalArgs& a, Analysis* an);
 salt_status eval_impl(const EvalArgs& a);
 salt_status nrm2_impl(int32_t dtype, int64_t n, const void* x, double* out, int32_t flags, cudaStream_t s);
 
+// Conjugate gradients for diag(d) x = b (salt_cg_diag): the programs over
+// operand slots 0 d, 1 p, 2 q, 3 x, 4 r, 5 b, one checked or launched call,
+// and every check of a run before its first launch.
+extern const salt_insn kCgR0[8], kCgP0[9], kCgPQ[15], kCgXR[18];
+salt_status cg_call(const salt_insn* prog, int len, int32_t dtype, int64_t n, void* const* vecs, double* red,
+                    const double* ds0, const double* ds1, cudaStream_t s, bool check_only);
+salt_status cg_validate(int32_t dtype, int64_t n, void* const* vecs, int32_t iters, double* rho, cudaStream_t s);
+
+// The reduction workspace of stream `s`: FP64 partials (capacity doubles)
+// and a 256-byte slot of words whose first word is the reduction ticket
+// (zero between launches); the others are free for one launch's use.
+salt_status stream_workspace(cudaStream_t s, double** partials, unsigned** words, int* capacity);
+
 // SM count of the current device (cached); 0 and an error on failure.
 salt_status current_device(int* dev, int* sms);
 

@@ -263,3 +263,46 @@ def test_cg_diag_entry_point(saltlib, cuda_dev, dt):
         xo, ho = cg_diagonal_two_pass(lambda pr, vs, ds: oracle.eval_program(pr, vs, dscalars=ds), d, b, x0, iters)
         assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < (1e-10 if dt == np.float64 else 1e-5)
         assert abs(g[2] - ho[2]) <= (1e-9 if dt == np.float64 else 1e-5) * ho[2]
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_cg_persistent(saltlib, cuda_dev, dt):
+    """salt_cg_diag_persistent (one cooperative launch, grid barriers): the
+    same convergence, residual history and agreement with the oracle's CG as
+    the launch-per-pass form, and agreement with that form to the reductions'
+    tolerance."""
+    s = saltlib
+    rng = np.random.default_rng(39)
+    for n, iters in ((0, 3), (1, 1), (999, 4), (4096, 0), ((1 << 20) + 5, 4)):
+        d = rng.choice([1.0, 2.0, 5.0, 8.0], n).astype(dt)
+        b = rng.uniform(-1, 1, n).astype(dt)
+        x0 = rng.uniform(-3, 3, n).astype(dt)
+        runs = {}
+        for persistent in (False, True):
+            td, tb, tx = (torch.from_numpy(v.copy()).to(cuda_dev) for v in (d, b, x0))
+            tr, tp, tq = (torch.zeros(n, dtype=TDT[dt], device=cuda_dev) for _ in range(3))
+            rho = torch.full((2 * iters + 1,), float("nan"), dtype=torch.float64, device=cuda_dev)
+            s.salt_cg_diag(td, tb, tx, tr, tp, tq, iters, rho, persistent=persistent)
+            torch.cuda.synchronize()
+            runs[persistent] = (tx.cpu().numpy().astype(np.float64), tr.cpu().numpy(), rho.cpu().numpy())
+        xg, rg, g = runs[True]
+        xl, _, gl = runs[False]
+        assert not np.any(np.isnan(g)) or n == 0, g
+        if n == 0:
+            assert np.all(xg.shape == (0,)) and g[0] == 0.0
+            continue
+        r0 = b.astype(np.float64) - d.astype(np.float64) * x0.astype(np.float64)
+        assert abs(g[0] - float(r0 @ r0)) <= 1e-5 * float(r0 @ r0) + 1e-300
+        assert abs(g[-1] - exact.exact_sumsq(rg)) <= TOL[dt] * exact.exact_sumsq(rg) + 1e-300
+        if iters == 4 and n > 1:
+            xs = b.astype(np.float64) / d.astype(np.float64)
+            tol = 1e-12 if dt == np.float64 else 2e-5
+            assert np.linalg.norm(xg - xs) / np.linalg.norm(xs) < tol
+            xo, _ = cg_diagonal_two_pass(lambda pr, vs, ds: oracle.eval_program(pr, vs, dscalars=ds), d, b, x0,
+                                         iters)
+            assert np.linalg.norm(xg - xo) / np.linalg.norm(xo) < (1e-10 if dt == np.float64 else 1e-5)
+        # against the launch-per-pass form: the start residual agrees to the
+        # reduction tolerance, the iterates to the propagated rounding
+        assert abs(g[0] - gl[0]) <= 2 * TOL[dt] * gl[0] + 1e-300
+        if iters:
+            assert np.linalg.norm(xg - xl) <= (1e-10 if dt == np.float64 else 1e-4) * max(np.linalg.norm(xl), 1.0)
