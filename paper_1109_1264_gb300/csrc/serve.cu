@@ -121,14 +121,14 @@ struct Slot {
   cudaEvent_t done = nullptr;
   char* d_mem = nullptr;
   char* h_mem = nullptr;
-  // device layout
-  BatchHeader* d_hdr[2] = {nullptr, nullptr};  // [0] fill, [1] compute
-  BatchItem* d_items[2] = {nullptr, nullptr};
+  // device layout: the tables (packed per step at the start of d_mem), then
+  // the per-table tile counters, the partials and the results
   unsigned* d_counters[2] = {nullptr, nullptr};
   double* d_partials = nullptr;
   double* d_red = nullptr;
-  // host staging (pinned), mirrors [hdr0 | items0 | hdr1 | items1], then red
+  // host staging (pinned): the packed tables, then red
   size_t table_bytes = 0;
+  std::vector<BatchItem> compute_items;  // built aside, copied after the fill items
   double* h_red = nullptr;
   std::vector<Request*> reqs;
   bool busy = false;
@@ -227,9 +227,11 @@ int64_t tiles_of(const salt_server* s, int dtype, int64_t n) {
 salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch) {
   size_t off_items[2], off_counters[2], off_partials, off_red;
   slot_device_bytes(s, off_items, off_counters, &off_partials, &off_red);
-  // host tables in the pinned staging area
-  BatchHeader* h_hdr[2] = {(BatchHeader*)slot.h_mem, (BatchHeader*)(slot.h_mem + off_items[1] - 256)};
-  BatchItem* h_items[2] = {(BatchItem*)(slot.h_mem + off_items[0]), (BatchItem*)(slot.h_mem + off_items[1])};
+  // Host tables in the pinned staging area, packed so that one copy of
+  // only the bytes in use moves them: [hdr0 | hdr1 | fill items | compute
+  // items].  Compute items are built aside, then placed after the fills.
+  BatchHeader* h_hdr[2] = {(BatchHeader*)slot.h_mem, (BatchHeader*)(slot.h_mem + 256)};
+  BatchItem* h_items[2] = {(BatchItem*)(slot.h_mem + 512), slot.compute_items.data()};
   int nitems[2] = {0, 0};
   int64_t tiles[2] = {0, 0};
   int nred = 0;
@@ -264,20 +266,24 @@ salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch
     tiles[1] += c.ntiles;
     nred += r->nred;
   }
+  const size_t off_compute = 512 + round_up(sizeof(BatchItem) * (size_t)nitems[0]);
+  memcpy(slot.h_mem + off_compute, slot.compute_items.data(), sizeof(BatchItem) * (size_t)nitems[1]);
+  const size_t used = off_compute + sizeof(BatchItem) * (size_t)nitems[1];
   for (int t = 0; t < 2; ++t) {
     memset(h_hdr[t], 0, sizeof(BatchHeader));
     h_hdr[t]->nitems = nitems[t];
     h_hdr[t]->total_tiles = tiles[t];
     h_hdr[t]->tile_bytes = s->cfg.tile_bytes;
   }
-  cudaError_t e = cudaMemcpyAsync(slot.d_mem, slot.h_mem, slot.table_bytes, cudaMemcpyHostToDevice, slot.stream);
+  BatchHeader* d_hdr[2] = {(BatchHeader*)slot.d_mem, (BatchHeader*)(slot.d_mem + 256)};
+  BatchItem* d_items[2] = {(BatchItem*)(slot.d_mem + 512), (BatchItem*)(slot.d_mem + off_compute)};
+  cudaError_t e = cudaMemcpyAsync(slot.d_mem, slot.h_mem, used, cudaMemcpyHostToDevice, slot.stream);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(slot.d_counters[0], 0, off_partials - off_counters[0], slot.stream);
   KernelFn k = kernel_for(s->cfg.unroll);
   for (int t = 0; t < 2 && e == cudaSuccess; ++t) {
     if (nitems[t] == 0) continue;
-    BatchParams p{slot.d_hdr[t], slot.d_items[t], slot.d_counters[t], slot.d_counters[t] + 1, slot.d_partials,
-                  slot.d_red};
+    BatchParams p{d_hdr[t], d_items[t], slot.d_counters[t], slot.d_counters[t] + 1, slot.d_partials, slot.d_red};
     const int grid = (int)std::min<int64_t>(s->grid, tiles[t]);
     k<<<grid, s->cfg.block, 0, slot.stream>>>(p);
     count_launch();
@@ -367,7 +373,15 @@ void scheduler(salt_server* s) {
         }
       }
       if (batch.empty() && !did) {
-        s->cv.wait_for(lk, std::chrono::microseconds(any_busy ? 5 : 200));
+        if (any_busy) {
+          // A step is in flight: poll its event again at once (a timed wait
+          // of a few microseconds sleeps for the kernel's timer slack, tens
+          // of microseconds, which would show up in every latency).
+          lk.unlock();
+          std::this_thread::yield();
+        } else {
+          s->cv.wait_for(lk, std::chrono::microseconds(200));  // idle: woken by submit
+        }
         continue;
       }
     }
@@ -549,11 +563,8 @@ salt_status salt_serve_start(salt_server** out, const salt_serve_config* cfg) {
     if (e == cudaSuccess)
       e = cudaHostAlloc(&slot.h_red, sizeof(double) * kBatchPartials * cfg->max_batch, cudaHostAllocDefault);
     if (e != cudaSuccess) break;
-    for (int t = 0; t < 2; ++t) {
-      slot.d_hdr[t] = (BatchHeader*)(slot.d_mem + off_items[t] - 256);
-      slot.d_items[t] = (BatchItem*)(slot.d_mem + off_items[t]);
-      slot.d_counters[t] = (unsigned*)(slot.d_mem + off_counters[t]);
-    }
+    slot.compute_items.resize((size_t)s->cfg.max_batch);
+    for (int t = 0; t < 2; ++t) slot.d_counters[t] = (unsigned*)(slot.d_mem + off_counters[t]);
     slot.d_partials = (double*)(slot.d_mem + off_partials);
     slot.d_red = (double*)(slot.d_mem + off_red);
   }
@@ -765,8 +776,17 @@ salt_status replay_impl(salt_server* s, int32_t count, const double* arrival_us,
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->stop && !s->sched_error.empty()) return fail(SALT_ERR_CUDA, s->sched_error);
       if (s->completed.empty()) {
+        // Sleep only well ahead of the next arrival (a timed wait may
+        // oversleep by the timer slack, tens of microseconds); close to it,
+        // or while requests are in flight, yield and look again.
         const double wait = next < count ? std::max(0.0, arrival_us[next] - (now_us() - t0)) : 200.0;
-        if (wait > 2.0) s->cv.wait_for(lk, std::chrono::microseconds((int64_t)std::min(wait, 200.0)));
+        if (wait > 150.0) {
+          s->cv.wait_for(lk, std::chrono::microseconds((int64_t)std::min(wait - 100.0, 200.0)));
+        } else {
+          lk.unlock();
+          std::this_thread::yield();
+          lk.lock();
+        }
       }
       while (!s->completed.empty()) {
         finished.push_back(s->completed.front());
