@@ -483,7 +483,7 @@ def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096, fixed: bool
     out = {}
     stream = torch.cuda.current_stream()
     for dt, tdt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
-        align = 16 // es
+        align = 32 // es  # items start on 32-byte boundaries (256-bit accesses)
         offs, o = [], 0
         for n in lens:
             offs.append(o)
