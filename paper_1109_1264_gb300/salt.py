@@ -209,24 +209,24 @@ def salt_eval(prog, vecs, scalars=(), red_out=None, n: int | None = None, stream
     arr, m = program(prog)
     ptrs = (ctypes.c_void_p * max(len(vecs), 1))(*[_ptr(v) for v in vecs])
     sc = (ctypes.c_double * max(len(scalars), 1))(*[float(s) for s in scalars])
+    contiguous = all(v is None or v.is_contiguous() for v in vecs)
+    st = None
+    if not contiguous:
+        strides = []
+        for v in vecs:
+            if v is not None and (v.dim() != 1 or v.stride(0) < 1):
+                raise SaltError(ERR_ARG, "SALT_ERR_ARG", "operands must be 1-D with a positive stride")
+            strides.append(1 if v is None else int(v.stride(0)))
+        st = (ctypes.c_int64 * max(len(vecs), 1))(*strides)
     if dscalars is not None:
-        strides = None
-        if not all(v is None or v.is_contiguous() for v in vecs):
-            strides = (ctypes.c_int64 * max(len(vecs), 1))(*[1 if v is None else int(v.stride(0)) for v in vecs])
         ds = (ctypes.c_void_p * max(len(dscalars), 1))(*[_dscal_ptr(d) for d in dscalars])
-        _check(lib.salt_eval_ex(arr, m, dt, int(n), ptrs, strides, len(vecs), sc, len(scalars), ds,
+        _check(lib.salt_eval_ex(arr, m, dt, int(n), ptrs, st, len(vecs), sc, len(scalars), ds,
                                 len(dscalars), _ptr(red_out), _stream_ptr(stream)))
         return
-    if all(v is None or v.is_contiguous() for v in vecs):
+    if contiguous:
         _check(lib.salt_eval(arr, m, dt, int(n), ptrs, len(vecs), sc, len(scalars), _ptr(red_out),
                              _stream_ptr(stream)))
         return
-    strides = []
-    for v in vecs:
-        if v is not None and (v.dim() != 1 or v.stride(0) < 1):
-            raise SaltError(ERR_ARG, "SALT_ERR_ARG", "operands must be 1-D with a positive stride")
-        strides.append(1 if v is None else int(v.stride(0)))
-    st = (ctypes.c_int64 * max(len(vecs), 1))(*strides)
     _check(lib.salt_eval_strided(arr, m, dt, int(n), ptrs, st, len(vecs), sc, len(scalars), _ptr(red_out),
                                  _stream_ptr(stream)))
 
