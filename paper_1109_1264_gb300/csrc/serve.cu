@@ -132,6 +132,15 @@ struct Slot {
   double* h_red = nullptr;
   std::vector<Request*> reqs;
   bool busy = false;
+  // The step as one CUDA graph: table upload -> counter reset -> [fill
+  // launch ->] compute launch -> result read-back, instantiated once with
+  // and once without the fill launch; each step updates the sizes and
+  // launch parameters of one of them and replays it.
+  struct StepGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t n_up = nullptr, n_reset = nullptr, n_fill = nullptr, n_comp = nullptr, n_down = nullptr;
+  } g[2];  // [0] without, [1] with the fill launch
 };
 
 using KernelFn = void (*)(const BatchParams);
@@ -222,6 +231,50 @@ int64_t tiles_of(const salt_server* s, int dtype, int64_t n) {
   return n > 0 ? (n + te - 1) / te : 1;
 }
 
+// Builds a step graph with placeholder sizes and launch shapes (every step
+// sets its own before replaying it).
+cudaError_t build_step_graph(salt_server* s, Slot& slot, size_t counter_bytes, bool with_fill,
+                             Slot::StepGraph* sg) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  e = cudaGraphAddMemcpyNode1D(&sg->n_up, g, nullptr, 0, slot.d_mem, slot.h_mem, 512, cudaMemcpyHostToDevice);
+  cudaMemsetParams mp{};
+  mp.dst = slot.d_counters[0];
+  mp.value = 0;
+  mp.elementSize = sizeof(unsigned);
+  mp.width = counter_bytes / sizeof(unsigned);
+  mp.height = 1;
+  mp.pitch = 0;
+  if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&sg->n_reset, g, &sg->n_up, 1, &mp);
+  BatchParams prm{(BatchHeader*)slot.d_mem, (BatchItem*)(slot.d_mem + 512), slot.d_counters[0],
+                  slot.d_counters[0] + 1, slot.d_partials, slot.d_red};
+  void* args[] = {&prm};
+  cudaKernelNodeParams kp{};
+  kp.func = (void*)kernel_for(s->cfg.unroll);
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3((unsigned)s->cfg.block);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  cudaGraphNode_t before = sg->n_reset;
+  if (e == cudaSuccess && with_fill) {
+    e = cudaGraphAddKernelNode(&sg->n_fill, g, &before, 1, &kp);
+    before = sg->n_fill;
+  }
+  if (e == cudaSuccess) e = cudaGraphAddKernelNode(&sg->n_comp, g, &before, 1, &kp);
+  if (e == cudaSuccess)
+    e = cudaGraphAddMemcpyNode1D(&sg->n_down, g, &sg->n_comp, 1, slot.h_red, slot.d_red, sizeof(double),
+                                 cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&sg->exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return e;
+  }
+  sg->graph = g;
+  return cudaSuccess;
+}
+
 // Builds and launches one step on `slot` from the front of `pending`
 // (scheduler thread, lock not held while launching).
 salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch) {
@@ -277,20 +330,36 @@ salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch
   }
   BatchHeader* d_hdr[2] = {(BatchHeader*)slot.d_mem, (BatchHeader*)(slot.d_mem + 256)};
   BatchItem* d_items[2] = {(BatchItem*)(slot.d_mem + 512), (BatchItem*)(slot.d_mem + off_compute)};
-  cudaError_t e = cudaMemcpyAsync(slot.d_mem, slot.h_mem, used, cudaMemcpyHostToDevice, slot.stream);
-  if (e == cudaSuccess)
-    e = cudaMemsetAsync(slot.d_counters[0], 0, off_partials - off_counters[0], slot.stream);
   KernelFn k = kernel_for(s->cfg.unroll);
-  for (int t = 0; t < 2 && e == cudaSuccess; ++t) {
-    if (nitems[t] == 0) continue;
-    BatchParams p{d_hdr[t], d_items[t], slot.d_counters[t], slot.d_counters[t] + 1, slot.d_partials, slot.d_red};
-    const int grid = (int)std::min<int64_t>(s->grid, tiles[t]);
-    k<<<grid, s->cfg.block, 0, slot.stream>>>(p);
-    count_launch();
-    e = cudaGetLastError();
+  BatchParams prm[2];
+  cudaKernelNodeParams kp[2];
+  for (int t = 0; t < 2; ++t) {
+    prm[t] = BatchParams{d_hdr[t], d_items[t], slot.d_counters[t], slot.d_counters[t] + 1, slot.d_partials,
+                         slot.d_red};
+    kp[t] = cudaKernelNodeParams{};
+    kp[t].func = (void*)k;
+    kp[t].gridDim = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(s->grid, tiles[t])));
+    kp[t].blockDim = dim3((unsigned)s->cfg.block);
+    kp[t].sharedMemBytes = 0;
+    kp[t].extra = nullptr;
   }
-  if (e == cudaSuccess && nred > 0)
-    e = cudaMemcpyAsync(slot.h_red, slot.d_red, sizeof(double) * nred, cudaMemcpyDeviceToHost, slot.stream);
+  void* args0[] = {&prm[0]};
+  void* args1[] = {&prm[1]};
+  kp[0].kernelParams = args0;
+  kp[1].kernelParams = args1;
+  Slot::StepGraph& sg = slot.g[nitems[0] > 0 ? 1 : 0];
+  cudaError_t e = cudaGraphExecMemcpyNodeSetParams1D(sg.exec, sg.n_up, slot.d_mem, slot.h_mem, used,
+                                                     cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && nitems[0] > 0) e = cudaGraphExecKernelNodeSetParams(sg.exec, sg.n_fill, &kp[0]);
+  if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(sg.exec, sg.n_comp, &kp[1]);
+  if (e == cudaSuccess)
+    e = cudaGraphExecMemcpyNodeSetParams1D(sg.exec, sg.n_down, slot.h_red, slot.d_red,
+                                           sizeof(double) * (size_t)std::max(nred, 1), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaGraphLaunch(sg.exec, slot.stream);
+  if (e == cudaSuccess) {
+    if (nitems[0] > 0) count_launch();
+    count_launch();
+  }
   if (e == cudaSuccess) e = cudaEventRecord(slot.done, slot.stream);
   if (e != cudaSuccess) return cuda_fail(e, "serving step");
   slot.reqs = batch;
@@ -567,12 +636,18 @@ salt_status salt_serve_start(salt_server** out, const salt_serve_config* cfg) {
     for (int t = 0; t < 2; ++t) slot.d_counters[t] = (unsigned*)(slot.d_mem + off_counters[t]);
     slot.d_partials = (double*)(slot.d_mem + off_partials);
     slot.d_red = (double*)(slot.d_mem + off_red);
+    for (int f = 0; f < 2 && e == cudaSuccess; ++f)
+      e = build_step_graph(s, slot, off_partials - off_counters[0], f == 1, &slot.g[f]);
   }
   if (e != cudaSuccess) {
     for (Slot& slot : s->slots) {
       if (slot.d_mem) cudaFree(slot.d_mem);
       if (slot.h_mem) cudaFreeHost(slot.h_mem);
       if (slot.h_red) cudaFreeHost(slot.h_red);
+      for (Slot::StepGraph& sg : slot.g) {
+        if (sg.exec) cudaGraphExecDestroy(sg.exec);
+        if (sg.graph) cudaGraphDestroy(sg.graph);
+      }
       if (slot.done) cudaEventDestroy(slot.done);
       if (slot.stream) cudaStreamDestroy(slot.stream);
     }
@@ -700,6 +775,10 @@ salt_status salt_serve_stop(salt_server* s) {
     if (slot.d_mem) cudaFree(slot.d_mem);
     if (slot.h_mem) cudaFreeHost(slot.h_mem);
     if (slot.h_red) cudaFreeHost(slot.h_red);
+    for (Slot::StepGraph& sg : slot.g) {
+      if (sg.exec) cudaGraphExecDestroy(sg.exec);
+      if (sg.graph) cudaGraphDestroy(sg.graph);
+    }
     if (slot.done) cudaEventDestroy(slot.done);
     if (slot.stream) cudaStreamDestroy(slot.stream);
   }
