@@ -171,3 +171,20 @@ def test_explain_shows_the_cse_and_folding(saltlib):
     hp, slots, _ = s.salt_explain([("SCAL", 0), ("SCAL", 1), ("ADD", 0), ("VEC", 0), ("SMUL", 0),
                                    ("STORE", 1)], 2, (1.0, 2.0 ** -24), s.F64)
     assert slots[2] == 1.0 + 2.0 ** -24
+
+
+@pytest.mark.parametrize("entry", ["salt_cg_diag", "salt_cg_diag_persistent"])
+def test_cg_argument_errors(saltlib, entry):
+    """Both CG entry points check every call of the run on the host before
+    the first launch."""
+    s = saltlib
+    fn = getattr(s.lib, entry)
+    v = [BASE + k * (1 << 24) for k in range(6)]  # d, b, x, r, p, q
+    rho = BASE + (1 << 30)
+    assert fn(1, 100, *v, -1, rho, None) == s.ERR_ARG             # iters < 0
+    assert fn(1, 100, *v, 4, None, None) == s.ERR_ARG             # rho NULL
+    assert fn(2, 100, *v, 4, rho, None) == s.ERR_DTYPE
+    assert fn(1, 100, v[0] + 4, *v[1:], 4, rho, None) == s.ERR_ALIGN   # d not 8-byte aligned
+    assert fn(1, 100, v[0], v[1], v[2], v[3], v[2] + 8, v[5], 4, rho, None) == s.ERR_ALIAS  # p overlaps x
+    assert fn(1, 100, *v, 4, v[3] + 16, None) == s.ERR_ALIAS      # rho inside r
+    assert fn(1, 100, *v, 4, rho, None) == s.ERR_CUDA             # valid: fails only for want of a GPU
