@@ -915,9 +915,42 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
     combine()
     ms = e0.elapsed_time(e1)
     step_bytes = sum(abytes[(dt, op)] for dt, op, _ in steps)
+    # The host link on this machine, measured the same way: one pinned 1 GiB
+    # buffer copied host -> device, and both directions at once.
+    hb = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+    db = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    hb2 = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+    db2 = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        db.copy_(hb, non_blocking=True)
+    torch.cuda.synchronize()
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(4):
+        db.copy_(hb, non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = 4 * (1 << 30) / (c0.elapsed_time(c1) * 1e-3) / 1e9
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    c0.record(stream)
+    with torch.cuda.stream(side):
+        for _ in range(4):
+            hb2.copy_(db2, non_blocking=True)
+    for _ in range(4):
+        db.copy_(hb, non_blocking=True)
+    stream.wait_stream(side)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    both_gbs = 8 * (1 << 30) / (c0.elapsed_time(c1) * 1e-3) / 1e9
+    del hb, db, hb2, db2
+    bound_ms = max(h2d / (h2d_gbs * 1e9), (h2d + d2h) / (both_gbs * 1e9)) * 1e3
     return {"value": round(world * step_bytes * k / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
             "ms_per_step": round(ms / k, 3),
+            "link_h2d_gbs": round(h2d_gbs, 1), "link_both_directions_gbs": round(both_gbs, 1),
+            "link_bound_ms_per_step": round(bound_ms, 2), "frac_of_link_bound": round(bound_ms / (ms / k), 3),
             "pipeline": f"{nchunks} chunks per vector; upload, compute and read-back streams overlap"}
 
 
