@@ -454,6 +454,7 @@ def main():
     if not args.no_served:
         torch.cuda.empty_cache()
         result["served"] = served_measure(salt)
+    result["config1_figure1"] = config1_measure(torch, salt)
     if not args.no_cg:
         torch.cuda.empty_cache()
         result["cg"] = cg_measure(torch, salt, log2n=args.cg_log2)
@@ -716,6 +717,46 @@ def precision_measure(torch, salt, log2n: int = 26) -> dict:
                     "relative_to_value_compensated_f32": float(abs(comp - ref) / abs(ref))},
             "nrm2": {"compensated_f32": rel(nc, nref, nref), "plain_f32": rel(npl, nref, nref),
                      "f64_widened": rel(nw, nref, nref), "cpu_oracle": rel(onrm, nref, nref)}}
+
+
+def config1_measure(torch, salt, reps: int = 100) -> dict:
+    """Figure 1's d = a + (b - c), FP64, n = 2^20 (a, b, c from
+    default_rng(0).uniform(-1, 1) in order): one plain launch timed with CUDA
+    events, median of `reps`, with the 32 MiB working set warm in L2 and with
+    L2 flushed (a 256 MiB write) before each launch."""
+    import numpy as np
+
+    from paper_1109_1264_gb300 import inputs
+    from paper_1109_1264_gb300.programs import PROG_D
+    n = 1 << 20
+    a, b, c = (torch.from_numpy(v).cuda() for v in inputs.uniform_vectors(0, n, 3, np.float64))
+    d = torch.empty(n, dtype=torch.float64, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(flush_l2):
+        ts = []
+        for _ in range(reps + 3):
+            if flush_l2:
+                flush.zero_()
+            # keep the GPU busy while the host issues the launch, so that the
+            # events time the kernel, not the host's launch latency
+            torch.cuda._sleep(100_000)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            salt.salt_eval(PROG_D, [a, b, c, d])
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts[3:]))
+
+    warm, cold = timed(False), timed(True)
+    nbytes = 32 * n
+    return {"n": n, "dtype": "f64", "bytes": nbytes, "reps": reps,
+            "l2_warm_us": round(warm * 1e3, 2), "l2_warm_gbs": round(nbytes / (warm * 1e-3) / 1e9, 1),
+            "l2_flushed_us": round(cold * 1e3, 2), "l2_flushed_gbs": round(nbytes / (cold * 1e-3) / 1e9, 1),
+            "note": "32 MiB fits in the 129 MB L2: the warm figure is not an HBM rate"}
 
 
 def cg_latency_measure(torch, salt, sizes=(1 << 14, 1 << 17, 1 << 20, 1 << 24), iters: int = 100,

@@ -271,3 +271,22 @@ def test_replay_resident_store(salt, cuda_dev):
         assert srv.stats()["resident_bytes"] == 0
     finally:
         srv.stop()
+
+
+def test_server_rejects_programs_outside_the_batch_kernel(salt):
+    """The server runs the batch kernel's compiled shapes only: elementwise
+    DIV, device scalars and the CG pass shapes are refused at submission."""
+    srv = salt.Server(budget_bytes=1 << 24, max_n=1 << 16)
+    try:
+        div = [("VEC", 0), ("VEC", 1), ("DIV", 0), ("STORE", 2)]
+        ds = [("DSCAL", 0), ("VEC", 0), ("SMUL", 0), ("STORE", 1)]
+        cgxr = [("VEC", 3), ("SCAL", 0), ("VEC", 1), ("SMUL", 0), ("ADD", 0), ("STORE", 3),
+                ("VEC", 4), ("SCAL", 0), ("VEC", 2), ("SMUL", 0), ("SUB", 0), ("STORE", 4),
+                ("VEC", 4), ("SUMSQ", 0)]
+        for prog, nk, sc in ((div, 3, ()), (ds, 2, ()), (cgxr, 5, (0.5,))):
+            with pytest.raises(salt.SaltError) as ei:
+                srv.submit(prog, salt.F32, 100, list(range(1, nk + 1)), sc)
+            assert ei.value.status == salt.ERR_PROGRAM, prog
+        assert srv.stats()["waiting"] == 0
+    finally:
+        srv.stop()
