@@ -406,3 +406,51 @@ def test_precision_form_config3(salt):
     assert abs(nc - nref) <= 1e-6 * nref
     assert abs(nw - nref) <= 1e-13 * nref
     assert abs(npl - nref) <= plain_gamma * nref
+
+
+def test_concurrent_host_threads_on_separate_streams(salt):
+    """Four host threads, each on its own stream, run reductions and fused
+    expressions at the same time: every result equals the single-threaded
+    one (per-stream workspaces, thread-safe tables, thread-local errors)."""
+    import threading
+    dev = torch.device("cuda:0")
+    n = (1 << 20) + 3
+    x, y = (torch.from_numpy(v).to(dev) for v in inputs.uniform_vectors(77, n, 2, np.float64))
+    ref = torch.zeros(2, dtype=torch.float64, device=dev)
+    salt.salt_dot(x, y, ref[0:1])
+    salt.salt_nrm2(x, ref[1:2])
+    torch.cuda.synchronize()
+    want = ref.cpu().numpy()
+    outs, errors = {}, []
+
+    def work(t):
+        try:
+            s = torch.cuda.Stream()
+            red = torch.zeros(2 * 50, dtype=torch.float64, device=dev)
+            z = torch.empty(n, dtype=torch.float64, device=dev)
+            with torch.cuda.stream(s):
+                for i in range(50):
+                    salt.salt_dot(x, y, red[2 * i:2 * i + 1], stream=s)
+                    salt.salt_nrm2(x, red[2 * i + 1:2 * i + 2], stream=s)
+                    salt.salt_eval(oracle.PROG_SCALE, [x, z], [0.5 + t], stream=s)
+                    try:  # an error on one thread stays on that thread
+                        salt.salt_eval([("ADD", 0)], [x])
+                    except salt.SaltError as e:
+                        assert "needs two operands" in e.message
+            s.synchronize()
+            outs[t] = (red.cpu().numpy(), z.cpu().numpy())
+        except Exception as e:  # noqa: BLE001
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=work, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    xh = x.cpu().numpy()
+    for t, (red, z) in outs.items():
+        assert np.array_equal(red.reshape(-1, 2), np.tile(want, (50, 1))), t
+        want_z = [xh.copy(), np.zeros(n)]
+        oracle.eval_program(oracle.PROG_SCALE, want_z, [0.5 + t])
+        assert_bits_equal(z, want_z[1], f"thread {t}")
