@@ -209,3 +209,32 @@ def test_cg_batch_sample_config4(salt, cuda_dev):
         b.close()
         del bufs
         torch.cuda.empty_cache()
+
+
+def test_fp32_items_both_access_widths(salt, cuda_dev):
+    """FP32 items whose operands are all 32-byte aligned take 32-byte
+    accesses, the others 16-byte accesses: in one batch, both give the
+    oracle's bits, and their reductions are within tolerance."""
+    rng = np.random.default_rng(17)
+    items, tensors, slots = [], [], []
+    for n in (5, 1000, 4096 + 3, 70001, 300007):
+        for off in (0, 4):  # elements: 0 -> 32-byte aligned views, 4 -> 16-byte aligned only
+            for prog, nv, ns in ((P.PROG_E, 5, 2), (P.PROG_CG, 3, 2), (P.PROG_DOT, 2, 0)):
+                vecs = [rng.uniform(-1, 1, n).astype(np.float32) for _ in range(nv)]
+                tv = []
+                for v in vecs:
+                    buf = torch.zeros(n + 8, dtype=torch.float32, device=cuda_dev)
+                    view = buf[off:off + n]
+                    view.copy_(torch.from_numpy(v))
+                    tv.append(view)
+                assert all((t.data_ptr() % 32 == 0) == (off == 0) for t in tv)
+                items.append((prog, np.float32, vecs, list(rng.uniform(-2, 2, ns))))
+                tensors.append(tv)
+    b = salt.Batch(len(items))
+    for (prog, dt, vecs, scal), tv in zip(items, tensors):
+        slots.append(b.add(prog, tv, scal))
+    red = torch.full((max(b.info()["results"], 1),), float("nan"), dtype=torch.float64, device=cuda_dev)
+    b.launch(red)
+    torch.cuda.synchronize()
+    check(items, tensors, slots, red.cpu().numpy())
+    b.close()
