@@ -974,12 +974,13 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
     combine()
     ms = e0.elapsed_time(e1)
     step_bytes = sum(abytes[(dt, op)] for dt, op, _ in steps)
-    # The host link on this machine, measured the same way: one pinned 1 GiB
+    # The host link on this machine, measured the same way: one pinned 256 MiB
     # buffer copied host -> device, and both directions at once.
-    hb = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
-    db = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
-    hb2 = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
-    db2 = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    lb = 1 << 28
+    hb = torch.empty(lb, dtype=torch.uint8, pin_memory=True)
+    db = torch.empty(lb, dtype=torch.uint8, device="cuda")
+    hb2 = torch.empty(lb, dtype=torch.uint8, pin_memory=True)
+    db2 = torch.empty(lb, dtype=torch.uint8, device="cuda")
     for _ in range(2):
         db.copy_(hb, non_blocking=True)
     torch.cuda.synchronize()
@@ -990,7 +991,7 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
         db.copy_(hb, non_blocking=True)
     c1.record(stream)
     torch.cuda.synchronize()
-    h2d_gbs = 4 * (1 << 30) / (c0.elapsed_time(c1) * 1e-3) / 1e9
+    h2d_gbs = 4 * lb / (c0.elapsed_time(c1) * 1e-3) / 1e9
     side = torch.cuda.Stream()
     side.wait_stream(stream)
     c0.record(stream)
@@ -1002,7 +1003,7 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
     stream.wait_stream(side)
     c1.record(stream)
     torch.cuda.synchronize()
-    both_gbs = 8 * (1 << 30) / (c0.elapsed_time(c1) * 1e-3) / 1e9
+    both_gbs = 8 * lb / (c0.elapsed_time(c1) * 1e-3) / 1e9
     del hb, db, hb2, db2
     bound_ms = max(h2d / (h2d_gbs * 1e9), (h2d + d2h) / (both_gbs * 1e9)) * 1e3
     return {"value": round(world * step_bytes * k / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
