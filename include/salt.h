@@ -456,8 +456,9 @@ salt_status salt_batch_destroy(salt_batch* b);
 
 /* Adds one program item; arguments as salt_eval (device operands, host
  * program and scalars read during the call).  The program must have a
- * compiled instantiation (salt_check_program's compiled_out), at most 5
- * vector operands and 2 scalars.  *red_index_out (may be NULL) receives the
+ * compiled instantiation (salt_check_program's compiled_out) among the
+ * batch kernel's shapes, at most 5 vector operands and 2 scalars, once its
+ * scalar subexpressions (by-value scalars only; no DSCAL) are folded.  *red_index_out (may be NULL) receives the
  * index in the launch's red_out of the item's first DOT/SUMSQ result, or -1.
  * Errors: as salt_eval, SALT_ERR_BUDGET when full. */
 salt_status salt_batch_add(salt_batch* b, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
@@ -536,7 +537,9 @@ salt_status salt_serve_start(salt_server** out, const salt_serve_config* cfg);
 salt_status salt_serve_stop(salt_server* s);
 
 /* Submits a request.  prog/nprog: a program with a compiled instantiation
- * (<= 5 vector operands, <= 2 scalars); prog == NULL requests the Euclidean
+ * among the batch kernel's shapes (<= 5 vector operands, <= 2 scalars) once
+ * its by-value scalar subexpressions are folded (no DSCAL; SALT_ERR_PROGRAM
+ * otherwise); prog == NULL requests the Euclidean
  * norm of one operand.  keys[k] (nkeys entries, one per operand index) seeds
  * operand k's contents: element i is value i of the counter-based uniform
  * stream `keys[k]` (salt_fill_uniform); keys of output-only operands are

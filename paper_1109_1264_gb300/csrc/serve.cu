@@ -519,6 +519,25 @@ salt_status submit_impl(salt_server* s, const salt_insn* prog, int32_t nprog, in
       delete r;
       return fail(SALT_ERR_ARG, "scalars is NULL");
     }
+    // Scalar subexpressions of by-value scalars are computed here, once
+    // (a served request takes no device scalars).
+    Hoisted h;
+    double sc2[kMaxScals] = {};
+    if (an.scalar_nodes) {
+      st = hoist_scalars(prog, nprog, nscal, &h, &err);
+      if (st != SALT_OK) {
+        delete r;
+        return fail(st, err);
+      }
+      for (int k = 0; k < nscal; ++k) sc2[k] = scalars[k];
+      for (int j = 0; j < h.nhoist; ++j)
+        sc2[nscal + j] = dtype == SALT_F32 ? host_scalar_value_f32(prog, h, j, sc2)
+                                           : host_scalar_value_f64(prog, h, j, sc2);
+      prog = h.prog;
+      nprog = h.nprog;
+      nscal = h.nscal;
+      scalars = sc2;
+    }
     Canonical c;
     canonicalise(prog, nprog, &c);
     const int shape = find_shape(c);

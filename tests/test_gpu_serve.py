@@ -290,3 +290,24 @@ def test_server_rejects_programs_outside_the_batch_kernel(salt):
         assert srv.stats()["waiting"] == 0
     finally:
         srv.stop()
+
+
+def test_server_folds_by_value_scalar_subexpressions(salt):
+    """A request whose scalars form a subexpression of by-value scalars runs
+    on the compiled shape with the folded value: the oracle's bits."""
+    srv = salt.Server(budget_bytes=1 << 26, max_n=1 << 16)
+    try:
+        prog = [("SCAL", 0), ("SCAL", 1), ("DIV", 0), ("VEC", 0), ("SMUL", 0), ("SCAL", 2), ("VEC", 1),
+                ("SMUL", 0), ("ADD", 0), ("STORE", 1)]
+        for dt, code in ((np.float32, salt.F32), (np.float64, salt.F64)):
+            n = 4099
+            keys = [inputs.vector_key(41, code, k) for k in range(2)]
+            rid = srv.submit(prog, code, n, keys, [1.0, 3.0, -0.5])
+            srv.wait(rid, 20_000_000)
+            got = srv.read(rid, 1, np.empty(n, dt))
+            want = host_inputs(keys, 2, n, dt)
+            oracle.eval_program(prog, want, [1.0, 3.0, -0.5])
+            assert_bits_equal(got, want[1], f"folded {dt}")
+            srv.release(rid)
+    finally:
+        srv.stop()
