@@ -595,11 +595,13 @@ salt_status salt_serve_replay(salt_server* s, int32_t count, const double* arriv
  * instead of a per-request fill: operand k of request i reads elements
  * [o, o + n[i]) of store vector (5 i + k) mod nstore of its dtype, with
  *   h = (key * 0x9E3779B97F4A7C15 mod 2^64) >> 11,
- *   o = (h mod (len - n[i] + 1)), rounded down to a multiple of 4,
+ *   o = (h mod (len - n[i] + 1)), rounded down to a multiple of 32 bytes
+ *       (8 FP32 or 4 FP64 elements),
  * key the operand's key above.  Stored operands (d, y, e) stay server-owned
  * (y, read and written, is filled from its key).  store_f32 / store_f64:
  * nstore_f32 / nstore_f64 device vectors of len_f32 / len_f64 elements,
- * 16-byte aligned; every n[i] <= the length of its dtype's vectors. */
+ * 16-byte aligned (32-byte aligned, as cudaMalloc's are, for 256-bit
+ * accesses); every n[i] <= the length of its dtype's vectors. */
 salt_status salt_serve_replay_store(salt_server* s, int32_t count, const double* arrival_us, const int32_t* shape,
                                     const int32_t* dtype, const int64_t* n, uint64_t seed,
                                     const void* const* store_f32, int32_t nstore_f32, int64_t len_f32,

@@ -474,13 +474,13 @@ uint64_t vector_key(uint64_t seed, uint64_t item, uint64_t slot) {
 
 // Store vector and element offset of input operand k of replayed request i
 // (salt_serve_replay_store): vector (5 i + k) mod count, offset a multiple of
-// 4 elements (16-byte aligned) in [0, len - n], spread by a multiplicative
+// 32 bytes (`align` elements) in [0, len - n], spread by a multiplicative
 // hash of the operand's key.
 int32_t store_vector(int64_t i, int k, int32_t count) { return (int32_t)(((uint64_t)i * 5u + (uint64_t)k) % (uint64_t)count); }
-int64_t store_offset(uint64_t seed, uint64_t i, uint64_t k, int64_t n, int64_t len) {
+int64_t store_offset(uint64_t seed, uint64_t i, uint64_t k, int64_t n, int64_t len, int64_t align) {
   const uint64_t h = (vector_key(seed, i, k) * 0x9E3779B97F4A7C15ull) >> 11;
   const int64_t o = (int64_t)(h % (uint64_t)(len - n + 1));
-  return o - o % 4;
+  return o - o % align;
 }
 
 salt_status submit_impl(salt_server* s, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
@@ -857,7 +857,8 @@ salt_status replay_impl(salt_server* s, int32_t count, const double* arrival_us,
           const int64_t len = store->len[t2], nn = n[next];
           if (store->count[t2] < 1 || nn > len) return fail(SALT_ERR_ARG, "store has no vector long enough");
           ptrs[k] = (const char*)store->vec[t2][store_vector(next, k, store->count[t2])] +
-                    store_offset(seed, (uint64_t)next, (uint64_t)k, nn, len) * (dtype[next] == SALT_F64 ? 8 : 4);
+                    store_offset(seed, (uint64_t)next, (uint64_t)k, nn, len, dtype[next] == SALT_F64 ? 4 : 8) *
+                        (dtype[next] == SALT_F64 ? 8 : 4);
         }
       }
       int64_t id = 0;

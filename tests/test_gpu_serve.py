@@ -185,13 +185,13 @@ def test_replay_poisson_trace(salt):
 M64 = (1 << 64) - 1
 
 
-def store_place(seed, i, k, n, length, count):
+def store_place(seed, i, k, n, length, count, itemsize):
     """Store vector and offset of input operand k of replayed request i
     (the formula salt_serve_replay_store documents)."""
     key = (seed * 0x100000001B3 + i * 16 + k + 1) & M64
     h = ((key * 0x9E3779B97F4A7C15) & M64) >> 11
     o = h % (length - n + 1)
-    return (i * 5 + k) % count, o - o % 4
+    return (i * 5 + k) % count, o - o % (32 // itemsize)
 
 
 def test_caller_owned_operands(salt, cuda_dev):
@@ -259,7 +259,7 @@ def test_replay_resident_store(salt, cuda_dev):
             n = int(lens[i])
             vecs = []
             for k in range(SHAPES[si][1]):
-                j, o = store_place(13, i, k, n, length, len(skeys[dt]))
+                j, o = store_place(13, i, k, n, length, len(skeys[dt]), np.dtype(dt).itemsize)
                 vecs.append(inputs.hash_uniform(skeys[dt][j], n, dt, offset=o))
             if si == 4:
                 ref, scale = exact.exact_nrm2(vecs[0]), exact.exact_nrm2(vecs[0])
