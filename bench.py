@@ -870,12 +870,18 @@ def served_measure(salt, count: int = 3000, seed: int = 0) -> dict:
         _, wall1, _ = saturation(srv1, True)
     finally:
         srv1.stop()
+    srv4 = salt.Server(streams=4)  # beyond the 2 steps in flight of the served configuration
+    try:
+        _, wall4, _ = saturation(srv4, True)
+    finally:
+        srv4.stop()
     del store
     torch.cuda.empty_cache()
     unbatched_gbs = total_bytes / (wall1 * 1e-6) / 1e9
     return {"saturation_rps": round(sat_rps, 1), "saturation_gbs": round(sat_gbs, 1), "saturation_steps": steps,
             "unbatched_saturation_gbs": round(unbatched_gbs, 1), "batched_vs_unbatched": round(sat_gbs / unbatched_gbs, 2),
             "fill_per_request_saturation_gbs": round(total_bytes / (wall_f * 1e-6) / 1e9, 1),
+            "four_streams_saturation_gbs": round(total_bytes / (wall4 * 1e-6) / 1e9, 1),
             "fill_per_request_steps": steps_f,
             "requests_per_point": count, "bytes_per_point": total_bytes, "points": points,
             "workload": "5 shapes uniform, n log-uniform [2^8, 2^24], 70% FP32 / 30% FP64; inputs from an 8 GiB "
