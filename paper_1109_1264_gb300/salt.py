@@ -93,12 +93,26 @@ def _check(status: int) -> None:
 
 # ------------------------------------------------------------ marshalling --
 
+_PROGRAM_CACHE: dict = {}
+
+
 def program(prog) -> tuple[ctypes.Array, int]:
-    """[(name, arg), ...] or [(opcode, arg), ...] -> (salt_insn array, length)."""
+    """[(name, arg), ...] or [(opcode, arg), ...] -> (salt_insn array, length).
+    The library only reads the array, so the marshalled form of a program is
+    kept and reused (repeated calls skip the per-instruction conversion)."""
+    try:
+        key = tuple((op, int(arg)) for op, arg in prog)
+        hit = _PROGRAM_CACHE.get(key)
+    except TypeError:  # unhashable operands: marshal afresh
+        key, hit = None, None
+    if hit is not None:
+        return hit
     arr = (Insn * max(len(prog), 1))()
     for i, (op, arg) in enumerate(prog):
         arr[i].op = OPS[op] if isinstance(op, str) else int(op)
         arr[i].arg = int(arg)
+    if key is not None and len(_PROGRAM_CACHE) < 4096:
+        _PROGRAM_CACHE[key] = (arr, len(prog))
     return arr, len(prog)
 
 
