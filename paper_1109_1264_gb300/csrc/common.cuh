@@ -244,6 +244,13 @@ __device__ __forceinline__ bool grid_combine(R (&vals)[NV], R* partials, unsigne
   R tot[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) tot[k] = block_sum<R>(vals[k], smem);
+  if (gridDim.x == 1) {
+    // one block: its sums are the totals (the same bits as the combine,
+    // which would add zeros to them), no partials, ticket or fences
+#pragma unroll
+    for (int k = 0; k < NV; ++k) vals[k] = tot[k];
+    return true;
+  }
   __shared__ bool is_last;
   if (threadIdx.x == 0) {
 #pragma unroll
