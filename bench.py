@@ -635,6 +635,28 @@ def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> 
         rho = torch.zeros(2 * iters + 1, dtype=torch.float64, device="cuda")
         rho_u = torch.zeros(2 * iters + 1, dtype=torch.float64, device="cuda")
         vecs = [d, p, q, x, r, b]
+        # The autotuner on the two passes' shapes (by-value scalars: the same
+        # compiled shapes and launch-shape table entries as the device-scalar
+        # form); setup, untimed.
+        p.copy_(b)
+        r.copy_(b)
+        tune = torch.zeros(2, dtype=torch.float64, device="cuda")
+        cgpq = [("VEC", 4), ("SCAL", 0), ("VEC", 1), ("SMUL", 0), ("ADD", 0), ("STORE", 1), ("VEC", 0), ("VEC", 1),
+                ("MUL", 0), ("STORE", 2), ("VEC", 1), ("VEC", 2), ("DOT", 0)]
+        cgxr = [("VEC", 3), ("SCAL", 0), ("VEC", 1), ("SMUL", 0), ("ADD", 0), ("STORE", 3), ("VEC", 4), ("SCAL", 0),
+                ("VEC", 2), ("SMUL", 0), ("SUB", 0), ("STORE", 4), ("VEC", 4), ("SUMSQ", 0)]
+        tuned = {"pq": salt.salt_autotune(salt.KERNEL_PROGRAM, cgpq, vecs, [0.0], red_out=tune[0:1], reps=2)[0],
+                 "xr": salt.salt_autotune(salt.KERNEL_PROGRAM, cgxr, vecs, [0.0], red_out=tune[1:2], reps=2)[0]}
+        # ... and on the compiled shapes the six-call form uses (AXPBY, DOT,
+        # AXPY, SUMSQ, COPY), so that both schedules run tuned launch shapes
+        for prog, sc, red in (([("SCAL", 0), ("VEC", 4), ("SMUL", 0), ("SCAL", 1), ("VEC", 1), ("SMUL", 0),
+                                ("ADD", 0), ("STORE", 1)], [1.0, 0.0], None),
+                               ([("VEC", 1), ("VEC", 2), ("DOT", 0)], [], tune[0:1]),
+                               ([("SCAL", 0), ("VEC", 1), ("SMUL", 0), ("VEC", 3), ("ADD", 0), ("STORE", 3)], [0.0],
+                                None),
+                               ([("VEC", 4), ("SUMSQ", 0)], [], tune[1:2]),
+                               ([("VEC", 4), ("STORE", 1)], [], None)):
+            salt.salt_autotune(salt.KERNEL_PROGRAM, prog, vecs, sc, red_out=red, reps=2)
         r0 = [("VEC", 5), ("VEC", 0), ("VEC", 3), ("MUL", 0), ("SUB", 0), ("STORE", 4), ("VEC", 4), ("SUMSQ", 0)]
         quot = [("DSCAL", 0), ("DSCAL", 1), ("DIV", 0)]
         p_upd = [("SCAL", 0), ("VEC", 4), ("SMUL", 0)] + quot + [("VEC", 1), ("SMUL", 0), ("ADD", 0), ("STORE", 1)]
@@ -690,7 +712,7 @@ def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> 
                    "gbs_fused": round(abytes / (ms_f * 1e-3) / 1e9, 1),
                    "gbs_unfused_same_bytes": round(abytes / (ms_u * 1e-3) / 1e9, 1),
                    "speedup": round(ms_u / ms_f, 3),
-                   "launches_fused": 1 + 2 * iters, "launches_unfused": 1 + 6 * iters,
+                   "launches_fused": 1 + 2 * iters, "launches_unfused": 1 + 6 * iters, "tuned": tuned,
                    "rel_residual": float(np.sqrt(h_f[-1] / h_f[0])),
                    "rho_rel_diff_fused_vs_unfused": float(abs(h_f[-1] - h_u[-1]) / h_f[-1])}
         del d, b, x, r, p, q, vecs
