@@ -61,6 +61,8 @@ def f64_alu_peak_gops(sm_mhz: float) -> float:
 KERNEL_SOURCES = {
     "e_f64": ["prog.cuh", "common.cuh", "fused.cuh", "reduce.cuh", "shapes.h", "registry.h", "inst.cuh",
               "inst_f64_vb16.cu", "inst_f64_vb32.cu"],
+    "e_f64_staged": ["prog.cuh", "common.cuh", "fused.cuh", "staged.cuh", "shapes.h", "registry.h",
+                     "inst_staged.cu"],
 }
 
 
@@ -293,7 +295,7 @@ def main():
     ap.add_argument("--only-cg", action="store_true", help="run only the CG leg (profiling runs)")
     ap.add_argument("--only-served", action="store_true", help="run only the served leg (profiling runs)")
     ap.add_argument("--fixed-e-cfg", default=None,
-                    help="profiling runs: skip the autotuner and launch e with U,VB,BLOCK,BLOCKS_PER_SM")
+                    help="profiling runs: skip the autotuner and launch e with U,VB,BLOCK,BLOCKS_PER_SM[,STAGE_BYTES]")
     ap.add_argument("--cg-log2", type=int, default=28)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
@@ -341,10 +343,13 @@ def main():
     loads = {dt: Workload(torch, salt, dt, n, seed=rank) for dt in DTYPES}
     if args.fixed_e_cfg:
         from paper_1109_1264_gb300.programs import PROG_E
-        u, vb, blk, bps = (int(v) for v in args.fixed_e_cfg.split(","))
+        vals = [int(v) for v in args.fixed_e_cfg.split(",")]
+        u, vb, blk, bps = vals[:4]
+        sb = vals[4] if len(vals) > 4 else 0
         for code in (salt.F32, salt.F64):
-            salt.salt_tune_set(PROG_E, code, n, u, vb, blk, bps)
-        tuned = {"e": {"unroll": u, "vec_bytes": vb, "block": blk, "blocks_per_sm": bps}, "others": "defaults"}
+            salt.salt_tune_set(PROG_E, code, n, u, vb, blk, bps, sb)
+        tuned = {"e": {"unroll": u, "vec_bytes": vb, "block": blk, "blocks_per_sm": bps, "stage_bytes": sb},
+                 "others": "defaults"}
     elif args.tune_load:
         salt.salt_tune_load(args.tune_load)
         tuned = {"loaded": os.path.basename(args.tune_load)}
@@ -426,7 +431,15 @@ def main():
         roof.update({"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(hbm_frac, 4)})
     roof["peak_kind"] = peak_kind
-    roof["traffic"] = traffic_for(f"{dop}_{ddt}", n)
+    # the traffic figure belongs to the schedule (register-tiled or staged) the op ran
+    tkey = f"{dop}_{ddt}"
+    if dop in ("e", "axpby", "dot"):
+        from paper_1109_1264_gb300.programs import PROG_AXPBY, PROG_DOT, PROG_E
+        prog = {"e": PROG_E, "axpby": PROG_AXPBY, "dot": PROG_DOT}[dop]
+        if salt.salt_tune_get(prog, salt.F32 if ddt == "f32" else salt.F64, n)["stage_bytes"]:
+            tkey += "_staged"
+    roof["schedule"] = "staged" if tkey.endswith("_staged") else "register-tiled"
+    roof["traffic"] = traffic_for(tkey, n)
     roof["algorithmic_bytes"] = abytes[(ddt, dop)]
 
     result = {

@@ -381,15 +381,27 @@ salt_status salt_release_workspaces(void);
  *   block         threads per block (64..256, multiple of 32)
  *   blocks_per_sm resident blocks per SM the grid is sized for (1..32; 0:
  *                 as many as fit, from the occupancy calculator)
+ *   stage_bytes   0: operands are loaded into registers by vector loads (the
+ *                 register-tiled loop, shaped by unroll and vec_bytes).
+ *                 4096, 8192 or 16384: the staged loop — each block copies
+ *                 tiles of stage_bytes per loaded operand into shared memory
+ *                 by bulk asynchronous copies, two stages deep, and computes
+ *                 on one stage while the next fills; unroll and vec_bytes are
+ *                 not used.  Only programs with a compile-time instantiation
+ *                 whose operands are 16-byte aligned and contiguous take it
+ *                 (others use their usual kernel).  Element results are
+ *                 bit-identical either way; reduction results are summed in
+ *                 another order (same error bounds).
  * salt_tune_set pins a configuration for (program, dtype, n bucket) where the
  * bucket is floor(log2(max(n,1))); salt_tune_get reports the configuration a
- * call would use.  Returns SALT_ERR_ARG for an invalid configuration or
- * SALT_ERR_PROGRAM for a program without a compile-time instantiation. */
+ * call would use.  Returns SALT_ERR_ARG for an invalid configuration (also
+ * stage_bytes != 0 for a program without a compile-time instantiation). */
 typedef struct {
   int32_t unroll;
   int32_t vec_bytes;
   int32_t block;
   int32_t blocks_per_sm;
+  int32_t stage_bytes;
 } salt_launch_cfg;
 
 salt_status salt_tune_set(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
@@ -408,19 +420,30 @@ salt_status salt_tune_clear(void);
 /* Autotuner: runs the call (arguments as salt_eval; for the other families
  * vecs / red_out as noted above) under every configuration of unroll {1,2,4}
  * x vec_bytes {16,32} x block {128,256} x blocks_per_sm {as many as fit, 2,
- * 4}, `reps` timed runs each after one warm-up, on `stream`, and pins the
- * fastest for (family, dtype, n bucket) in the tuning table.  *best and
- * *best_ms (either may be NULL) receive it and its time per call.  The call
- * runs (reps + 1) times per configuration (36 configurations; 12 for the
- * interpreter, which has no unroll): in-place programs update their operands
- * each time. */
+ * 4} of the register-tiled loop, and for programs with a compile-time
+ * instantiation also the staged loop at stage_bytes {4096, 8192, 16384} x
+ * block {128, 256} (as many blocks as fit), `reps` timed runs each after one
+ * warm-up, on `stream`, and pins the fastest for (family, dtype, n bucket) in
+ * the tuning table.  *best and *best_ms (either may be NULL) receive it and
+ * its time per call.  The call runs (reps + 1) times per configuration (42
+ * configurations for a compiled shape; 36 for nrm2 and the plain dot; 12 for
+ * the interpreter, which has no unroll): in-place programs update their
+ * operands each time. */
 salt_status salt_autotune(int32_t kernel, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
                           void* const* vecs, int32_t nvecs, const double* scalars, int32_t nscal, double* red_out,
                           int32_t reps, salt_launch_cfg* best, double* best_ms, void* stream);
 /* Writes the tuning table as text (one line per entry) / merges such a file
- * into it.  Errors: SALT_ERR_ARG (unreadable, unwritable or malformed). */
+ * into it (lines without the stage_bytes column read as stage_bytes 0).
+ * Errors: SALT_ERR_ARG (unreadable, unwritable or malformed). */
 salt_status salt_tune_save(const char* path);
 salt_status salt_tune_load(const char* path);
+
+/* Waits of staged-loop launches (stage_bytes != 0) on the current device that
+ * ran out of their bound (one second) since the library was loaded: *count.
+ * A block whose stage copies did not arrive in time finishes its tiles from
+ * direct loads (results unchanged) and counts one here.  Synchronous (reads a
+ * device counter).  Errors: SALT_ERR_ARG (count NULL), SALT_ERR_CUDA. */
+salt_status salt_staged_timeouts(uint64_t* count);
 
 /* Number of kernel launches this library has issued on the calling process
  * (all threads), for accounting in benchmarks. */

@@ -10,6 +10,7 @@
 #include <mutex>
 #include <string>
 #include <tuple>
+#include <vector>
 
 #include "../../include/salt.h"
 #include "fused.cuh"
@@ -18,6 +19,7 @@
 #include "interp.cuh"
 #include "reduce.cuh"
 #include "registry.h"
+#include "staged.cuh"
 
 namespace salt {
 
@@ -46,6 +48,7 @@ Registry& registry() {
     register_f64_vb32(r);
     register_misc(r);
     register_elementwise(r);
+    register_staged(r);
   });
   return r;
 }
@@ -127,7 +130,8 @@ static int bucket_of(int64_t n) {
 static bool cfg_valid(const salt_launch_cfg& c) {
   return unroll_index(c.unroll) >= 0 && vb_index(c.vec_bytes) >= 0 && c.block >= 64 &&
          c.block <= 256 && c.block % 32 == 0 && c.blocks_per_sm >= 0 &&
-         c.blocks_per_sm <= kMaxBlocksPerSM && c.block * c.blocks_per_sm <= 2048;
+         c.blocks_per_sm <= kMaxBlocksPerSM && c.block * c.blocks_per_sm <= 2048 &&
+         stage_bytes_valid(c.stage_bytes);
 }
 
 static salt_launch_cfg default_cfg(int family, int dt) {
@@ -136,6 +140,7 @@ static salt_launch_cfg default_cfg(int family, int dt) {
   c.vec_bytes = 16;
   c.block = 256;
   c.blocks_per_sm = 0;  // 0: as many as fit (occupancy)
+  c.stage_bytes = 0;    // register-tiled loop
   (void)family;
   (void)dt;
   return c;
@@ -170,6 +175,26 @@ static int occupancy_blocks(const void* kernel, int block, size_t smem) {
   std::lock_guard<std::mutex> lk(g_occ_mu);
   g_occ[key] = nb;
   return nb;
+}
+
+// Raises a kernel's dynamic shared-memory limit to at least `smem` (once per
+// device, kernel and size; before occupancy queries).  Needed whenever the
+// kernel's static plus dynamic shared memory exceeds 48 KiB, so it is done
+// for any non-zero size rather than from an estimate of the static part.
+static std::mutex g_smem_mu;
+static std::map<std::pair<int, const void*>, size_t> g_smem_limit;
+
+static cudaError_t ensure_dyn_smem(const void* kernel, size_t smem) {
+  if (smem == 0) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  size_t& have = g_smem_limit[std::make_pair(dev, kernel)];
+  if (have >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) have = smem;
+  return e;
 }
 
 static int grid_for(int64_t n, int64_t tile_elems, int sms, int bps) {
@@ -250,6 +275,35 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
 
   if (shape >= 0) {
     salt_launch_cfg cfg = lookup_cfg(shape, dt, a.n);
+    if (cfg.stage_bytes > 0) {
+      // staged loop: tiles copied into shared memory (operands 16-byte aligned here)
+      const KernelEntry& ke = reg.staged[shape][dt];
+      const size_t smem = reg.staged_smem[shape](cfg.stage_bytes);
+      cudaError_t e = ensure_dyn_smem(ke.kernel, smem);
+      if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(staged kernel)");
+      int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy_blocks(ke.kernel, cfg.block, smem);
+      if (bps > kMaxBlocksPerSM) bps = kMaxBlocksPerSM;
+      const int grid = grid_for(a.n, cfg.stage_bytes / (int64_t)sizeof(T), info.sms, bps);
+      StagedParams<T> sp;
+      memset(&sp, 0, sizeof sp);
+      MapParams<T>& p = sp.m;
+      for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]];
+      for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
+      if (scode) p.scode = *scode;
+      p.n = a.n;
+      p.red_out = a.red_out;
+      p.partials = ws.partials;
+      p.ticket = ws.ticket;
+      sp.stage_bytes = cfg.stage_bytes;
+      e = ke.launch(&sp, grid, cfg.block, smem, a.stream);
+      g_launches.fetch_add(1);
+      if (e != cudaSuccess) {
+        const std::string what = "staged kernel launch (grid " + std::to_string(grid) + ", block " +
+                                 std::to_string(cfg.block) + ", shared " + std::to_string(smem) + " B)";
+        return cuda_error(e, what.c_str());
+      }
+      return SALT_OK;
+    }
     if (cfg.vec_bytes == 32 && !all32) cfg.vec_bytes = 16;
     if (scode) cfg.unroll = kDsUnroll<T>;  // one unroll per device-scalar instantiation
     const KernelEntry& ke = scode ? reg.fused_ds[shape][dt][vb_index(cfg.vec_bytes)]
@@ -326,8 +380,8 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
   if (cfg.vec_bytes == 32 && !all32) cfg.vec_bytes = 16;
   const KernelEntry& ke = reg.interp[dt][vb_index(cfg.vec_bytes)];
   const size_t smem = (size_t)kRegs * cfg.block * cfg.vec_bytes;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(ke.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = ensure_dyn_smem(ke.kernel, smem);
     if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute");
   }
   int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy_blocks(ke.kernel, cfg.block, smem);
@@ -863,6 +917,8 @@ salt_status salt_tune_set(const salt_insn* prog, int32_t nprog, int32_t dtype, i
   int fam = 0;
   st = tune_family(prog, nprog, scal_count(prog, nprog), &fam);
   if (st != SALT_OK) return st;
+  if (cfg->stage_bytes != 0 && fam >= NUM_SHAPES)
+    return set_error(SALT_ERR_ARG, "the staged loop needs a program with a compile-time instantiation");
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[TuneKey(fam, dtype == SALT_F32 ? DT_F32 : DT_F64, bucket_of(n))] = *cfg;
   return SALT_OK;
@@ -931,37 +987,36 @@ salt_status salt_autotune(int32_t kernel, const salt_insn* prog, int32_t nprog, 
     return set_error(SALT_ERR_CUDA, "cudaEventCreate");
   salt_launch_cfg best = default_cfg(family, dt);
   float best_t = 1e30f;
+  std::vector<salt_launch_cfg> cands;
   for (int u : {1, 2, 4}) {
     if (family == 200 && u != 1) continue;  // the interpreter has no unroll
-    for (int vb : {16, 32}) {
-      for (int blk : {128, 256}) {
-        for (int bps : {0, 2, 4}) {
-          const salt_launch_cfg c{u, vb, blk, bps};
-          {
-            std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tune[key] = c;
-          }
-          st = run();
-          if (st == SALT_OK) cudaEventRecord(e0, s);
-          for (int r = 0; r < reps && st == SALT_OK; ++r) st = run();
-          if (st != SALT_OK) break;
-          cudaEventRecord(e1, s);
-          if (cudaEventSynchronize(e1) != cudaSuccess) {
-            st = set_error(SALT_ERR_CUDA, "cudaEventSynchronize");
-            break;
-          }
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (ms / reps < best_t) {
-            best_t = ms / reps;
-            best = c;
-          }
-        }
-        if (st != SALT_OK) break;
-      }
-      if (st != SALT_OK) break;
+    for (int vb : {16, 32})
+      for (int blk : {128, 256})
+        for (int bps : {0, 2, 4}) cands.push_back(salt_launch_cfg{u, vb, blk, bps, 0});
+  }
+  if (family < NUM_SHAPES)  // the staged loop (compiled shapes only)
+    for (int sb : {4096, 8192, 16384})
+      for (int blk : {128, 256}) cands.push_back(salt_launch_cfg{1, 16, blk, 0, sb});
+  for (const salt_launch_cfg& c : cands) {
+    {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune[key] = c;
     }
+    st = run();
+    if (st == SALT_OK) cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && st == SALT_OK; ++r) st = run();
     if (st != SALT_OK) break;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = set_error(SALT_ERR_CUDA, "cudaEventSynchronize");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms / reps < best_t) {
+      best_t = ms / reps;
+      best = c;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -981,10 +1036,11 @@ salt_status salt_tune_save(const char* path) {
   FILE* f = fopen(path, "w");
   if (!f) return set_error(SALT_ERR_ARG, std::string("cannot write ") + path);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  fprintf(f, "# salt tuning table: family dtype log2n_bucket unroll vec_bytes block blocks_per_sm\n");
+  fprintf(f, "# salt tuning table: family dtype log2n_bucket unroll vec_bytes block blocks_per_sm stage_bytes\n");
   for (const auto& kv : g_tune)
-    fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-            kv.second.unroll, kv.second.vec_bytes, kv.second.block, kv.second.blocks_per_sm);
+    fprintf(f, "%d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+            kv.second.unroll, kv.second.vec_bytes, kv.second.block, kv.second.blocks_per_sm,
+            kv.second.stage_bytes);
   fclose(f);
   return SALT_OK;
 }
@@ -999,15 +1055,16 @@ salt_status salt_tune_load(const char* path) {
     if (line[0] == '#' || line[0] == '\n') continue;
     int fam, dt, b;
     salt_launch_cfg c;
-    if (sscanf(line, "%d %d %d %d %d %d %d", &fam, &dt, &b, &c.unroll, &c.vec_bytes, &c.block,
-               &c.blocks_per_sm) != 7) {
+    c.stage_bytes = 0;  // a line without the column: register-tiled loop
+    const int got = sscanf(line, "%d %d %d %d %d %d %d %d", &fam, &dt, &b, &c.unroll, &c.vec_bytes, &c.block,
+                           &c.blocks_per_sm, &c.stage_bytes);
+    if (got != 7 && got != 8) {
       fclose(f);
       return set_error(SALT_ERR_ARG, std::string("malformed tuning line: ") + line);
     }
-    salt_launch_cfg chk = c;
-    if (chk.blocks_per_sm == 0) chk.blocks_per_sm = 1;  // 0 = as many as fit
-    if (!cfg_valid(chk) || (dt != DT_F32 && dt != DT_F64) || b < 0 || b > 62 ||
-        !((fam >= 0 && fam < NUM_SHAPES) || (fam >= 100 && fam < 100 + NUM_SPECIAL) || fam == 200)) {
+    if (!cfg_valid(c) || (dt != DT_F32 && dt != DT_F64) || b < 0 || b > 62 ||
+        !((fam >= 0 && fam < NUM_SHAPES) || (fam >= 100 && fam < 100 + NUM_SPECIAL) || fam == 200) ||
+        (c.stage_bytes != 0 && fam >= NUM_SHAPES)) {
       fclose(f);
       return set_error(SALT_ERR_ARG, std::string("invalid tuning line: ") + line);
     }
@@ -1020,5 +1077,14 @@ salt_status salt_tune_load(const char* path) {
 }
 
 int64_t salt_launch_count(void) { return g_launches.load(); }
+
+salt_status salt_staged_timeouts(uint64_t* count) {
+  if (!count) return set_error(SALT_ERR_ARG, "count is NULL");
+  unsigned long long v = 0;
+  cudaError_t e = staged_timeouts(&v);
+  if (e != cudaSuccess) return cuda_error(e, "reading the staged-loop timeout counter");
+  *count = v;
+  return SALT_OK;
+}
 
 }  // extern "C"

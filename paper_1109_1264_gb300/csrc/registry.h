@@ -37,6 +37,8 @@ struct Registry {
   KernelEntry fill[2];
   KernelEntry strided[NUM_SHAPES][2];  // strided_kernel<P, T, kElemUnroll>
   KernelEntry nrm2_elem[2];            // nrm2_elem_kernel<T>
+  KernelEntry staged[NUM_SHAPES][2];   // staged_kernel<P, T>: params StagedParams<T>
+  size_t (*staged_smem[NUM_SHAPES])(int stage_bytes);  // its dynamic shared memory
 };
 
 Registry& registry();
@@ -48,8 +50,15 @@ void register_f64_vb16(Registry&);
 void register_f64_vb32(Registry&);
 void register_misc(Registry&);
 void register_elementwise(Registry&);
+void register_staged(Registry&);
+
+// Timed-out stage waits of staged kernels since the library was loaded
+// (synchronous read of a device counter).
+cudaError_t staged_timeouts(unsigned long long* out);
 
 inline int unroll_index(int u) { return u == 1 ? 0 : u == 2 ? 1 : u == 4 ? 2 : -1; }
 inline int vb_index(int vb) { return vb == 16 ? 0 : vb == 32 ? 1 : -1; }
+// Stage sizes of the staged schedule (bytes per loaded operand per stage).
+inline bool stage_bytes_valid(int sb) { return sb == 0 || sb == 4096 || sb == 8192 || sb == 16384; }
 
 }  // namespace salt

@@ -24,8 +24,8 @@ MAX_PROG, MAX_VECS, MAX_SCALS, MAX_STACK, MAX_REDS, MAX_DSCALS = 32, 8, 8, 8, 4,
 # Symbols that include/salt.h declares (checked by the test suite).
 EXPORTS = ["salt_version", "salt_status_str", "salt_last_error", "salt_check_program", "salt_eval",
            "salt_axpby", "salt_dot", "salt_nrm2", "salt_fill_uniform", "salt_release_workspaces",
-           "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_dot_noalloc",
-           "salt_eval_strided", "salt_eval_ex", "salt_explain", "salt_cg_diag", "salt_cg_diag_persistent"]
+           "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_staged_timeouts",
+           "salt_dot_noalloc", "salt_eval_strided", "salt_eval_ex", "salt_explain", "salt_cg_diag", "salt_cg_diag_persistent"]
 
 
 class Insn(ctypes.Structure):
@@ -34,7 +34,11 @@ class Insn(ctypes.Structure):
 
 class LaunchCfg(ctypes.Structure):
     _fields_ = [("unroll", ctypes.c_int32), ("vec_bytes", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("blocks_per_sm", ctypes.c_int32)]
+                ("blocks_per_sm", ctypes.c_int32), ("stage_bytes", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"unroll": self.unroll, "vec_bytes": self.vec_bytes, "block": self.block,
+                "blocks_per_sm": self.blocks_per_sm, "stage_bytes": self.stage_bytes}
 
 
 class SaltError(RuntimeError):
@@ -66,6 +70,7 @@ def _load() -> ctypes.CDLL:
         "salt_tune_get": (i32, [ip, i32, i32, i64, ctypes.POINTER(LaunchCfg)]),
         "salt_tune_clear": (i32, []),
         "salt_launch_count": (i64, []),
+        "salt_staged_timeouts": (i32, [ctypes.POINTER(u64)]),
         "salt_dot_noalloc": (i32, [i32, i64, vp, vp, vp, vp]),
         "salt_eval_strided": (i32, [ip, i32, i32, i64, ctypes.POINTER(vp), ctypes.POINTER(i64), i32, dp, i32, vp,
                                     vp]),
@@ -286,9 +291,10 @@ def salt_release_workspaces() -> None:
     _check(lib.salt_release_workspaces())
 
 
-def salt_tune_set(prog, dtype: int, n: int, unroll: int, vec_bytes: int, block: int, blocks_per_sm: int) -> None:
+def salt_tune_set(prog, dtype: int, n: int, unroll: int, vec_bytes: int, block: int, blocks_per_sm: int,
+                  stage_bytes: int = 0) -> None:
     arr, m = program(prog)
-    cfg = LaunchCfg(unroll, vec_bytes, block, blocks_per_sm)
+    cfg = LaunchCfg(unroll, vec_bytes, block, blocks_per_sm, stage_bytes)
     _check(lib.salt_tune_set(arr, m, dtype, int(n), ctypes.byref(cfg)))
 
 
@@ -296,8 +302,13 @@ def salt_tune_get(prog, dtype: int, n: int) -> dict:
     arr, m = program(prog)
     cfg = LaunchCfg()
     _check(lib.salt_tune_get(arr, m, dtype, int(n), ctypes.byref(cfg)))
-    return {"unroll": cfg.unroll, "vec_bytes": cfg.vec_bytes, "block": cfg.block,
-            "blocks_per_sm": cfg.blocks_per_sm}
+    return cfg.as_dict()
+
+
+def salt_staged_timeouts() -> int:
+    out = ctypes.c_uint64()
+    _check(lib.salt_staged_timeouts(ctypes.byref(out)))
+    return out.value
 
 
 def salt_tune_clear() -> None:
@@ -584,8 +595,7 @@ def salt_autotune(kernel: int, prog, vecs, scalars=(), red_out=None, reps: int =
     ms = ctypes.c_double()
     _check(lib.salt_autotune(kernel, arr, m, dt, int(n), ptrs, len(vecs), sc, len(scalars), _ptr(red_out),
                              int(reps), ctypes.byref(cfg), ctypes.byref(ms), _stream_ptr(stream)))
-    return ({"unroll": cfg.unroll, "vec_bytes": cfg.vec_bytes, "block": cfg.block,
-             "blocks_per_sm": cfg.blocks_per_sm}, ms.value)
+    return cfg.as_dict(), ms.value
 
 
 def salt_tune_save(path: str) -> None:

@@ -131,17 +131,39 @@ def test_tune_table(saltlib):
     assert default["block"] == 256
     saltlib.salt_tune_set(D, saltlib.F32, 1 << 20, 4, 32, 128, 8)
     assert saltlib.salt_tune_get(D, saltlib.F32, (1 << 21) - 1) == {"unroll": 4, "vec_bytes": 32, "block": 128,
-                                                                    "blocks_per_sm": 8}
+                                                                    "blocks_per_sm": 8, "stage_bytes": 0}
     assert saltlib.salt_tune_get(D, saltlib.F32, 1 << 21) == default  # other bucket
     assert saltlib.salt_tune_get(D, saltlib.F64, 1 << 20) == default  # other dtype
     saltlib.salt_tune_set(D, saltlib.F32, 1 << 22, 2, 32, 256, 0)  # 0: as many blocks as fit
     assert saltlib.salt_tune_get(D, saltlib.F32, 1 << 22)["blocks_per_sm"] == 0
     for bad in ((3, 16, 128, 4), (2, 8, 128, 4), (2, 16, 100, 4), (2, 16, 512, 4), (2, 16, 256, 9),
-                (2, 16, 256, -1)):
+                (2, 16, 256, -1), (1, 16, 128, 0, 2048), (1, 16, 128, 0, 6000), (1, 16, 128, 0, 32768),
+                (1, 16, 128, 0, -4096)):
         with pytest.raises(saltlib.SaltError):
             saltlib.salt_tune_set(D, saltlib.F32, 1 << 20, *bad)
     saltlib.salt_tune_clear()
     assert saltlib.salt_tune_get(D, saltlib.F32, 1 << 20) == default
+
+
+def test_tune_table_staged_loop(saltlib):
+    """The staged loop (stage_bytes 4096 / 8192 / 16384) is pinned like any
+    configuration, for compiled shapes only."""
+    s = saltlib
+    s.salt_tune_clear()
+    try:
+        for sb in (4096, 8192, 16384):
+            s.salt_tune_set(D, s.F64, 1 << 26, 1, 16, 128, 0, sb)
+            assert s.salt_tune_get(D, s.F64, 1 << 26) == {"unroll": 1, "vec_bytes": 16, "block": 128,
+                                                          "blocks_per_sm": 0, "stage_bytes": sb}
+        # a program that runs on the interpreter has no staged form
+        interp = [("VEC", 0), ("VEC", 1), ("MUL", 0), ("VEC", 2), ("MUL", 0), ("VEC", 0), ("ADD", 0),
+                  ("STORE", 3)]
+        with pytest.raises(s.SaltError) as ei:
+            s.salt_tune_set(interp, s.F32, 1 << 20, 1, 16, 128, 0, 4096)
+        assert ei.value.status == s.ERR_ARG
+        s.salt_tune_set(interp, s.F32, 1 << 20, 1, 16, 128, 0, 0)
+    finally:
+        s.salt_tune_clear()
 
 
 def test_tune_save_load_roundtrip(saltlib, tmp_path):
@@ -149,17 +171,30 @@ def test_tune_save_load_roundtrip(saltlib, tmp_path):
     s.salt_tune_clear()
     s.salt_tune_set(D, s.F64, 1 << 24, 4, 32, 128, 2)
     s.salt_tune_set(CG, s.F32, 1000, 1, 16, 64, 8)
+    s.salt_tune_set(D, s.F32, 1 << 26, 1, 16, 256, 0, 16384)
     path = str(tmp_path / "tune.txt")
     s.salt_tune_save(path)
     s.salt_tune_clear()
     assert s.salt_tune_get(D, s.F64, 1 << 24)["block"] == 256
     s.salt_tune_load(path)
-    assert s.salt_tune_get(D, s.F64, 1 << 24) == {"unroll": 4, "vec_bytes": 32, "block": 128, "blocks_per_sm": 2}
-    assert s.salt_tune_get(CG, s.F32, 1000) == {"unroll": 1, "vec_bytes": 16, "block": 64, "blocks_per_sm": 8}
-    bad = tmp_path / "bad.txt"
-    bad.write_text("0 0 20 3 16 128 2\n")
-    with pytest.raises(s.SaltError):
-        s.salt_tune_load(str(bad))
+    assert s.salt_tune_get(D, s.F64, 1 << 24) == {"unroll": 4, "vec_bytes": 32, "block": 128, "blocks_per_sm": 2,
+                                                  "stage_bytes": 0}
+    assert s.salt_tune_get(CG, s.F32, 1000) == {"unroll": 1, "vec_bytes": 16, "block": 64, "blocks_per_sm": 8,
+                                                "stage_bytes": 0}
+    assert s.salt_tune_get(D, s.F32, 1 << 26)["stage_bytes"] == 16384
+    # a table written without the stage_bytes column still loads (register-tiled loop)
+    s.salt_tune_clear()
+    old = tmp_path / "old.txt"
+    old.write_text("# family dtype bucket unroll vec_bytes block blocks_per_sm\n0 1 24 4 32 128 2\n")
+    s.salt_tune_load(str(old))
+    assert s.salt_tune_get(D, s.F64, 1 << 24) == {"unroll": 4, "vec_bytes": 32, "block": 128, "blocks_per_sm": 2,
+                                                  "stage_bytes": 0}
+    for text in ("0 0 20 3 16 128 2\n", "0 0 20 1 16 128 0 1000\n", "200 0 20 1 16 128 0 4096\n",
+                 "101 1 20 1 16 128 0 8192\n"):
+        bad = tmp_path / "bad.txt"
+        bad.write_text(text)
+        with pytest.raises(s.SaltError):
+            s.salt_tune_load(str(bad))
     with pytest.raises(s.SaltError):
         s.salt_tune_load(str(tmp_path / "missing.txt"))
     s.salt_tune_clear()

@@ -29,10 +29,14 @@ def gather_inputs(key, idx, dt):
     return (2.0 * ((h >> np.uint64(40)).astype(np.float64) * 2.0 ** -24) - 1.0).astype(np.float32)
 
 
+@pytest.mark.parametrize("sched", ["tuned", "staged"])
 @pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
-def test_elementwise_full_size_sampled(saltlib, cuda_dev, dt):
+def test_elementwise_full_size_sampled(saltlib, cuda_dev, dt, sched):
+    """sched "tuned": the configuration the autotuner picks; "staged": the
+    staged loop pinned (16 KiB stages for e, 8 KiB for axpby)."""
     s = saltlib
     tdt = torch.float32 if dt == np.float32 else torch.float64
+    code = s.F32 if dt == np.float32 else s.F64
     keys = [101, 102, 103, 104, 105]
     a, b, c, d, y = (torch.empty(N, dtype=tdt, device=cuda_dev) for _ in range(5))
     out = torch.empty(N, dtype=tdt, device=cuda_dev)
@@ -40,10 +44,14 @@ def test_elementwise_full_size_sampled(saltlib, cuda_dev, dt):
         s.salt_fill_uniform(t, key=k)
     s.salt_tune_clear()
     try:
-        s.salt_autotune(s.KERNEL_PROGRAM, P.PROG_E, [a, b, c, d, out], [ALPHA, BETA], reps=1)
-        s.salt_autotune(s.KERNEL_PROGRAM, P.PROG_AXPBY, [a, y], [ALPHA, BETA], reps=1)
-        # the autotuner ran axpby in place: start y afresh
-        s.salt_fill_uniform(y, key=keys[4])
+        if sched == "tuned":
+            s.salt_autotune(s.KERNEL_PROGRAM, P.PROG_E, [a, b, c, d, out], [ALPHA, BETA], reps=1)
+            s.salt_autotune(s.KERNEL_PROGRAM, P.PROG_AXPBY, [a, y], [ALPHA, BETA], reps=1)
+            # the autotuner ran axpby in place: start y afresh
+            s.salt_fill_uniform(y, key=keys[4])
+        else:
+            s.salt_tune_set(P.PROG_E, code, N, 1, 16, 256, 0, 16384)
+            s.salt_tune_set(P.PROG_AXPBY, code, N, 1, 16, 128, 0, 8192)
         s.salt_eval(P.PROG_E, [a, b, c, d, out], [ALPHA, BETA])
         s.salt_axpby(ALPHA, a, BETA, y)
         torch.cuda.synchronize()
@@ -65,15 +73,18 @@ def test_elementwise_full_size_sampled(saltlib, cuda_dev, dt):
     assert np.array_equal(got_y.view(iu), want_y[1].view(iu))
 
 
+@pytest.mark.parametrize("sched", ["tuned", "staged"])
 @pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
-def test_reductions_full_size_closed_form(saltlib, cuda_dev, dt):
+def test_reductions_full_size_closed_form(saltlib, cuda_dev, dt, sched):
     """x_i = (i mod 1024) - 512, y_i = ((7 i) mod 512) - 256, n = 2^28: every
     product and partial sum is an integer below 2^53, so the compensated FP32
     and the FP64 paths must return the exact integer, and the norm the
-    correctly rounded square root of the exact sum of squares."""
+    correctly rounded square root of the exact sum of squares.  sched
+    "staged": the dot products on the staged loop (4 KiB stages)."""
     s = saltlib
     n = 1 << 28
     tdt = torch.float32 if dt == np.float32 else torch.float64
+    code = s.F32 if dt == np.float32 else s.F64
     i = torch.arange(n, device=cuda_dev, dtype=torch.int64)
     x = ((i % 1024) - 512).to(tdt)
     yv = (((7 * i) % 512) - 256).to(tdt)
@@ -81,7 +92,10 @@ def test_reductions_full_size_closed_form(saltlib, cuda_dev, dt):
     outv = torch.zeros(3, dtype=torch.float64, device=cuda_dev)
     s.salt_tune_clear()
     try:
-        s.salt_autotune(s.KERNEL_PROGRAM, P.PROG_DOT, [x, yv], red_out=outv[0:1], reps=1)
+        if sched == "tuned":
+            s.salt_autotune(s.KERNEL_PROGRAM, P.PROG_DOT, [x, yv], red_out=outv[0:1], reps=1)
+        else:
+            s.salt_tune_set(P.PROG_DOT, code, n, 1, 16, 128, 0, 4096)
         s.salt_autotune(s.KERNEL_NRM2, None, [x], red_out=outv[1:2], reps=1)
         s.salt_dot(x, yv, outv[0:1])
         s.salt_nrm2(x, outv[1:2])
