@@ -63,6 +63,8 @@ KERNEL_SOURCES = {
               "inst_f64_vb16.cu", "inst_f64_vb32.cu"],
     "e_f64_staged": ["prog.cuh", "common.cuh", "fused.cuh", "staged.cuh", "shapes.h", "registry.h",
                      "inst_staged.cu"],
+    "dot_f64_staged": ["prog.cuh", "common.cuh", "fused.cuh", "staged.cuh", "shapes.h", "registry.h",
+                       "inst_staged.cu"],
 }
 
 
@@ -146,12 +148,13 @@ class Workload:
         """Autotunes the launch shape of each op of the step (setup, untimed)."""
         from paper_1109_1264_gb300.programs import PROG_AXPBY, PROG_DOT, PROG_E
         got = {}
+        r = 4  # timed calls per candidate: the schedules differ by a few percent at this size
         got["e"], _ = salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_E, [self.a, self.b, self.c, self.d, self.out],
-                                         [ALPHA, BETA], reps=2)
-        got["axpby"], _ = salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_AXPBY, [self.a, self.y], [ALPHA, BETA], reps=2)
+                                         [ALPHA, BETA], reps=r)
+        got["axpby"], _ = salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_AXPBY, [self.a, self.y], [ALPHA, BETA], reps=r)
         got["dot"], _ = salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_DOT, [self.a, self.b], red_out=self.red[0:1],
-                                           reps=2)
-        got["nrm2"], _ = salt.salt_autotune(salt.KERNEL_NRM2, None, [self.c], red_out=self.red[1:2], reps=2)
+                                           reps=r)
+        got["nrm2"], _ = salt.salt_autotune(salt.KERNEL_NRM2, None, [self.c], red_out=self.red[1:2], reps=r)
         return got
 
     def ops(self, salt):
@@ -294,6 +297,11 @@ def main():
                     help="profiling runs: load a saved launch table instead of autotuning")
     ap.add_argument("--only-cg", action="store_true", help="run only the CG leg (profiling runs)")
     ap.add_argument("--only-served", action="store_true", help="run only the served leg (profiling runs)")
+    ap.add_argument("--schedules", action="store_true",
+                    help="register-tiled versus staged loop for the compiled shapes (n = 2^24, 2^28); one JSON line")
+    ap.add_argument("--fixed-cfg", action="append", default=None,
+                    help="profiling runs: skip the autotuner and pin OP[_f32|_f64]=U,VB,BLOCK,BLOCKS_PER_SM[,STAGE_BYTES]"
+                         " for OP in e, axpby, dot (repeatable)")
     ap.add_argument("--fixed-e-cfg", default=None,
                     help="profiling runs: skip the autotuner and launch e with U,VB,BLOCK,BLOCKS_PER_SM[,STAGE_BYTES]")
     ap.add_argument("--cg-log2", type=int, default=28)
@@ -321,6 +329,11 @@ def main():
             print(json.dumps(sweep_measure(torch, salt)), flush=True)
         return
 
+    if args.schedules:
+        if rank == 0:
+            print(json.dumps(schedules_measure(torch, salt)), flush=True)
+        return
+
     if args.only_served:
         if rank == 0:
             print(json.dumps({"served": served_measure(salt)}), flush=True)
@@ -341,15 +354,23 @@ def main():
 
     n = 1 << args.log2n
     loads = {dt: Workload(torch, salt, dt, n, seed=rank) for dt in DTYPES}
-    if args.fixed_e_cfg:
-        from paper_1109_1264_gb300.programs import PROG_E
-        vals = [int(v) for v in args.fixed_e_cfg.split(",")]
-        u, vb, blk, bps = vals[:4]
-        sb = vals[4] if len(vals) > 4 else 0
-        for code in (salt.F32, salt.F64):
-            salt.salt_tune_set(PROG_E, code, n, u, vb, blk, bps, sb)
-        tuned = {"e": {"unroll": u, "vec_bytes": vb, "block": blk, "blocks_per_sm": bps, "stage_bytes": sb},
-                 "others": "defaults"}
+    fixed = list(args.fixed_cfg or []) + ([f"e={args.fixed_e_cfg}"] if args.fixed_e_cfg else [])
+    if fixed:
+        from paper_1109_1264_gb300.programs import PROG_AXPBY, PROG_DOT, PROG_E
+        progs = {"e": PROG_E, "axpby": PROG_AXPBY, "dot": PROG_DOT}
+        tuned = {"others": "defaults"}
+        for spec in fixed:
+            key, _, cfg = spec.partition("=")
+            op, _, dtn = key.partition("_")
+            vals = [int(v) for v in cfg.split(",")]
+            if op not in progs or dtn not in ("", "f32", "f64") or len(vals) not in (4, 5):
+                raise SystemExit(f"--fixed-cfg: cannot parse {spec!r}")
+            u, vb, blk, bps = vals[:4]
+            sb = vals[4] if len(vals) > 4 else 0
+            codes = {"f32": [salt.F32], "f64": [salt.F64], "": [salt.F32, salt.F64]}[dtn]
+            for code in codes:
+                salt.salt_tune_set(progs[op], code, n, u, vb, blk, bps, sb)
+            tuned[key] = {"unroll": u, "vec_bytes": vb, "block": blk, "blocks_per_sm": bps, "stage_bytes": sb}
     elif args.tune_load:
         salt.salt_tune_load(args.tune_load)
         tuned = {"loaded": os.path.basename(args.tune_load)}
@@ -625,6 +646,80 @@ def sweep_measure(torch, salt, reps: int = 21, max_log2: int = 28) -> dict:
         del xb, yb
     return {"sweep": out, "note": "GB/s of algorithmic bytes; launch shapes autotuned per size bucket from 2^24 "
                                   "on; L2 flushed before each timed call; median of %d" % reps}
+
+
+def schedules_measure(torch, salt, log2ns=(24, 28), reps: int = 15) -> dict:
+    """Register-tiled loop versus staged loop (operand tiles copied into shared
+    memory by bulk asynchronous copies) for the compiled shapes, through the
+    library's own calls: each configuration pinned with salt_tune_set, timed
+    as the median of `reps` calls (L2 flushed by a 256 MiB read before each),
+    the best of each schedule reported with its configuration."""
+    import numpy as np
+
+    from paper_1109_1264_gb300.programs import PROG_AXPBY, PROG_CG, PROG_D, PROG_DOT, PROG_E, PROG_SUMSQ
+    axpy = [("SCAL", 0), ("VEC", 0), ("SMUL", 0), ("VEC", 1), ("ADD", 0), ("STORE", 1)]
+    scal = [("SCAL", 0), ("VEC", 0), ("SMUL", 0), ("STORE", 0)]
+    copy = [("VEC", 0), ("STORE", 1)]
+    cgxr = [("VEC", 0), ("SCAL", 0), ("VEC", 1), ("SMUL", 0), ("ADD", 0), ("STORE", 0), ("VEC", 2), ("SCAL", 0),
+            ("VEC", 3), ("SMUL", 0), ("SUB", 0), ("STORE", 2), ("VEC", 2), ("SUMSQ", 0)]
+    # name: (program, operands, scalars (bounded under repetition), bytes per element / element size)
+    shapes = {"e": (PROG_E, 5, [1.5, -0.25], 5), "axpby": (PROG_AXPBY, 2, [1.5, -0.25], 3),
+              "axpy": (axpy, 2, [1e-3], 3), "d": (PROG_D, 4, [], 4), "scal": (scal, 1, [0.999], 2),
+              "copy": (copy, 2, [], 2), "dot": (PROG_DOT, 2, [], 2), "sumsq": (PROG_SUMSQ, 1, [], 1),
+              "cg": (PROG_CG, 3, [1e-3, 0.5], 5), "cgxr": (cgxr, 4, [1e-3], 6)}
+    register = [(1, 32, 256, 0, 0), (2, 32, 256, 0, 0), (2, 32, 128, 0, 0), (4, 32, 128, 0, 0),
+                (4, 16, 256, 0, 0), (2, 32, 256, 4, 0)]
+    staged = [(1, 16, 128, 0, 4096), (1, 16, 128, 0, 8192), (1, 16, 128, 0, 16384), (1, 16, 256, 0, 8192),
+              (1, 16, 256, 0, 16384)]
+    flush = torch.zeros(64 << 20, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    red = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.sum()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    out = {}
+    for lg in log2ns:
+        n = 1 << lg
+        rows = {}
+        for dt, tdt, es, code in (("f32", torch.float32, 4, salt.F32), ("f64", torch.float64, 8, salt.F64)):
+            bufs = [torch.empty(n, dtype=tdt, device="cuda") for _ in range(5)]
+            for k, t in enumerate(bufs):
+                salt.salt_fill_uniform(t, 40 + k)
+            for name, (prog, nv, sc, bpe) in shapes.items():
+                vecs = bufs[:nv]
+                nred = sum(1 for o, _ in prog if o in ("DOT", "SUMSQ"))
+                best = {}
+                for kind, cands in (("register", register), ("staged", staged)):
+                    top = None
+                    for cfg in cands:
+                        salt.salt_tune_set(prog, code, n, *cfg)
+                        ms = timed(lambda: salt.salt_eval(prog, vecs, sc, red_out=red if nred else None))
+                        gbs = bpe * es * n / (ms * 1e-3) / 1e9
+                        if top is None or gbs > top["gbs"]:
+                            top = {"gbs": round(gbs, 1), "ms": round(ms, 4),
+                                   "cfg": dict(zip(("unroll", "vec_bytes", "block", "blocks_per_sm",
+                                                    "stage_bytes"), cfg))}
+                    best[kind] = top
+                best["staged_over_register"] = round(best["staged"]["gbs"] / best["register"]["gbs"], 3)
+                rows[f"{name}_{dt}"] = best
+            salt.salt_tune_clear()
+            del bufs
+        out[f"2^{lg}"] = rows
+    return {"schedules": out, "note": "GB/s of algorithmic bytes, best configuration of each schedule, "
+                                      "L2 flushed before each timed call, median of %d" % reps}
 
 
 def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> dict:
