@@ -56,7 +56,7 @@ struct salt_batch {
   int64_t tiles_capacity = 0;
   BatchHeader* d_hdr = nullptr;
   BatchItem* d_items = nullptr;
-  unsigned* d_counters = nullptr;  // [0] tile counter, [1..capacity] tickets
+  unsigned* d_counters = nullptr;  // [0] tile counter, [1] finished blocks, [2..capacity+1] tickets
   double* d_partials = nullptr;
   int64_t total_tiles = 0;
   bool dirty = true;
@@ -146,7 +146,7 @@ salt_status rebuild(salt_batch* b, cudaStream_t s) {
     b->dmem = nullptr;
     const int64_t tiles_cap = std::max<int64_t>(tile, 1024);
     const size_t items_bytes = ((sizeof(BatchItem) * (size_t)b->capacity + 255) / 256) * 256;
-    const size_t counters_bytes = ((sizeof(unsigned) * (size_t)(b->capacity + 1) + 255) / 256) * 256;
+    const size_t counters_bytes = ((sizeof(unsigned) * (size_t)(b->capacity + 2) + 255) / 256) * 256;
     const size_t partial_bytes = sizeof(double) * kBatchPartials * (size_t)tiles_cap;
     const size_t total = kHeaderBytes + items_bytes + counters_bytes + partial_bytes;
     e = cudaMalloc(&b->dmem, total);
@@ -205,7 +205,7 @@ salt_status build_graph(salt_batch* b, double* red_out) {
   mp.dst = b->d_counters;
   mp.value = 0;
   mp.elementSize = sizeof(unsigned);
-  mp.width = (size_t)b->items.size() + 1;
+  mp.width = (size_t)b->items.size() + 2;
   mp.height = 1;
   mp.pitch = 0;
   cudaGraphNode_t mnode = nullptr, knode = nullptr;
@@ -214,7 +214,7 @@ salt_status build_graph(salt_batch* b, double* red_out) {
     cudaGraphDestroy(g);
     return cuda_fail(e, "cudaGraphAddMemsetNode");
   }
-  BatchParams p{b->d_hdr, b->d_items, b->d_counters, b->d_counters + 1, b->d_partials, red_out};
+  BatchParams p{b->d_hdr, b->d_items, b->d_counters, b->d_counters + 1, b->d_counters + 2, b->d_partials, red_out};
   void* args[] = {&p};
   cudaKernelNodeParams kp{};
   kp.func = (void*)k;

@@ -50,9 +50,10 @@ struct BatchParams {
   const BatchHeader* hdr;
   const BatchItem* items;
   unsigned* counter;  // global tile counter; zero at launch
+  unsigned* exits;    // blocks that have finished; zero at launch
   unsigned* tickets;  // per-item tile tickets; zero at launch
   double* partials;   // kBatchPartials per global tile
-  double* red_out;
+  double* red_out;    // device or mapped pinned host memory
 };
 
 // One block evaluates program P on elements [lo, hi) of an item: whole
@@ -330,6 +331,17 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchParams p) {
     __syncthreads();  // every thread has read s_tile / s_item / s_last of this tile
     if (threadIdx.x == 0) s_tile = (int64_t)next;
     __syncthreads();
+  }
+  // Every counter is zero again when the launch ends, so the next launch
+  // needs no reset: the tickets are cleared by each item's last tile, and
+  // the last block to finish (its tile fetches are all done) clears the tile
+  // counter and this count.
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(p.exits, 1u) == gridDim.x - 1u) {
+      atomicExch(p.counter, 0u);
+      atomicExch(p.exits, 0u);
+    }
   }
 }
 

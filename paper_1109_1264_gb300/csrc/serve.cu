@@ -125,21 +125,23 @@ struct Slot {
   // the per-table tile counters, the partials and the results
   unsigned* d_counters[2] = {nullptr, nullptr};
   double* d_partials = nullptr;
-  double* d_red = nullptr;
   // host staging (pinned): the packed tables, then red
   size_t table_bytes = 0;
   std::vector<BatchItem> compute_items;  // built aside, copied after the fill items
-  double* h_red = nullptr;
+  double* h_red = nullptr;      // pinned and mapped: the kernel writes the results here
+  double* h_red_dev = nullptr;  // its device address
   std::vector<Request*> reqs;
   bool busy = false;
-  // The step as one CUDA graph: table upload -> counter reset -> [fill
-  // launch ->] compute launch -> result read-back, instantiated once with
-  // and once without the fill launch; each step updates the sizes and
-  // launch parameters of one of them and replays it.
+  // The step as one CUDA graph: table upload -> [fill launch ->] compute
+  // launch, instantiated once with and once without the fill launch; each
+  // step updates the upload size and launch parameters of one of them and
+  // replays it.  No reset or read-back nodes: the batch kernel leaves its
+  // counters at zero, and writes the results straight into mapped pinned
+  // host memory.
   struct StepGraph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t n_up = nullptr, n_reset = nullptr, n_fill = nullptr, n_comp = nullptr, n_down = nullptr;
+    cudaGraphNode_t n_up = nullptr, n_fill = nullptr, n_comp = nullptr;
   } g[2];  // [0] without, [1] with the fill launch
 };
 
@@ -186,21 +188,19 @@ struct salt_server {
 
 namespace {
 
-size_t slot_device_bytes(const salt_server* s, size_t* off_items, size_t* off_counters, size_t* off_partials,
-                         size_t* off_red) {
+size_t slot_device_bytes(const salt_server* s, size_t* off_items, size_t* off_counters, size_t* off_partials) {
   const size_t hdr = 256;
   const size_t items = round_up(sizeof(BatchItem) * (size_t)s->items_cap);
-  const size_t counters = round_up(sizeof(unsigned) * (size_t)(s->items_cap + 1));
+  // tile counter, finished blocks, per-item tickets
+  const size_t counters = round_up(sizeof(unsigned) * (size_t)(s->items_cap + 2));
   const size_t partials = round_up(sizeof(double) * kBatchPartials * (size_t)s->tiles_cap);
-  const size_t red = round_up(sizeof(double) * kBatchPartials * (size_t)s->cfg.max_batch);
-  // [hdr0 items0 hdr1 items1 | counters0 counters1 | partials | red]
+  // [hdr0 items0 hdr1 items1 | counters0 counters1 | partials]
   off_items[0] = hdr;
   off_items[1] = hdr + items + hdr;
   off_counters[0] = 2 * (hdr + items);
   off_counters[1] = off_counters[0] + counters;
   *off_partials = off_counters[1] + counters;
-  *off_red = *off_partials + partials;
-  return *off_red + red;
+  return *off_partials + partials;
 }
 
 // Called with the request's shape/dtype set: lay out its operands in the arena.
@@ -233,22 +233,13 @@ int64_t tiles_of(const salt_server* s, int dtype, int64_t n) {
 
 // Builds a step graph with placeholder sizes and launch shapes (every step
 // sets its own before replaying it).
-cudaError_t build_step_graph(salt_server* s, Slot& slot, size_t counter_bytes, bool with_fill,
-                             Slot::StepGraph* sg) {
+cudaError_t build_step_graph(salt_server* s, Slot& slot, bool with_fill, Slot::StepGraph* sg) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return e;
   e = cudaGraphAddMemcpyNode1D(&sg->n_up, g, nullptr, 0, slot.d_mem, slot.h_mem, 512, cudaMemcpyHostToDevice);
-  cudaMemsetParams mp{};
-  mp.dst = slot.d_counters[0];
-  mp.value = 0;
-  mp.elementSize = sizeof(unsigned);
-  mp.width = counter_bytes / sizeof(unsigned);
-  mp.height = 1;
-  mp.pitch = 0;
-  if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&sg->n_reset, g, &sg->n_up, 1, &mp);
   BatchParams prm{(BatchHeader*)slot.d_mem, (BatchItem*)(slot.d_mem + 512), slot.d_counters[0],
-                  slot.d_counters[0] + 1, slot.d_partials, slot.d_red};
+                  slot.d_counters[0] + 1, slot.d_counters[0] + 2, slot.d_partials, slot.h_red_dev};
   void* args[] = {&prm};
   cudaKernelNodeParams kp{};
   kp.func = (void*)kernel_for(s->cfg.unroll);
@@ -257,15 +248,12 @@ cudaError_t build_step_graph(salt_server* s, Slot& slot, size_t counter_bytes, b
   kp.sharedMemBytes = 0;
   kp.kernelParams = args;
   kp.extra = nullptr;
-  cudaGraphNode_t before = sg->n_reset;
+  cudaGraphNode_t before = sg->n_up;
   if (e == cudaSuccess && with_fill) {
     e = cudaGraphAddKernelNode(&sg->n_fill, g, &before, 1, &kp);
     before = sg->n_fill;
   }
   if (e == cudaSuccess) e = cudaGraphAddKernelNode(&sg->n_comp, g, &before, 1, &kp);
-  if (e == cudaSuccess)
-    e = cudaGraphAddMemcpyNode1D(&sg->n_down, g, &sg->n_comp, 1, slot.h_red, slot.d_red, sizeof(double),
-                                 cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaGraphInstantiate(&sg->exec, g, 0);
   if (e != cudaSuccess) {
     cudaGraphDestroy(g);
@@ -278,8 +266,8 @@ cudaError_t build_step_graph(salt_server* s, Slot& slot, size_t counter_bytes, b
 // Builds and launches one step on `slot` from the front of `pending`
 // (scheduler thread, lock not held while launching).
 salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch) {
-  size_t off_items[2], off_counters[2], off_partials, off_red;
-  slot_device_bytes(s, off_items, off_counters, &off_partials, &off_red);
+  size_t off_items[2], off_counters[2], off_partials;
+  slot_device_bytes(s, off_items, off_counters, &off_partials);
   // Host tables in the pinned staging area, packed so that one copy of
   // only the bytes in use moves them: [hdr0 | hdr1 | fill items | compute
   // items].  Compute items are built aside, then placed after the fills.
@@ -334,8 +322,8 @@ salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch
   BatchParams prm[2];
   cudaKernelNodeParams kp[2];
   for (int t = 0; t < 2; ++t) {
-    prm[t] = BatchParams{d_hdr[t], d_items[t], slot.d_counters[t], slot.d_counters[t] + 1, slot.d_partials,
-                         slot.d_red};
+    prm[t] = BatchParams{d_hdr[t], d_items[t], slot.d_counters[t], slot.d_counters[t] + 1,
+                         slot.d_counters[t] + 2, slot.d_partials, slot.h_red_dev};
     kp[t] = cudaKernelNodeParams{};
     kp[t].func = (void*)k;
     kp[t].gridDim = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(s->grid, tiles[t])));
@@ -352,9 +340,6 @@ salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch
                                                      cudaMemcpyHostToDevice);
   if (e == cudaSuccess && nitems[0] > 0) e = cudaGraphExecKernelNodeSetParams(sg.exec, sg.n_fill, &kp[0]);
   if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(sg.exec, sg.n_comp, &kp[1]);
-  if (e == cudaSuccess)
-    e = cudaGraphExecMemcpyNodeSetParams1D(sg.exec, sg.n_down, slot.h_red, slot.d_red,
-                                           sizeof(double) * (size_t)std::max(nred, 1), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaGraphLaunch(sg.exec, slot.stream);
   if (e == cudaSuccess) {
     if (nitems[0] > 0) count_launch();
@@ -640,8 +625,8 @@ salt_status salt_serve_start(salt_server** out, const salt_serve_config* cfg) {
   }
   s->arena.init((size_t)cfg->budget_bytes);
   s->slots.resize((size_t)cfg->streams);
-  size_t off_items[2], off_counters[2], off_partials, off_red;
-  const size_t dbytes = slot_device_bytes(s, off_items, off_counters, &off_partials, &off_red);
+  size_t off_items[2], off_counters[2], off_partials;
+  const size_t dbytes = slot_device_bytes(s, off_items, off_counters, &off_partials);
   for (Slot& slot : s->slots) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming);
@@ -649,14 +634,15 @@ salt_status salt_serve_start(salt_server** out, const salt_serve_config* cfg) {
     slot.table_bytes = off_counters[0];
     if (e == cudaSuccess) e = cudaHostAlloc(&slot.h_mem, slot.table_bytes, cudaHostAllocDefault);
     if (e == cudaSuccess)
-      e = cudaHostAlloc(&slot.h_red, sizeof(double) * kBatchPartials * cfg->max_batch, cudaHostAllocDefault);
+      e = cudaHostAlloc(&slot.h_red, sizeof(double) * kBatchPartials * cfg->max_batch, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&slot.h_red_dev, slot.h_red, 0);
     if (e != cudaSuccess) break;
     slot.compute_items.resize((size_t)s->cfg.max_batch);
     for (int t = 0; t < 2; ++t) slot.d_counters[t] = (unsigned*)(slot.d_mem + off_counters[t]);
     slot.d_partials = (double*)(slot.d_mem + off_partials);
-    slot.d_red = (double*)(slot.d_mem + off_red);
-    for (int f = 0; f < 2 && e == cudaSuccess; ++f)
-      e = build_step_graph(s, slot, off_partials - off_counters[0], f == 1, &slot.g[f]);
+    // the counters start at zero; every launch leaves them at zero
+    e = cudaMemset(slot.d_mem + off_counters[0], 0, off_partials - off_counters[0]);
+    for (int f = 0; f < 2 && e == cudaSuccess; ++f) e = build_step_graph(s, slot, f == 1, &slot.g[f]);
   }
   if (e != cudaSuccess) {
     for (Slot& slot : s->slots) {

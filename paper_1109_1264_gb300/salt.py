@@ -99,45 +99,97 @@ def _check(status: int) -> None:
 # ------------------------------------------------------------ marshalling --
 
 _PROGRAM_CACHE: dict = {}
+_PROGRAM_BY_ID: dict = {}  # id(list) -> (the list, a shallow copy, marshalled form)
 
 
 def program(prog) -> tuple[ctypes.Array, int]:
     """[(name, arg), ...] or [(opcode, arg), ...] -> (salt_insn array, length).
     The library only reads the array, so the marshalled form of a program is
-    kept and reused (repeated calls skip the per-instruction conversion)."""
+    kept and reused (repeated calls skip the per-instruction conversion).  A
+    list of tuples passed again is recognised by identity plus an equality
+    check against the copy taken when it was first marshalled, so an edited
+    list is marshalled afresh."""
+    ent = _PROGRAM_BY_ID.get(id(prog))
+    if ent is not None and ent[0] is prog and ent[1] == prog:
+        return ent[2]
     try:
         key = tuple((op, int(arg)) for op, arg in prog)
         hit = _PROGRAM_CACHE.get(key)
     except TypeError:  # unhashable operands: marshal afresh
         key, hit = None, None
-    if hit is not None:
-        return hit
-    arr = (Insn * max(len(prog), 1))()
-    for i, (op, arg) in enumerate(prog):
-        arr[i].op = OPS[op] if isinstance(op, str) else int(op)
-        arr[i].arg = int(arg)
-    if key is not None and len(_PROGRAM_CACHE) < 4096:
-        _PROGRAM_CACHE[key] = (arr, len(prog))
-    return arr, len(prog)
+    if hit is None:
+        arr = (Insn * max(len(prog), 1))()
+        for i, (op, arg) in enumerate(prog):
+            arr[i].op = OPS[op] if isinstance(op, str) else int(op)
+            arr[i].arg = int(arg)
+        hit = (arr, len(prog))
+        if key is not None and len(_PROGRAM_CACHE) < 4096:
+            _PROGRAM_CACHE[key] = hit
+    if type(prog) is list and len(_PROGRAM_BY_ID) < 1024 and all(type(x) is tuple for x in prog):
+        _PROGRAM_BY_ID[id(prog)] = (prog, list(prog), hit)  # holds the list: its id stays unique
+    return hit
+
+
+_DT_CODES: dict = {}
 
 
 def _dtype_code(t) -> int:
-    import torch
-    if t.dtype == torch.float32:
-        return F32
-    if t.dtype == torch.float64:
-        return F64
-    raise SaltError(ERR_DTYPE, "SALT_ERR_DTYPE", f"unsupported dtype {t.dtype}")
+    if not _DT_CODES:
+        import torch
+        _DT_CODES.update({torch.float32: F32, torch.float64: F64})
+    code = _DT_CODES.get(t.dtype)
+    if code is None:
+        raise SaltError(ERR_DTYPE, "SALT_ERR_DTYPE", f"unsupported dtype {t.dtype}")
+    return code
+
+
+_RAW_STREAM = None
 
 
 def _stream_ptr(stream=None) -> int:
-    import torch
-    s = stream if stream is not None else torch.cuda.current_stream()
-    return int(s.cuda_stream)
+    """The raw handle of ``stream``, else of torch's current stream on the
+    current device."""
+    global _RAW_STREAM
+    if stream is not None:
+        return int(stream.cuda_stream)
+    if _RAW_STREAM is None:
+        import torch
+        c = torch._C
+        if hasattr(c, "_cuda_getCurrentRawStream") and hasattr(c, "_cuda_getDevice"):
+            _RAW_STREAM = lambda: c._cuda_getCurrentRawStream(c._cuda_getDevice())
+        else:
+            _RAW_STREAM = lambda: int(torch.cuda.current_stream().cuda_stream)
+    return _RAW_STREAM()
 
 
 def _ptr(t) -> int | None:
-    return None if t is None else int(t.data_ptr())
+    return None if t is None else t.data_ptr()
+
+
+def _operands(vecs, same_length: bool = True):
+    """(dtype code, common length, pointers, all contiguous) of the operand
+    tensors (None entries: unused slots), in one pass.  same_length=False
+    (the caller states n) skips the equal-length check and returns the first
+    operand's length."""
+    code = n = None
+    contiguous = True
+    ptrs = []
+    for v in vecs:
+        if v is None:
+            ptrs.append(None)
+            continue
+        c = _dtype_code(v)
+        m = v.numel()
+        if code is None:
+            code, n = c, m
+        elif c != code:
+            raise SaltError(ERR_DTYPE, "SALT_ERR_DTYPE", "operands of one call must share a dtype")
+        elif m != n and same_length:
+            raise SaltError(ERR_ARG, "SALT_ERR_ARG", "operands of one call must have the same length")
+        if contiguous and not v.is_contiguous():
+            contiguous = False
+        ptrs.append(v.data_ptr())
+    return (F32 if code is None else code), (0 if n is None else n), ptrs, contiguous
 
 
 def _common_dtype(tensors) -> int:
@@ -222,13 +274,15 @@ def salt_eval(prog, vecs, scalars=(), red_out=None, n: int | None = None, stream
     are passed to salt_eval_strided.  ``dscalars`` (device scalars for DSCAL
     nodes: float64 CUDA tensor views, e.g. ``red[0:1]``) route the call to
     salt_eval_ex."""
-    dt = _common_dtype(vecs)
+    dt, nn, plist, contiguous = _operands(vecs, same_length=n is None)
     if n is None:
-        n = _n_of(vecs)
+        n = nn
     arr, m = program(prog)
-    ptrs = (ctypes.c_void_p * max(len(vecs), 1))(*[_ptr(v) for v in vecs])
-    sc = (ctypes.c_double * max(len(scalars), 1))(*[float(s) for s in scalars])
-    contiguous = all(v is None or v.is_contiguous() for v in vecs)
+    ptrs = (ctypes.c_void_p * max(len(vecs), 1))(*plist)
+    try:
+        sc = (ctypes.c_double * max(len(scalars), 1))(*scalars)
+    except TypeError:  # e.g. numpy float32 scalars
+        sc = (ctypes.c_double * max(len(scalars), 1))(*[float(x) for x in scalars])
     st = None
     if not contiguous:
         strides = []
@@ -252,24 +306,26 @@ def salt_eval(prog, vecs, scalars=(), red_out=None, n: int | None = None, stream
 
 def salt_axpby(alpha: float, x, beta: float, y, stream=None) -> None:
     """y <- alpha*x + beta*y."""
-    _contig([x, y])
-    dt = _common_dtype([x, y])
-    _check(lib.salt_axpby(dt, _n_of([x, y]), float(alpha), _ptr(x), float(beta), _ptr(y), _stream_ptr(stream)))
+    dt, n, (px, py), contiguous = _operands((x, y))
+    if not contiguous:
+        raise SaltError(ERR_ARG, "SALT_ERR_ARG", "operands must be contiguous")
+    _check(lib.salt_axpby(dt, n, float(alpha), px, float(beta), py, _stream_ptr(stream)))
 
 
 def salt_dot(x, y, out, plain: bool = False, stream=None) -> None:
     """out[0] <- sum x_i y_i (out: float64 CUDA tensor)."""
-    _contig([x, y])
-    dt = _common_dtype([x, y])
-    _check(lib.salt_dot(dt, _n_of([x, y]), _ptr(x), _ptr(y), _ptr(out), PLAIN if plain else DEFAULT,
-                        _stream_ptr(stream)))
+    dt, n, (px, py), contiguous = _operands((x, y))
+    if not contiguous:
+        raise SaltError(ERR_ARG, "SALT_ERR_ARG", "operands must be contiguous")
+    _check(lib.salt_dot(dt, n, px, py, _ptr(out), PLAIN if plain else DEFAULT, _stream_ptr(stream)))
 
 
 def salt_nrm2(x, out, plain: bool = False, stream=None) -> None:
     """out[0] <- ||x||_2."""
-    _contig([x])
-    _check(lib.salt_nrm2(_dtype_code(x), x.numel(), _ptr(x), _ptr(out), PLAIN if plain else DEFAULT,
-                         _stream_ptr(stream)))
+    dt, n, (px,), contiguous = _operands((x,))
+    if not contiguous:
+        raise SaltError(ERR_ARG, "SALT_ERR_ARG", "operands must be contiguous")
+    _check(lib.salt_nrm2(dt, n, px, _ptr(out), PLAIN if plain else DEFAULT, _stream_ptr(stream)))
 
 
 def salt_fill_uniform(x, key: int, offset: int = 0, stream=None) -> None:
