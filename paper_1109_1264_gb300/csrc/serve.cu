@@ -44,6 +44,10 @@ double now_us() {
 }
 
 constexpr size_t kAlign = 256;
+// After its last step the scheduler keeps polling (yielding) this long before
+// it sleeps on the condition variable: waking a sleeping thread costs several
+// microseconds, which the next arrival would pay in its latency.
+constexpr double kIdleSpinUs = 1000.0;
 size_t round_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // First-fit allocator over [0, size) with coalescing of freed neighbours.
@@ -374,6 +378,7 @@ void complete_slot(salt_server* s, Slot& slot) {
 void scheduler(salt_server* s) {
   cudaSetDevice(s->device);
   std::vector<Request*> batch;
+  double last_active = now_us();
   for (;;) {
     bool did = false;
     for (Slot& slot : s->slots) {
@@ -427,10 +432,10 @@ void scheduler(salt_server* s) {
         }
       }
       if (batch.empty() && !did) {
-        if (any_busy) {
-          // A step is in flight: poll its event again at once (a timed wait
-          // of a few microseconds sleeps for the kernel's timer slack, tens
-          // of microseconds, which would show up in every latency).
+        if (any_busy || now_us() - last_active < kIdleSpinUs) {
+          // A step is in flight, or one ended moments ago: poll again at once
+          // (a timed wait of a few microseconds sleeps for the kernel's timer
+          // slack, tens of microseconds, which would show up in every latency).
           lk.unlock();
           std::this_thread::yield();
         } else {
@@ -439,6 +444,7 @@ void scheduler(salt_server* s) {
         continue;
       }
     }
+    last_active = now_us();
     if (!batch.empty()) {
       salt_status st = launch_step(s, *free_slot, batch);
       if (st != SALT_OK) {
