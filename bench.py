@@ -1100,15 +1100,21 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
     for _ in range(3):
         step()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(k):
+    # Each step starts after the previous one ended on all three streams, so
+    # events on the issuing stream delimit the steps.  The host link is
+    # shared with the machine's other GPUs' jobs; the median step is reported
+    # (the mean beside it) so that a transient contention does not decide it.
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
+    evs[0].record(stream)
+    for j in range(k):
         step()
-    e1.record(stream)
+        evs[j + 1].record(stream)
     torch.cuda.synchronize()
     combine()
-    ms = e0.elapsed_time(e1)
+    step_ms = sorted(evs[j].elapsed_time(evs[j + 1]) for j in range(k))
+    ms_mean = evs[0].elapsed_time(evs[k]) / k
+    ms = step_ms[k // 2] if k % 2 else 0.5 * (step_ms[k // 2 - 1] + step_ms[k // 2])
+    ms *= k  # the k steps at the median rate
     step_bytes = sum(abytes[(dt, op)] for dt, op, _ in steps)
     # The host link on this machine, measured the same way: one pinned 256 MiB
     # buffer copied host -> device, and both directions at once.
@@ -1144,7 +1150,8 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
     bound_ms = max(h2d / (h2d_gbs * 1e9), (h2d + d2h) / (both_gbs * 1e9)) * 1e3
     return {"value": round(world * step_bytes * k / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": k,
-            "ms_per_step": round(ms / k, 3),
+            "ms_per_step": round(ms / k, 3), "ms_per_step_mean": round(ms_mean, 3),
+            "ms_per_step_min_max": [round(step_ms[0], 3), round(step_ms[-1], 3)],
             "link_h2d_gbs": round(h2d_gbs, 1), "link_both_directions_gbs": round(both_gbs, 1),
             "link_bound_ms_per_step": round(bound_ms, 2), "frac_of_link_bound": round(bound_ms / (ms / k), 3),
             "pipeline": f"{nchunks} chunks per vector; upload, compute and read-back streams overlap"}
