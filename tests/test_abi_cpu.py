@@ -232,3 +232,22 @@ def test_strided_argument_errors(saltlib):
     st = (ctypes.c_int64 * 4)(1, 1, 1, 100000)
     q = (ctypes.c_void_p * 4)(BASE, BASE + 2 ** 20, BASE + 2 ** 21, BASE + 2 ** 20 - 4096)
     assert s.lib.salt_eval_strided(arr, m, 0, 10, q, st, 4, sc, 0, None, None) == s.ERR_ALIAS
+
+
+def test_program_marshalling_cache_sees_edits(saltlib):
+    """A program list passed again reuses its marshalled form; a list edited
+    in place is marshalled afresh (the cache compares it with its copy)."""
+    s = saltlib
+    prog = [("VEC", 0), ("VEC", 1), ("ADD", 0), ("STORE", 2)]
+    a1, m1 = s.program(prog)
+    a2, m2 = s.program(prog)
+    assert a1 is a2 and m1 == m2 == 4
+    prog[2] = ("SUB", 0)
+    a3, m3 = s.program(prog)
+    assert m3 == 4 and a3[2].op == s.OPS["SUB"] and a1[2].op == s.OPS["ADD"]
+    prog.append(("VEC", 2))
+    a4, m4 = s.program(prog)
+    assert m4 == 5 and a4[4].op == s.OPS["VEC"] and a4[4].arg == 2
+    # the same instructions in a fresh list or a tuple give the same codes
+    a5, m5 = s.program(tuple(prog))
+    assert m5 == 5 and [(a5[i].op, a5[i].arg) for i in range(5)] == [(a4[i].op, a4[i].arg) for i in range(5)]
