@@ -156,18 +156,26 @@ def test_cg_passes_full_size_sampled(saltlib, cuda_dev, dt):
 BIG = (1 << 31) + 13  # more elements than a 32-bit index can address
 
 
-def test_elementwise_beyond_2e31_elements_sampled(saltlib, cuda_dev):
+@pytest.mark.parametrize("sched", ["default", "staged"])
+def test_elementwise_beyond_2e31_elements_sampled(saltlib, cuda_dev, sched):
     """axpby and e over n = 2^31 + 13 FP32 elements (every index computation
     must be 64-bit): sampled elements, including both sides of 2^31 and the
-    tail, bit-identical to the oracle on the counter-based inputs."""
+    tail, bit-identical to the oracle on the counter-based inputs.  sched
+    "staged": both on the staged loop (16 KiB stages)."""
     s = saltlib
     keys = [131, 132, 133, 134, 135]
     a, b, c, d, y, out = (torch.empty(BIG, dtype=torch.float32, device=cuda_dev) for _ in range(6))
     for t, k in zip((a, b, c, d, y), keys):
         s.salt_fill_uniform(t, key=k)
-    s.salt_axpby(ALPHA, a, BETA, y)
-    s.salt_eval(P.PROG_E, [a, b, c, d, out], [ALPHA, BETA])
-    torch.cuda.synchronize()
+    try:
+        if sched == "staged":
+            s.salt_tune_set(P.PROG_E, s.F32, BIG, 1, 16, 256, 0, 16384)
+            s.salt_tune_set(P.PROG_AXPBY, s.F32, BIG, 1, 16, 128, 0, 16384)
+        s.salt_axpby(ALPHA, a, BETA, y)
+        s.salt_eval(P.PROG_E, [a, b, c, d, out], [ALPHA, BETA])
+        torch.cuda.synchronize()
+    finally:
+        s.salt_tune_clear()
     rng = np.random.default_rng(5)
     idx = np.unique(np.concatenate([np.arange(4096), np.arange((1 << 31) - 4096, BIG),
                                     rng.integers(0, BIG, 100_000)]))
@@ -182,23 +190,31 @@ def test_elementwise_beyond_2e31_elements_sampled(saltlib, cuda_dev):
     assert np.array_equal(out[tidx].cpu().numpy().view(np.uint32), want_e[4].view(np.uint32))
 
 
+@pytest.mark.parametrize("sched", ["default", "staged"])
 @pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
-def test_reductions_beyond_2e31_elements(saltlib, cuda_dev, dt):
+def test_reductions_beyond_2e31_elements(saltlib, cuda_dev, dt, sched):
     """dot and nrm2 over n = 2^31 + 13 integer-valued elements: the FP64 path
     returns the exact integer (every partial sum is below 2^53), the
-    compensated FP32 path is within 1e-6 of it."""
+    compensated FP32 path is within 1e-6 of it.  sched "staged": the dot
+    products on the staged loop (8 KiB stages)."""
     s = saltlib
     tdt = torch.float32 if dt == np.float32 else torch.float64
+    code = s.F32 if dt == np.float32 else s.F64
     i = torch.arange(BIG, device=cuda_dev, dtype=torch.int64)
     x = ((i % 1024) - 512).to(tdt)
     yv = (((7 * i) % 512) - 256).to(tdt)
     del i
     torch.cuda.empty_cache()
     outv = torch.zeros(3, dtype=torch.float64, device=cuda_dev)
-    s.salt_dot(x, yv, outv[0:1])
-    s.salt_nrm2(x, outv[1:2])
-    s.salt_dot(x, x, outv[2:3])
-    torch.cuda.synchronize()
+    try:
+        if sched == "staged":
+            s.salt_tune_set(P.PROG_DOT, code, BIG, 1, 16, 128, 0, 8192)
+        s.salt_dot(x, yv, outv[0:1])
+        s.salt_nrm2(x, outv[1:2])
+        s.salt_dot(x, x, outv[2:3])
+        torch.cuda.synchronize()
+    finally:
+        s.salt_tune_clear()
     got_dot, got_nrm, got_sq = outv.cpu().tolist()
     j = np.arange(BIG % 1024, dtype=np.int64)  # the partial period at the end
     full = BIG // 1024
