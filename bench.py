@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "fused vector-expr HBM GB/s (% of peak), batched vs plain; served p50/p99 µs"
 ALPHA, BETA = 1.5, -0.25
 DTYPES = ("f32", "f64")
+NOMINAL_HBM_GBS = 8000.0  # GB300 HBM3e, nominal (~8 TB/s); the measured copy rate is the roofline peak
 # (op, bytes moved per element in units of the element size, flops per element)
 OPS = {"e": (5, 5), "axpby": (3, 3), "dot": (2, 2), "nrm2": (1, 2)}
 # FP64 instructions per element of each op's kernel (ALU roofline of FP64)
@@ -470,10 +471,13 @@ def main():
         "data": "synthetic: counter-based uniform[-1,1) (SplitMix64) operands, alpha=1.5, beta=-0.25",
         "config": dict(workload_config(args.log2n, world), tuned=tuned),
         "frac_of_measured_hbm": round(value / world / hbm_peak, 4),
+        "frac_of_nominal_hbm": round(value / world / NOMINAL_HBM_GBS, 4),
         "roofline": roof,
         "per_kernel_ms": {f"{op}_{dt}": round(ms, 4) for (dt, op), ms in per_kernel.items()},
         "per_kernel_gbs": {f"{op}_{dt}": round(abytes[(dt, op)] / (ms * 1e-3) / 1e9, 1)
                            for (dt, op), ms in per_kernel.items()},
+        "per_kernel_frac_of_measured_hbm": {f"{op}_{dt}": round(abytes[(dt, op)] / (ms * 1e-3) / 1e9 / hbm_peak, 3)
+                                            for (dt, op), ms in per_kernel.items()},
         "gpu_launches": int(launches),
         "clocks": clk,
     }
