@@ -428,7 +428,10 @@ salt_status salt_tune_clear(void);
  * its time per call.  The call runs (reps + 1) times per configuration (42
  * configurations for a compiled shape; 36 for nrm2 and the plain dot; 12 for
  * the interpreter, which has no unroll): in-place programs update their
- * operands each time. */
+ * operands each time.  When the operands total less than four times the L2
+ * size, each timed call is preceded by a read of a scratch buffer twice the
+ * L2 size (allocated for the call and freed at its end), so that the shape
+ * is chosen for operands that come from device memory, not from L2. */
 salt_status salt_autotune(int32_t kernel, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
                           void* const* vecs, int32_t nvecs, const double* scalars, int32_t nscal, double* red_out,
                           int32_t reps, salt_launch_cfg* best, double* best_ms, void* stream);

@@ -52,6 +52,10 @@ void register_misc(Registry&);
 void register_elementwise(Registry&);
 void register_staged(Registry&);
 
+// Reads `bytes` of `buf` on `s` (16-byte multiple) so that L2 holds other,
+// clean lines afterwards; one word of `sink` may be written.
+cudaError_t launch_l2_flush(const void* buf, size_t bytes, unsigned* sink, int sms, cudaStream_t s);
+
 // Timed-out stage waits of staged kernels since the library was loaded
 // (synchronous read of a device counter).
 cudaError_t staged_timeouts(unsigned long long* out);
