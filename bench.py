@@ -619,17 +619,15 @@ def sweep_measure(torch, salt, reps: int = 21, max_log2: int = 28) -> dict:
                 continue
             x, y = xb[:n], yb[:n]
             r = {"n": n}
-            if n & (n - 1) == 0 and n >= (1 << 24):
+            if n & (n - 1) == 0:
                 # the library's autotuner, once per size bucket (untimed
-                # setup).  It times back to back, so below 2^24 elements the
-                # operands sit in L2 while it tunes, and its choice would not
-                # fit the cold-L2 calls timed here: smaller sizes keep the
-                # default shape.
-                salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_DOT, [x, y], red_out=red, reps=2)
-                salt.salt_autotune(salt.KERNEL_PROGRAM, scal, [x], [1.0], reps=2)
-                salt.salt_autotune(salt.KERNEL_PROGRAM, axpy, [x, y], [0.0], reps=2)
-                salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_SCALE, [x, y], [1.0], reps=2)
-                salt.salt_autotune(salt.KERNEL_PROGRAM, copy, [x, y], reps=2)
+                # setup); for operands that fit in L2 it flushes L2 before
+                # each timed call, like the calls timed here.
+                salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_DOT, [x, y], red_out=red, reps=5)
+                salt.salt_autotune(salt.KERNEL_PROGRAM, scal, [x], [1.0], reps=5)
+                salt.salt_autotune(salt.KERNEL_PROGRAM, axpy, [x, y], [0.0], reps=5)
+                salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_SCALE, [x, y], [1.0], reps=5)
+                salt.salt_autotune(salt.KERNEL_PROGRAM, copy, [x, y], reps=5)
             ms = timed(lambda: salt.salt_eval(PROG_DOT, [x, y], red_out=red))
             r["dot"] = round(2 * es * n / (ms * 1e-3) / 1e9, 1)
             ms = timed(lambda: salt.salt_eval(scal, [x], [0.999]))
@@ -648,8 +646,8 @@ def sweep_measure(torch, salt, reps: int = 21, max_log2: int = 28) -> dict:
         out[dt] = rows
         salt.salt_tune_clear()
         del xb, yb
-    return {"sweep": out, "note": "GB/s of algorithmic bytes; launch shapes autotuned per size bucket from 2^24 "
-                                  "on; L2 flushed before each timed call; median of %d" % reps}
+    return {"sweep": out, "note": "GB/s of algorithmic bytes; launch shapes autotuned per size bucket; "
+                                  "L2 flushed before each timed call; median of %d" % reps}
 
 
 def schedules_measure(torch, salt, log2ns=(24, 28), reps: int = 15) -> dict:
