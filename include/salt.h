@@ -391,7 +391,11 @@ salt_status salt_release_workspaces(void);
  *                 whose operands are 16-byte aligned and contiguous take it
  *                 (others use their usual kernel).  Element results are
  *                 bit-identical either way; reduction results are summed in
- *                 another order (same error bounds).
+ *                 another order (same error bounds).  The first staged launch
+ *                 on a device allocates the 8-byte counter that
+ *                 salt_staged_timeouts reads (so it cannot be the first
+ *                 library call inside a CUDA-graph capture, like any call that
+ *                 first needs a stream's reduction workspace).
  * salt_tune_set pins a configuration for (program, dtype, n bucket) where the
  * bucket is floor(log2(max(n,1))); salt_tune_get reports the configuration a
  * call would use.  Returns SALT_ERR_ARG for an invalid configuration (also
