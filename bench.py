@@ -1032,7 +1032,6 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
         hs = {k: torch.empty(w.n, dtype=w.a.dtype, pin_memory=True) for k in ("a", "b", "c", "d", "y", "out", "y_out")}
         for k in ("a", "b", "c", "d", "y"):
             hs[k].copy_(getattr(w, k))
-        hs["red"] = torch.empty(2, dtype=torch.float64, pin_memory=True)
         host[dt] = hs
         h2d += 5 * w.n * ES[dt]
         d2h += 2 * w.n * ES[dt] + 16
@@ -1041,26 +1040,34 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
     # chunks; one stream uploads every chunk back to back (the host->device
     # engine never waits on a read-back), a second runs each chunk's ops as
     # soon as its upload has landed, a third reads the chunk's results back.
+    # Consecutive steps overlap chunk by chunk: a chunk of the next step is
+    # uploaded once this step has read that chunk's results back (its
+    # compute, which reads the inputs, is then done too), so the upload
+    # engine runs without a gap between steps.  The reduction outputs
+    # alternate between two buffers (step parity), so a step's compute never
+    # overwrites the sums the previous step still has to read back.
     nchunks = args.e2e_chunks
     up, comp, down = (torch.cuda.Stream() for _ in range(3))
-    dred = {dt: torch.zeros(2 * nchunks, dtype=torch.float64, device="cuda") for dt in loads}
-    for dt in loads:
-        host[dt]["red"] = torch.empty(2 * nchunks, dtype=torch.float64, pin_memory=True)
-        d2h += 16 * nchunks - 16
+    dred = [{dt: torch.zeros(2 * nchunks, dtype=torch.float64, device="cuda") for dt in loads} for _ in range(2)]
+    hred = [{dt: torch.empty(2 * nchunks, dtype=torch.float64, pin_memory=True) for dt in loads} for _ in range(2)]
+    d2h += len(loads) * (16 * nchunks - 16)
+    work = []
+    for dt, w in loads.items():
+        n = w.n
+        bounds = [n * k // nchunks for k in range(nchunks + 1)]
+        bounds = [b - b % 4 for b in bounds[:-1]] + [n]
+        for k in range(nchunks):
+            work.append((dt, w, k, bounds[k], bounds[k + 1]))
+    state = {"read": None, "parity": 0}
 
-    def step():
-        for s in (up, comp, down):
-            s.wait_stream(stream)
-        work = []
-        for dt, w in loads.items():
-            n = w.n
-            bounds = [n * k // nchunks for k in range(nchunks + 1)]
-            bounds = [b - b % 4 for b in bounds[:-1]] + [n]
-            for k in range(nchunks):
-                work.append((dt, w, k, bounds[k], bounds[k + 1]))
+    def step(end_event=None):
+        par = state["parity"]
+        prev_read = state["read"]
         landed = []
         with torch.cuda.stream(up):
-            for dt, w, k, lo, hi in work:
+            for i, (dt, w, k, lo, hi) in enumerate(work):
+                if prev_read is not None:
+                    up.wait_event(prev_read[i])
                 hs = host[dt]
                 for key in ("a", "b", "c", "d", "y"):
                     getattr(w, key)[lo:hi].copy_(hs[key][lo:hi], non_blocking=True)
@@ -1072,49 +1079,61 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
             for (dt, w, k, lo, hi), ev in zip(work, landed):
                 comp.wait_event(ev)
                 dv = {key: getattr(w, key)[lo:hi] for key in ("a", "b", "c", "d", "y", "out")}
+                red = dred[par][dt]
                 salt.salt_eval(PROG_E, [dv["a"], dv["b"], dv["c"], dv["d"], dv["out"]], [ALPHA, BETA], stream=comp)
                 salt.salt_axpby(ALPHA, dv["a"], BETA, dv["y"], stream=comp)
-                salt.salt_dot(dv["a"], dv["b"], dred[dt][2 * k:2 * k + 1], stream=comp)
-                salt.salt_nrm2(dv["c"], dred[dt][2 * k + 1:2 * k + 2], stream=comp)
+                salt.salt_dot(dv["a"], dv["b"], red[2 * k:2 * k + 1], stream=comp)
+                salt.salt_nrm2(dv["c"], red[2 * k + 1:2 * k + 2], stream=comp)
                 ev2 = torch.cuda.Event()
                 ev2.record(comp)
                 done.append(ev2)
+        read = []
         with torch.cuda.stream(down):
             for (dt, w, k, lo, hi), ev in zip(work, done):
                 down.wait_event(ev)
                 hs = host[dt]
                 hs["out"][lo:hi].copy_(w.out[lo:hi], non_blocking=True)
                 hs["y_out"][lo:hi].copy_(w.y[lo:hi], non_blocking=True)
+                ev3 = torch.cuda.Event()
+                ev3.record(down)
+                read.append(ev3)
             for dt in loads:
-                host[dt]["red"].copy_(dred[dt], non_blocking=True)
-        for s in (up, comp, down):
-            stream.wait_stream(s)
+                hred[par][dt].copy_(dred[par][dt], non_blocking=True)
+            if end_event is not None:
+                end_event.record(down)
+        state["read"] = read
+        state["parity"] = 1 - par
 
     def combine():
         # dot = sum of chunk dots; nrm2 = sqrt(sum of chunk norms squared)
         out = {}
+        last = 1 - state["parity"]
         for dt in loads:
-            r = host[dt]["red"].tolist()
+            r = hred[last][dt].tolist()
             out[dt] = (sum(r[0::2]), sum(v * v for v in r[1::2]) ** 0.5)
         return out
 
     k = max(3, min(args.steps, 10))
+    for s_ in (up, comp, down):
+        s_.wait_stream(stream)
     for _ in range(3):
         step()
     torch.cuda.synchronize()
-    # Each step starts after the previous one ended on all three streams, so
-    # events on the issuing stream delimit the steps.  The host link is
-    # shared with the machine's other GPUs' jobs; the median step is reported
-    # (the mean beside it) so that a transient contention does not decide it.
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
-    evs[0].record(stream)
+    # Step j ends when its last read-back has landed; with steps overlapping,
+    # the interval between consecutive ends is the steady-state step time.
+    # The host link is shared with the machine's other GPUs' jobs; the
+    # median interval is reported (the mean beside it) so that a transient
+    # contention does not decide it.
+    start = torch.cuda.Event(enable_timing=True)
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+    start.record(up)
     for j in range(k):
-        step()
-        evs[j + 1].record(stream)
+        step(ends[j])
     torch.cuda.synchronize()
     combine()
-    step_ms = sorted(evs[j].elapsed_time(evs[j + 1]) for j in range(k))
-    ms_mean = evs[0].elapsed_time(evs[k]) / k
+    marks = [start] + ends
+    step_ms = sorted(marks[j].elapsed_time(marks[j + 1]) for j in range(k))
+    ms_mean = start.elapsed_time(ends[-1]) / k
     ms = step_ms[k // 2] if k % 2 else 0.5 * (step_ms[k // 2 - 1] + step_ms[k // 2])
     ms *= k  # the k steps at the median rate
     step_bytes = sum(abytes[(dt, op)] for dt, op, _ in steps)
@@ -1156,7 +1175,8 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
             "ms_per_step_min_max": [round(step_ms[0], 3), round(step_ms[-1], 3)],
             "link_h2d_gbs": round(h2d_gbs, 1), "link_both_directions_gbs": round(both_gbs, 1),
             "link_bound_ms_per_step": round(bound_ms, 2), "frac_of_link_bound": round(bound_ms / (ms / k), 3),
-            "pipeline": f"{nchunks} chunks per vector; upload, compute and read-back streams overlap"}
+            "pipeline": f"{nchunks} chunks per vector; upload, compute and read-back streams overlap, "
+                        "consecutive steps overlap chunk by chunk"}
 
 
 if __name__ == "__main__":
