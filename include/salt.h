@@ -428,7 +428,8 @@ salt_status salt_tune_clear(void);
  * instantiation also the staged loop at stage_bytes {4096, 8192, 16384} x
  * block {128, 256} (as many blocks as fit), `reps` timed runs each after one
  * warm-up, on `stream`, and pins the fastest for (family, dtype, n bucket) in
- * the tuning table.  *best and *best_ms (either may be NULL) receive it and
+ * the tuning table (a staged configuration only if it is more than 1% faster
+ * than the best register-tiled one).  *best and *best_ms (either may be NULL) receive it and
  * its time per call.  The call runs (reps + 1) times per configuration (42
  * configurations for a compiled shape; 36 for nrm2 and the plain dot; 12 for
  * the interpreter, which has no unroll): in-place programs update their

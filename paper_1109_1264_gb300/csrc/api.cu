@@ -222,12 +222,47 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
   const int dt = sizeof(T) == 4 ? DT_F32 : DT_F64;
   // 32-byte vectors need 32-byte aligned operands; operands that are not
   // 16-byte aligned or not contiguous take the element-access kernels.
-  bool all32 = true, elementwise = false;
+  bool all32 = true, elementwise = false, strided = false;
   for (int k = 0; k < c.nvec; ++k) {
     all32 = all32 && aligned(a.vecs[c.vec_user[k]], 32);
-    elementwise = elementwise || !aligned(a.vecs[c.vec_user[k]], 16) ||
-                  (a.strides && a.strides[c.vec_user[k]] != 1);
+    elementwise = elementwise || !aligned(a.vecs[c.vec_user[k]], 16);
+    strided = strided || (a.strides && a.strides[c.vec_user[k]] != 1);
   }
+  // Contiguous operands that all sit at the same offset within an aligned
+  // block (an element multiple): the vector kernels run from the next
+  // boundary and evaluate the `head` elements before it one by one (kernels
+  // with a compile-time instantiation; the interpreter keeps its element
+  // mode).  The boundary is 128 bytes, else 32, whichever the operands share
+  // an offset within, so that the body's accesses fill whole 32-byte
+  // sectors: a body that starts 16 bytes into a sector half-covers a sector
+  // at every warp's edge, which measured up to 27% slower than the element
+  // accesses for in-place updates, so operands that agree only modulo 16
+  // bytes keep the element-access kernels.  FP32 only: for FP64 the element
+  // kernels (8-byte accesses) measured as fast as the peeled vector loop or
+  // faster (dot at 2^28: 6.8 against 6.5 TB/s), while for FP32 they lose a
+  // fifth (5.3 against 6.4 TB/s).
+  int64_t head = 0;
+  if (sizeof(T) == 4 && elementwise && !strided && (shape >= 0 || jit_mode() == SALT_JIT_ON)) {
+    uintptr_t span = 0;
+    for (uintptr_t A : {(uintptr_t)128, (uintptr_t)32}) {
+      const uintptr_t off = (uintptr_t)a.vecs[c.vec_user[0]] % A;
+      bool same = off % sizeof(T) == 0;
+      for (int k = 1; k < c.nvec && same; ++k) same = (uintptr_t)a.vecs[c.vec_user[k]] % A == off;
+      if (same) {
+        span = A;
+        break;
+      }
+    }
+    const uintptr_t off = span ? (uintptr_t)a.vecs[c.vec_user[0]] % span : 0;
+    const int64_t h = span ? (int64_t)((span - off) % span / sizeof(T)) : 0;
+    if (span && h < a.n) {
+      head = h;
+      elementwise = false;
+      all32 = true;
+      for (int k = 0; k < c.nvec; ++k) all32 = all32 && aligned((const T*)a.vecs[c.vec_user[k]] + head, 32);
+    }
+  }
+  elementwise = elementwise || strided;
 
   Workspace ws;
   if (c.nred > 0) {
@@ -283,14 +318,15 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
       if (e != cudaSuccess) return cuda_error(e, "cudaFuncSetAttribute(staged kernel)");
       int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy_blocks(ke.kernel, cfg.block, smem);
       if (bps > kMaxBlocksPerSM) bps = kMaxBlocksPerSM;
-      const int grid = grid_for(a.n, cfg.stage_bytes / (int64_t)sizeof(T), info.sms, bps);
+      const int grid = grid_for(a.n - head, cfg.stage_bytes / (int64_t)sizeof(T), info.sms, bps);
       StagedParams<T> sp;
       memset(&sp, 0, sizeof sp);
       MapParams<T>& p = sp.m;
-      for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]];
+      for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]] + head;
       for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
       if (scode) p.scode = *scode;
-      p.n = a.n;
+      p.n = a.n - head;
+      p.head = (int32_t)head;
       p.red_out = a.red_out;
       p.partials = ws.partials;
       p.ticket = ws.ticket;
@@ -311,13 +347,14 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
     int bps = cfg.blocks_per_sm > 0 ? cfg.blocks_per_sm : occupancy_blocks(ke.kernel, cfg.block, 0);
     if (bps > kMaxBlocksPerSM) bps = kMaxBlocksPerSM;
     const int64_t vec = cfg.vec_bytes / (int64_t)sizeof(T);
-    const int grid = grid_for(a.n, (int64_t)cfg.unroll * cfg.block * vec, info.sms, bps);
+    const int grid = grid_for(a.n - head, (int64_t)cfg.unroll * cfg.block * vec, info.sms, bps);
     MapParams<T> p;
     memset(&p, 0, sizeof p);
-    for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]];
+    for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]] + head;
     for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
     if (scode) p.scode = *scode;
-    p.n = a.n;
+    p.n = a.n - head;
+    p.head = (int32_t)head;
     p.red_out = a.red_out;
     p.partials = ws.partials;
     p.ticket = ws.ticket;
@@ -340,13 +377,14 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
     int bps = occupancy_blocks(k, block, 0);
     if (bps > kMaxBlocksPerSM) bps = kMaxBlocksPerSM;
     const int64_t vec = vb / (int64_t)sizeof(T);
-    const int grid = grid_for(a.n, (int64_t)unroll * block * vec, info.sms, bps);
+    const int grid = grid_for(a.n - head, (int64_t)unroll * block * vec, info.sms, bps);
     MapParams<T> p;
     memset(&p, 0, sizeof p);
-    for (int j = 0; j < c.nvec; ++j) p.v[j] = (T*)a.vecs[c.vec_user[j]];
+    for (int j = 0; j < c.nvec; ++j) p.v[j] = (T*)a.vecs[c.vec_user[j]] + head;
     for (int j = 0; j < c.nscal; ++j) p.sc[j] = (T)a.scalars[c.scal_user[j]];
     if (scode) p.scode = *scode;
-    p.n = a.n;
+    p.n = a.n - head;
+    p.head = (int32_t)head;
     p.red_out = a.red_out;
     p.partials = ws.partials;
     p.ticket = ws.ticket;
@@ -1054,7 +1092,10 @@ salt_status salt_autotune(int32_t kernel, const salt_insn* prog, int32_t nprog, 
       }
       if (st != SALT_OK) break;
     }
-    if (ms / reps < best_t) {
+    // the staged loop must win by more than 1% (near-ties go to the
+    // register-tiled loop, which inside a longer sequence of kernels
+    // measured the steadier of the two)
+    if (ms / reps < best_t * (c.stage_bytes ? 0.99f : 1.0f)) {
       best_t = ms / reps;
       best = c;
     }

@@ -23,6 +23,9 @@ struct MapParams {
   unsigned* ticket;     // workspace: zero between launches
   int64_t stride[kMaxVecs];  // element strides (strided_kernel only)
   ScalarCode scode;          // scalar slots computed on the device (len 0: none)
+  int32_t head;              // elements before the aligned body (fused and staged kernels):
+                             // v[k] points at element `head` of operand k, and elements
+                             // 0 .. head-1 sit just before it; 0 for the strided kernel
 };
 
 // Per-element evaluation of program P: node I at compile-time stack depth.
@@ -79,6 +82,26 @@ __device__ __forceinline__ void exec_chunk(T (&x)[kMaxVecs][NE], const T (&sc)[k
   }
 }
 
+// The head of operands that share one misalignment: the host moved every
+// operand pointer forward to the next 16-byte boundary, and threads
+// 0 .. head-1 of block 0 evaluate the elements it stepped over, one each,
+// with the same per-element operations (Section 4.3's single_op, before the
+// vectorised loop instead of after it).
+template <class P, typename T, class Acc>
+__device__ __forceinline__ void run_head(const MapParams<T>& p, const T (&sc)[kMaxScals], Acc (&acc)[kMaxReds]) {
+  constexpr unsigned LM = P::load_mask(), SMASK = P::store_mask();
+  if (blockIdx.x == 0 && (int)threadIdx.x < p.head) {
+    const int64_t i = (int64_t)threadIdx.x - p.head;  // negative: before the body
+    T x[kMaxVecs][1];
+#pragma unroll
+    for (int s = 0; s < kMaxVecs; ++s) x[s][0] = ((LM >> s) & 1u) ? p.v[s][i] : T(0);
+    exec_chunk<P, T, Acc, 1>(x, sc, acc);
+#pragma unroll
+    for (int s = 0; s < kMaxVecs; ++s)
+      if ((SMASK >> s) & 1u) p.v[s][i] = x[s][0];
+  }
+}
+
 // DS: some scalar slots are computed on the device from p.scode at kernel
 // start.  A separate instantiation, because scalars that may come from
 // shared memory occupy registers for the whole loop, while by-value
@@ -99,6 +122,7 @@ __global__ void __launch_bounds__(256) fused_kernel(const MapParams<T> p) {
     for (int k = 0; k < kMaxScals; ++k) sc[k] = p.sc[k];
   }
   Acc acc[kMaxReds];
+  run_head<P, T, Acc>(p, sc, acc);
 
   const int64_t n = p.n;
   const int64_t bd = blockDim.x;

@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(256) staged_kernel(const StagedParams<T> sp) {
   T sc[kMaxScals];
   load_scalars<T>(p.sc, p.scode, sc);
   Acc acc[kMaxReds];
+  run_head<P, T, Acc>(p, sc, acc);
 
   const int64_t n = p.n;
   const int sb = sp.stage_bytes;

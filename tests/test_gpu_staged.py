@@ -98,19 +98,31 @@ def test_staged_device_scalar_passes(salt, cuda_dev, dt):
     assert salt.salt_staged_timeouts() == 0
 
 
-def test_staged_unaligned_operand_takes_element_kernel(salt, cuda_dev):
-    """A staged configuration does not apply to operands that are not 16-byte
-    aligned: the call runs the element-access kernel and still matches."""
+@pytest.mark.parametrize("layout", ["same_offset", "mixed_offsets"])
+def test_staged_unaligned_operands(salt, cuda_dev, layout):
+    """A staged configuration with FP32 operands that are not 16-byte
+    aligned: all at the same offset, the staged loop runs from the next
+    128-byte boundary and the head elements are evaluated one by one; at
+    different offsets the element-access kernel runs.  Both match the
+    oracle, and the elements around the views stay untouched."""
     prog, nv, ns = PROGS["D"]
-    n = 3 * 4096 + 11
-    vecs = inputs.uniform_vectors(55, n + 1, nv, np.float32)
     try:
-        salt.salt_tune_set(prog, salt.F32, n, 1, 16, 128, 0, 4096)
-        tv = [torch.from_numpy(v.copy()).to(cuda_dev)[1:] for v in vecs]  # 4-byte offset
-        salt.salt_eval(prog, tv)
-        torch.cuda.synchronize()
-        want, _ = run_oracle(prog, [v[1:].copy() for v in vecs], [])
-        assert_bits_equal(tv[3].cpu().numpy(), want[3], "unaligned D")
+        for n in (3, 4 * 1024 + 1, 3 * 4096 + 11, (1 << 20) + 3):
+            vecs = inputs.uniform_vectors(55 + n, n, nv, np.float32)
+            salt.salt_tune_set(prog, salt.F32, n, 1, 16, 128, 0, 4096)
+            offs = [1, 1, 1, 1] if layout == "same_offset" else [1, 2, 3, 1]
+            bufs = [torch.full((n + 8,), 7.0, dtype=torch.float32, device=cuda_dev) for _ in range(nv)]
+            tv = []
+            for b, v, o in zip(bufs, vecs, offs):
+                b[o:o + n] = torch.from_numpy(v).to(cuda_dev)
+                tv.append(b[o:o + n])
+            salt.salt_eval(prog, tv)
+            torch.cuda.synchronize()
+            want, _ = run_oracle(prog, vecs, [])
+            for k, (b, o) in enumerate(zip(bufs, offs)):
+                h = b.cpu().numpy()
+                assert_bits_equal(h[o:o + n], want[k], f"{layout} n={n} operand {k}")
+                assert np.all(np.delete(h, np.arange(o, o + n)) == 7.0)
     finally:
         salt.salt_tune_clear()
 

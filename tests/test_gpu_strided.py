@@ -19,13 +19,16 @@ ODD = [("VEC", 0), ("NEG", 0), ("VEC", 1), ("MUL", 0), ("VEC", 2), ("ADD", 0), (
 
 def views(vecs, dt, layout, dev):
     """Device views of the host vectors: layout 'offset' puts each at a
-    1-element (unaligned) offset, 'stride' at a stride of 2 or 3; returns
-    (views, backing buffers, positions of the views in the buffers)."""
+    1- to 3-element (unaligned) offset, different per operand; 'same_offset'
+    puts every operand at the same 1-element offset (for FP32 the vector
+    kernels then start at the next 128-byte boundary and evaluate the head
+    elements one by one); 'stride' at a stride of 2 or 3; returns (views,
+    backing buffers, positions of the views in the buffers)."""
     out, bufs, pos = [], [], []
     for k, v in enumerate(vecs):
         n = len(v)
-        if layout == "offset":
-            off = 1 + k % 3
+        if layout in ("offset", "same_offset"):
+            off = 1 + k % 3 if layout == "offset" else 1
             buf = torch.full((n + 8,), 7.0, dtype=TDT[dt], device=dev)
             idx = np.arange(off, off + n)
             buf[off:off + n] = torch.from_numpy(v).to(dev)
@@ -41,7 +44,7 @@ def views(vecs, dt, layout, dev):
     return out, bufs, pos
 
 
-@pytest.mark.parametrize("layout", ["offset", "stride"])
+@pytest.mark.parametrize("layout", ["offset", "same_offset", "stride"])
 @pytest.mark.parametrize("name", ["D", "E", "AXPBY", "CG", "DOT", "SUMSQ", "ODD", "ODD_JIT"])
 @pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
 def test_unaligned_and_strided(saltlib, cuda_dev, layout, name, dt):
@@ -53,11 +56,11 @@ def test_unaligned_and_strided(saltlib, cuda_dev, layout, name, dt):
     if name == "ODD_JIT":
         s.salt_set_jit(s.JIT_ON)
     try:
-        for n in (1, 5, 1000, 70001):
+        for n in (1, 2, 3, 4, 5, 1000, 70001):
             vecs = inputs.uniform_vectors(50 + n, n, nv, dt)
             scalars = [1.5, -0.25][:ns]
             tv, bufs, pos = views(vecs, dt, layout, cuda_dev)
-            if layout == "offset":
+            if layout != "stride":
                 assert any(t.data_ptr() % 16 for t in tv)
             elif n > 1:  # a one-element view is contiguous whatever its stride
                 assert all(not t.is_contiguous() for t in tv)
