@@ -187,12 +187,15 @@ salt_status salt_eval(const salt_insn* prog, int32_t nprog, int32_t dtype, int64
                       void* const* vecs, int32_t nvecs, const double* scalars, int32_t nscal,
                       double* red_out, void* stream);
 
-/* salt_eval with strided operands (BLAS incx semantics, positive strides):
- * element i of operand k is vecs[k][i * strides[k]]; strides is a host array
- * of nvecs element strides, each >= 1 for the operands the program names
- * (SALT_ERR_ARG otherwise).  Elements between the strided positions are never
- * read or written.  Aliasing is judged on the whole address range an operand
- * spans, ((n - 1) * stride + 1) elements.  Otherwise as salt_eval. */
+/* salt_eval with strided operands (BLAS incx semantics): element i of operand
+ * k is vecs[k][i * strides[k]]; strides is a host array of nvecs element
+ * strides, nonzero for the operands the program names (SALT_ERR_ARG
+ * otherwise).  A negative stride walks the vector backwards from vecs[k]:
+ * for BLAS's incx < 0 over an array starting at x, pass
+ * x + (n - 1) * |incx| and the negative incx.  Elements between the strided
+ * positions are never read or written.  Aliasing is judged on the whole
+ * address range an operand spans, ((n - 1) * |stride| + 1) elements.
+ * Otherwise as salt_eval. */
 salt_status salt_eval_strided(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
                               void* const* vecs, const int64_t* strides, int32_t nvecs, const double* scalars,
                               int32_t nscal, double* red_out, void* stream);

@@ -470,25 +470,31 @@ salt_status validate_eval(const EvalArgs& a, Analysis* an_out) {
       snprintf(b, sizeof b, "vector operand %d is not aligned to its element size", k);
       return set_error(SALT_ERR_ALIGN, b);
     }
-    if (a.strides && a.strides[k] < 1) {
+    if (a.strides && a.strides[k] == 0) {
       char b[96];
-      snprintf(b, sizeof b, "stride of vector operand %d must be >= 1", k);
+      snprintf(b, sizeof b, "stride of vector operand %d must not be 0", k);
       return set_error(SALT_ERR_ARG, b);
     }
   }
   // An output may share memory with an input only through the same operand
   // index (exact in-place update).  Strided operands are judged by the whole
-  // address range they span.
+  // address range they span: from element n-1 to element 0 for a negative
+  // stride.
+  auto low = [&](int k) -> uintptr_t {
+    const int64_t s = a.strides ? a.strides[k] : 1;
+    return (uintptr_t)a.vecs[k] + (uintptr_t)((s < 0 && a.n > 0 ? (a.n - 1) * s : 0) * (int64_t)es);
+  };
   auto extent = [&](int k) -> uintptr_t {
     const int64_t s = a.strides ? a.strides[k] : 1;
-    return a.n > 0 ? (uintptr_t)(((a.n - 1) * s + 1) * (int64_t)es) : 0;
+    const int64_t m = s < 0 ? -s : s;
+    return a.n > 0 ? (uintptr_t)(((a.n - 1) * m + 1) * (int64_t)es) : 0;
   };
   for (int i = 0; i < a.nvecs; ++i) {
     if (!((an.used_vecs >> i) & 1u)) continue;
     for (int j = i + 1; j < a.nvecs; ++j) {
       if (!((an.used_vecs >> j) & 1u)) continue;
       if (!(((an.stored_vecs >> i) | (an.stored_vecs >> j)) & 1u)) continue;
-      const uintptr_t pi = (uintptr_t)a.vecs[i], pj = (uintptr_t)a.vecs[j];
+      const uintptr_t pi = low(i), pj = low(j);
       const uintptr_t bi = extent(i), bj = extent(j);
       if (bi > 0 && bj > 0 && pi < pj + bj && pj < pi + bi) {
         char b[128];
@@ -507,7 +513,7 @@ salt_status validate_eval(const EvalArgs& a, Analysis* an_out) {
                q < (uintptr_t)a.red_out + 8 * (uintptr_t)an.nred;
     for (int i = 0; i < a.nvecs && !hit; ++i) {
       if (!((an.stored_vecs >> i) & 1u)) continue;
-      const uintptr_t pi = (uintptr_t)a.vecs[i], bi = extent(i);
+      const uintptr_t pi = low(i), bi = extent(i);
       hit = bi > 0 && q + 8 > pi && q < pi + bi;
     }
     if (hit) {

@@ -232,6 +232,15 @@ def test_strided_argument_errors(saltlib):
     st = (ctypes.c_int64 * 4)(1, 1, 1, 100000)
     q = (ctypes.c_void_p * 4)(BASE, BASE + 2 ** 20, BASE + 2 ** 21, BASE + 2 ** 20 - 4096)
     assert s.lib.salt_eval_strided(arr, m, 0, 10, q, st, 4, sc, 0, None, None) == s.ERR_ALIAS
+    # a negative stride spans downwards from the pointer (element n-1 lowest):
+    # output d walks back from 4 KiB above b's start over b's memory
+    neg = (ctypes.c_int64 * 4)(1, 1, 1, -2)
+    r = (ctypes.c_void_p * 4)(BASE, BASE + 2 ** 20, BASE + 2 ** 21, BASE + 2 ** 20 + 40)
+    assert s.lib.salt_eval_strided(arr, m, 0, 10, r, neg, 4, sc, 0, None, None) == s.ERR_ALIAS
+    # the same walk starting below b overlaps nothing: validation passes (then,
+    # with no GPU, the call fails at the device)
+    r2 = (ctypes.c_void_p * 4)(BASE, BASE + 2 ** 20, BASE + 2 ** 21, BASE + 2 ** 20 - 4)
+    assert s.lib.salt_eval_strided(arr, m, 0, 10, r2, neg, 4, sc, 0, None, None) not in (s.ERR_ALIAS, s.ERR_ARG)
 
 
 def test_program_marshalling_cache_sees_edits(saltlib):

@@ -97,3 +97,58 @@ def test_unaligned_dot_and_nrm2(saltlib, cuda_dev, dt):
         assert abs(d - exact.exact_dot(x, y)) <= TOL[dt] * exact.abs_dot(x, y)
         ref = exact.exact_nrm2(x)
         assert abs(nr - ref) <= TOL[dt] * ref
+
+
+@pytest.mark.parametrize("name", ["D", "E", "AXPBY", "CG", "DOT", "ODD", "ODD_JIT"])
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_negative_strides(saltlib, cuda_dev, name, dt):
+    """BLAS incx < 0 through the C ABI: element i of operand k at
+    vecs[k][i * strides[k]] with strides -1, -2, -3 mixed with positive
+    ones; the oracle's bits at exactly those positions, nothing else
+    written, reductions within tolerance."""
+    import ctypes
+    s = saltlib
+    if name.startswith("ODD"):
+        prog, nv, ns = ODD, 3, 0
+    else:
+        prog, nv, ns = PROGS[name]
+    es = np.dtype(dt).itemsize
+    code = s.F32 if dt == np.float32 else s.F64
+    if name == "ODD_JIT":
+        s.salt_set_jit(s.JIT_ON)
+    try:
+        for n in (1, 5, 1000, 70001):
+            vecs = inputs.uniform_vectors(90 + n, n, nv, dt)
+            scalars = [1.5, -0.25][:ns]
+            strides = [-(1 + k % 3) if k % 2 == 0 else 1 + k % 2 for k in range(nv)]
+            bufs, pos, ptrs = [], [], []
+            for v, st in zip(vecs, strides):
+                m = abs(st)
+                buf = torch.full((n * m + 1,), 7.0, dtype=TDT[dt], device=cuda_dev)
+                first = (n - 1) * m if st < 0 else 0  # element 0's position in the buffer
+                idx = first + np.arange(n, dtype=np.int64) * st
+                assert idx.min() >= 0 and idx.max() < buf.numel()
+                buf[torch.from_numpy(idx).to(cuda_dev)] = torch.from_numpy(v).to(cuda_dev)
+                bufs.append(buf)
+                pos.append(idx)
+                ptrs.append(buf.data_ptr() + first * es)
+            nred = sum(1 for o, _ in prog if o in ("DOT", "SUMSQ"))
+            red = torch.full((max(nred, 1),), float("nan"), dtype=torch.float64, device=cuda_dev)
+            arr, m_ = s.program(prog)
+            cp = (ctypes.c_void_p * nv)(*ptrs)
+            cs = (ctypes.c_int64 * nv)(*strides)
+            sc = (ctypes.c_double * max(ns, 1))(*scalars)
+            stream = torch.cuda.current_stream().cuda_stream
+            st_ = s.lib.salt_eval_strided(arr, m_, code, n, cp, cs, nv, sc, ns,
+                                          red.data_ptr() if nred else None, stream)
+            assert st_ == s.OK, s.lib.salt_last_error()
+            torch.cuda.synchronize()
+            want = [v.copy() for v in vecs]
+            oracle.eval_program(prog, want, scalars)
+            for k, (buf, idx) in enumerate(zip(bufs, pos)):
+                b = buf.cpu().numpy()
+                assert_bits_equal(b[idx], want[k], f"{name} negative strides n={n} operand {k}")
+                assert np.all(np.delete(b, idx) == 7.0), f"{name}: elements outside the strided positions written"
+            check_reductions(prog, vecs, scalars, red.cpu().numpy()[:nred], dt, f"{name} negative strides")
+    finally:
+        s.salt_set_jit(s.JIT_OFF)
