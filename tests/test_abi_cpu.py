@@ -260,3 +260,31 @@ def test_program_marshalling_cache_sees_edits(saltlib):
     # the same instructions in a fresh list or a tuple give the same codes
     a5, m5 = s.program(tuple(prog))
     assert m5 == 5 and [(a5[i].op, a5[i].arg) for i in range(5)] == [(a4[i].op, a4[i].arg) for i in range(5)]
+
+
+def test_binding_operand_checks(saltlib):
+    """The binding's one-pass operand marshalling: mixed dtypes and unequal
+    lengths are rejected before the library is called; an explicit n skips
+    the length check (the library then sees the call)."""
+    torch = pytest.importorskip("torch")
+    s = saltlib
+    a32 = torch.zeros(8, dtype=torch.float32)
+    b32 = torch.zeros(8, dtype=torch.float32)
+    c64 = torch.zeros(8, dtype=torch.float64)
+    short = torch.zeros(5, dtype=torch.float32)
+    prog = [("VEC", 0), ("VEC", 1), ("ADD", 0), ("STORE", 2)]
+    with pytest.raises(s.SaltError) as ei:
+        s.salt_eval(prog, [a32, b32, c64])
+    assert ei.value.status == s.ERR_DTYPE
+    with pytest.raises(s.SaltError) as ei:
+        s.salt_eval(prog, [a32, b32, short])
+    assert ei.value.status == s.ERR_ARG
+    with pytest.raises(s.SaltError) as ei:
+        s.salt_dot(a32, short, torch.zeros(1, dtype=torch.float64))
+    assert ei.value.status == s.ERR_ARG
+    with pytest.raises(s.SaltError) as ei:
+        s.salt_axpby(1.0, a32, 2.0, c64)
+    assert ei.value.status == s.ERR_DTYPE
+    dt, n, ptrs, contiguous = s._operands([a32, None, short], same_length=False)
+    assert dt == s.F32 and n == 8 and ptrs[1] is None and contiguous
+    assert s._operands([a32[::2]])[3] is False
