@@ -335,6 +335,51 @@ def cg_diagonal_two_pass(evalp, d, b, x0, iters):
     return x, hist
 
 
+# Conjugate gradients with one reduction phase per iteration (Chronopoulos
+# and Gear 1989): with w = A r kept implicit (diag(d) o r), each iteration
+# updates p = r + beta p and s = A r + beta s (s = A p in exact arithmetic),
+# then x = x + alpha p, r = r - alpha s, and reduces gamma = r.r and
+# delta = (A r).r of the new residual in the same pass; the scalars are
+# beta = gamma_k / gamma_{k-1} and alpha_k = gamma_k / (delta_k - beta_k
+# gamma_k / alpha_{k-1}), alpha_0 = gamma_0 / delta_0.  In exact arithmetic
+# the iterates are those of Hestenes-Stiefel CG.  Slots: 0 d, 1 p, 2 s, 3 x,
+# 4 r, 5 b; device scalars: 0 beta, 1 alpha (values in T, so exact).
+CGC_START = [("VEC", 5), ("VEC", 0), ("VEC", 3), ("MUL", 0), ("SUB", 0), ("STORE", 4),
+             ("VEC", 4), ("SUMSQ", 0), ("VEC", 0), ("VEC", 4), ("MUL", 0), ("VEC", 4), ("DOT", 0)]
+_CGC_TAIL = [("VEC", 3), ("DSCAL", 1), ("VEC", 1), ("SMUL", 0), ("ADD", 0), ("STORE", 3),
+             ("VEC", 4), ("DSCAL", 1), ("VEC", 2), ("SMUL", 0), ("SUB", 0), ("STORE", 4),
+             ("VEC", 4), ("SUMSQ", 0), ("VEC", 0), ("VEC", 4), ("MUL", 0), ("VEC", 4), ("DOT", 0)]
+CGC_FIRST = [("VEC", 4), ("STORE", 1), ("VEC", 0), ("VEC", 4), ("MUL", 0), ("STORE", 2)] + _CGC_TAIL
+CGC_STEP = [("VEC", 4), ("DSCAL", 0), ("VEC", 1), ("SMUL", 0), ("ADD", 0), ("STORE", 1),
+            ("VEC", 0), ("VEC", 4), ("MUL", 0), ("DSCAL", 0), ("VEC", 2), ("SMUL", 0), ("ADD", 0),
+            ("STORE", 2)] + _CGC_TAIL
+
+
+def cg_diagonal_one_reduction(evalp, d, b, x0, iters):
+    """The one-reduction-phase CG from x0 with one program per iteration;
+    the scalars are computed in the vectors' precision from the reductions
+    rounded to it (as a DSCAL node reads them).  Returns x and the history
+    [gamma_0, delta_0, gamma_1, delta_1, ..., gamma_iters, delta_iters]."""
+    n = d.shape[0]
+    dt = d.dtype.type
+    p, s, r = np.zeros(n, d.dtype), np.zeros(n, d.dtype), np.zeros(n, d.dtype)
+    x = x0.copy()
+    vecs = [d, p, s, x, r, b]
+    hist = list(evalp(CGC_START, vecs, []))
+    alpha = None
+    for k in range(iters):
+        g, dl = dt(hist[2 * k]), dt(hist[2 * k + 1])
+        if k == 0:
+            alpha = g / dl
+            out = evalp(CGC_FIRST, vecs, [0.0, float(alpha)])
+        else:
+            beta = g / dt(hist[2 * k - 2])
+            alpha = g / (dl - beta * g / alpha)
+            out = evalp(CGC_STEP, vecs, [float(beta), float(alpha)])
+        hist.extend(out)
+    return x, hist
+
+
 def check_cg_distinct_eigenvalues(path):
     """CG on an SPD matrix with k distinct eigenvalues reaches the solution
     in at most k iterations in exact arithmetic (Hestenes and Stiefel 1952;
@@ -366,6 +411,41 @@ def check_cg_distinct_eigenvalues(path):
         x0 = rng.uniform(-3, 3, n).astype(dt)
         x5, _ = cg_diagonal_two_pass(evalp, d, b, x0, 4)
         assert np.linalg.norm(x5 - xs) / np.linalg.norm(xs) < 10 * tol, dt
+        # the one-reduction form: the same termination in 4 iterations (not 3),
+        # from zero and from x0
+        for start in (np.zeros(n, dt), x0):
+            xc3, _ = cg_diagonal_one_reduction(evalp, d, b, start, 3)
+            xc4, hc = cg_diagonal_one_reduction(evalp, d, b, start, 4)
+            assert np.linalg.norm(xc4 - xs) / np.linalg.norm(xs) < 10 * tol, dt
+            assert np.linalg.norm(xc3 - xs) / np.linalg.norm(xs) > 1e-3, dt
+            assert hc[-2] < (10 * tol) ** 2 * hc[0] * 100, (dt, hc)
+
+
+def check_cg_one_reduction_matches_cg(path):
+    """In exact arithmetic the one-reduction CG produces the Hestenes-Stiefel
+    iterates: on a well-conditioned diagonal system (d in [1, 4]) the two
+    oracles' x after k iterations agree to rounding, for every k, while the
+    residual falls by orders of magnitude; and gamma_k = r_k.r_k matches the
+    two-pass rho_k."""
+    rng = np.random.default_rng(29)
+
+    def evalp(prog, vecs, ds):
+        return oracle.eval_program(prog, vecs, dscalars=ds, path=path)
+
+    for dt, tol in ((np.float64, 1e-12), (np.float32, 1e-4)):
+        n = 777
+        d = rng.uniform(1.0, 4.0, n).astype(dt)
+        b = rng.uniform(-1, 1, n).astype(dt)
+        x0 = rng.uniform(-1, 1, n).astype(dt)
+        for k in (1, 2, 5, 12):
+            xh, hh = cg_diagonal_two_pass(evalp, d, b, x0, k)
+            xc, hc = cg_diagonal_one_reduction(evalp, d, b, x0, k)
+            scale = max(np.linalg.norm(xh.astype(np.float64)), 1.0)
+            assert np.linalg.norm(xc.astype(np.float64) - xh) / scale < tol, (dt, k)
+            for j in range(k + 1):
+                assert abs(hc[2 * j] - hh[2 * j]) <= tol * hh[0] + 1e-300, (dt, k, j, hc[2 * j], hh[2 * j])
+        _, hc = cg_diagonal_one_reduction(evalp, d, b, x0, 12)
+        assert hc[-2] < 1e-6 * hc[0], (dt, hc[-2], hc[0])
 
 
 def check_tail_lengths(path):
@@ -509,6 +589,7 @@ ALL_CHECKS = [
     check_div_exact,
     check_scalar_nodes,
     check_cg_distinct_eigenvalues,
+    check_cg_one_reduction_matches_cg,
     check_tail_lengths,
     check_cg_store_then_load,
     check_special_values,

@@ -88,3 +88,51 @@ def test_unfused_oracle_is_immune_to_fma_contraction(tmp_path):
     out = str(tmp_path / "libfma.so")
     subprocess.run(["gcc", *cflags, *extra, "-o", out, SRC, "-lm"], check=True)
     assert _pins_fail(out) is None
+
+
+@pytest.mark.parametrize("mistake", ["alpha_sign", "beta_inverted", "s_uses_new_r"])
+def test_one_reduction_cg_mistakes_are_caught(monkeypatch, mistake):
+    """Plausible mistakes in the one-reduction CG recurrence (a sign in the
+    alpha denominator, beta upside down, the s update reading the updated
+    residual) must fail its pins."""
+    import numpy as np
+    op = oracle_pins
+    step = list(op.CGC_STEP)
+    if mistake == "s_uses_new_r":
+        # the x and r updates before the p and s updates
+        step = [("VEC", 4), ("DSCAL", 0), ("VEC", 1), ("SMUL", 0), ("ADD", 0), ("STORE", 1)] + \
+            op._CGC_TAIL[:12] + \
+            [("VEC", 0), ("VEC", 4), ("MUL", 0), ("DSCAL", 0), ("VEC", 2), ("SMUL", 0), ("ADD", 0), ("STORE", 2)] + \
+            op._CGC_TAIL[12:]
+
+    def mutant(evalp, d, b, x0, iters):
+        n = d.shape[0]
+        dt = d.dtype.type
+        p, s, r = np.zeros(n, d.dtype), np.zeros(n, d.dtype), np.zeros(n, d.dtype)
+        x = x0.copy()
+        vecs = [d, p, s, x, r, b]
+        hist = list(evalp(op.CGC_START, vecs, []))
+        alpha = None
+        for k in range(iters):
+            g, dl = dt(hist[2 * k]), dt(hist[2 * k + 1])
+            if k == 0:
+                alpha = g / dl
+                out = evalp(op.CGC_FIRST, vecs, [0.0, float(alpha)])
+            else:
+                beta = g / dt(hist[2 * k - 2])
+                if mistake == "beta_inverted":
+                    beta = dt(hist[2 * k - 2]) / g
+                den = dl + beta * g / alpha if mistake == "alpha_sign" else dl - beta * g / alpha
+                alpha = g / den
+                out = evalp(step, vecs, [float(beta), float(alpha)])
+            hist.extend(out)
+        return x, hist
+
+    monkeypatch.setattr(op, "cg_diagonal_one_reduction", mutant)
+    caught = 0
+    for check in (op.check_cg_distinct_eigenvalues, op.check_cg_one_reduction_matches_cg):
+        try:
+            check(oracle._LIB)
+        except AssertionError:
+            caught += 1
+    assert caught >= 1, mistake
