@@ -867,6 +867,12 @@ def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> 
         passes = 4 + 4 + 6 + 11 * (iters - 1)
         abytes = passes * es * n
         h_f, h_u = rho.cpu().numpy(), rho_u.cpu().numpy()
+        # the one-reduction recurrence in one cooperative launch: start (reads
+        # b, d, x; writes r) + first pass (reads d, r, x; writes p, s, x, r)
+        # + 9 vectors per later iteration
+        rho_c = torch.zeros(2 * iters + 2, dtype=torch.float64, device="cuda")
+        ms_c = timed(lambda: salt.salt_cg_diag(d, b, x, r, p, q, iters, rho_c, one_reduction=True))
+        cbytes = (4 + 7 + 9 * (iters - 1)) * es * n
         out[dt] = {"n": n, "iters": iters, "ms_fused": round(ms_f, 3), "ms_unfused": round(ms_u, 3),
                    "ms_per_iter_fused": round(ms_f / iters, 4),
                    "gbs_fused": round(abytes / (ms_f * 1e-3) / 1e9, 1),
@@ -874,7 +880,10 @@ def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> 
                    "speedup": round(ms_u / ms_f, 3),
                    "launches_fused": 1 + 2 * iters, "launches_unfused": 1 + 6 * iters, "tuned": tuned,
                    "rel_residual": float(np.sqrt(h_f[-1] / h_f[0])),
-                   "rho_rel_diff_fused_vs_unfused": float(abs(h_f[-1] - h_u[-1]) / h_f[-1])}
+                   "rho_rel_diff_fused_vs_unfused": float(abs(h_f[-1] - h_u[-1]) / h_f[-1]),
+                   "one_reduction": {"ms": round(ms_c, 3), "gbs": round(cbytes / (ms_c * 1e-3) / 1e9, 1),
+                                     "speedup_vs_fused": round(ms_f / ms_c, 3),
+                                     "rel_residual": float(np.sqrt(rho_c[-2].item() / rho_c[0].item()))}}
         del d, b, x, r, p, q, vecs
         torch.cuda.empty_cache()
     return out
@@ -963,7 +972,9 @@ def cg_latency_measure(torch, salt, sizes=(1 << 14, 1 << 17, 1 << 20, 1 << 24), 
                        reps: int = 3) -> dict:
     """Microseconds per CG iteration, launch-per-pass (salt_cg_diag: two fused
     launches per iteration) against one cooperative launch with grid
-    barriers (salt_cg_diag_persistent), for sizes where launches matter."""
+    barriers (salt_cg_diag_persistent: two barriers per iteration; and
+    salt_cg_diag_one_reduction: one pass and one barrier per iteration), for
+    sizes where launches matter."""
     import numpy as np
 
     stream = torch.cuda.current_stream()
@@ -975,9 +986,10 @@ def cg_latency_measure(torch, salt, sizes=(1 << 14, 1 << 17, 1 << 20, 1 << 24), 
             salt.salt_fill_uniform(d, 31)
             d.add_(1.0).mul_(3.5).add_(1.0)
             salt.salt_fill_uniform(b, 32)
-            rho = torch.zeros(2 * iters + 1, dtype=torch.float64, device="cuda")
+            rho = torch.zeros(2 * iters + 2, dtype=torch.float64, device="cuda")
             row = {"n": n}
-            for label, pers in (("launch_per_pass_us", False), ("persistent_us", True)):
+            for label, kw in (("launch_per_pass_us", {}), ("persistent_us", {"persistent": True}),
+                              ("one_reduction_us", {"one_reduction": True})):
                 ts = []
                 for _ in range(reps + 1):
                     x.zero_()
@@ -985,12 +997,13 @@ def cg_latency_measure(torch, salt, sizes=(1 << 14, 1 << 17, 1 << 20, 1 << 24), 
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    salt.salt_cg_diag(d, b, x, r, p, q, iters, rho, persistent=pers)
+                    salt.salt_cg_diag(d, b, x, r, p, q, iters, rho, **kw)
                     e1.record(stream)
                     torch.cuda.synchronize()
                     ts.append(e0.elapsed_time(e1))
                 row[label] = round(float(np.median(ts[1:])) * 1e3 / iters, 2)
             row["speedup"] = round(row["launch_per_pass_us"] / row["persistent_us"], 2)
+            row["speedup_one_reduction"] = round(row["launch_per_pass_us"] / row["one_reduction_us"], 2)
             rows.append(row)
             del d, b, x, r, p, q
         out[dt] = rows

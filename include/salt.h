@@ -255,6 +255,28 @@ salt_status salt_cg_diag(int32_t dtype, int64_t n, const void* d, const void* b,
 salt_status salt_cg_diag_persistent(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r,
                                     void* p, void* q, int32_t iters, double* rho, void* stream);
 
+/* Conjugate gradients for diag(d) x = b with ONE reduction phase per
+ * iteration (Chronopoulos and Gear's recurrence), in one cooperative launch
+ * with one grid barrier per iteration (salt_cg_diag_persistent has two).
+ * Each iteration is one pass over the elements:
+ *   p = r + beta p,  s = d o r + beta s   (s = A p in exact arithmetic)
+ *   x = x + alpha p, r = r - alpha s
+ *   gamma = r . r,   delta = (d o r) . r  of the new residual
+ * with beta = gamma_k / gamma_{k-1} and alpha_k = gamma_k / (delta_k -
+ * beta_k gamma_k / alpha_{k-1}) (alpha_0 = gamma_0 / delta_0), every scalar
+ * node computed in the vectors' precision from the totals rounded to it.
+ * In exact arithmetic the iterates are those of salt_cg_diag; in floating
+ * point they differ by rounding.  It moves 9 vectors per iteration (reads
+ * d, r, x, p, s; writes p, s, x, r) against 11 for the two-pass form.
+ *   d, b, x, r, p as salt_cg_diag; s the work vector in salt_cg_diag's q slot
+ *   rho   device array of >= 2 * iters + 2 doubles: rho[0] = gamma_0 (the
+ *         squared residual norm of x's start), rho[1] = delta_0, then
+ *         rho[2k+2] = gamma_{k+1}, rho[2k+3] = delta_{k+1}
+ * Launch, residency, bounded barriers and errors as salt_cg_diag_persistent.
+ * Not in the paper. */
+salt_status salt_cg_diag_one_reduction(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r,
+                                       void* p, void* s, int32_t iters, double* rho, void* stream);
+
 /* salt_explain -- host only (no GPU): the program the kernels evaluate for
  * `prog`, after its scalar subexpressions are hoisted, with the values of
  * the scalar slots.  Not part of the paper; an inspection aid.

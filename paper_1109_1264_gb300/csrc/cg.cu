@@ -106,6 +106,48 @@ __device__ bool grid_sum(double v, double* partials, int slot, unsigned long lon
   return true;
 }
 
+// Two block sums written to partials[slot0 * G + block] and
+// partials[(slot0 + 1) * G + block], then ONE barrier, then every block adds
+// each set of G partials in block order (the same fixed-order tree as
+// grid_sum, so every block holds the same totals).
+__device__ bool grid_sum2(double v0, double v1, double* partials, int slot0, unsigned long long* counter,
+                          unsigned* status, unsigned long long target, double* smem, double* out0, double* out1) {
+  const double b0 = block_sum<double>(v0, smem);
+  const double b1 = block_sum<double>(v1, smem);
+  if (threadIdx.x == 0) {
+    partials[(size_t)slot0 * gridDim.x + blockIdx.x] = b0;
+    partials[(size_t)(slot0 + 1) * gridDim.x + blockIdx.x] = b1;
+  }
+  if (!grid_barrier(counter, status, target)) return false;
+  const volatile double* part0 = (const volatile double*)partials + (size_t)slot0 * gridDim.x;
+  const volatile double* part1 = part0 + gridDim.x;
+  if (gridDim.x <= 32) {
+    __shared__ double s_tot[2];
+    if (threadIdx.x == 0) {
+      double a0 = 0.0, a1 = 0.0;
+      for (unsigned k = 0; k < gridDim.x; ++k) {
+        a0 += part0[k];
+        a1 += part1[k];
+      }
+      s_tot[0] = a0;
+      s_tot[1] = a1;
+    }
+    __syncthreads();
+    *out0 = s_tot[0];
+    *out1 = s_tot[1];
+    __syncthreads();  // s_tot is read before the next call overwrites it
+    return true;
+  }
+  double a0 = 0.0, a1 = 0.0;
+  for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+    a0 += part0[k];
+    a1 += part1[k];
+  }
+  *out0 = block_sum<double>(a0, smem);
+  *out1 = block_sum<double>(a1, smem);
+  return true;
+}
+
 // W consecutive elements of one operand: one 16-byte access when W > 1.
 template <typename T, int W>
 __device__ __forceinline__ void load_w(T (&v)[W], const T* src) {
@@ -174,6 +216,49 @@ __device__ __forceinline__ void pass2_w(const CgParams<T>& p, int64_t j, T alpha
     r[e] = Arith<T>::sub(r[e], Arith<T>::mul(alpha, q[e]));
     acc.add_prod(r[e], r[e]);
   }
+  store_w<T, W>(p.x + j, x);
+  store_w<T, W>(p.r + j, r);
+}
+
+// One-reduction CG (q holds s = A p): the start and the single pass.
+template <typename T, int W, class Acc>
+__device__ __forceinline__ void cgc_start_w(const CgParams<T>& p, int64_t j, Acc& ag, Acc& ad) {
+  T b[W], d[W], x[W], r[W];
+  load_w<T, W>(b, p.b + j);
+  load_w<T, W>(d, p.d + j);
+  load_w<T, W>(x, p.x + j);
+#pragma unroll
+  for (int e = 0; e < W; ++e) {
+    r[e] = Arith<T>::sub(b[e], Arith<T>::mul(d[e], x[e]));
+    ag.add_prod(r[e], r[e]);
+    ad.add_prod(Arith<T>::mul(d[e], r[e]), r[e]);
+  }
+  store_w<T, W>(p.r + j, r);
+}
+
+template <typename T, int W, class Acc>
+__device__ __forceinline__ void cgc_pass_w(const CgParams<T>& p, int64_t j, bool first, T beta, T alpha, Acc& ag,
+                                           Acc& ad) {
+  T d[W], r[W], pv[W], sv[W], x[W];
+  load_w<T, W>(d, p.d + j);
+  load_w<T, W>(r, p.r + j);
+  load_w<T, W>(x, p.x + j);
+  if (!first) {
+    load_w<T, W>(pv, p.p + j);
+    load_w<T, W>(sv, p.q + j);
+  }
+#pragma unroll
+  for (int e = 0; e < W; ++e) {
+    const T dr = Arith<T>::mul(d[e], r[e]);
+    pv[e] = first ? r[e] : Arith<T>::add(r[e], Arith<T>::mul(beta, pv[e]));
+    sv[e] = first ? dr : Arith<T>::add(dr, Arith<T>::mul(beta, sv[e]));
+    x[e] = Arith<T>::add(x[e], Arith<T>::mul(alpha, pv[e]));
+    r[e] = Arith<T>::sub(r[e], Arith<T>::mul(alpha, sv[e]));
+    ag.add_prod(r[e], r[e]);
+    ad.add_prod(Arith<T>::mul(d[e], r[e]), r[e]);
+  }
+  store_w<T, W>(p.p + j, pv);
+  store_w<T, W>(p.q + j, sv);
   store_w<T, W>(p.x + j, x);
   store_w<T, W>(p.r + j, r);
 }
@@ -247,10 +332,78 @@ __global__ void __launch_bounds__(kCgBlock) cg_persistent_kernel(const CgParams<
     rho = rho_next;
   }
 }
+// Conjugate gradients with one reduction phase per iteration (Chronopoulos
+// and Gear): each iteration is one pass -- p = r + beta p, s = d o r +
+// beta s, x = x + alpha p, r = r - alpha s, and gamma = r.r, delta =
+// (d o r).r of the new residual -- and one grid barrier; every block then
+// computes beta = gamma / gamma_prev and alpha = gamma / (delta - beta gamma
+// / alpha_prev) in T from the totals rounded to T.  The partials of
+// consecutive iterations alternate between slots {0, 1} and {2, 3}, so a
+// block that has moved on never overwrites sums another block still reads.
+// History: rho[0] = gamma_0, rho[1] = delta_0, rho[2k+2] = gamma_{k+1},
+// rho[2k+3] = delta_{k+1}.
+template <typename T>
+__global__ void __launch_bounds__(kCgBlock) cg_one_reduction_kernel(const CgParams<T> p, int vec) {
+  using Acc = typename AccOf<T>::type;
+  constexpr int VW = 16 / (int)sizeof(T);
+  __shared__ double smem[kMaxBlock];
+  const int64_t n = p.n;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const unsigned long long G = gridDim.x;
+  unsigned long long target = 0;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+
+  Acc ag, ad;
+#define SALT_CGC_START(W, J) cgc_start_w<T, W>(p, J, ag, ad)
+  SALT_CG_EACH(SALT_CGC_START)
+#undef SALT_CGC_START
+  double gamma = 0.0, delta = 0.0;
+  target += G;
+  if (!grid_sum2(ag.value(), ad.value(), p.partials, 0, p.counter, p.status, target, smem, &gamma, &delta)) {
+    if (lead) p.rho[0] = NAN;
+    return;
+  }
+  if (lead) {
+    p.rho[0] = gamma;
+    p.rho[1] = delta;
+  }
+  T alpha = T(0), beta = T(0);
+  double gamma_prev = 0.0;
+  for (int k = 0; k < p.iters; ++k) {
+    const bool first = k == 0;
+    const T g = (T)gamma, dl = (T)delta;
+    if (first) {
+      alpha = Arith<T>::div(g, dl);
+    } else {
+      beta = Arith<T>::div(g, (T)gamma_prev);
+      alpha = Arith<T>::div(g, Arith<T>::sub(dl, Arith<T>::div(Arith<T>::mul(beta, g), alpha)));
+    }
+    Acc bg, bd;
+#define SALT_CGC_PASS(W, J) cgc_pass_w<T, W>(p, J, first, beta, alpha, bg, bd)
+    SALT_CG_EACH(SALT_CGC_PASS)
+#undef SALT_CGC_PASS
+    double gn = 0.0, dn = 0.0;
+    target += G;
+    if (!grid_sum2(bg.value(), bd.value(), p.partials, (k & 1) ? 0 : 2, p.counter, p.status, target, smem, &gn,
+                   &dn)) {
+      if (lead) p.rho[0] = NAN;
+      return;
+    }
+    if (lead) {
+      p.rho[2 * k + 2] = gn;
+      p.rho[2 * k + 3] = dn;
+    }
+    gamma_prev = gamma;
+    gamma = gn;
+    delta = dn;
+  }
+}
 #undef SALT_CG_EACH
 
 template <typename T>
-salt_status launch_cg(int64_t n, void* const* v, int32_t iters, double* rho, cudaStream_t s) {
+salt_status launch_cg(int64_t n, void* const* v, int32_t iters, double* rho, cudaStream_t s,
+                      bool one_reduction) {
   double* partials = nullptr;
   unsigned* words = nullptr;
   int cap = 0;
@@ -259,13 +412,15 @@ salt_status launch_cg(int64_t n, void* const* v, int32_t iters, double* rho, cud
   int dev = 0, sms = 0;
   st = current_device(&dev, &sms);
   if (st != SALT_OK) return st;
+  const void* kern = one_reduction ? (const void*)cg_one_reduction_kernel<T> : (const void*)cg_persistent_kernel<T>;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_persistent_kernel<T>, kCgBlock, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kCgBlock, 0);
   if (e != cudaSuccess || per_sm < 1) return report_error(SALT_ERR_CUDA, "occupancy of the CG kernel");
   // one block per 4 tiles of the block's width, at most all resident blocks
   int64_t want = (n + 4 * kCgBlock - 1) / (4 * kCgBlock);
   int64_t cap_blocks = (int64_t)sms * per_sm;
-  if (cap_blocks > cap / 2) cap_blocks = cap / 2;  // two partial slots per block
+  const int slots = one_reduction ? 4 : 2;  // partial slots per block
+  if (cap_blocks > cap / slots) cap_blocks = cap / slots;
   const int grid = (int)(want < 1 ? 1 : (want < cap_blocks ? want : cap_blocks));
   // words[0] is the reduction ticket; words[1] = status, words[2..3] = the
   // 64-bit barrier counter (8-byte aligned: the slot is 256-byte aligned)
@@ -276,7 +431,7 @@ salt_status launch_cg(int64_t n, void* const* v, int32_t iters, double* rho, cud
   int vec = 1;
   for (int k = 0; k < 6; ++k) vec = vec && ((uintptr_t)v[k] % 16 == 0);
   void* args[] = {&prm, &vec};
-  e = cudaLaunchCooperativeKernel((const void*)cg_persistent_kernel<T>, dim3(grid), dim3(kCgBlock), args, 0, s);
+  e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kCgBlock), args, 0, s);
   count_launch();
   if (e != cudaSuccess)
     return report_error(SALT_ERR_CUDA, std::string("cooperative CG launch: ") + cudaGetErrorString(e));
@@ -296,5 +451,17 @@ extern "C" salt_status salt_cg_diag_persistent(int32_t dtype, int64_t n, const v
   const cudaStream_t s = (cudaStream_t)stream;
   salt_status st = cg_validate(dtype, n, vecs, iters, rho, s);
   if (st != SALT_OK) return st;
-  return dtype == SALT_F32 ? launch_cg<float>(n, vecs, iters, rho, s) : launch_cg<double>(n, vecs, iters, rho, s);
+  return dtype == SALT_F32 ? launch_cg<float>(n, vecs, iters, rho, s, false)
+                           : launch_cg<double>(n, vecs, iters, rho, s, false);
+}
+
+extern "C" salt_status salt_cg_diag_one_reduction(int32_t dtype, int64_t n, const void* d, const void* b, void* x,
+                                                  void* r, void* p, void* s_, int32_t iters, double* rho,
+                                                  void* stream) {
+  void* vecs[6] = {const_cast<void*>(d), p, s_, x, r, const_cast<void*>(b)};
+  const cudaStream_t s = (cudaStream_t)stream;
+  salt_status st = cg_validate(dtype, n, vecs, iters, rho, s);
+  if (st != SALT_OK) return st;
+  return dtype == SALT_F32 ? launch_cg<float>(n, vecs, iters, rho, s, true)
+                           : launch_cg<double>(n, vecs, iters, rho, s, true);
 }

@@ -25,7 +25,8 @@ MAX_PROG, MAX_VECS, MAX_SCALS, MAX_STACK, MAX_REDS, MAX_DSCALS = 32, 8, 8, 8, 4,
 EXPORTS = ["salt_version", "salt_status_str", "salt_last_error", "salt_check_program", "salt_eval",
            "salt_axpby", "salt_dot", "salt_nrm2", "salt_fill_uniform", "salt_release_workspaces",
            "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_staged_timeouts",
-           "salt_dot_noalloc", "salt_eval_strided", "salt_eval_ex", "salt_explain", "salt_cg_diag", "salt_cg_diag_persistent"]
+           "salt_dot_noalloc", "salt_eval_strided", "salt_eval_ex", "salt_explain", "salt_cg_diag", "salt_cg_diag_persistent",
+           "salt_cg_diag_one_reduction"]
 
 
 class Insn(ctypes.Structure):
@@ -80,6 +81,7 @@ def _load() -> ctypes.CDLL:
                                ctypes.POINTER(i32), ctypes.POINTER(i32)]),
         "salt_cg_diag": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp]),
         "salt_cg_diag_persistent": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp]),
+        "salt_cg_diag_one_reduction": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -254,15 +256,21 @@ def salt_explain(prog, nvecs: int, scalars=(), dtype: int = F64, dvals=()):
     return hp, [slots[i] for i in range(nslots.value)], bool(comp.value)
 
 
-def salt_cg_diag(d, b, x, r, p, q, iters: int, rho, stream=None, persistent: bool = False) -> None:
+def salt_cg_diag(d, b, x, r, p, q, iters: int, rho, stream=None, persistent: bool = False,
+                 one_reduction: bool = False) -> None:
     """``iters`` CG iterations for diag(d) x = b, scalars on the device;
     ``rho`` (float64 CUDA tensor, >= 2*iters + 1 entries) receives the
     history rho_0, (p.q)_0, rho_1, ...  ``persistent``: one cooperative
-    launch (salt_cg_diag_persistent)."""
+    launch (salt_cg_diag_persistent).  ``one_reduction``: the one-reduction
+    recurrence in one cooperative launch (salt_cg_diag_one_reduction; ``q``
+    holds s, ``rho`` >= 2*iters + 2 entries: gamma_0, delta_0, gamma_1, ...)."""
     vs = [d, b, x, r, p, q]
     _contig(vs)
     dt = _common_dtype(vs)
-    fn = lib.salt_cg_diag_persistent if persistent else lib.salt_cg_diag
+    if one_reduction:
+        fn = lib.salt_cg_diag_one_reduction
+    else:
+        fn = lib.salt_cg_diag_persistent if persistent else lib.salt_cg_diag
     _check(fn(dt, _n_of(vs), *[_ptr(v) for v in vs], int(iters), _ptr(rho), _stream_ptr(stream)))
 
 

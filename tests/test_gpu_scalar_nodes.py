@@ -306,3 +306,55 @@ def test_cg_persistent(saltlib, cuda_dev, dt):
         assert abs(g[0] - gl[0]) <= 2 * TOL[dt] * gl[0] + 1e-300
         if iters:
             assert np.linalg.norm(xg - xl) <= (1e-10 if dt == np.float64 else 1e-4) * max(np.linalg.norm(xl), 1.0)
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_cg_one_reduction(saltlib, cuda_dev, dt):
+    """salt_cg_diag_one_reduction (one pass and one grid barrier per
+    iteration): its start gamma_0 and last gamma equal r.r of the start and
+    returned residuals within the reduction tolerance; after 4 iterations on
+    4 distinct eigenvalues it reaches the solution; its iterates agree with
+    the oracle's one-reduction CG (same recurrence; the scalars differ only
+    through the reductions' rounding) and with the two-pass Hestenes-Stiefel
+    form on the GPU to the propagated rounding."""
+    from oracle_pins import cg_diagonal_one_reduction
+    s = saltlib
+    rng = np.random.default_rng(41)
+    for n, iters in ((0, 3), (1, 1), (999, 4), (4096, 0), ((1 << 20) + 5, 4), (70001, 9)):
+        if iters == 9:
+            d = rng.uniform(1.0, 4.0, n).astype(dt)
+        else:
+            d = rng.choice([1.0, 2.0, 5.0, 8.0], n).astype(dt)
+        b = rng.uniform(-1, 1, n).astype(dt)
+        x0 = rng.uniform(-3, 3, n).astype(dt)
+        td, tb, tx = (torch.from_numpy(v.copy()).to(cuda_dev) for v in (d, b, x0))
+        tr, tp, ts = (torch.zeros(n, dtype=TDT[dt], device=cuda_dev) for _ in range(3))
+        rho = torch.full((2 * iters + 2,), float("nan"), dtype=torch.float64, device=cuda_dev)
+        s.salt_cg_diag(td, tb, tx, tr, tp, ts, iters, rho, one_reduction=True)
+        td2, tb2, tx2 = (torch.from_numpy(v.copy()).to(cuda_dev) for v in (d, b, x0))
+        tr2, tp2, tq2 = (torch.zeros(n, dtype=TDT[dt], device=cuda_dev) for _ in range(3))
+        rho2 = torch.full((2 * iters + 1,), float("nan"), dtype=torch.float64, device=cuda_dev)
+        s.salt_cg_diag(td2, tb2, tx2, tr2, tp2, tq2, iters, rho2)
+        torch.cuda.synchronize()
+        xg, rg, g = tx.cpu().numpy().astype(np.float64), tr.cpu().numpy(), rho.cpu().numpy()
+        xl = tx2.cpu().numpy().astype(np.float64)
+        if n == 0:
+            assert xg.shape == (0,) and g[0] == 0.0
+            continue
+        assert not np.any(np.isnan(g)), g
+        r0 = b.astype(np.float64) - d.astype(np.float64) * x0.astype(np.float64)
+        assert abs(g[0] - float(r0 @ r0)) <= 1e-5 * float(r0 @ r0) + 1e-300
+        assert abs(g[-2] - exact.exact_sumsq(rg)) <= TOL[dt] * exact.exact_sumsq(rg) + 1e-300
+        if iters == 4 and n > 1:
+            xs = b.astype(np.float64) / d.astype(np.float64)
+            tol = 1e-11 if dt == np.float64 else 1e-4
+            assert np.linalg.norm(xg - xs) / np.linalg.norm(xs) < tol
+        if iters:
+            xo, ho = cg_diagonal_one_reduction(lambda pr, vs, ds: oracle.eval_program(pr, vs, dscalars=ds), d, b,
+                                               x0, iters)
+            scale = max(np.linalg.norm(xo.astype(np.float64)), 1.0)
+            tx_ = 1e-10 if dt == np.float64 else 1e-4
+            assert np.linalg.norm(xg - xo) <= tx_ * scale, (n, iters)
+            assert np.linalg.norm(xg - xl) <= tx_ * max(np.linalg.norm(xl), 1.0), (n, iters)
+            for j in range(iters + 1):
+                assert abs(g[2 * j] - ho[2 * j]) <= tx_ * ho[0] + 1e-300, (n, iters, j)
