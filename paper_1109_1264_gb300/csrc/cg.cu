@@ -17,6 +17,10 @@
 // NaN into rho[0] (block 0) and returns, and every other block returns at
 // its next barrier, so a launch that cannot make progress ends instead of
 // hanging.  The cooperative launch guarantees that all blocks are resident.
+//
+// salt_cg_diag_one_reduction uses the same launch, barrier and reductions
+// for Chronopoulos and Gear's recurrence: one pass and one barrier per
+// iteration (cg_one_reduction_kernel below).
 #include <cuda_runtime.h>
 
 #include <cmath>
