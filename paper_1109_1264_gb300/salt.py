@@ -256,6 +256,25 @@ def salt_explain(prog, nvecs: int, scalars=(), dtype: int = F64, dvals=()):
     return hp, [slots[i] for i in range(nslots.value)], bool(comp.value)
 
 
+def _check_rho(rho, iters: int, one_reduction: bool) -> None:
+    """The history buffer the CG entry points write: the library is given
+    only its address, so its length, dtype and placement are checked here,
+    before the call (a short buffer would be written past its end)."""
+    need = 2 * iters + (2 if one_reduction else 1)
+    if rho is None:
+        raise SaltError(ERR_ARG, "SALT_ERR_ARG", "rho is None")
+    import torch
+    if rho.dtype != torch.float64:
+        raise SaltError(ERR_DTYPE, "SALT_ERR_DTYPE", f"rho must be float64, not {rho.dtype}")
+    if rho.numel() < need:
+        raise SaltError(ERR_ARG, "SALT_ERR_ARG",
+                        f"rho has {rho.numel()} entries; {iters} iterations write {need}")
+    if not rho.is_contiguous():
+        raise SaltError(ERR_ARG, "SALT_ERR_ARG", "rho must be contiguous")
+    if not rho.is_cuda:
+        raise SaltError(ERR_ARG, "SALT_ERR_ARG", "rho must be a CUDA tensor")
+
+
 def salt_cg_diag(d, b, x, r, p, q, iters: int, rho, stream=None, persistent: bool = False,
                  one_reduction: bool = False) -> None:
     """``iters`` CG iterations for diag(d) x = b, scalars on the device;
@@ -267,6 +286,7 @@ def salt_cg_diag(d, b, x, r, p, q, iters: int, rho, stream=None, persistent: boo
     vs = [d, b, x, r, p, q]
     _contig(vs)
     dt = _common_dtype(vs)
+    _check_rho(rho, int(iters), one_reduction)
     if one_reduction:
         fn = lib.salt_cg_diag_one_reduction
     else:

@@ -188,3 +188,29 @@ def test_cg_argument_errors(saltlib, entry):
     assert fn(1, 100, v[0], v[1], v[2], v[3], v[2] + 8, v[5], 4, rho, None) == s.ERR_ALIAS  # p overlaps x
     assert fn(1, 100, *v, 4, v[3] + 16, None) == s.ERR_ALIAS      # rho inside r
     assert fn(1, 100, *v, 4, rho, None) == s.ERR_CUDA             # valid: fails only for want of a GPU
+
+
+@pytest.mark.parametrize("one_reduction", [False, True])
+def test_cg_binding_checks_rho_before_the_call(saltlib, one_reduction):
+    """The C entry points receive only rho's address, so the binding checks
+    its length (2*iters + 1 entries, 2*iters + 2 for the one-reduction form),
+    dtype, layout and placement before calling: a buffer one entry short is
+    rejected, never written past its end."""
+    import torch
+    s = saltlib
+    n, iters = 64, 5
+    vecs = [torch.zeros(n, dtype=torch.float64) for _ in range(6)]
+    need = 2 * iters + (2 if one_reduction else 1)
+    with pytest.raises(s.SaltError) as e:
+        s.salt_cg_diag(*vecs, iters, torch.zeros(need - 1, dtype=torch.float64), one_reduction=one_reduction)
+    assert e.value.status == s.ERR_ARG and f"write {need}" in e.value.message
+    with pytest.raises(s.SaltError) as e:
+        s.salt_cg_diag(*vecs, iters, torch.zeros(need, dtype=torch.float32), one_reduction=one_reduction)
+    assert e.value.status == s.ERR_DTYPE
+    with pytest.raises(s.SaltError) as e:
+        s.salt_cg_diag(*vecs, iters, torch.zeros(2 * need, dtype=torch.float64)[::2], one_reduction=one_reduction)
+    assert "contiguous" in e.value.message
+    # the right length on the host: rejected for its placement, still before the call
+    with pytest.raises(s.SaltError) as e:
+        s.salt_cg_diag(*vecs, iters, torch.zeros(need, dtype=torch.float64), one_reduction=one_reduction)
+    assert "CUDA tensor" in e.value.message
