@@ -88,8 +88,77 @@ def exact_sumsq(x: np.ndarray) -> float:
 
 
 def abs_dot(x: np.ndarray, y: np.ndarray) -> float:
-    """sum_i |x_i*y_i| (the condition scale of a dot product), exactly rounded."""
-    return exact_sum(np.abs(_exact_products(np.asarray(x), np.asarray(y))))
+    """sum_i |x_i*y_i| (the condition scale of a dot product), exactly rounded.
+    Taken as the exact dot of |x| and |y|: the absolute values of Dekker's
+    partial products would over-count, since the two halves of a split
+    value may differ in sign."""
+    return exact_dot(np.abs(np.asarray(x)), np.abs(np.asarray(y)))
+
+
+class FixedPointDot:
+    """Exact dot product of two long vectors whose elements are integers
+    times one power of two, fed in pieces (so that n = 2^28 and beyond needs
+    no more host memory than one piece).
+
+    The counter-based inputs are such vectors: an FP64 value ``2 (h >> 11)
+    2^-53 - 1`` is ``a 2^-52`` with an integer |a| <= 2^52, an FP32 value
+    ``2 (h >> 40) 2^-24 - 1`` is ``a 2^-23`` with |a| <= 2^23.  Each integer
+    is split as ``a = a1 2^26 + a0`` (``a1 = floor(a / 2^26)``,
+    0 <= a0 < 2^26), so every partial product of the four ``ai bj`` has
+    magnitude below 2^53 and a sum of 2^9 of them stays below 2^63: int64
+    arithmetic is exact.  Row sums are then combined in Python integers;
+    ``sum_i a_i b_i = S11 2^52 + (S10 + S01) 2^26 + S00`` exactly, and the
+    result is rounded once (Python's int -> float conversion is correctly
+    rounded) and scaled by ``2^-(fa + fb)``.  The sum of |a_i b_i| -- the
+    condition scale -- is formed the same way from |a|, |b|."""
+
+    ROW = 512
+
+    def __init__(self, frac_bits_x: int, frac_bits_y: int):
+        self.fx, self.fy = frac_bits_x, frac_bits_y
+        self.s = 0
+        self.sabs = 0
+
+    @staticmethod
+    def _integers(v: np.ndarray, frac_bits: int) -> np.ndarray:
+        a = np.ldexp(np.asarray(v, dtype=np.float64), frac_bits)
+        ai = a.astype(np.int64)
+        if not np.array_equal(ai.astype(np.float64), a) or np.any(np.abs(ai) > 2 ** 52):
+            raise ValueError("values are not integers times 2^-frac_bits with |integer| <= 2^52")
+        return ai
+
+    @classmethod
+    def _int_dot(cls, a: np.ndarray, b: np.ndarray) -> int:
+        pad = (-a.size) % cls.ROW
+        if pad:
+            a = np.concatenate([a, np.zeros(pad, np.int64)])
+            b = np.concatenate([b, np.zeros(pad, np.int64)])
+        a1, a0 = a >> 26, a & ((1 << 26) - 1)
+        b1, b0 = b >> 26, b & ((1 << 26) - 1)
+        tot = 0
+        for u, v, shift in ((a1, b1, 52), (a1, b0, 26), (a0, b1, 26), (a0, b0, 0)):
+            rows = (u * v).reshape(-1, cls.ROW).sum(axis=1)
+            tot += sum(int(r) for r in rows) << shift
+        return tot
+
+    def add(self, x: np.ndarray, y: np.ndarray) -> None:
+        a = self._integers(x, self.fx)
+        b = self._integers(y, self.fy)
+        if a.size != b.size:
+            raise ValueError("pieces of unequal length")
+        self.s += self._int_dot(a, b)
+        self.sabs += self._int_dot(np.abs(a), np.abs(b))
+
+    def _round(self, v: int) -> float:
+        return math.ldexp(float(v), -(self.fx + self.fy))
+
+    def value(self) -> float:
+        """sum x_i y_i of every piece added, rounded once to FP64."""
+        return self._round(self.s)
+
+    def abs_value(self) -> float:
+        """sum |x_i y_i|, rounded once to FP64."""
+        return self._round(self.sabs)
 
 
 def exact_nrm2(x: np.ndarray) -> float:
