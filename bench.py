@@ -474,6 +474,16 @@ def main():
     per_kernel = {}
     for i, (dt, name, _) in enumerate(steps):
         per_kernel[(dt, name)] = sum(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)) / args.steps
+    # the step's reduction results (judged in the CPU leg), and the same dot
+    # over the first 2^26 elements (after the timed region)
+    step_red = {}
+    for dt in DTYPES:
+        dot, nrm = loads[dt].red.cpu().tolist()
+        step_red[dt] = {"dot": dot, "nrm2": nrm}
+        if n > (1 << 26):
+            r26 = torch.zeros(1, dtype=torch.float64, device="cuda")
+            salt.salt_dot(loads[dt].a[:1 << 26], loads[dt].b[:1 << 26], r26)
+            step_red[dt]["dot_2e26"] = r26.item()
 
     ms_per_step = total_ms / args.steps
     value = whole_job_gbs(step_bytes, args.steps, world, total_ms)
@@ -502,7 +512,9 @@ def main():
     else:
         roof.update({"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                      "frac": round(hbm_frac, 4)})
-    roof["peak_kind"] = peak_kind
+    # the HBM peak is the measured copy rate; the FP64 peak is derived from
+    # unit counts and the clock (the live probe below gives a measured rate)
+    roof["peak_kind"] = "derived" if roof["bound"] == "alu" else peak_kind
     # the traffic figure belongs to the schedule (register-tiled or staged) the op ran
     tkey = f"{dop}_{ddt}"
     if dop in ("e", "axpby", "dot"):
@@ -537,34 +549,128 @@ def main():
     del loads
     steps = None
     torch.cuda.empty_cache()
-    if not args.no_batched:
-        result["batched"] = batched_measure(torch, salt, nitems=args.batched_items, fixed=args.batched_fixed)
-    if not args.no_served:
-        torch.cuda.empty_cache()
-        result["served"] = served_measure(salt)
-    result["config1_figure1"] = config1_measure(torch, salt)
+    samples = {"batched": [], "served": []}
     if not args.no_cg:
         torch.cuda.empty_cache()
         result["cg"] = cg_measure(torch, salt, log2n=args.cg_log2)
         result["cg"]["per_iteration_latency"] = cg_latency_measure(torch, salt)
+    if not args.no_batched:
+        torch.cuda.empty_cache()
+        result["batched"] = batched_measure(torch, salt, nitems=args.batched_items, fixed=args.batched_fixed,
+                                            collect=samples["batched"])
+    if not args.no_served:
+        torch.cuda.empty_cache()
+        result["served"] = served_measure(salt, collect=samples["served"])
+    result["config1_figure1"] = config1_measure(torch, salt)
+    probe = fp64_probe(torch, salt)
+    result["fp64_probe"] = probe
+    if roof["bound"] == "alu" and probe.get("gops"):
+        roof["probe_gops"] = probe["gops"]
+        roof["frac_vs_probe"] = round(roof["achieved"] * 1e3 / probe["gops"], 4)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         # The CPU-oracle leg: the oracle timed on the host, and the oracle's
         # exact references judging the GPU reductions' precision.
         result["cpu_baseline"] = cpu_baseline(1 << args.cpu_log2)
         torch.cuda.empty_cache()
-        result["cpu_baseline"]["precision_vs_exact"] = precision_measure(torch, salt)
+        prec = {"measure": "rel_value = |got - exact| / |exact| (the tolerance's measure); "
+                           "rel_scale = |got - exact| / sum|x_i y_i|",
+                "step_n2e28": step_precision(step_red, n, seed=rank)}
+        if samples["batched"]:
+            prec["batched_rho"] = batched_precision(samples["batched"])
+        if samples["served"]:
+            prec["served"] = served_precision(samples["served"])
+        prec["config3"] = precision_measure(torch, salt)
+        result["cpu_baseline"]["precision_vs_exact"] = prec
     if rank == 0:
+        result["summary"] = summary_of(result)
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096, fixed: bool = False) -> dict:
+def summary_of(r: dict) -> dict:
+    """The headline numbers of every leg in a compact object that the line
+    ends with: the step, batched vs plain, served saturation and p50 / p99
+    per load, Figure 1, the CG forms and the precision of every reduction."""
+    out = {"step_gbs": r["value"], "frac_of_measured_hbm": r.get("frac_of_measured_hbm"),
+           "roofline": {k: r["roofline"].get(k) for k in ("kernel", "bound", "frac", "hbm_frac", "frac_vs_probe")}}
+    if "e2e" in r:
+        out["e2e_gbs"] = r["e2e"]["value"]
+    b = r.get("batched")
+    if b:
+        out["batched"] = {dt: {"gbs": b[dt]["batched_gbs"], "plain_gbs": b[dt]["plain_gbs"],
+                               "ratio": b[dt]["ratio"]} for dt in DTYPES if dt in b}
+    sv = r.get("served")
+    if sv:
+        out["served"] = {"saturation_gbs": sv["saturation_gbs"], "vs_unbatched": sv["batched_vs_unbatched"],
+                         "p50_p99_us": {str(pt["load"]): [pt["p50_us"], pt["p99_us"]] for pt in sv["points"]}}
+    if "config1_figure1" in r:
+        c = r["config1_figure1"]
+        out["figure1_us"] = {k: c[k] for k in ("l2_warm_us", "l2_flushed_us") if k in c}
+    cg = r.get("cg")
+    if cg:
+        out["cg_gbs"] = {dt: {"two_pass": cg[dt]["gbs_fused"], "one_reduction": cg[dt]["one_reduction"]["gbs"]}
+                         for dt in DTYPES if dt in cg}
+    pv = r.get("cpu_baseline", {}).get("precision_vs_exact")
+    if pv:
+        worst = {}
+        for dt, row in pv.get("step_n2e28", {}).items():
+            worst[f"step_dot_{dt}"] = row["dot"]["rel_value"]
+            worst[f"step_nrm2_{dt}"] = row["nrm2"]["rel_value"]
+        for dt, row in pv.get("batched_rho", {}).items():
+            worst[f"batched_rho_{dt}"] = row["max_rel_value"]
+        for k, row in pv.get("served", {}).items():
+            worst[f"served_{k}"] = row["max_rel_value"]
+        out["precision_rel_value"] = {k: float(f"{v:.3g}") for k, v in worst.items()}
+    return out
+
+
+def fp64_probe(torch, salt, log2n: int = 26, reps: int = 5) -> dict:
+    """FP64 instruction rate through the library's own fused kernel: a
+    program of 14 FP64 nodes per element (t <- t o x + x, seven times from
+    t = x: 7 multiplies and 7 adds), compiled at run time, on n = 2^26
+    elements -- 16 bytes per element against 14 FP64 instructions, so the
+    FP64 pipe, not HBM, bounds it.  The measured denominator beside the
+    derived one."""
+    n = 1 << log2n
+    prog = [("VEC", 0)]
+    for _ in range(7):
+        prog += [("VEC", 0), ("MUL", 0), ("VEC", 0), ("ADD", 0)]
+    prog += [("STORE", 1)]
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    salt.salt_fill_uniform(x, key=977)
+    try:
+        salt.salt_set_jit(salt.JIT_ON)
+        for _ in range(3):
+            salt.salt_eval(prog, [x, y])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            salt.salt_eval(prog, [x, y])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+    except salt.SaltError as e:
+        return {"gops": None, "error": e.message[:200]}
+    finally:
+        salt.salt_set_jit(salt.JIT_OFF)
+    return {"gops": round(14 * n / (ms * 1e-3) / 1e9, 1), "ms": round(ms, 4), "n": n,
+            "program": "14 FP64 nodes per element (7 x (t*x + x)), 16 B per element, run-time compiled"}
+
+
+def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096, fixed: bool = False,
+                    collect: list | None = None) -> dict:
     """4096 CG-style updates (r <- r - alpha q; rho = r.r; p <- r + beta p),
     lengths log-uniform in [64, 2^20], in one persistent graph-replayed launch
-    (autotuned) versus 4096 plain per-call launches on one stream."""
+    (autotuned) versus 4096 plain per-call launches on one stream.  With
+    `collect`, a sample of items (their operands before one more launch and
+    the rho it returns) is appended for the CPU leg to judge."""
+    import numpy as np
+
     from paper_1109_1264_gb300 import inputs
     from paper_1109_1264_gb300.programs import PROG_CG
     lens = inputs.loguniform_lengths(0, nitems, 64, 1 << 20)
@@ -581,9 +687,10 @@ def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096, fixed: bool
         for k, buf in enumerate(bufs):
             salt.salt_fill_uniform(buf, inputs.vector_key(0, 0, k))
         b = salt.Batch(nitems)
+        slots = []
         for i in range(nitems):
             n = int(lens[i])
-            b.add(PROG_CG, [buf[offs[i]:offs[i] + n] for buf in bufs], list(ab[i]))
+            slots.append(b.add(PROG_CG, [buf[offs[i]:offs[i] + n] for buf in bufs], list(ab[i])))
         red = torch.zeros(nitems, dtype=torch.float64, device="cuda")
         nbytes = b.info()["bytes"]
         if fixed:  # the shape the autotuner picks on GB300 (for profiling runs)
@@ -608,6 +715,15 @@ def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096, fixed: bool
 
         ms_b = timed(lambda: b.launch(red), reps)
         ms_p = timed(lambda: b.launch_plain(red), max(3, reps // 4))
+        if collect is not None:
+            # the 4 longest items and 12 more spread over the table
+            pick = sorted(set(np.argsort(lens)[-4:].tolist()) | set(range(0, nitems, nitems // 12)))
+            before = {i: [buf[offs[i]:offs[i] + int(lens[i])].cpu().numpy() for buf in bufs] for i in pick}
+            b.launch(red)
+            redh = red.cpu().numpy()
+            for i in pick:
+                collect.append({"dt": dt, "item": i, "ab": list(ab[i]), "operands": before[i],
+                                "got": float(redh[slots[i]])})
         out[dt] = {"batched_gbs": round(nbytes / (ms_b * 1e-3) / 1e9, 1),
                    "plain_gbs": round(nbytes / (ms_p * 1e-3) / 1e9, 1),
                    "ratio": round(ms_p / ms_b, 2), "batched_ms": round(ms_b, 4), "plain_ms": round(ms_p, 4),
@@ -889,14 +1005,111 @@ def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> 
     return out
 
 
+def _errors(got: float, exact_value: float, scale: float) -> dict:
+    """Error of one reduction result: relative to its exact value (the
+    measure the tolerances are stated in) and relative to sum|x_i y_i|."""
+    err = abs(got - exact_value)
+    return {"rel_value": float(err / abs(exact_value)) if exact_value else float(err),
+            "rel_scale": float(err / scale) if scale else float(err)}
+
+
+def counter_dot_exact(kx: int, ky: int, n: int, npdt, offset: int = 0, piece: int = 1 << 22, offset_y=None):
+    """Exact sum x_i y_i and sum |x_i y_i| of counter-based vectors (keys kx,
+    ky, elements from `offset` (`offset_y` for y); the same key and offset
+    give the sum of squares), by the oracle's fixed-point exact dot on host
+    threads."""
+    oy = offset if offset_y is None else offset_y
+    import concurrent.futures as cf
+
+    from oracle import exact
+    from paper_1109_1264_gb300 import inputs
+    fb = 52 if npdt.__name__ == "float64" else 23
+
+    def one(lo):
+        m = min(piece, n - lo)
+        x = inputs.hash_uniform(kx, m, npdt, offset=offset + lo)
+        y = x if (ky, oy) == (kx, offset) else inputs.hash_uniform(ky, m, npdt, offset=oy + lo)
+        f = exact.FixedPointDot(fb, fb)
+        f.add(x, y)
+        return f
+
+    with cf.ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        parts = list(ex.map(one, range(0, n, piece)))
+    f = exact.FixedPointDot.combine(parts)
+    return f.value(), f.abs_value()
+
+
+def step_precision(step_red: dict, n: int, seed: int = 0) -> dict:
+    """The timed step's own reduction results (dot(a, b) and nrm2(c) of the
+    counter-based inputs, FP32 and FP64, n = 2^28) against their exact
+    values, and the same dot over the first 2^26 elements."""
+    import math
+
+    import numpy as np
+    out = {}
+    for dt, r in step_red.items():
+        npdt = np.float32 if dt == "f32" else np.float64
+        ka, kb, kc = seed * 16 + 1, seed * 16 + 2, seed * 16 + 3
+        ref, scale = counter_dot_exact(ka, kb, n, npdt)
+        sq, _ = counter_dot_exact(kc, kc, n, npdt)
+        nref = math.sqrt(sq)  # within one rounding of the exact norm
+        row = {"dot": _errors(r["dot"], ref, scale), "dot_cond": round(scale / abs(ref), 1),
+               "nrm2": _errors(r["nrm2"], nref, nref)}
+        if "dot_2e26" in r:
+            ref26, scale26 = counter_dot_exact(ka, kb, 1 << 26, npdt)
+            row["dot_n2e26"] = _errors(r["dot_2e26"], ref26, scale26)
+        out[dt] = row
+    return out
+
+
+def batched_precision(samples: list) -> dict:
+    """rho of the sampled batch items against the exact sum of squares of r
+    after the update, which the oracle recomputes from the operands."""
+    import oracle
+    from oracle import exact
+    from paper_1109_1264_gb300.programs import PROG_CG
+    worst = {}
+    for smp in samples:
+        want = [v.copy() for v in smp["operands"]]
+        oracle.eval_program(PROG_CG, want, smp["ab"])
+        ref = exact.exact_sumsq(want[0])
+        e = _errors(smp["got"], ref, ref)
+        w = worst.setdefault(smp["dt"], {"items": 0, "max_rel_value": 0.0})
+        w["items"] += 1
+        w["max_rel_value"] = max(w["max_rel_value"], e["rel_value"])
+    return worst
+
+
+def served_precision(samples: list) -> dict:
+    """Served dot and norm results against the exact values of the store
+    slices the requests read."""
+    import math
+
+    import numpy as np
+    worst = {}
+    for smp in samples:
+        npdt = np.float64 if smp["dt"] == "f64" else np.float32
+        (kx, ox), (ky, oy) = smp["operands"][0], smp["operands"][-1]
+        ref, scale = counter_dot_exact(kx, ky, smp["n"], npdt, offset=ox, offset_y=oy, piece=1 << 20)
+        if smp["shape"] == "nrm2":
+            ref = scale = math.sqrt(ref)
+        e = _errors(smp["got"], ref, scale)
+        w = worst.setdefault(f"{smp['shape']}_{smp['dt']}", {"requests": 0, "max_rel_value": 0.0,
+                                                             "max_rel_scale": 0.0})
+        w["requests"] += 1
+        w["max_rel_value"] = max(w["max_rel_value"], e["rel_value"])
+        w["max_rel_scale"] = max(w["max_rel_scale"], e["rel_scale"])
+    return worst
+
+
 def precision_measure(torch, salt, log2n: int = 26) -> dict:
     """The precision comparison of the dot product and norm: FP32 inputs of
     random sign and magnitudes 10^U(-3, 3), n = 2^26.  Errors of the
     compensated FP32 path (the default), the plain FP32 path (FP32
     accumulation and combination) and the FP64 path on the widened data,
-    relative to the exactly rounded value, beside the CPU oracle's own
-    sequential FP64 sum.  Part of the CPU-oracle leg (it uses the oracle's
-    exact references)."""
+    relative to the exactly rounded value and to sum|x_i y_i|, beside the CPU
+    oracle's own sequential FP64 sum.  Part of the CPU-oracle leg (it uses
+    the oracle's exact references)."""
     import numpy as np
 
     from oracle import exact
@@ -915,17 +1128,12 @@ def precision_measure(torch, salt, log2n: int = 26) -> dict:
     salt.salt_nrm2(tx.double(), out[5:6])
     comp, plain, wide, nc, npl, nw = out.cpu().tolist()
     odot, onrm = orc.dot(x, y), orc.nrm2(x)
-
-    def rel(v, r, sc):
-        return float(abs(v - r) / sc)
-
     return {"n": n, "data": "FP32, random sign x 10^U(-3,3), numpy default_rng(0)",
-            "error_measure": "|got - exact| / sum|x_i y_i| (dot), / exact (nrm2)",
-            "dot": {"compensated_f32": rel(comp, ref, scale), "plain_f32": rel(plain, ref, scale),
-                    "f64_widened": rel(wide, ref, scale), "cpu_oracle_sequential_f64": rel(odot, ref, scale),
-                    "relative_to_value_compensated_f32": float(abs(comp - ref) / abs(ref))},
-            "nrm2": {"compensated_f32": rel(nc, nref, nref), "plain_f32": rel(npl, nref, nref),
-                     "f64_widened": rel(nw, nref, nref), "cpu_oracle": rel(onrm, nref, nref)}}
+            "dot_cond": round(scale / abs(ref), 1),
+            "dot": {"compensated_f32": _errors(comp, ref, scale), "plain_f32": _errors(plain, ref, scale),
+                    "f64_widened": _errors(wide, ref, scale), "cpu_oracle_sequential_f64": _errors(odot, ref, scale)},
+            "nrm2": {"compensated_f32": _errors(nc, nref, nref), "plain_f32": _errors(npl, nref, nref),
+                     "f64_widened": _errors(nw, nref, nref), "cpu_oracle": _errors(onrm, nref, nref)}}
 
 
 def config1_measure(torch, salt, reps: int = 100) -> dict:
@@ -1010,7 +1218,17 @@ def cg_latency_measure(torch, salt, sizes=(1 << 14, 1 << 17, 1 << 20, 1 << 24), 
     return {"iters": iters, "rows": out}
 
 
-def served_measure(salt, count: int = 3000, seed: int = 0) -> dict:
+def store_place(seed: int, i: int, k: int, n: int, length: int, nstore: int, itemsize: int):
+    """(store vector, first element) that operand k of replayed request i
+    reads, by the placement rule salt_serve_replay_store documents."""
+    m64 = (1 << 64) - 1
+    key = (seed * 0x100000001B3 + i * 16 + k + 1) & m64
+    h = ((key * 0x9E3779B97F4A7C15) & m64) >> 11
+    o = h % (length - n + 1)
+    return (i * 5 + k) % nstore, o - o % (32 // itemsize)
+
+
+def served_measure(salt, count: int = 3000, seed: int = 0, collect: list | None = None) -> dict:
     """Poisson stream of requests over the 5 served shapes (d = a + (b - c),
     axpby, e, dot, nrm2), n log-uniform in [2^8, 2^24], 70% FP32 / 30% FP64.
     Inputs come from a resident store of counter-filled vectors (8 GiB: four
@@ -1047,6 +1265,19 @@ def served_measure(salt, count: int = 3000, seed: int = 0) -> dict:
     srv = salt.Server()
     try:
         _, wall, steps = saturation(srv, True)
+        if collect is not None:
+            # dot (shape 3) and norm (shape 4) results of one more saturated replay
+            _, red, _ = srv.replay(zeros, shapes, d32, lens, seed, store=store)
+            keys = [inputs.vector_key(seed + 1000, j, 0) for j in range(6)]
+            for shp in (3, 4):
+                for i in [int(i) for i in np.nonzero(shapes == shp)[0][:8]]:
+                    f64 = bool(is64[i])
+                    ops_ = []
+                    for k in range(2 if shp == 3 else 1):
+                        j, o = store_place(seed, i, k, int(lens[i]), slen, 2 if f64 else 4, 8 if f64 else 4)
+                        ops_.append((keys[4 + j] if f64 else keys[j], int(o)))
+                    collect.append({"dt": "f64" if f64 else "f32", "shape": "dot" if shp == 3 else "nrm2",
+                                    "n": int(lens[i]), "operands": ops_, "got": float(red[i])})
         sat_rps = count / (wall * 1e-6)
         sat_gbs = total_bytes / (wall * 1e-6) / 1e9
         points = []

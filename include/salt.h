@@ -349,11 +349,10 @@ salt_status salt_fill_uniform(int32_t dtype, int64_t n, uint64_t key, int64_t of
  * SALT_DEFAULT, but without any device allocation.  (The paper has no
  * counterpart: it is an interface for callers of this library.)
  * salt_dot's partial sums live in a workspace the library cudaMalloc's on the
- * first reducing call on a stream.  Callers that cannot allow that -- code
- * issuing work while its stream is captured into a CUDA graph, runtimes that
- * hand out all device memory from a fixed up-front reservation, loops that
- * cannot afford cudaMalloc's implicit device synchronisation -- use this entry
- * point instead.  Its scratch is a static device array of 32 KiB + 256 B that
+ * first reducing call on a stream.  Callers that cannot allow that -- runtimes
+ * that hand out all device memory from a fixed up-front reservation, loops
+ * that cannot afford cudaMalloc's implicit device synchronisation -- use this
+ * entry point instead.  Its scratch is a static device array of 32 KiB + 256 B that
  * every GPU loading the library holds until process exit; it never calls
  * cudaMalloc, cudaFree or any allocating routine.
  *   n      0 <= n <= 2^28 (268435456); larger n returns SALT_ERR_BUDGET

@@ -149,6 +149,18 @@ class FixedPointDot:
         self.s += self._int_dot(a, b)
         self.sabs += self._int_dot(np.abs(a), np.abs(b))
 
+    @classmethod
+    def combine(cls, parts: list["FixedPointDot"]) -> "FixedPointDot":
+        """One accumulator holding the sums of several (same scales), e.g.
+        pieces accumulated on separate threads."""
+        out = cls(parts[0].fx, parts[0].fy)
+        for f in parts:
+            if (f.fx, f.fy) != (out.fx, out.fy):
+                raise ValueError("accumulators of different scales")
+            out.s += f.s
+            out.sabs += f.sabs
+        return out
+
     def _round(self, v: int) -> float:
         return math.ldexp(float(v), -(self.fx + self.fy))
 

@@ -2,13 +2,13 @@
 //
 // salt_dot keeps its per-block partial sums in a workspace that the library
 // allocates with cudaMalloc on the first reducing call on a stream.  Some
-// callers cannot let a library allocate: code running while a stream is being
-// captured into a CUDA graph (cudaMalloc is not allowed inside a capture),
-// runtimes that reserve all device memory up front under a fixed budget, and
-// latency-critical loops where cudaMalloc's implicit device synchronisation is
-// unacceptable.  This entry point serves them: its scratch is a file-scope
-// static device array of fixed size that exists, on every GPU that loads the
-// library, from module load until process exit.
+// callers cannot let a library allocate: runtimes that reserve all device
+// memory up front under a fixed budget, and latency-critical loops where
+// cudaMalloc's implicit device synchronisation is unacceptable.  This entry
+// point serves them: its scratch is a file-scope static device array of fixed
+// size that exists, on every GPU that loads the library, from module load
+// until process exit.  The first call on a device looks up the array's
+// device address (set-up); make that call before any stream capture.
 //
 // The scratch holds a ticket word and one FP64 partial per span of
 // kSpan = 65536 elements, kMaxSpans = 4096 spans in all (32 KiB + 256 B), so

@@ -8,11 +8,12 @@ import oracle
 from oracle import exact
 from paper_1109_1264_gb300 import inputs
 from paper_1109_1264_gb300 import programs as P
+import tolerance
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-TOL = {np.float64: 1e-13, np.float32: 1e-6}
+TOL = tolerance.TOL
 TDT = {np.float64: torch.float64, np.float32: torch.float32}
 SHAPES = [  # (program, vectors, scalars)
     (P.PROG_D, 4, 0), (P.PROG_AXPBY, 2, 2), (P.PROG_E, 5, 2), (P.PROG_CG, 3, 2), (P.PROG_DOT, 2, 0),
@@ -79,7 +80,7 @@ def check(items, tensors, slots, red):
             assert_bits_equal(t.cpu().numpy(), w, f"{prog} n={len(vecs[0])} operand {k}")
         for r, (ref, sc) in enumerate(zip(refs, scales)):
             got = red[slot + r]
-            assert abs(got - ref) <= TOL[dt] * sc, (prog, dt, len(vecs[0]), got, ref)
+            tolerance.check(got, ref, sc, dt, (prog, dt, len(vecs[0])))
             if len(vecs[0]) == 0:
                 assert got == 0.0
 
@@ -205,7 +206,7 @@ def test_cg_batch_sample_config4(salt, cuda_dev):
             assert_bits_equal(got_r, want[0], f"item {i} r")
             assert_bits_equal(got_p, want[2], f"item {i} p")
             ref = exact.exact_sumsq(want[0])
-            assert abs(redh[slots[i]] - ref) <= TOL[dt] * ref, (i, redh[slots[i]], ref)
+            tolerance.check(redh[slots[i]], ref, ref, dt, ("item", i))
         b.close()
         del bufs
         torch.cuda.empty_cache()

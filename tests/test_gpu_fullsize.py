@@ -229,3 +229,71 @@ def test_reductions_beyond_2e31_elements(saltlib, cuda_dev, dt, sched):
     else:
         assert abs(got_dot - dot) <= 1e-6 * absdot, (got_dot, dot)
         assert abs(got_sq - sumsq) <= 1e-6 * sumsq and abs(got_nrm - math.sqrt(sumsq)) <= 1e-6 * math.sqrt(sumsq)
+
+
+def host_dot_reference(kx: int, ky: int, n: int, dt, same_sign: bool, piece: int = 1 << 22):
+    """Exact sum x_i y_i and sum |x_i y_i| of the counter-based vectors keyed
+    kx, ky (absolute values when same_sign), generated on the host piece by
+    piece on a thread pool and summed in exact integer arithmetic."""
+    import concurrent.futures as cf
+    import os
+    from oracle import exact
+    fb = 52 if dt == np.float64 else 23
+
+    def one(lo):
+        m = min(piece, n - lo)
+        x = inputs.hash_uniform(kx, m, dt, offset=lo)
+        y = inputs.hash_uniform(ky, m, dt, offset=lo)
+        if same_sign:
+            x, y = np.abs(x), np.abs(y)
+        f = exact.FixedPointDot(fb, fb)
+        f.add(x, y)
+        return f
+
+    with cf.ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        parts = list(ex.map(one, range(0, n, piece)))
+    f = exact.FixedPointDot.combine(parts)
+    return f.value(), f.abs_value()
+
+
+@pytest.mark.parametrize("data", ["random_sign", "same_sign"])
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_dot_full_size_relative_error(saltlib, cuda_dev, dt, data):
+    """dot at the bench's size n = 2^28 on the counter-based uniform[-1, 1)
+    data (random sign), and on its absolute values (one sign: the relative
+    error of the result and the error relative to sum|x_i y_i| coincide),
+    in the autotuned configuration and on the staged loop: the relative
+    error of the result against the exact value is within 1e-13 (FP64) /
+    1e-6 (compensated FP32) -- the tolerance stated on the value itself."""
+    import tolerance
+    s = saltlib
+    n = 1 << 28
+    tdt = torch.float32 if dt == np.float32 else torch.float64
+    code = s.F32 if dt == np.float32 else s.F64
+    kx, ky = 141, 142
+    x, y = torch.empty(n, dtype=tdt, device=cuda_dev), torch.empty(n, dtype=tdt, device=cuda_dev)
+    s.salt_fill_uniform(x, key=kx)
+    s.salt_fill_uniform(y, key=ky)
+    if data == "same_sign":
+        x.abs_()
+        y.abs_()
+    out = torch.zeros(2, dtype=torch.float64, device=cuda_dev)
+    s.salt_tune_clear()
+    try:
+        s.salt_autotune(s.KERNEL_PROGRAM, P.PROG_DOT, [x, y], red_out=out[0:1], reps=1)
+        s.salt_dot(x, y, out[0:1])
+        s.salt_tune_set(P.PROG_DOT, code, n, 1, 16, 128, 0, 16384)
+        s.salt_dot(x, y, out[1:2])
+        torch.cuda.synchronize()
+    finally:
+        s.salt_tune_clear()
+    del x, y
+    ref, scale = host_dot_reference(kx, ky, n, dt, data == "same_sign")
+    for got, sched in zip(out.cpu().tolist(), ("tuned", "staged")):
+        e = tolerance.check(got, ref, scale, dt, (data, sched))
+        # judged on the relative error of the result, not on sum|x_i y_i|
+        assert e["cond"] <= tolerance.COND_LITERAL, e
+        if data == "same_sign":
+            assert e["rel_value"] == e["rel_scale"]
+        print(f"dot {dt.__name__} n=2^28 {data} {sched}: rel_value {e['rel_value']:.3e} "
+              f"rel_scale {e['rel_scale']:.3e} cond {e['cond']:.3e}")

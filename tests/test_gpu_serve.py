@@ -8,11 +8,12 @@ import oracle
 from oracle import exact
 from paper_1109_1264_gb300 import inputs
 from paper_1109_1264_gb300 import programs as P
+import tolerance
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-TOL = {np.float64: 1e-13, np.float32: 1e-6}
+TOL = tolerance.TOL
 SHAPES = [(P.PROG_D, 4, 3), (P.PROG_AXPBY, 2, 1), (P.PROG_E, 5, 4), (P.PROG_DOT, 2, None), (None, 1, None)]
 SC = [1.5, -0.25]
 
@@ -67,7 +68,7 @@ def test_served_results_match_oracle(salt):
                 got = srv.read(rid, out, np.empty(n, dt))
                 assert_bits_equal(got, want[out], f"shape {si} n={n}")
             if ref is not None:
-                assert abs(red[0] - ref) <= TOL[dt] * scale, (si, dt, n, red[0], ref)
+                tolerance.check(red[0], ref, scale, dt, (si, dt, n))
             srv.release(rid)
         st = srv.stats()
         assert st["completed"] == len(reqs) and st["resident_bytes"] == 0 and st["waiting"] == 0
@@ -176,7 +177,7 @@ def test_replay_poisson_trace(salt):
                 dt = np.float64 if is64[i] else np.float32
                 keys = [inputs.vector_key(9, i, k) for k in range(SHAPES[si][1])]
                 _, _, ref, scale = expected(si, keys, int(lens[i]), dt)
-                assert abs(red[i] - ref) <= TOL[dt] * scale, (i, red[i], ref)
+                tolerance.check(red[i], ref, scale, dt, ("request", i))
         assert srv.stats()["resident_bytes"] == 0
     finally:
         srv.stop()
@@ -219,8 +220,7 @@ def test_caller_owned_operands(salt, cuda_dev):
                 assert_bits_equal(out_dev.cpu().numpy(), want[4], f"caller-owned out n={n}")
                 assert_bits_equal(srv.read(b, 0, np.empty(n, dt)), host[0], "read of a caller-owned operand")
                 red = srv.poll(c)[2][0]
-                ref = exact.exact_dot(host[0], host[1])
-                assert abs(red - ref) <= TOL[dt] * exact.abs_dot(host[0], host[1])
+                tolerance.check_dot(red, host[0], host[1], dt, ("caller-owned dot", n))
                 for rid in (a, b, c):
                     srv.release(rid)
         assert srv.stats()["resident_bytes"] == 0
@@ -265,7 +265,7 @@ def test_replay_resident_store(salt, cuda_dev):
                 ref, scale = exact.exact_nrm2(vecs[0]), exact.exact_nrm2(vecs[0])
             else:
                 ref, scale = exact.exact_dot(vecs[0], vecs[1]), exact.abs_dot(vecs[0], vecs[1])
-            assert abs(red[i] - ref) <= TOL[dt] * scale, (i, red[i], ref)
+            tolerance.check(red[i], ref, scale, dt, ("request", i))
             checked += 1
         assert checked > 100
         assert srv.stats()["resident_bytes"] == 0

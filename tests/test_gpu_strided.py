@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 from paper_1109_1264_gb300 import inputs
+import tolerance
 from test_gpu_parity import PROGS, TOL, assert_bits_equal, check_reductions
 
 pytestmark = pytest.mark.gpu
@@ -94,9 +95,9 @@ def test_unaligned_dot_and_nrm2(saltlib, cuda_dev, dt):
         s.salt_dot(bx[1:], by[3:], out[0:1])
         s.salt_nrm2(bx[1:], out[1:2])
         d, nr = out.cpu().tolist()
-        assert abs(d - exact.exact_dot(x, y)) <= TOL[dt] * exact.abs_dot(x, y)
+        tolerance.check_dot(d, x, y, dt, ("unaligned dot", n))
         ref = exact.exact_nrm2(x)
-        assert abs(nr - ref) <= TOL[dt] * ref
+        tolerance.check(nr, ref, ref, dt, ("unaligned nrm2", n))
 
 
 @pytest.mark.parametrize("name", ["D", "E", "AXPBY", "CG", "DOT", "ODD", "ODD_JIT"])
