@@ -277,6 +277,36 @@ salt_status salt_cg_diag_persistent(int32_t dtype, int64_t n, const void* d, con
 salt_status salt_cg_diag_one_reduction(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r,
                                        void* p, void* s, int32_t iters, double* rho, void* stream);
 
+/* Status of the last cooperative CG launch (salt_cg_diag_persistent or
+ * salt_cg_diag_one_reduction) on `stream`: synchronises the stream, then
+ * returns SALT_OK if every grid barrier of that launch completed, or
+ * SALT_ERR_TIMEOUT if one ran out of its poll limit (the launch then ended
+ * early with NaN in rho[0]; x, r, p and q hold partial updates).  Reads a
+ * word of the stream's reduction workspace (created by the first reducing
+ * call on the stream).  Not in the paper.  Errors: SALT_ERR_TIMEOUT,
+ * SALT_ERR_CUDA. */
+salt_status salt_cg_status(void* stream);
+
+/* Limits of the two bounded device waits, for tests that make a wait run out
+ * on purpose (both are process-wide and read at each launch):
+ *   SALT_WAIT_STAGED      polls thread 0 of a staged-loop block spends on a
+ *                         tile's bulk copies before it stops staging and
+ *                         computes from direct loads (results unchanged;
+ *                         counted by salt_staged_timeouts); 0: give up at
+ *                         once.  The copies already issued are still waited
+ *                         for, with the full bound, before the block exits.
+ *   SALT_WAIT_CG_BARRIER  polls of one grid barrier of the cooperative CG
+ *                         launches before it records a timeout (see
+ *                         salt_cg_status); 0: give up unless already passed.
+ * Default for both: 2^26 polls (besides the staged wait's one-second timer
+ * bound).  polls in [0, 2^32); errors: SALT_ERR_ARG (unknown wait, polls
+ * out of range or NULL).  Not in the paper. */
+#define SALT_WAIT_STAGED 1
+#define SALT_WAIT_CG_BARRIER 2
+#define SALT_WAIT_DEFAULT_POLLS 67108864
+salt_status salt_set_wait_limit(int32_t which, int64_t polls);
+salt_status salt_get_wait_limit(int32_t which, int64_t* polls);
+
 /* salt_explain -- host only (no GPU): the program the kernels evaluate for
  * `prog`, after its scalar subexpressions are hoisted, with the values of
  * the scalar slots.  Not part of the paper; an inspection aid.

@@ -1170,6 +1170,27 @@ salt_status salt_tune_load(const char* path) {
 
 int64_t salt_launch_count(void) { return g_launches.load(); }
 
+salt_status salt_set_wait_limit(int32_t which, int64_t polls) {
+  if (polls < 0 || polls > (int64_t)0xFFFFFFFFu) return set_error(SALT_ERR_ARG, "polls must be in [0, 2^32)");
+  if (which == SALT_WAIT_STAGED) {
+    staged_tile_polls(polls);
+    return SALT_OK;
+  }
+  if (which == SALT_WAIT_CG_BARRIER) {
+    cg_barrier_polls(polls);
+    return SALT_OK;
+  }
+  return set_error(SALT_ERR_ARG, "unknown wait (SALT_WAIT_STAGED or SALT_WAIT_CG_BARRIER)");
+}
+
+salt_status salt_get_wait_limit(int32_t which, int64_t* polls) {
+  if (!polls) return set_error(SALT_ERR_ARG, "polls is NULL");
+  if (which == SALT_WAIT_STAGED) *polls = staged_tile_polls(-1);
+  else if (which == SALT_WAIT_CG_BARRIER) *polls = cg_barrier_polls(-1);
+  else return set_error(SALT_ERR_ARG, "unknown wait (SALT_WAIT_STAGED or SALT_WAIT_CG_BARRIER)");
+  return SALT_OK;
+}
+
 salt_status salt_staged_timeouts(uint64_t* count) {
   if (!count) return set_error(SALT_ERR_ARG, "count is NULL");
   unsigned long long v = 0;

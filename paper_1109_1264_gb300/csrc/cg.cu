@@ -13,16 +13,19 @@
 //
 // Barrier: a monotonic arrival counter (zeroed before the launch); barrier
 // m is passed when the counter reaches m * gridDim.x.  Waits are bounded:
-// after kMaxSpins polls a block records a timeout in the status word, writes
-// NaN into rho[0] (block 0) and returns, and every other block returns at
-// its next barrier, so a launch that cannot make progress ends instead of
-// hanging.  The cooperative launch guarantees that all blocks are resident.
+// after max_polls polls (kMaxSpins unless a test sets a smaller limit) a
+// block records a timeout in the status word, writes NaN into rho[0] (block
+// 0) and returns, and every other block returns at its next barrier, so a
+// launch that cannot make progress ends instead of hanging; salt_cg_status
+// reports the status word.  The cooperative launch guarantees that all
+// blocks are resident.
 //
 // salt_cg_diag_one_reduction uses the same launch, barrier and reductions
 // for Chronopoulos and Gear's recurrence: one pass and one barrier per
 // iteration (cg_one_reduction_kernel below).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <string>
 
@@ -36,6 +39,7 @@ namespace {
 
 constexpr unsigned kMaxSpins = 1u << 26;  // polls of >= 32 ns and an L2 round trip: seconds
 constexpr int kCgBlock = 256;
+std::atomic<unsigned> g_barrier_polls{kMaxSpins};  // tests lower it to make a barrier run out
 
 template <typename T>
 struct CgParams {
@@ -51,10 +55,12 @@ struct CgParams {
   double* partials;   // 2 * gridDim.x values
   unsigned long long* counter;  // barrier arrivals, zero at launch
   unsigned* status;             // 0, or 1 after a barrier timeout
+  unsigned max_polls;           // polls of one barrier before it records a timeout
 };
 
 // Returns false if the barrier timed out (here or in another block).
-__device__ bool grid_barrier(unsigned long long* counter, unsigned* status, unsigned long long target) {
+__device__ bool grid_barrier(unsigned long long* counter, unsigned* status, unsigned long long target,
+                             unsigned max_polls) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -68,7 +74,7 @@ __device__ bool grid_barrier(unsigned long long* counter, unsigned* status, unsi
         break;
       }
       if (*(volatile unsigned long long*)counter >= target) break;
-      if (++spins > kMaxSpins) {
+      if (++spins > max_polls) {
         atomicExch(status, 1u);
         ok = 0;
         break;
@@ -86,10 +92,10 @@ __device__ bool grid_barrier(unsigned long long* counter, unsigned* status, unsi
 // after the barrier every block adds the G partials in block order.
 template <typename T>
 __device__ bool grid_sum(double v, double* partials, int slot, unsigned long long* counter, unsigned* status,
-                         unsigned long long target, double* smem, double* out) {
+                         unsigned long long target, unsigned max_polls, double* smem, double* out) {
   const double bs = block_sum<double>(v, smem);
   if (threadIdx.x == 0) partials[(size_t)slot * gridDim.x + blockIdx.x] = bs;
-  if (!grid_barrier(counter, status, target)) return false;
+  if (!grid_barrier(counter, status, target, max_polls)) return false;
   const volatile double* part = (const volatile double*)partials + (size_t)slot * gridDim.x;
   if (gridDim.x <= 32) {
     // few blocks: one thread adds them in block order (no tree, one barrier)
@@ -115,14 +121,15 @@ __device__ bool grid_sum(double v, double* partials, int slot, unsigned long lon
 // each set of G partials in block order (the same fixed-order tree as
 // grid_sum, so every block holds the same totals).
 __device__ bool grid_sum2(double v0, double v1, double* partials, int slot0, unsigned long long* counter,
-                          unsigned* status, unsigned long long target, double* smem, double* out0, double* out1) {
+                          unsigned* status, unsigned long long target, unsigned max_polls, double* smem,
+                          double* out0, double* out1) {
   const double b0 = block_sum<double>(v0, smem);
   const double b1 = block_sum<double>(v1, smem);
   if (threadIdx.x == 0) {
     partials[(size_t)slot0 * gridDim.x + blockIdx.x] = b0;
     partials[(size_t)(slot0 + 1) * gridDim.x + blockIdx.x] = b1;
   }
-  if (!grid_barrier(counter, status, target)) return false;
+  if (!grid_barrier(counter, status, target, max_polls)) return false;
   const volatile double* part0 = (const volatile double*)partials + (size_t)slot0 * gridDim.x;
   const volatile double* part1 = part0 + gridDim.x;
   if (gridDim.x <= 32) {
@@ -299,7 +306,7 @@ __global__ void __launch_bounds__(kCgBlock) cg_persistent_kernel(const CgParams<
 #undef SALT_CG_START
   double rho = 0.0, rho_prev = 0.0, pq = 0.0;
   target += G;
-  if (!grid_sum<T>(acc.value(), p.partials, 0, p.counter, p.status, target, smem, &rho)) {
+  if (!grid_sum<T>(acc.value(), p.partials, 0, p.counter, p.status, target, p.max_polls, smem, &rho)) {
     if (lead) p.rho[0] = NAN;
     return;
   }
@@ -314,7 +321,7 @@ __global__ void __launch_bounds__(kCgBlock) cg_persistent_kernel(const CgParams<
     SALT_CG_EACH(SALT_CG_PASS1)
 #undef SALT_CG_PASS1
     target += G;
-    if (!grid_sum<T>(a1.value(), p.partials, 1, p.counter, p.status, target, smem, &pq)) {
+    if (!grid_sum<T>(a1.value(), p.partials, 1, p.counter, p.status, target, p.max_polls, smem, &pq)) {
       if (lead) p.rho[0] = NAN;
       return;
     }
@@ -327,7 +334,7 @@ __global__ void __launch_bounds__(kCgBlock) cg_persistent_kernel(const CgParams<
 #undef SALT_CG_PASS2
     double rho_next = 0.0;
     target += G;
-    if (!grid_sum<T>(a2.value(), p.partials, 0, p.counter, p.status, target, smem, &rho_next)) {
+    if (!grid_sum<T>(a2.value(), p.partials, 0, p.counter, p.status, target, p.max_polls, smem, &rho_next)) {
       if (lead) p.rho[0] = NAN;
       return;
     }
@@ -364,7 +371,8 @@ __global__ void __launch_bounds__(kCgBlock) cg_one_reduction_kernel(const CgPara
 #undef SALT_CGC_START
   double gamma = 0.0, delta = 0.0;
   target += G;
-  if (!grid_sum2(ag.value(), ad.value(), p.partials, 0, p.counter, p.status, target, smem, &gamma, &delta)) {
+  if (!grid_sum2(ag.value(), ad.value(), p.partials, 0, p.counter, p.status, target, p.max_polls, smem, &gamma,
+                 &delta)) {
     if (lead) p.rho[0] = NAN;
     return;
   }
@@ -389,8 +397,8 @@ __global__ void __launch_bounds__(kCgBlock) cg_one_reduction_kernel(const CgPara
 #undef SALT_CGC_PASS
     double gn = 0.0, dn = 0.0;
     target += G;
-    if (!grid_sum2(bg.value(), bd.value(), p.partials, (k & 1) ? 0 : 2, p.counter, p.status, target, smem, &gn,
-                   &dn)) {
+    if (!grid_sum2(bg.value(), bd.value(), p.partials, (k & 1) ? 0 : 2, p.counter, p.status, target, p.max_polls,
+                   smem, &gn, &dn)) {
       if (lead) p.rho[0] = NAN;
       return;
     }
@@ -431,7 +439,8 @@ salt_status launch_cg(int64_t n, void* const* v, int32_t iters, double* rho, cud
   e = cudaMemsetAsync(words + 1, 0, 3 * sizeof(unsigned), s);
   if (e != cudaSuccess) return report_error(SALT_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   CgParams<T> prm{(const T*)v[0], (const T*)v[5], (T*)v[3], (T*)v[4], (T*)v[1], (T*)v[2],
-                  n, iters, rho, partials, (unsigned long long*)(words + 2), words + 1};
+                  n, iters, rho, partials, (unsigned long long*)(words + 2), words + 1,
+                  g_barrier_polls.load()};
   int vec = 1;
   for (int k = 0; k < 6; ++k) vec = vec && ((uintptr_t)v[k] % 16 == 0);
   void* args[] = {&prm, &vec};
@@ -444,9 +453,31 @@ salt_status launch_cg(int64_t n, void* const* v, int32_t iters, double* rho, cud
 
 }  // namespace
 
+unsigned cg_barrier_polls(int64_t set) {
+  if (set >= 0) g_barrier_polls.store((unsigned)set);
+  return g_barrier_polls.load();
+}
+
 }  // namespace salt
 
 using namespace salt;
+
+extern "C" salt_status salt_cg_status(void* stream) {
+  const cudaStream_t s = (cudaStream_t)stream;
+  double* partials = nullptr;
+  unsigned* words = nullptr;
+  int cap = 0;
+  salt_status st = stream_workspace(s, &partials, &words, &cap);
+  if (st != SALT_OK) return st;
+  unsigned status = 0;
+  cudaError_t e = cudaMemcpyAsync(&status, words + 1, sizeof status, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return report_error(SALT_ERR_CUDA, std::string("reading the CG status: ") + cudaGetErrorString(e));
+  if (status != 0u)
+    return report_error(SALT_ERR_TIMEOUT, "a grid barrier of the last cooperative CG launch on this stream ran out "
+                                          "of its poll limit; rho[0] is NaN and x, r, p, q are not valid");
+  return SALT_OK;
+}
 
 extern "C" salt_status salt_cg_diag_persistent(int32_t dtype, int64_t n, const void* d, const void* b, void* x,
                                                void* r, void* p, void* q, int32_t iters, double* rho,

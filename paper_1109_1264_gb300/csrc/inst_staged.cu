@@ -1,4 +1,5 @@
 // Instantiations of the staged schedule (staged.cuh): every shape and dtype.
+#include <atomic>
 #include <mutex>
 
 #include "registry.h"
@@ -11,6 +12,7 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_counter_mu;
 unsigned long long* g_counter[kMaxDevices];  // per device: timed-out stage waits
+std::atomic<unsigned> g_tile_polls{kStageSpins};  // polls of a tile's copies (tests lower it)
 
 // The current device's counter, allocated and zeroed on first use.
 cudaError_t counter_address(unsigned long long** out) {
@@ -41,6 +43,7 @@ cudaError_t launch_staged(const void* prm, int grid, int block, size_t smem, cud
   StagedParams<T> sp = *static_cast<const StagedParams<T>*>(prm);
   cudaError_t e = counter_address(&sp.timeouts);
   if (e != cudaSuccess) return e;
+  sp.tile_polls = g_tile_polls.load();
   staged_kernel<P, T><<<grid, block, smem, s>>>(sp);
   return cudaGetLastError();
 }
@@ -61,6 +64,11 @@ void register_staged(Registry& r) {
   r.staged_smem[SHAPE_##name] = &smem_of<Prog_##name>;
   SALT_SHAPE_LIST(SALT_REG_STAGED)
 #undef SALT_REG_STAGED
+}
+
+unsigned staged_tile_polls(int64_t set) {
+  if (set >= 0) g_tile_polls.store((unsigned)set);
+  return g_tile_polls.load();
 }
 
 cudaError_t staged_timeouts(unsigned long long* out) {

@@ -56,6 +56,10 @@ salt_status current_device(int* dev, int* sms);
 // Number of kernel launches issued by the library (all threads).
 void count_launch();
 
+// Polls one grid barrier of the cooperative CG kernels spends before it
+// records a timeout; `set` >= 0 replaces the limit first.  Returns the limit.
+unsigned cg_barrier_polls(int64_t set);
+
 // Run-time compiled fused kernels (csrc/jit.cu): the current mode
 // (SALT_JIT_OFF / SALT_JIT_ON) and the kernel for a canonical program
 // (compiled and cached on first use).

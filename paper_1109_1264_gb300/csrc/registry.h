@@ -59,6 +59,9 @@ cudaError_t launch_l2_flush(const void* buf, size_t bytes, unsigned* sink, int s
 // Timed-out stage waits of staged kernels since the library was loaded
 // (synchronous read of a device counter).
 cudaError_t staged_timeouts(unsigned long long* out);
+// Polls a staged-loop block spends on a tile's copies before it falls back to
+// direct loads; `set` >= 0 replaces the limit first.  Returns the limit.
+unsigned staged_tile_polls(int64_t set);
 
 inline int unroll_index(int u) { return u == 1 ? 0 : u == 2 ? 1 : u == 4 ? 2 : -1; }
 inline int vb_index(int vb) { return vb == 16 ? 0 : vb == 32 ? 1 : -1; }

@@ -15,10 +15,11 @@
 // trial on the target machine).
 //
 // Waits on an mbarrier are bounded.  If a tile's copies have not completed
-// within kStageWaitNs (or kStageSpins polls), the block counts a timeout in
-// *timeouts, stops issuing copies, computes that tile and every later one
-// from direct global loads (so the results do not change), and before it
-// exits waits, again bounded, for the copies it still has in flight.
+// within kStageWaitNs (or `tile_polls` polls, kStageSpins unless a test sets
+// a smaller limit), the block counts a timeout in *timeouts, stops issuing
+// copies, computes that tile and every later one from direct global loads
+// (so the results do not change), and before it exits waits, with the full
+// bound, for the copies it still has in flight.
 #pragma once
 
 #include "fused.cuh"
@@ -33,6 +34,7 @@ template <typename T>
 struct StagedParams {
   MapParams<T> m;
   int32_t stage_bytes;            // per loaded operand per stage: 4096, 8192 or 16384
+  unsigned tile_polls;            // polls of a tile's copies before the fallback (0: none)
   unsigned long long* timeouts;   // device counter of timed-out waits
 };
 
@@ -79,10 +81,13 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+// At most `polls` tests of the phase (none when polls is 0) and at most
+// kStageWaitNs of the global timer.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned polls = kStageSpins) {
+  if (polls == 0u) return false;
   if (mbar_test(bar, parity)) return true;
   const uint64_t t0 = global_ns();
-  for (unsigned k = 0; k < kStageSpins; ++k) {
+  for (unsigned k = 1; k < polls; ++k) {
     if (mbar_test(bar, parity)) return true;
     if (global_ns() - t0 > kStageWaitNs) return false;
   }
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(256) staged_kernel(const StagedParams<T> sp) {
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gstep, ++it) {
     const int st = it % kStages;
     if (threadIdx.x == 0) {
-      bool ok = staging && mbar_wait_bounded(&bars[st], (parity >> st) & 1u);
+      bool ok = staging && mbar_wait_bounded(&bars[st], (parity >> st) & 1u, sp.tile_polls);
       if (ok) {
         pending &= ~(1u << st);
         parity ^= 1u << st;

@@ -26,7 +26,7 @@ EXPORTS = ["salt_version", "salt_status_str", "salt_last_error", "salt_check_pro
            "salt_axpby", "salt_dot", "salt_nrm2", "salt_fill_uniform", "salt_release_workspaces",
            "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_staged_timeouts",
            "salt_dot_noalloc", "salt_eval_strided", "salt_eval_ex", "salt_explain", "salt_cg_diag", "salt_cg_diag_persistent",
-           "salt_cg_diag_one_reduction"]
+           "salt_cg_diag_one_reduction", "salt_cg_status", "salt_set_wait_limit", "salt_get_wait_limit"]
 
 
 class Insn(ctypes.Structure):
@@ -82,6 +82,9 @@ def _load() -> ctypes.CDLL:
         "salt_cg_diag": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp]),
         "salt_cg_diag_persistent": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp]),
         "salt_cg_diag_one_reduction": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp]),
+        "salt_cg_status": (i32, [vp]),
+        "salt_set_wait_limit": (i32, [i32, i64]),
+        "salt_get_wait_limit": (i32, [i32, ctypes.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -292,6 +295,26 @@ def salt_cg_diag(d, b, x, r, p, q, iters: int, rho, stream=None, persistent: boo
     else:
         fn = lib.salt_cg_diag_persistent if persistent else lib.salt_cg_diag
     _check(fn(dt, _n_of(vs), *[_ptr(v) for v in vs], int(iters), _ptr(rho), _stream_ptr(stream)))
+
+
+def salt_cg_status(stream=None) -> None:
+    """Raises SaltError(SALT_ERR_TIMEOUT) if a grid barrier of the last
+    cooperative CG launch on ``stream`` ran out (synchronises the stream)."""
+    _check(lib.salt_cg_status(_stream_ptr(stream)))
+
+
+WAIT_STAGED, WAIT_CG_BARRIER = 1, 2
+WAIT_DEFAULT_POLLS = 1 << 26
+
+
+def salt_set_wait_limit(which: int, polls: int) -> None:
+    _check(lib.salt_set_wait_limit(int(which), int(polls)))
+
+
+def salt_get_wait_limit(which: int) -> int:
+    v = ctypes.c_int64()
+    _check(lib.salt_get_wait_limit(int(which), ctypes.byref(v)))
+    return v.value
 
 
 def salt_eval(prog, vecs, scalars=(), red_out=None, n: int | None = None, stream=None,

@@ -288,3 +288,21 @@ def test_binding_operand_checks(saltlib):
     dt, n, ptrs, contiguous = s._operands([a32, None, short], same_length=False)
     assert dt == s.F32 and n == 8 and ptrs[1] is None and contiguous
     assert s._operands([a32[::2]])[3] is False
+
+
+def test_wait_limits(saltlib):
+    """The poll limits of the two bounded device waits: defaults, round
+    trip, argument errors (no GPU needed)."""
+    s = saltlib
+    for which in (s.WAIT_STAGED, s.WAIT_CG_BARRIER):
+        assert s.salt_get_wait_limit(which) == s.WAIT_DEFAULT_POLLS
+        s.salt_set_wait_limit(which, 0)
+        assert s.salt_get_wait_limit(which) == 0
+        s.salt_set_wait_limit(which, s.WAIT_DEFAULT_POLLS)
+        assert s.salt_get_wait_limit(which) == s.WAIT_DEFAULT_POLLS
+    assert s.lib.salt_set_wait_limit(3, 5) == s.ERR_ARG
+    assert s.lib.salt_set_wait_limit(s.WAIT_STAGED, -1) == s.ERR_ARG
+    assert s.lib.salt_set_wait_limit(s.WAIT_STAGED, 1 << 32) == s.ERR_ARG
+    assert s.lib.salt_get_wait_limit(s.WAIT_STAGED, None) == s.ERR_ARG
+    # without a GPU the status query fails like every device call
+    assert s.lib.salt_cg_status(None) == s.ERR_CUDA
