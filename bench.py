@@ -354,6 +354,8 @@ def main():
     ap.add_argument("--fixed-e-cfg", default=None,
                     help="profiling runs: skip the autotuner and launch e with U,VB,BLOCK,BLOCKS_PER_SM[,STAGE_BYTES]")
     ap.add_argument("--cg-log2", type=int, default=28)
+    ap.add_argument("--trace-reductions", action="store_true",
+                    help="per-block timelines of dot and nrm2 from n = 2^4 to 2^26 (launch ramp, tail, combine)")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
 
@@ -381,6 +383,11 @@ def main():
     if args.schedules:
         if rank == 0:
             print(json.dumps(schedules_measure(torch, salt)), flush=True)
+        return
+
+    if args.trace_reductions:
+        if rank == 0:
+            print(json.dumps(reduction_trace_measure(torch, salt)), flush=True)
         return
 
     if args.only_served:
@@ -814,6 +821,81 @@ def sweep_measure(torch, salt, reps: int = 21, max_log2: int = 28) -> dict:
         del xb, yb
     return {"sweep": out, "note": "GB/s of algorithmic bytes; launch shapes autotuned per size bucket; "
                                   "L2 flushed before each timed call; median of %d" % reps}
+
+
+def reduction_trace_measure(torch, salt, log2ns=(4, 12, 16, 20, 22, 24, 26), reps: int = 7) -> dict:
+    """Where a reduction's time goes: dot and nrm2, FP32 and FP64, autotuned
+    as in the sweep, each call timed with CUDA events after an L2 flush while
+    every block records its timeline (salt_trace_set).  Per call (the median
+    by event time of `reps`):
+      event_us        CUDA-event time of the call
+      span_us         first block start to last block end (global timer)
+      outside_us      event_us - span_us: launch latency outside the blocks
+      start_spread_us last block start - first block start (dispatch ramp)
+      tiles_us        median over blocks of (whole tiles done - block start)
+      tail_us         last block's deposit - median block's deposit
+      combine_us      end of the final combine - last deposit
+      hbm_us          algorithmic bytes / the measured copy rate"""
+    import numpy as np
+
+    from paper_1109_1264_gb300.programs import PROG_DOT
+    hbm_peak, _, _ = load_peaks()
+    flush = torch.zeros(64 << 20, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    cap = 152 * 32
+    trace = torch.zeros(cap * salt.TRACE_WORDS, dtype=torch.int64, device="cuda")
+    out = {}
+    for dt, tdt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+        nmax = 1 << max(log2ns)
+        xb = torch.empty(nmax, dtype=tdt, device="cuda")
+        yb = torch.empty(nmax, dtype=tdt, device="cuda")
+        salt.salt_fill_uniform(xb, 11)
+        salt.salt_fill_uniform(yb, 12)
+        red = torch.zeros(1, dtype=torch.float64, device="cuda")
+        for lg in log2ns:
+            n = 1 << lg
+            x, y = xb[:n], yb[:n]
+            salt.salt_tune_clear()
+            cfg_dot, _ = salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_DOT, [x, y], red_out=red, reps=5)
+            cfg_nrm, _ = salt.salt_autotune(salt.KERNEL_NRM2, None, [x], red_out=red, reps=5)
+            for op, fn, nbytes, cfg in (("dot", lambda: salt.salt_dot(x, y, red), 2 * es * n, cfg_dot),
+                                        ("nrm2", lambda: salt.salt_nrm2(x, red), es * n, cfg_nrm)):
+                runs = []
+                salt.salt_trace_set(trace, cap)
+                try:
+                    for _ in range(reps):
+                        trace.zero_()
+                        flush.sum()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        fn()
+                        e1.record(stream)
+                        torch.cuda.synchronize()
+                        w = trace.view(-1, salt.TRACE_WORDS).cpu().numpy()
+                        w = w[w[:, 0] != 0]
+                        runs.append((e0.elapsed_time(e1) * 1e3, w))
+                finally:
+                    salt.salt_trace_set(None)
+                runs.sort(key=lambda r: r[0])
+                ev_us, w = runs[len(runs) // 2]
+                start, tiles, pre, end = (w[:, k].astype(np.float64) for k in range(4))
+                last = w[:, 5] == 1
+                t0 = start.min()
+                row = {"blocks": int(w.shape[0]), "config": cfg,
+                       "event_us": round(ev_us, 2), "span_us": round((end.max() - t0) / 1e3, 2),
+                       "outside_us": round(ev_us - (end.max() - t0) / 1e3, 2),
+                       "start_spread_us": round((start.max() - t0) / 1e3, 2),
+                       "tiles_us": round(float(np.median(tiles - start)) / 1e3, 2),
+                       "tail_us": round((pre.max() - np.median(pre)) / 1e3, 2),
+                       "combine_us": round(((end[last].max() if last.any() else end.max()) - pre.max()) / 1e3, 2),
+                       "hbm_us": round(nbytes / (hbm_peak * 1e9) * 1e6, 2),
+                       "gbs": round(nbytes / (ev_us * 1e-6) / 1e9, 1)}
+                out[f"{op}_{dt}_2^{lg}"] = row
+        salt.salt_tune_clear()
+        del xb, yb
+    return {"reduction_trace": out, "note": "median call of %d by CUDA-event time, L2 flushed before each; "
+                                            "global-timer stamps per block (salt_trace_set)" % reps}
 
 
 def schedules_measure(torch, salt, log2ns=(24, 28), reps: int = 15) -> dict:

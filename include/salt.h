@@ -301,6 +301,21 @@ salt_status salt_cg_status(void* stream);
  * Default for both: 2^26 polls (besides the staged wait's one-second timer
  * bound).  polls in [0, 2^32); errors: SALT_ERR_ARG (unknown wait, polls
  * out of range or NULL).  Not in the paper. */
+/* Per-block timeline of launches, for finding where a kernel's time goes
+ * (launch ramp, tail, cross-block combine).  With a buffer set, every
+ * launch of the fused kernels (register-tiled and staged loops) and of the
+ * norm kernel whose grid has at most `max_blocks` blocks writes, from
+ * thread 0 of block b, SALT_TRACE_WORDS 64-bit words at buf + b *
+ * SALT_TRACE_WORDS: [0] the global timer (ns) when the block starts, [1]
+ * after its whole tiles, [2] before the cross-block combine, [3] at its end,
+ * [4] its SM id, [5] 1 if it performed the final combine.  Each launch
+ * overwrites the words of its blocks; zero the buffer between launches to
+ * tell how many blocks wrote.  buf: caller-owned device memory, 8-byte
+ * aligned; NULL turns tracing off (the default; the kernels then skip it).
+ * Process-wide.  Errors: SALT_ERR_ARG, SALT_ERR_ALIGN.  Not in the paper. */
+#define SALT_TRACE_WORDS 8
+salt_status salt_trace_set(void* buf, int64_t max_blocks);
+
 #define SALT_WAIT_STAGED 1
 #define SALT_WAIT_CG_BARRIER 2
 #define SALT_WAIT_DEFAULT_POLLS 67108864

@@ -26,6 +26,16 @@ namespace salt {
 // ------------------------------------------------------------------ state --
 static thread_local std::string t_last_error;
 static std::atomic<int64_t> g_launches{0};
+// Per-block timeline buffer (salt_trace_set): device words, capacity in blocks.
+static std::atomic<unsigned long long*> g_trace{nullptr};
+static std::atomic<int64_t> g_trace_blocks{0};
+
+// The trace buffer for a launch of `grid` blocks, or NULL (tracing off or
+// the buffer too small for the launch).
+static unsigned long long* trace_for(int grid) {
+  unsigned long long* t = g_trace.load();
+  return (t && grid <= g_trace_blocks.load()) ? t : nullptr;
+}
 
 static salt_status set_error(salt_status st, const std::string& msg) {
   t_last_error = msg;
@@ -330,6 +340,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
       p.red_out = a.red_out;
       p.partials = ws.partials;
       p.ticket = ws.ticket;
+      p.trace = trace_for(grid);
       sp.stage_bytes = cfg.stage_bytes;
       e = ke.launch(&sp, grid, cfg.block, smem, a.stream);
       g_launches.fetch_add(1);
@@ -358,6 +369,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
     p.red_out = a.red_out;
     p.partials = ws.partials;
     p.ticket = ws.ticket;
+    p.trace = trace_for(grid);
     cudaError_t e = ke.launch(&p, grid, cfg.block, 0, a.stream);
     g_launches.fetch_add(1);
     if (e != cudaSuccess) return cuda_error(e, "fused kernel launch");
@@ -637,7 +649,7 @@ static salt_status run_special(int special, int dt, int64_t n, const void* x, co
     DotParams p{x, y, n, out, ws.partials, ws.ticket};
     e = ke.launch(&p, grid, cfg.block, 0, s);
   } else {
-    NrmParams p{x, n, out, ws.partials, ws.ticket};
+    NrmParams p{x, n, out, ws.partials, ws.ticket, trace_for(grid)};
     e = ke.launch(&p, grid, cfg.block, 0, s);
   }
   g_launches.fetch_add(1);
@@ -1169,6 +1181,14 @@ salt_status salt_tune_load(const char* path) {
 }
 
 int64_t salt_launch_count(void) { return g_launches.load(); }
+
+salt_status salt_trace_set(void* buf, int64_t max_blocks) {
+  if (buf && max_blocks < 1) return set_error(SALT_ERR_ARG, "max_blocks must be >= 1");
+  if (buf && (uintptr_t)buf % 8) return set_error(SALT_ERR_ALIGN, "the trace buffer must be 8-byte aligned");
+  g_trace_blocks.store(buf ? max_blocks : 0);
+  g_trace.store(static_cast<unsigned long long*>(buf));
+  return SALT_OK;
+}
 
 salt_status salt_set_wait_limit(int32_t which, int64_t polls) {
   if (polls < 0 || polls > (int64_t)0xFFFFFFFFu) return set_error(SALT_ERR_ARG, "polls must be in [0, 2^32)");

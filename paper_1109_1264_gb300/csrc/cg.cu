@@ -123,11 +123,11 @@ __device__ bool grid_sum(double v, double* partials, int slot, unsigned long lon
 __device__ bool grid_sum2(double v0, double v1, double* partials, int slot0, unsigned long long* counter,
                           unsigned* status, unsigned long long target, unsigned max_polls, double* smem,
                           double* out0, double* out1) {
-  const double b0 = block_sum<double>(v0, smem);
-  const double b1 = block_sum<double>(v1, smem);
+  double bs[2] = {v0, v1};
+  block_sum_n<double, 2>(bs, smem);
   if (threadIdx.x == 0) {
-    partials[(size_t)slot0 * gridDim.x + blockIdx.x] = b0;
-    partials[(size_t)(slot0 + 1) * gridDim.x + blockIdx.x] = b1;
+    partials[(size_t)slot0 * gridDim.x + blockIdx.x] = bs[0];
+    partials[(size_t)(slot0 + 1) * gridDim.x + blockIdx.x] = bs[1];
   }
   if (!grid_barrier(counter, status, target, max_polls)) return false;
   const volatile double* part0 = (const volatile double*)partials + (size_t)slot0 * gridDim.x;
@@ -149,13 +149,14 @@ __device__ bool grid_sum2(double v0, double v1, double* partials, int slot0, uns
     __syncthreads();  // s_tot is read before the next call overwrites it
     return true;
   }
-  double a0 = 0.0, a1 = 0.0;
+  double a[2] = {0.0, 0.0};
   for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
-    a0 += part0[k];
-    a1 += part1[k];
+    a[0] += part0[k];
+    a[1] += part1[k];
   }
-  *out0 = block_sum<double>(a0, smem);
-  *out1 = block_sum<double>(a1, smem);
+  block_sum_n<double, 2>(a, smem);
+  *out0 = a[0];
+  *out1 = a[1];
   return true;
 }
 

@@ -211,64 +211,126 @@ template <> struct AccOf<float> { using type = AccF32; };
 template <> struct AccOf<double> { using type = AccF64; };
 
 // ---------------------------------------------------------------------------
-// Deterministic block sum through shared memory: every thread deposits its
-// value, the part above the largest power of two is folded in, then a
-// halving tree.  The order depends only on blockDim.  It uses no warp
-// shuffles, so the result does not depend on how warps reconverge after the
-// divergent tail loops that precede it (a shuffle-based version lost lane
-// contributions after such a tail in one kernel).  Returned to every thread.
-constexpr int kMaxBlock = 256;
-template <typename R>
-__device__ __forceinline__ R block_sum(R v, R* buf /* >= blockDim.x entries */) {
-  __syncthreads();  // buf may still be read by a previous call
-  buf[threadIdx.x] = v;
-  __syncthreads();
-  unsigned p2 = 1;
-  while (p2 * 2 <= blockDim.x) p2 *= 2;
-  if (threadIdx.x < blockDim.x - p2) buf[threadIdx.x] += buf[threadIdx.x + p2];
-  __syncthreads();
-  for (unsigned s = p2 >> 1; s > 0; s >>= 1) {
-    if (threadIdx.x < s) buf[threadIdx.x] += buf[threadIdx.x + s];
-    __syncthreads();
+// Per-block timeline of a launch, for diagnosing where a kernel's time goes
+// (launch ramp, tail, cross-block combine).  Off unless the caller set a
+// trace buffer (salt_trace_set): then thread 0 of block b writes
+// kTraceWords words at trace[b * kTraceWords]: the global timer (ns) at
+// block start, after the whole tiles, before and after the cross-block
+// combine, then the SM id and 1 if the block performed the final combine.
+constexpr int kTraceWords = 8;
+enum : int { TR_START = 0, TR_TILES = 1, TR_PRE_COMBINE = 2, TR_END = 3, TR_SM = 4, TR_LAST = 5 };
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void trace_mark(unsigned long long* tr, int k) {
+  if (tr != nullptr && threadIdx.x == 0) tr[(size_t)blockIdx.x * kTraceWords + k] = global_ns();
+}
+
+__device__ __forceinline__ void trace_end(unsigned long long* tr, bool last) {
+  if (tr != nullptr && threadIdx.x == 0) {
+    unsigned sm;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+    unsigned long long* w = tr + (size_t)blockIdx.x * kTraceWords;
+    w[TR_END] = global_ns();
+    w[TR_SM] = sm;
+    w[TR_LAST] = last ? 1ull : 0ull;
   }
-  return buf[0];
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic block sums of NV values at once: a butterfly of warp
+// shuffles within each warp, then every thread adds the per-warp sums in
+// warp order.  Every lane of a warp ends the butterfly with the same bits
+// (each step adds the same two values, in either order), so the sums are
+// identical in every thread and depend only on blockDim (a multiple of 32,
+// at most kMaxBlock).  Every thread of the block must call it (it holds two
+// block barriers -- one pair for all NV values), so all 32 lanes of each
+// warp reach the full-mask shuffles; shfl.sync itself waits for every lane
+// named in its mask, whatever divergent code precedes the call.
+constexpr int kMaxBlock = 256;
+constexpr int kWarpSlots = 32;  // buf slots per value (>= warps per block)
+template <typename R, int NV>
+__device__ __forceinline__ void block_sum_n(R (&v)[NV], R* buf /* >= NV * kWarpSlots entries */) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  }
+  const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();  // buf may still be read by a previous call
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) buf[k * kWarpSlots + warp] = v[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    R t = buf[k * kWarpSlots];
+    for (unsigned w = 1; w < nw; ++w) t += buf[k * kWarpSlots + w];
+    v[k] = t;
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ R block_sum(R v, R* buf /* >= kWarpSlots entries */) {
+  R a[1] = {v};
+  block_sum_n<R, 1>(a, buf);
+  return a[0];
+}
+
+// Ticket increment with release and acquire semantics at GPU scope: the
+// caller's earlier writes are visible to whoever observes the increment,
+// and the caller observes every write released by earlier increments.
+__device__ __forceinline__ unsigned ticket_add_acq_rel(unsigned* t, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(t), "r"(v) : "memory");
+  return old;
 }
 
 // Cross-block combination: every block deposits NV partial values; the last
 // block to finish (atomic ticket, no waiting) adds them up in block order and
-// hands the NV totals to `finish` in thread 0, then re-arms the ticket.
-// Returns true in the last block.
+// returns the NV totals in vals, then re-arms the ticket.  Thread 0 writes
+// the block's partials and takes the ticket with release-acquire semantics,
+// so the last block's thread 0 observes every other block's partials, and
+// the barrier that follows orders its threads' reads after that.  Returns
+// true in the last block.
 template <typename R, int NV>
 __device__ __forceinline__ bool grid_combine(R (&vals)[NV], R* partials, unsigned* ticket,
-                                             R* smem) {
-  R tot[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) tot[k] = block_sum<R>(vals[k], smem);
-  if (gridDim.x == 1) {
-    // one block: its sums are the totals (the same bits as the combine,
-    // which would add zeros to them), no partials, ticket or fences
-#pragma unroll
-    for (int k = 0; k < NV; ++k) vals[k] = tot[k];
-    return true;
-  }
+                                             R* smem /* >= NV * kWarpSlots entries */) {
+  block_sum_n<R, NV>(vals, smem);
+  if (gridDim.x == 1) return true;  // one block: its sums are the totals (no partials, ticket or fences)
   __shared__ bool is_last;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) partials[(size_t)blockIdx.x * NV + k] = tot[k];
-    __threadfence();
-    const unsigned t = atomicAdd(ticket, 1u);
-    is_last = (t == gridDim.x - 1);
+    for (int k = 0; k < NV; ++k) partials[(size_t)blockIdx.x * NV + k] = vals[k];
+    is_last = ticket_add_acq_rel(ticket, 1u) == gridDim.x - 1;
   }
   __syncthreads();
   if (!is_last) return false;
-  __threadfence();
+  // Thread t adds partials t, t + blockDim.x, ... in that order; four loads
+  // are issued before their additions, so the reads overlap.
+  const volatile R* part = (const volatile R*)partials;
+  const unsigned G = gridDim.x, bd = blockDim.x;
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    R acc = R(0);
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
-      acc += ((volatile R*)partials)[(size_t)b * NV + k];
-    vals[k] = block_sum<R>(acc, smem);
+  for (int k = 0; k < NV; ++k) vals[k] = R(0);
+  unsigned b = threadIdx.x;
+  for (; b + 3 * bd < G; b += 4 * bd) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const R p0 = part[(size_t)b * NV + k], p1 = part[(size_t)(b + bd) * NV + k];
+      const R p2 = part[(size_t)(b + 2 * bd) * NV + k], p3 = part[(size_t)(b + 3 * bd) * NV + k];
+      vals[k] = (((vals[k] + p0) + p1) + p2) + p3;
+    }
   }
+  for (; b < G; b += bd) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) vals[k] += part[(size_t)b * NV + k];
+  }
+  block_sum_n<R, NV>(vals, smem);
   if (threadIdx.x == 0) *ticket = 0u;
   return true;
 }

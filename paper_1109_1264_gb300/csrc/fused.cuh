@@ -4,9 +4,11 @@
 // Each thread walks tiles in grid-stride order.  Per tile it issues, like one
 // of the paper's instruction packages, a burst of U vector loads for every
 // loaded operand, then the tree's operations on every element in registers,
-// then a burst of U vector stores for every stored operand.  Elements past the
-// last whole tile are finished by a guarded vector pass and a scalar pass,
-// with the same per-element operations (the paper's single_op tail).
+// then a burst of U vector stores for every stored operand.  Every block
+// takes the same number of whole tiles; what is left (less than one tile per
+// block) is spread evenly over all threads as whole vectors in one guarded
+// burst, then single elements, with the same per-element operations (the
+// paper's single_op tail).
 #pragma once
 
 #include "common.cuh"
@@ -26,6 +28,7 @@ struct MapParams {
   int32_t head;              // elements before the aligned body (fused and staged kernels):
                              // v[k] points at element `head` of operand k, and elements
                              // 0 .. head-1 sit just before it; 0 for the strided kernel
+  unsigned long long* trace; // per-block timeline (kTraceWords per block), or NULL
 };
 
 // Per-element evaluation of program P: node I at compile-time stack depth.
@@ -114,6 +117,7 @@ __global__ void __launch_bounds__(256) fused_kernel(const MapParams<T> p) {
   using Acc = typename AccOf<T>::type;
   using V = VecT<T, VB>;
 
+  trace_mark(p.trace, TR_START);
   T sc[kMaxScals];
   if constexpr (DS) {
     load_scalars<T>(p.sc, p.scode, sc);
@@ -127,9 +131,12 @@ __global__ void __launch_bounds__(256) fused_kernel(const MapParams<T> p) {
   const int64_t n = p.n;
   const int64_t bd = blockDim.x;
   const int64_t TE = (int64_t)U * bd * VEC;  // elements per tile
-  const int64_t ntiles = n / TE;
+  // Whole rounds of tiles in grid-stride order: every block takes exactly
+  // `rounds` tiles, so no block runs a tile longer than the others.
+  const int64_t rounds = (n / TE) / gridDim.x;
 
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int64_t tile = blockIdx.x + r * (int64_t)gridDim.x;
     const int64_t base = tile * TE + (int64_t)threadIdx.x * VEC;
     T x[kMaxVecs][U * VEC];
     // load burst
@@ -166,36 +173,54 @@ __global__ void __launch_bounds__(256) fused_kernel(const MapParams<T> p) {
     }
   }
 
-  // Remainder after the whole tiles: first whole vectors, one per thread of
-  // the grid, then single elements.
-  const int64_t rbase = ntiles * TE;
-  const int64_t nvr = (n - rbase) / VEC;
+  trace_mark(p.trace, TR_TILES);
+  // The remainder after the whole rounds -- fewer than gridDim.x tiles --
+  // spread evenly over every thread of the grid as whole vectors, at most U
+  // per thread, in one guarded burst (all loads first, then the operations
+  // and stores of the vectors that exist), then single elements.
+  const int64_t rbase = rounds * (int64_t)gridDim.x * TE;
+  const int64_t nvr = (n - rbase) / VEC;  // < gridDim.x * U * blockDim.x
   const int64_t gid = (int64_t)blockIdx.x * bd + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * bd;
-  for (int64_t j = gid; j < nvr; j += gstride) {
-    const int64_t off = rbase + j * VEC;
-    T x[kMaxVecs][VEC];
+  if (gid < nvr) {
+    T x[kMaxVecs][U * VEC];
 #pragma unroll
-    for (int s = 0; s < kMaxVecs; ++s) {
-      if ((LM >> s) & 1u) {
-        V t;
-        if ((SMASK >> s) & 1u) vload<false>(t, p.v[s] + off);
-        else vload<true>(t, p.v[s] + off);
+    for (int u = 0; u < U; ++u) {
+      const int64_t j = gid + u * gstride;
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) x[s][e] = t.e[e];
-      } else {
+      for (int s = 0; s < kMaxVecs; ++s) {
+        if (((LM >> s) & 1u) && j < nvr) {
+          V t;
+          if ((SMASK >> s) & 1u) vload<false>(t, p.v[s] + rbase + j * VEC);
+          else vload<true>(t, p.v[s] + rbase + j * VEC);
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) x[s][e] = T(0);
+          for (int e = 0; e < VEC; ++e) x[s][u * VEC + e] = t.e[e];
+        } else {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) x[s][u * VEC + e] = T(0);
+        }
       }
     }
-    exec_chunk<P, T, Acc, VEC>(x, sc, acc);
 #pragma unroll
-    for (int s = 0; s < kMaxVecs; ++s) {
-      if ((SMASK >> s) & 1u) {
-        V t;
+    for (int u = 0; u < U; ++u) {
+      const int64_t j = gid + u * gstride;
+      if (j < nvr) {
+        T xu[kMaxVecs][VEC];
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) t.e[e] = x[s][e];
-        vstore(p.v[s] + off, t);
+        for (int s = 0; s < kMaxVecs; ++s) {
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) xu[s][e] = x[s][u * VEC + e];
+        }
+        exec_chunk<P, T, Acc, VEC>(xu, sc, acc);
+#pragma unroll
+        for (int s = 0; s < kMaxVecs; ++s) {
+          if ((SMASK >> s) & 1u) {
+            V t;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) t.e[e] = xu[s][e];
+            vstore(p.v[s] + rbase + j * VEC, t);
+          }
+        }
       }
     }
   }
@@ -209,16 +234,20 @@ __global__ void __launch_bounds__(256) fused_kernel(const MapParams<T> p) {
       if ((SMASK >> s) & 1u) p.v[s][i] = x[s][0];
   }
 
+  trace_mark(p.trace, TR_PRE_COMBINE);
+  bool last = false;
   if constexpr (NR > 0) {
     __shared__ double smem[kMaxBlock];
     double vals[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) vals[r] = acc[r].value();
-    if (grid_combine<double, NR>(vals, (double*)p.partials, p.ticket, smem) && threadIdx.x == 0) {
+    last = grid_combine<double, NR>(vals, (double*)p.partials, p.ticket, smem);
+    if (last && threadIdx.x == 0) {
 #pragma unroll
       for (int r = 0; r < NR; ++r) p.red_out[r] = vals[r];
     }
   }
+  trace_end(p.trace, last);
 }
 
 // Element-wise access variant for operands that are not 16-byte aligned or

@@ -102,20 +102,24 @@ struct NrmParams {
   double* out;
   void* partials;
   unsigned* ticket;
+  unsigned long long* trace = nullptr;  // per-block timeline (kTraceWords per block), or NULL
 };
 
-// Tile loop shared by the norm and plain-dot kernels: calls f(element index
-// base, vector of x[, vector of y]) on whole vectors and f1 on single
-// elements.
+// Tile loop shared by the norm and plain-dot kernels: calls fv(vector of x,
+// vector of y) on whole vectors and f1 on single elements.  As in the fused
+// loop, every block takes the same number of whole tiles, and the remainder
+// (less than a tile per block) goes to every thread of the grid as at most U
+// whole vectors in one guarded burst.
 template <typename T, int U, int VB, int NIN, class FV, class F1>
-__device__ __forceinline__ void reduce_loop(const T* x, const T* y, int64_t n, FV fv, F1 f1) {
+__device__ __forceinline__ void reduce_loop(const T* x, const T* y, int64_t n, FV fv, F1 f1,
+                                            unsigned long long* trace) {
   constexpr int VEC = VB / (int)sizeof(T);
   using V = VecT<T, VB>;
   const int64_t bd = blockDim.x;
   const int64_t TE = (int64_t)U * bd * VEC;
-  const int64_t ntiles = n / TE;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t base = tile * TE + (int64_t)threadIdx.x * VEC;
+  const int64_t rounds = (n / TE) / gridDim.x;
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int64_t base = (blockIdx.x + r * (int64_t)gridDim.x) * TE + (int64_t)threadIdx.x * VEC;
     V a[U], b[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -125,15 +129,24 @@ __device__ __forceinline__ void reduce_loop(const T* x, const T* y, int64_t n, F
 #pragma unroll
     for (int u = 0; u < U; ++u) fv(a[u], b[u]);
   }
-  const int64_t rbase = ntiles * TE;
-  const int64_t nvr = (n - rbase) / VEC;
+  trace_mark(trace, TR_TILES);
+  const int64_t rbase = rounds * (int64_t)gridDim.x * TE;
+  const int64_t nvr = (n - rbase) / VEC;  // < gridDim.x * U * blockDim.x
   const int64_t gid = (int64_t)blockIdx.x * bd + threadIdx.x;
   const int64_t gstride = (int64_t)gridDim.x * bd;
-  for (int64_t j = gid; j < nvr; j += gstride) {
-    V a, b;
-    vload<true>(a, x + rbase + j * VEC);
-    if (NIN == 2) vload<true>(b, y + rbase + j * VEC);
-    fv(a, b);
+  if (gid < nvr) {
+    V a[U], b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t j = gid + u * gstride;
+      if (j < nvr) {
+        vload<true>(a[u], x + rbase + j * VEC);
+        if (NIN == 2) vload<true>(b[u], y + rbase + j * VEC);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (gid + u * gstride < nvr) fv(a[u], b[u]);
   }
   for (int64_t i = rbase + nvr * VEC + gid; i < n; i += gstride) f1(x[i], NIN == 2 ? y[i] : T(0));
 }
@@ -143,6 +156,8 @@ __global__ void __launch_bounds__(256) nrm2_kernel(const NrmParams p) {
   using V = VecT<T, VB>;
   constexpr int VEC = VB / (int)sizeof(T);
   const T* x = (const T*)p.x;
+  trace_mark(p.trace, TR_START);
+  bool last = false;
   if constexpr (sizeof(T) == 4 && PLAIN) {
     Nrm2F32Plain acc;
     reduce_loop<T, U, VB, 1>(x, nullptr, p.n,
@@ -150,11 +165,12 @@ __global__ void __launch_bounds__(256) nrm2_kernel(const NrmParams p) {
 #pragma unroll
           for (int e = 0; e < VEC; ++e) acc.add(a.e[e]);
         },
-        [&](T a, T) { acc.add(a); });
+        [&](T a, T) { acc.add(a); }, p.trace);
     __shared__ float smem[kMaxBlock];
     float vals[1] = {acc.s};
-    if (grid_combine<float, 1>(vals, (float*)p.partials, p.ticket, smem) && threadIdx.x == 0)
-      *p.out = (double)sqrtf(vals[0]);
+    trace_mark(p.trace, TR_PRE_COMBINE);
+    last = grid_combine<float, 1>(vals, (float*)p.partials, p.ticket, smem);
+    if (last && threadIdx.x == 0) *p.out = (double)sqrtf(vals[0]);
   } else if constexpr (sizeof(T) == 4) {
     Nrm2F32 acc;
     reduce_loop<T, U, VB, 1>(x, nullptr, p.n,
@@ -162,11 +178,12 @@ __global__ void __launch_bounds__(256) nrm2_kernel(const NrmParams p) {
 #pragma unroll
           for (int e = 0; e < VEC; ++e) acc.add(a.e[e]);
         },
-        [&](T a, T) { acc.add(a); });
+        [&](T a, T) { acc.add(a); }, p.trace);
     __shared__ double smem[kMaxBlock];
     double vals[1] = {acc.value()};
-    if (grid_combine<double, 1>(vals, (double*)p.partials, p.ticket, smem) && threadIdx.x == 0)
-      *p.out = __dsqrt_rn(vals[0]);
+    trace_mark(p.trace, TR_PRE_COMBINE);
+    last = grid_combine<double, 1>(vals, (double*)p.partials, p.ticket, smem);
+    if (last && threadIdx.x == 0) *p.out = __dsqrt_rn(vals[0]);
   } else {
     Nrm2F64 acc;
     reduce_loop<T, U, VB, 1>(x, nullptr, p.n,
@@ -174,12 +191,14 @@ __global__ void __launch_bounds__(256) nrm2_kernel(const NrmParams p) {
 #pragma unroll
           for (int e = 0; e < VEC; ++e) acc.add(a.e[e]);
         },
-        [&](T a, T) { acc.add(a); });
+        [&](T a, T) { acc.add(a); }, p.trace);
     __shared__ double smem[kMaxBlock];
     double vals[3] = {acc.sml, acc.med, acc.big};
-    if (grid_combine<double, 3>(vals, (double*)p.partials, p.ticket, smem) && threadIdx.x == 0)
-      *p.out = blue_finish(vals[0], vals[1], vals[2]);
+    trace_mark(p.trace, TR_PRE_COMBINE);
+    last = grid_combine<double, 3>(vals, (double*)p.partials, p.ticket, smem);
+    if (last && threadIdx.x == 0) *p.out = blue_finish(vals[0], vals[1], vals[2]);
   }
+  trace_end(p.trace, last);
 }
 
 // Norm of an operand that is not 16-byte aligned: element loads (consecutive
@@ -212,6 +231,7 @@ struct DotParams {
   double* out;
   void* partials;
   unsigned* ticket;
+  unsigned long long* trace = nullptr;  // per-block timeline, or NULL
 };
 
 // Plain FP32 dot: FP32 accumulation and FP32 combination.
@@ -225,7 +245,7 @@ __global__ void __launch_bounds__(256) dot_plain_kernel(const DotParams p) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) acc.add_prod(a.e[e], b.e[e]);
       },
-      [&](float a, float b) { acc.add_prod(a, b); });
+      [&](float a, float b) { acc.add_prod(a, b); }, p.trace);
   __shared__ float smem[kMaxBlock];
   float vals[1] = {acc.s};
   if (grid_combine<float, 1>(vals, (float*)p.partials, p.ticket, smem) && threadIdx.x == 0)

@@ -75,12 +75,6 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, unsigned parity) {
   return done != 0;
 }
 
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
 // At most `polls` tests of the phase (none when polls is 0) and at most
 // kStageWaitNs of the global timer.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned polls = kStageSpins) {
@@ -116,6 +110,7 @@ __global__ void __launch_bounds__(256) staged_kernel(const StagedParams<T> sp) {
   __shared__ int s_ok;  // 1: this tile is in shared memory; 0: read it from global memory
 
   const MapParams<T>& p = sp.m;
+  trace_mark(p.trace, TR_START);
   T sc[kMaxScals];
   load_scalars<T>(p.sc, p.scode, sc);
   Acc acc[kMaxReds];
@@ -223,6 +218,7 @@ __global__ void __launch_bounds__(256) staged_kernel(const StagedParams<T> sp) {
       if ((pending >> st) & 1u) mbar_wait_bounded(&bars[st], (parity >> st) & 1u);
   }
 
+  trace_mark(p.trace, TR_TILES);
   // elements after the last whole tile
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t gstride = gstep * blockDim.x;
@@ -236,16 +232,20 @@ __global__ void __launch_bounds__(256) staged_kernel(const StagedParams<T> sp) {
       if ((SMASK >> s) & 1u) p.v[s][i] = x[s][0];
   }
 
+  trace_mark(p.trace, TR_PRE_COMBINE);
+  bool last = false;
   if constexpr (NR > 0) {
     __shared__ double smem[kMaxBlock];
     double vals[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) vals[r] = acc[r].value();
-    if (grid_combine<double, NR>(vals, (double*)p.partials, p.ticket, smem) && threadIdx.x == 0) {
+    last = grid_combine<double, NR>(vals, (double*)p.partials, p.ticket, smem);
+    if (last && threadIdx.x == 0) {
 #pragma unroll
       for (int r = 0; r < NR; ++r) p.red_out[r] = vals[r];
     }
   }
+  trace_end(p.trace, last);
 }
 
 }  // namespace salt

@@ -26,7 +26,7 @@ EXPORTS = ["salt_version", "salt_status_str", "salt_last_error", "salt_check_pro
            "salt_axpby", "salt_dot", "salt_nrm2", "salt_fill_uniform", "salt_release_workspaces",
            "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_staged_timeouts",
            "salt_dot_noalloc", "salt_eval_strided", "salt_eval_ex", "salt_explain", "salt_cg_diag", "salt_cg_diag_persistent",
-           "salt_cg_diag_one_reduction", "salt_cg_status", "salt_set_wait_limit", "salt_get_wait_limit"]
+           "salt_cg_diag_one_reduction", "salt_cg_status", "salt_set_wait_limit", "salt_get_wait_limit", "salt_trace_set"]
 
 
 class Insn(ctypes.Structure):
@@ -83,6 +83,7 @@ def _load() -> ctypes.CDLL:
         "salt_cg_diag_persistent": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp]),
         "salt_cg_diag_one_reduction": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp]),
         "salt_cg_status": (i32, [vp]),
+        "salt_trace_set": (i32, [vp, i64]),
         "salt_set_wait_limit": (i32, [i32, i64]),
         "salt_get_wait_limit": (i32, [i32, ctypes.POINTER(i64)]),
     }
@@ -301,6 +302,20 @@ def salt_cg_status(stream=None) -> None:
     """Raises SaltError(SALT_ERR_TIMEOUT) if a grid barrier of the last
     cooperative CG launch on ``stream`` ran out (synchronises the stream)."""
     _check(lib.salt_cg_status(_stream_ptr(stream)))
+
+
+TRACE_WORDS = 8
+
+
+def salt_trace_set(buf, max_blocks: int = 0) -> None:
+    """Per-block timelines into ``buf`` (an int64 CUDA tensor of at least
+    max_blocks * TRACE_WORDS entries; max_blocks defaults to what it holds);
+    None turns tracing off."""
+    if buf is None:
+        _check(lib.salt_trace_set(None, 0))
+        return
+    cap = buf.numel() // TRACE_WORDS
+    _check(lib.salt_trace_set(_ptr(buf), int(max_blocks or cap)))
 
 
 WAIT_STAGED, WAIT_CG_BARRIER = 1, 2
