@@ -618,8 +618,11 @@ def summary_of(r: dict) -> dict:
         out["figure1_us"] = {k: c[k] for k in ("l2_warm_us", "l2_flushed_us") if k in c}
     cg = r.get("cg")
     if cg:
-        out["cg_gbs"] = {dt: {"two_pass": cg[dt]["gbs_fused"], "one_reduction": cg[dt]["one_reduction"]["gbs"]}
+        out["cg_gbs"] = {dt: {"two_pass": cg[dt]["gbs_fused"], "one_reduction": cg[dt]["one_reduction"]["gbs"],
+                              "auto": cg[dt]["auto"]["form"], "auto_vs_best": cg[dt]["auto"]["vs_best"]}
                          for dt in DTYPES if dt in cg}
+        lat = cg.get("per_iteration_latency", {}).get("rows", {})
+        out["cg_auto_vs_best_per_iteration"] = {dt: [r.get("auto_vs_best") for r in rows] for dt, rows in lat.items()}
     pv = r.get("cpu_baseline", {}).get("precision_vs_exact")
     if pv:
         worst = {}
@@ -1071,6 +1074,9 @@ def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> 
         rho_c = torch.zeros(2 * iters + 2, dtype=torch.float64, device="cuda")
         ms_c = timed(lambda: salt.salt_cg_diag(d, b, x, r, p, q, iters, rho_c, one_reduction=True))
         cbytes = (4 + 7 + 9 * (iters - 1)) * es * n
+        x.zero_()
+        form, _ = salt.salt_cg_autotune(d, b, x, r, p, q, iters, rho_c, reps=1)  # setup, untimed
+        ms_a = timed(lambda: salt.salt_cg_diag_auto(d, b, x, r, p, q, iters, rho_c))
         out[dt] = {"n": n, "iters": iters, "ms_fused": round(ms_f, 3), "ms_unfused": round(ms_u, 3),
                    "ms_per_iter_fused": round(ms_f / iters, 4),
                    "gbs_fused": round(abytes / (ms_f * 1e-3) / 1e9, 1),
@@ -1081,7 +1087,9 @@ def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> 
                    "rho_rel_diff_fused_vs_unfused": float(abs(h_f[-1] - h_u[-1]) / h_f[-1]),
                    "one_reduction": {"ms": round(ms_c, 3), "gbs": round(cbytes / (ms_c * 1e-3) / 1e9, 1),
                                      "speedup_vs_fused": round(ms_f / ms_c, 3),
-                                     "rel_residual": float(np.sqrt(rho_c[-2].item() / rho_c[0].item()))}}
+                                     "rel_residual": float(np.sqrt(rho_c[-2].item() / rho_c[0].item()))},
+                   "auto": {"form": ("two_pass", "persistent", "one_reduction")[form], "ms": round(ms_a, 3),
+                            "vs_best": round(min(ms_f, ms_c) / ms_a, 3)}}
         del d, b, x, r, p, q, vecs
         torch.cuda.empty_cache()
     return out
@@ -1278,8 +1286,15 @@ def cg_latency_measure(torch, salt, sizes=(1 << 14, 1 << 17, 1 << 20, 1 << 24), 
             salt.salt_fill_uniform(b, 32)
             rho = torch.zeros(2 * iters + 2, dtype=torch.float64, device="cuda")
             row = {"n": n}
-            for label, kw in (("launch_per_pass_us", {}), ("persistent_us", {"persistent": True}),
-                              ("one_reduction_us", {"one_reduction": True})):
+            x.zero_()
+            form, _ = salt.salt_cg_autotune(d, b, x, r, p, q, iters, rho, reps=2)  # setup, untimed
+            row["auto_form"] = ("two_pass", "persistent", "one_reduction")[form]
+            for label, fn in (("launch_per_pass_us", lambda: salt.salt_cg_diag(d, b, x, r, p, q, iters, rho)),
+                              ("persistent_us", lambda: salt.salt_cg_diag(d, b, x, r, p, q, iters, rho,
+                                                                          persistent=True)),
+                              ("one_reduction_us", lambda: salt.salt_cg_diag(d, b, x, r, p, q, iters, rho,
+                                                                             one_reduction=True)),
+                              ("auto_us", lambda: salt.salt_cg_diag_auto(d, b, x, r, p, q, iters, rho))):
                 ts = []
                 for _ in range(reps + 1):
                     x.zero_()
@@ -1287,13 +1302,15 @@ def cg_latency_measure(torch, salt, sizes=(1 << 14, 1 << 17, 1 << 20, 1 << 24), 
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    salt.salt_cg_diag(d, b, x, r, p, q, iters, rho, **kw)
+                    fn()
                     e1.record(stream)
                     torch.cuda.synchronize()
                     ts.append(e0.elapsed_time(e1))
                 row[label] = round(float(np.median(ts[1:])) * 1e3 / iters, 2)
             row["speedup"] = round(row["launch_per_pass_us"] / row["persistent_us"], 2)
             row["speedup_one_reduction"] = round(row["launch_per_pass_us"] / row["one_reduction_us"], 2)
+            row["auto_vs_best"] = round(min(row["launch_per_pass_us"], row["persistent_us"],
+                                            row["one_reduction_us"]) / row["auto_us"], 3)
             rows.append(row)
             del d, b, x, r, p, q
         out[dt] = rows

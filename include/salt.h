@@ -277,6 +277,40 @@ salt_status salt_cg_diag_persistent(int32_t dtype, int64_t n, const void* d, con
 salt_status salt_cg_diag_one_reduction(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r,
                                        void* p, void* s, int32_t iters, double* rho, void* stream);
 
+/* salt_cg_diag_auto -- the same CG for diag(d) x = b in whichever of the
+ * three forms is fastest for the dtype and size: SALT_CG_TWO_PASS
+ * (salt_cg_diag), SALT_CG_PERSISTENT (salt_cg_diag_persistent) or
+ * SALT_CG_ONE_REDUCTION (salt_cg_diag_one_reduction), looked up per dtype and
+ * n's log2 bucket in a table whose defaults come from measurements on GB300
+ * (FP32: the one-reduction form, except 2^19 <= n < 2^22 where the forms tie
+ * and the two-pass form is kept; FP64: the one-reduction form below 2^19,
+ * the two-pass form from 2^19, where the FP64 pipe bounds the
+ * one-reduction pass).  Arguments as the chosen form; rho must hold
+ * 2 * iters + 2 doubles (the most any form writes); in every form rho[2k]
+ * is the squared residual norm after k iterations, and rho[2k+1] is p.q
+ * (two-pass, persistent) or delta (one-reduction).  *form_used (may be
+ * NULL) receives the form.  Not in the paper.  Errors as the chosen form. */
+#define SALT_CG_TWO_PASS 0
+#define SALT_CG_PERSISTENT 1
+#define SALT_CG_ONE_REDUCTION 2
+salt_status salt_cg_diag_auto(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r, void* p,
+                              void* q, int32_t iters, double* rho, int32_t* form_used, void* stream);
+/* Pins the form salt_cg_diag_auto uses for dtype and n's log2 bucket
+ * (form < 0: back to the default) / reports it.  Errors: SALT_ERR_DTYPE,
+ * SALT_ERR_ARG. */
+salt_status salt_cg_form_set(int32_t dtype, int64_t n, int32_t form);
+salt_status salt_cg_form_get(int32_t dtype, int64_t n, int32_t* form);
+/* Times the three forms (reps runs each after one warm-up, CUDA events on
+ * `stream`) on the caller's vectors, every run starting from x as passed (it
+ * is saved to a temporary device buffer and restored, and left as passed at
+ * the end); r, p, q and rho are overwritten.  Pins the fastest for dtype and
+ * n's bucket and returns it (*best_form) with its milliseconds per run
+ * (*best_ms); either may be NULL.  Synchronous; allocates.  Errors as the
+ * forms, SALT_ERR_ARG (reps outside [1, 1000]), SALT_ERR_CUDA. */
+salt_status salt_cg_autotune(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r, void* p,
+                             void* q, int32_t iters, double* rho, int32_t reps, int32_t* best_form, double* best_ms,
+                             void* stream);
+
 /* Status of the last cooperative CG launch (salt_cg_diag_persistent or
  * salt_cg_diag_one_reduction) on `stream`: synchronises the stream, then
  * returns SALT_OK if every grid barrier of that launch completed, or

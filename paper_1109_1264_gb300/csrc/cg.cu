@@ -27,7 +27,10 @@
 
 #include <atomic>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 
 #include "../../include/salt.h"
 #include "common.cuh"
@@ -500,4 +503,135 @@ extern "C" salt_status salt_cg_diag_one_reduction(int32_t dtype, int64_t n, cons
   if (st != SALT_OK) return st;
   return dtype == SALT_F32 ? launch_cg<float>(n, vecs, iters, rho, s, true)
                            : launch_cg<double>(n, vecs, iters, rho, s, true);
+}
+
+// ------------------------------------------------------------------------
+// salt_cg_diag_auto: the form chosen per (dtype, log2 n) bucket.  Defaults
+// from per-iteration times measured on GB300 (100 iterations, n = 2^14 ..
+// 2^24, and 16 iterations at 2^28): the one-reduction form wins wherever
+// launches or barriers dominate and for FP32 at large n (9 vector passes
+// per iteration instead of 11); for FP64 at large n the two-pass form wins,
+// because the one-reduction pass needs more FP64 instructions per element
+// and FP64 kernels are bound by the FP64 pipe; around n = 2^20 FP32 the
+// forms tie and the two-pass form is kept.
+namespace salt {
+namespace {
+
+std::mutex g_form_mu;
+std::map<std::pair<int, int>, int> g_form;  // (dtype, bucket) -> SALT_CG_*
+
+int log2_bucket(int64_t n) {
+  int b = 0;
+  while (b < 62 && (int64_t(1) << (b + 1)) <= n) ++b;
+  return b;
+}
+
+int default_form(int32_t dtype, int64_t n) {
+  const int b = log2_bucket(n);
+  if (dtype == SALT_F64) return b < 19 ? SALT_CG_ONE_REDUCTION : SALT_CG_TWO_PASS;
+  return (b >= 19 && b < 22) ? SALT_CG_TWO_PASS : SALT_CG_ONE_REDUCTION;
+}
+
+int form_for(int32_t dtype, int64_t n) {
+  std::lock_guard<std::mutex> lk(g_form_mu);
+  auto it = g_form.find(std::make_pair((int)dtype, log2_bucket(n)));
+  return it != g_form.end() ? it->second : default_form(dtype, n);
+}
+
+salt_status run_form(int form, int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r, void* p,
+                     void* q, int32_t iters, double* rho, void* stream) {
+  if (form == SALT_CG_PERSISTENT) return salt_cg_diag_persistent(dtype, n, d, b, x, r, p, q, iters, rho, stream);
+  if (form == SALT_CG_ONE_REDUCTION) return salt_cg_diag_one_reduction(dtype, n, d, b, x, r, p, q, iters, rho, stream);
+  return salt_cg_diag(dtype, n, d, b, x, r, p, q, iters, rho, stream);
+}
+
+bool form_valid(int32_t form) {
+  return form == SALT_CG_TWO_PASS || form == SALT_CG_PERSISTENT || form == SALT_CG_ONE_REDUCTION;
+}
+
+}  // namespace
+}  // namespace salt
+
+extern "C" salt_status salt_cg_form_set(int32_t dtype, int64_t n, int32_t form) {
+  if (dtype != SALT_F32 && dtype != SALT_F64) return report_error(SALT_ERR_DTYPE, "dtype must be SALT_F32 or SALT_F64");
+  if (n < 0) return report_error(SALT_ERR_ARG, "n must be >= 0");
+  std::lock_guard<std::mutex> lk(g_form_mu);
+  const auto key = std::make_pair((int)dtype, log2_bucket(n));
+  if (form < 0) {
+    g_form.erase(key);  // back to the default
+    return SALT_OK;
+  }
+  if (!form_valid(form)) return report_error(SALT_ERR_ARG, "unknown CG form");
+  g_form[key] = form;
+  return SALT_OK;
+}
+
+extern "C" salt_status salt_cg_form_get(int32_t dtype, int64_t n, int32_t* form) {
+  if (dtype != SALT_F32 && dtype != SALT_F64) return report_error(SALT_ERR_DTYPE, "dtype must be SALT_F32 or SALT_F64");
+  if (!form) return report_error(SALT_ERR_ARG, "form is NULL");
+  *form = form_for(dtype, n < 0 ? 0 : n);
+  return SALT_OK;
+}
+
+extern "C" salt_status salt_cg_diag_auto(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r,
+                                         void* p, void* q, int32_t iters, double* rho, int32_t* form_used,
+                                         void* stream) {
+  if (dtype != SALT_F32 && dtype != SALT_F64) return report_error(SALT_ERR_DTYPE, "dtype must be SALT_F32 or SALT_F64");
+  const int form = form_for(dtype, n < 0 ? 0 : n);
+  if (form_used) *form_used = form;
+  return run_form(form, dtype, n, d, b, x, r, p, q, iters, rho, stream);
+}
+
+extern "C" salt_status salt_cg_autotune(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r,
+                                        void* p, void* q, int32_t iters, double* rho, int32_t reps,
+                                        int32_t* best_form, double* best_ms, void* stream) {
+  if (dtype != SALT_F32 && dtype != SALT_F64) return report_error(SALT_ERR_DTYPE, "dtype must be SALT_F32 or SALT_F64");
+  if (reps < 1 || reps > 1000) return report_error(SALT_ERR_ARG, "reps must be in [1, 1000]");
+  if (n < 0) return report_error(SALT_ERR_ARG, "n must be >= 0");
+  const cudaStream_t s = (cudaStream_t)stream;
+  // every form is validated (and its workspace created) before anything runs
+  void* vecs[6] = {const_cast<void*>(d), p, q, x, r, const_cast<void*>(b)};
+  salt_status st = cg_validate(dtype, n, vecs, iters, rho, s);
+  if (st != SALT_OK) return st;
+  const size_t bytes = (size_t)n * (dtype == SALT_F32 ? 4 : 8);
+  void* x0 = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = bytes ? cudaMalloc(&x0, bytes) : cudaSuccess;
+  if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(x0, x, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  int best = -1;
+  float best_t = 0.f;
+  for (int form = SALT_CG_TWO_PASS; form <= SALT_CG_ONE_REDUCTION && e == cudaSuccess && st == SALT_OK; ++form) {
+    float total = 0.f;
+    for (int k = 0; k <= reps && e == cudaSuccess && st == SALT_OK; ++k) {  // k = 0: warm-up
+      if (bytes) e = cudaMemcpyAsync(x, x0, bytes, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      if (e == cudaSuccess) st = run_form(form, dtype, n, d, b, x, r, p, q, iters, rho, stream);
+      if (e == cudaSuccess && st == SALT_OK) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess && st == SALT_OK) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess && st == SALT_OK) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (k > 0) total += ms;
+    }
+    if (e == cudaSuccess && st == SALT_OK && (best < 0 || total < best_t)) {
+      best = form;
+      best_t = total;
+    }
+  }
+  // x is given back as the caller passed it
+  if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(x, x0, bytes, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (x0) cudaFree(x0);
+  if (st != SALT_OK) return st;
+  if (e != cudaSuccess) return report_error(SALT_ERR_CUDA, std::string("CG autotuner: ") + cudaGetErrorString(e));
+  {
+    std::lock_guard<std::mutex> lk(g_form_mu);
+    g_form[std::make_pair((int)dtype, log2_bucket(n))] = best;
+  }
+  if (best_form) *best_form = best;
+  if (best_ms) *best_ms = best_t / reps;
+  return SALT_OK;
 }

@@ -26,7 +26,8 @@ EXPORTS = ["salt_version", "salt_status_str", "salt_last_error", "salt_check_pro
            "salt_axpby", "salt_dot", "salt_nrm2", "salt_fill_uniform", "salt_release_workspaces",
            "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_staged_timeouts",
            "salt_dot_noalloc", "salt_eval_strided", "salt_eval_ex", "salt_explain", "salt_cg_diag", "salt_cg_diag_persistent",
-           "salt_cg_diag_one_reduction", "salt_cg_status", "salt_set_wait_limit", "salt_get_wait_limit", "salt_trace_set"]
+           "salt_cg_diag_one_reduction", "salt_cg_status", "salt_set_wait_limit", "salt_get_wait_limit", "salt_trace_set",
+           "salt_cg_diag_auto", "salt_cg_form_set", "salt_cg_form_get", "salt_cg_autotune"]
 
 
 class Insn(ctypes.Structure):
@@ -84,6 +85,11 @@ def _load() -> ctypes.CDLL:
         "salt_cg_diag_one_reduction": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp, vp]),
         "salt_cg_status": (i32, [vp]),
         "salt_trace_set": (i32, [vp, i64]),
+        "salt_cg_diag_auto": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp, ctypes.POINTER(i32), vp]),
+        "salt_cg_form_set": (i32, [i32, i64, i32]),
+        "salt_cg_form_get": (i32, [i32, i64, ctypes.POINTER(i32)]),
+        "salt_cg_autotune": (i32, [i32, i64, vp, vp, vp, vp, vp, vp, i32, vp, i32, ctypes.POINTER(i32),
+                                   ctypes.POINTER(ctypes.c_double), vp]),
         "salt_set_wait_limit": (i32, [i32, i64]),
         "salt_get_wait_limit": (i32, [i32, ctypes.POINTER(i64)]),
     }
@@ -296,6 +302,45 @@ def salt_cg_diag(d, b, x, r, p, q, iters: int, rho, stream=None, persistent: boo
     else:
         fn = lib.salt_cg_diag_persistent if persistent else lib.salt_cg_diag
     _check(fn(dt, _n_of(vs), *[_ptr(v) for v in vs], int(iters), _ptr(rho), _stream_ptr(stream)))
+
+
+CG_TWO_PASS, CG_PERSISTENT, CG_ONE_REDUCTION = 0, 1, 2
+
+
+def salt_cg_diag_auto(d, b, x, r, p, q, iters: int, rho, stream=None) -> int:
+    """CG for diag(d) x = b in the form the table picks for the dtype and n
+    (salt_cg_diag_auto); ``rho`` >= 2*iters + 2 entries.  Returns the form."""
+    vs = [d, b, x, r, p, q]
+    _contig(vs)
+    dt = _common_dtype(vs)
+    _check_rho(rho, int(iters), True)
+    form = ctypes.c_int32(-1)
+    _check(lib.salt_cg_diag_auto(dt, _n_of(vs), *[_ptr(v) for v in vs], int(iters), _ptr(rho), ctypes.byref(form),
+                                 _stream_ptr(stream)))
+    return form.value
+
+
+def salt_cg_form_set(dtype: int, n: int, form: int) -> None:
+    _check(lib.salt_cg_form_set(int(dtype), int(n), int(form)))
+
+
+def salt_cg_form_get(dtype: int, n: int) -> int:
+    f = ctypes.c_int32()
+    _check(lib.salt_cg_form_get(int(dtype), int(n), ctypes.byref(f)))
+    return f.value
+
+
+def salt_cg_autotune(d, b, x, r, p, q, iters: int, rho, reps: int = 3, stream=None) -> tuple[int, float]:
+    """Times the three CG forms on these vectors (x restored), pins the
+    fastest for the dtype and n's bucket; returns (form, ms per run)."""
+    vs = [d, b, x, r, p, q]
+    _contig(vs)
+    dt = _common_dtype(vs)
+    _check_rho(rho, int(iters), True)
+    form, ms = ctypes.c_int32(-1), ctypes.c_double()
+    _check(lib.salt_cg_autotune(dt, _n_of(vs), *[_ptr(v) for v in vs], int(iters), _ptr(rho), int(reps),
+                                ctypes.byref(form), ctypes.byref(ms), _stream_ptr(stream)))
+    return form.value, ms.value
 
 
 def salt_cg_status(stream=None) -> None:

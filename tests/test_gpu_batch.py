@@ -239,3 +239,41 @@ def test_fp32_items_both_access_widths(salt, cuda_dev):
     torch.cuda.synchronize()
     check(items, tensors, slots, red.cpu().numpy())
     b.close()
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32], ids=["f64", "f32"])
+def test_reductions_after_divergent_tails(salt, cuda_dev, dt):
+    """Lengths whose last elements are taken by lane 0 alone (a scalar tail
+    after the vector loop) or by a partial warp: n in 1..13, 64, 65, 100, 101,
+    513, 1025, 4097, for DOT, SUMSQ and the CG update, at every unroll depth,
+    in the batch kernel and in the single-expression kernel.  The block sums
+    that follow the divergent tails use full-warp shuffles; every reduction
+    must be within tolerance of its exact value."""
+    import tolerance
+    code = salt.F32 if dt == np.float32 else salt.F64
+    lengths = list(range(1, 14)) + [64, 65, 100, 101, 513, 1025, 4097]
+    progs = [(P.PROG_DOT, 2, 0), (P.PROG_SUMSQ, 1, 0), (P.PROG_CG, 3, 2)]
+    rng = np.random.default_rng(61)
+    items = []
+    for prog, nv, ns in progs:
+        for n in lengths:
+            items.append((prog, dt, [rng.uniform(-1, 1, n).astype(dt) for _ in range(nv)],
+                          list(rng.uniform(-2, 2, ns))))
+    for unroll in (1, 2, 4):
+        b, tensors, slots = build(salt, items, cuda_dev)
+        b.set_config(unroll, 128, 0, 16 * 128 * unroll * 4)
+        red = torch.full((len(items),), float("nan"), dtype=torch.float64, device=cuda_dev)
+        b.launch(red)
+        torch.cuda.synchronize()
+        check(items, tensors, slots, red.cpu().numpy())
+        b.close()
+        for prog, _, vecs, scal in items:
+            n = len(vecs[0])
+            salt.salt_tune_set(prog, code, n, unroll, 16, 128, 0)
+            tv = [torch.from_numpy(v.copy()).to(cuda_dev) for v in vecs]
+            r = torch.full((1,), float("nan"), dtype=torch.float64, device=cuda_dev)
+            salt.salt_eval(prog, tv, scal, red_out=r)
+            torch.cuda.synchronize()
+            _, refs, scales = reference((prog, dt, vecs, scal))
+            tolerance.check(r.item(), refs[0], scales[0], dt, (prog, n, unroll))
+        salt.salt_tune_clear()

@@ -372,3 +372,48 @@ def test_cg_one_reduction(saltlib, cuda_dev, dt):
             assert np.linalg.norm(xg - xl) <= tx_ * max(np.linalg.norm(xl), 1.0), (n, iters)
             for j in range(iters + 1):
                 assert abs(g[2 * j] - ho[2 * j]) <= tx_ * ho[0] + 1e-300, (n, iters, j)
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_cg_auto_and_autotune(saltlib, cuda_dev, dt):
+    """salt_cg_diag_auto runs the form its table names, bit for bit the same
+    as calling that form directly; salt_cg_autotune times the three forms,
+    gives x back as passed, and pins the winner for the size's bucket."""
+    s = saltlib
+    rng = np.random.default_rng(43)
+    code = s.F32 if dt == np.float32 else s.F64
+    iters = 4
+    try:
+        for n in (999, 70001, (1 << 20) + 5):
+            d = rng.choice([1.0, 2.0, 5.0, 8.0], n).astype(dt)
+            b = rng.uniform(-1, 1, n).astype(dt)
+            x0 = rng.uniform(-3, 3, n).astype(dt)
+
+            def fresh():
+                td, tb, tx = (torch.from_numpy(v.copy()).to(cuda_dev) for v in (d, b, x0))
+                return [td, tb, tx] + [torch.zeros(n, dtype=TDT[dt], device=cuda_dev) for _ in range(3)]
+
+            for form in (s.CG_TWO_PASS, s.CG_PERSISTENT, s.CG_ONE_REDUCTION):
+                s.salt_cg_form_set(code, n, form)
+                va = fresh()
+                rho_a = torch.zeros(2 * iters + 2, dtype=torch.float64, device=cuda_dev)
+                assert s.salt_cg_diag_auto(*va, iters, rho_a) == form
+                vd = fresh()
+                rho_d = torch.zeros(2 * iters + 2, dtype=torch.float64, device=cuda_dev)
+                s.salt_cg_diag(*vd, iters, rho_d, persistent=form == s.CG_PERSISTENT,
+                               one_reduction=form == s.CG_ONE_REDUCTION)
+                torch.cuda.synchronize()
+                assert torch.equal(va[2], vd[2]) and torch.equal(rho_a, rho_d), (n, form)
+                xs = b.astype(np.float64) / d.astype(np.float64)
+                xg = va[2].cpu().numpy().astype(np.float64)
+                assert np.linalg.norm(xg - xs) / np.linalg.norm(xs) < (1e-11 if dt == np.float64 else 1e-4)
+            s.salt_cg_form_set(code, n, -1)
+            v = fresh()
+            rho = torch.zeros(2 * iters + 2, dtype=torch.float64, device=cuda_dev)
+            form, ms = s.salt_cg_autotune(*v, iters, rho, reps=2)
+            assert form in (s.CG_TWO_PASS, s.CG_PERSISTENT, s.CG_ONE_REDUCTION) and ms > 0
+            assert s.salt_cg_form_get(code, n) == form
+            assert np.array_equal(v[2].cpu().numpy(), x0)  # x given back as passed
+    finally:
+        for n in (999, 70001, (1 << 20) + 5):
+            s.salt_cg_form_set(code, n, -1)

@@ -214,3 +214,22 @@ def test_cg_binding_checks_rho_before_the_call(saltlib, one_reduction):
     with pytest.raises(s.SaltError) as e:
         s.salt_cg_diag(*vecs, iters, torch.zeros(need, dtype=torch.float64), one_reduction=one_reduction)
     assert "CUDA tensor" in e.value.message
+
+
+def test_cg_form_table(saltlib):
+    """salt_cg_diag_auto's form table: the measured defaults, pins per dtype
+    and log2 bucket, reset, argument errors (no GPU needed)."""
+    s = saltlib
+    assert s.salt_cg_form_get(s.F32, 1 << 14) == s.CG_ONE_REDUCTION
+    assert s.salt_cg_form_get(s.F32, 1 << 20) == s.CG_TWO_PASS
+    assert s.salt_cg_form_get(s.F32, 1 << 28) == s.CG_ONE_REDUCTION
+    assert s.salt_cg_form_get(s.F64, (1 << 19) - 1) == s.CG_ONE_REDUCTION
+    assert s.salt_cg_form_get(s.F64, 1 << 19) == s.CG_TWO_PASS
+    s.salt_cg_form_set(s.F64, 5000, s.CG_PERSISTENT)
+    assert s.salt_cg_form_get(s.F64, 4096) == s.CG_PERSISTENT  # same bucket [2^12, 2^13)
+    assert s.salt_cg_form_get(s.F64, 8192) == s.CG_ONE_REDUCTION
+    s.salt_cg_form_set(s.F64, 5000, -1)
+    assert s.salt_cg_form_get(s.F64, 4096) == s.CG_ONE_REDUCTION
+    assert s.lib.salt_cg_form_set(s.F32, 10, 3) == s.ERR_ARG
+    assert s.lib.salt_cg_form_set(7, 10, 0) == s.ERR_DTYPE
+    assert s.lib.salt_cg_form_get(s.F32, 10, None) == s.ERR_ARG
