@@ -354,6 +354,7 @@ def main():
     ap.add_argument("--fixed-e-cfg", default=None,
                     help="profiling runs: skip the autotuner and launch e with U,VB,BLOCK,BLOCKS_PER_SM[,STAGE_BYTES]")
     ap.add_argument("--cg-log2", type=int, default=28)
+    ap.add_argument("--no-generic", action="store_true")
     ap.add_argument("--trace-reductions", action="store_true",
                     help="per-block timelines of dot and nrm2 from n = 2^4 to 2^26 (launch ramp, tail, combine)")
     args = ap.parse_args()
@@ -569,6 +570,9 @@ def main():
         torch.cuda.empty_cache()
         result["served"] = served_measure(salt, collect=samples["served"])
     result["config1_figure1"] = config1_measure(torch, salt)
+    if not args.no_generic:
+        torch.cuda.empty_cache()
+        result["generic"] = generic_measure(torch, salt)
     probe = fp64_probe(torch, salt)
     result["fp64_probe"] = probe
     if roof["bound"] == "alu" and probe.get("gops"):
@@ -623,6 +627,9 @@ def summary_of(r: dict) -> dict:
                          for dt in DTYPES if dt in cg}
         lat = cg.get("per_iteration_latency", {}).get("rows", {})
         out["cg_auto_vs_best_per_iteration"] = {dt: [r.get("auto_vs_best") for r in rows] for dt, rows in lat.items()}
+    g = r.get("generic")
+    if g:
+        out["generic_gbs"] = {k: [v["interpreter"]["gbs"], v["jit"]["gbs"]] for k, v in g["rows"].items()}
     pv = r.get("cpu_baseline", {}).get("precision_vs_exact")
     if pv:
         worst = {}
@@ -635,6 +642,61 @@ def summary_of(r: dict) -> dict:
             worst[f"served_{k}"] = row["max_rel_value"]
         out["precision_rel_value"] = {k: float(f"{v:.3g}") for k, v in worst.items()}
     return out
+
+
+def generic_measure(torch, salt, log2ns=(24, 28), reps: int = 5) -> dict:
+    """The generic path: a program with no compiled instantiation (6
+    operands: f = (a - b) o (c + d) - 2.5 e, and sum f^2), FP32 and FP64, run
+    on the interpreter kernel (SALT_JIT_OFF) and as a run-time compiled fused
+    kernel (SALT_JIT_ON).  GB/s of algorithmic bytes (5 reads + 1 write per
+    element), fraction of the measured copy rate, and the first call's
+    compile time."""
+    import numpy as np
+
+    prog = [("VEC", 0), ("VEC", 1), ("SUB", 0), ("VEC", 2), ("VEC", 3), ("ADD", 0), ("MUL", 0),
+            ("SCAL", 0), ("VEC", 4), ("SMUL", 0), ("SUB", 0), ("STORE", 5), ("VEC", 5), ("SUMSQ", 0)]
+    hbm_peak, _, _ = load_peaks()
+    stream = torch.cuda.current_stream()
+    prev = salt.salt_jit_stats()["mode"]
+    out = {}
+    try:
+        for dt, tdt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
+            nmax = 1 << max(log2ns)
+            vb = [torch.empty(nmax, dtype=tdt, device="cuda") for _ in range(6)]
+            for k, t in enumerate(vb):
+                salt.salt_fill_uniform(t, 700 + k)
+            red = torch.zeros(1, dtype=torch.float64, device="cuda")
+            for lg in log2ns:
+                n = 1 << lg
+                v = [t[:n] for t in vb]
+                row = {}
+                for label, mode in (("interpreter", salt.JIT_OFF), ("jit", salt.JIT_ON)):
+                    salt.salt_set_jit(mode)
+                    st0 = salt.salt_jit_stats()
+                    t0 = time.perf_counter()
+                    salt.salt_eval(prog, v, [2.5], red_out=red)  # first call: compile (JIT)
+                    torch.cuda.synchronize()
+                    first_ms = (time.perf_counter() - t0) * 1e3
+                    st1 = salt.salt_jit_stats()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    for _ in range(reps):
+                        salt.salt_eval(prog, v, [2.5], red_out=red)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1) / reps
+                    gbs = 6 * es * n / (ms * 1e-3) / 1e9
+                    row[label] = {"ms": round(ms, 4), "gbs": round(gbs, 1), "frac_measured": round(gbs / hbm_peak, 3),
+                                  "first_call_ms": round(first_ms, 1),
+                                  "compiled": st1["kernels"] - st0["kernels"],
+                                  "from_disk": st1["disk_hits"] - st0["disk_hits"]}
+                row["jit_speedup"] = round(row["interpreter"]["ms"] / row["jit"]["ms"], 2)
+                out[f"{dt}_2^{lg}"] = row
+            del vb
+            torch.cuda.empty_cache()
+    finally:
+        salt.salt_set_jit(prev)
+    return {"program": "f = (a - b) o (c + d) - 2.5 e; sum f^2 (6 operands, no compiled shape)", "rows": out}
 
 
 def fp64_probe(torch, salt, log2n: int = 26, reps: int = 5) -> dict:
@@ -652,6 +714,7 @@ def fp64_probe(torch, salt, log2n: int = 26, reps: int = 5) -> dict:
     x = torch.empty(n, dtype=torch.float64, device="cuda")
     y = torch.empty(n, dtype=torch.float64, device="cuda")
     salt.salt_fill_uniform(x, key=977)
+    prev = salt.salt_jit_stats()["mode"]
     try:
         salt.salt_set_jit(salt.JIT_ON)
         for _ in range(3):
@@ -667,7 +730,7 @@ def fp64_probe(torch, salt, log2n: int = 26, reps: int = 5) -> dict:
     except salt.SaltError as e:
         return {"gops": None, "error": e.message[:200]}
     finally:
-        salt.salt_set_jit(salt.JIT_OFF)
+        salt.salt_set_jit(prev)
     return {"gops": round(14 * n / (ms * 1e-3) / 1e9, 1), "ms": round(ms, 4), "n": n,
             "program": "14 FP64 nodes per element (7 x (t*x + x)), 16 B per element, run-time compiled"}
 
@@ -747,26 +810,35 @@ def batched_measure(torch, salt, reps: int = 20, nitems: int = 4096, fixed: bool
 
 
 def sweep_measure(torch, salt, reps: int = 21, max_log2: int = 28) -> dict:
-    """The paper's benchmark set (Section 5) as a size sweep on the GPU: xDOT,
-    xSCAL (x = a x), xAXPY (y = a x + y) and the out-of-place scaling y = a x
-    that BLAS must express as xCOPY + xSCAL -- fused (one pass, 2 x es bytes
-    per element) versus the two calls (copy, then in-place scale: 4 x es).
-    L2 is flushed (a 256 MiB read, leaving clean lines) before every timed
-    call; median of reps.
-    torch's own kernels (torch.dot = cuBLAS dot, mul_, add_, copy_+mul_) are
-    timed the same way as context."""
+    """The BLAS-1 size sweep: every n = 2^k and 2^k + 7, k = 10 .. 28, FP32
+    and FP64, for y = a x + y (axpy), dot, nrm2 and the fused e = a a + b b -
+    c o d -- and the paper's own benchmark set (Section 5): xSCAL (x = a x)
+    and the out-of-place scaling y = a x that BLAS must express as xCOPY +
+    xSCAL, fused (one pass, 2 x es bytes per element) against the two calls
+    (4 x es).  Launch shapes autotuned per size bucket (untimed setup); L2
+    flushed (a 256 MiB read, leaving clean lines) before every timed call;
+    median of reps.  Per cell: GB/s of algorithmic bytes, its fraction of
+    the measured copy rate and of the nominal 8 TB/s, for FP64 the FP64-pipe
+    fraction (instructions per element x n / time against 2 / clock / SM x
+    152 SMs at the maximum clock), and whether it meets the 85%-of-HBM gate
+    (n >= 2^24).  torch's own kernels (torch.dot = cuBLAS dot, add_,
+    copy_ + mul_) are timed the same way as context."""
     import numpy as np
 
-    from paper_1109_1264_gb300.programs import PROG_DOT, PROG_SCALE
+    from paper_1109_1264_gb300.programs import PROG_DOT, PROG_E, PROG_SCALE
     scal = [("SCAL", 0), ("VEC", 0), ("SMUL", 0), ("STORE", 0)]
     axpy = [("SCAL", 0), ("VEC", 0), ("SMUL", 0), ("VEC", 1), ("ADD", 0), ("STORE", 1)]
     copy = [("VEC", 0), ("STORE", 1)]
+    hbm_peak, _, sm_max = load_peaks()
+    alu_peak = f64_alu_peak_gops(sm_max)
+    # FP64 instructions per element (one per node; the reductions' FMA)
+    f64_instr = {"axpy": 2, "dot": 1, "nrm2": 1, "e": 5, "scal": 1, "copy_scal_fused": 1}
     # L2 flush: READ a 256 MiB buffer before each timed call, so that L2 holds
     # clean lines of another buffer (a write-based flush would leave up to
     # the whole L2 dirty, and the timed kernel would pay its write-back).
     flush = torch.zeros(64 << 20, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    sizes = sorted({1 << k for k in range(10, max_log2 + 1)} | {(1 << k) + 7 for k in range(10, max_log2 + 1, 2)})
+    sizes = sorted({1 << k for k in range(10, max_log2 + 1)} | {(1 << k) + 7 for k in range(10, max_log2 + 1)})
     out = {}
 
     def timed(fn):
@@ -784,46 +856,61 @@ def sweep_measure(torch, salt, reps: int = 21, max_log2: int = 28) -> dict:
 
     for dt, tdt, es in (("f32", torch.float32, 4), ("f64", torch.float64, 8)):
         rows = []
-        xb = torch.empty(1 << max_log2, dtype=tdt, device="cuda")
-        yb = torch.empty(1 << max_log2, dtype=tdt, device="cuda")
-        salt.salt_fill_uniform(xb, 11)
-        salt.salt_fill_uniform(yb, 12)
+        nmax = (1 << max_log2) + 7
+        a, b, c, d, x, y = (torch.empty(nmax, dtype=tdt, device="cuda") for _ in range(6))
+        for k, t in enumerate((a, b, c, d, x, y)):
+            salt.salt_fill_uniform(t, 11 + k)
         red = torch.zeros(1, dtype=torch.float64, device="cuda")
         salt.salt_tune_clear()
         for n in sizes:
-            if n > (1 << max_log2):
+            if n > nmax:
                 continue
-            x, y = xb[:n], yb[:n]
+            va, vb, vc, vd, vx, vy = (t[:n] for t in (a, b, c, d, x, y))
             r = {"n": n}
             if n & (n - 1) == 0:
-                # the library's autotuner, once per size bucket (untimed
-                # setup); for operands that fit in L2 it flushes L2 before
-                # each timed call, like the calls timed here.
-                salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_DOT, [x, y], red_out=red, reps=5)
-                salt.salt_autotune(salt.KERNEL_PROGRAM, scal, [x], [1.0], reps=5)
-                salt.salt_autotune(salt.KERNEL_PROGRAM, axpy, [x, y], [0.0], reps=5)
-                salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_SCALE, [x, y], [1.0], reps=5)
-                salt.salt_autotune(salt.KERNEL_PROGRAM, copy, [x, y], reps=5)
-            ms = timed(lambda: salt.salt_eval(PROG_DOT, [x, y], red_out=red))
-            r["dot"] = round(2 * es * n / (ms * 1e-3) / 1e9, 1)
-            ms = timed(lambda: salt.salt_eval(scal, [x], [0.999]))
-            r["scal"] = round(2 * es * n / (ms * 1e-3) / 1e9, 1)
-            ms = timed(lambda: salt.salt_eval(axpy, [x, y], [1e-3]))
-            r["axpy"] = round(3 * es * n / (ms * 1e-3) / 1e9, 1)
-            ms_f = timed(lambda: salt.salt_eval(PROG_SCALE, [x, y], [1.5]))
-            ms_2 = timed(lambda: (salt.salt_eval(copy, [x, y]), salt.salt_eval(scal, [y], [1.5])))
-            # GB/s of the operation itself (2 x es bytes per element) under both schedules
-            r["copy_scal_fused"] = round(2 * es * n / (ms_f * 1e-3) / 1e9, 1)
-            r["copy_scal_two_calls"] = round(2 * es * n / (ms_2 * 1e-3) / 1e9, 1)
-            r["torch_dot"] = round(2 * es * n / (timed(lambda: torch.dot(x, y)) * 1e-3) / 1e9, 1)
-            r["torch_axpy"] = round(3 * es * n / (timed(lambda: y.add_(x, alpha=1e-3)) * 1e-3) / 1e9, 1)
-            r["torch_copy_scal"] = round(2 * es * n / (timed(lambda: y.copy_(x).mul_(1.5)) * 1e-3) / 1e9, 1)
+                # the library's autotuner, once per size bucket (untimed setup);
+                # for operands that fit in L2 it flushes L2 before each timed
+                # call, like the calls timed here
+                salt.salt_autotune(salt.KERNEL_PROGRAM, axpy, [vx, vy], [1e-3], reps=5)
+                salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_DOT, [vx, vy], red_out=red, reps=5)
+                salt.salt_autotune(salt.KERNEL_NRM2, None, [vx], red_out=red, reps=5)
+                salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_E, [va, vb, vc, vd, vy], [ALPHA, BETA], reps=5)
+                salt.salt_autotune(salt.KERNEL_PROGRAM, scal, [vx], [1.0], reps=5)
+                salt.salt_autotune(salt.KERNEL_PROGRAM, PROG_SCALE, [vx, vy], [1.0], reps=5)
+                salt.salt_autotune(salt.KERNEL_PROGRAM, copy, [vx, vy], reps=5)
+            cells = {
+                "axpy": (3, lambda: salt.salt_eval(axpy, [vx, vy], [1e-3])),
+                "dot": (2, lambda: salt.salt_eval(PROG_DOT, [vx, vy], red_out=red)),
+                "nrm2": (1, lambda: salt.salt_nrm2(vx, red)),
+                "e": (5, lambda: salt.salt_eval(PROG_E, [va, vb, vc, vd, vy], [ALPHA, BETA])),
+                "scal": (2, lambda: salt.salt_eval(scal, [vx], [0.999])),
+                "copy_scal_fused": (2, lambda: salt.salt_eval(PROG_SCALE, [vx, vy], [1.5])),
+                # GB/s of the operation itself (2 x es bytes per element), two calls
+                "copy_scal_two_calls": (2, lambda: (salt.salt_eval(copy, [vx, vy]),
+                                                    salt.salt_eval(scal, [vy], [1.5]))),
+            }
+            for op, (units, fn) in cells.items():
+                ms = timed(fn)
+                gbs = units * es * n / (ms * 1e-3) / 1e9
+                cell = {"gbs": round(gbs, 1), "frac_measured": round(gbs / hbm_peak, 3),
+                        "frac_nominal": round(gbs / NOMINAL_HBM_GBS, 3)}
+                if dt == "f64" and op in f64_instr:
+                    cell["frac_fp64_pipe"] = round(f64_instr[op] * n / (ms * 1e-3) / 1e9 / alu_peak, 3)
+                if n >= (1 << 24) and op != "copy_scal_two_calls":
+                    cell["gate_85"] = bool(gbs >= 0.85 * NOMINAL_HBM_GBS)
+                r[op] = cell
+            r["torch_dot_gbs"] = round(2 * es * n / (timed(lambda: torch.dot(vx, vy)) * 1e-3) / 1e9, 1)
+            r["torch_axpy_gbs"] = round(3 * es * n / (timed(lambda: vy.add_(vx, alpha=1e-3)) * 1e-3) / 1e9, 1)
+            r["torch_copy_scal_gbs"] = round(2 * es * n / (timed(lambda: vy.copy_(vx).mul_(1.5)) * 1e-3) / 1e9, 1)
             rows.append(r)
         out[dt] = rows
         salt.salt_tune_clear()
-        del xb, yb
-    return {"sweep": out, "note": "GB/s of algorithmic bytes; launch shapes autotuned per size bucket; "
-                                  "L2 flushed before each timed call; median of %d" % reps}
+        del a, b, c, d, x, y
+        torch.cuda.empty_cache()
+    return {"sweep": out, "hbm_peak_measured_gbs": hbm_peak, "nominal_gbs": NOMINAL_HBM_GBS,
+            "fp64_peak_derived_gops": round(alu_peak, 1),
+            "note": "GB/s of algorithmic bytes; launch shapes autotuned per size bucket; L2 flushed before each "
+                    "timed call; median of %d; CUDA events on this GPU advance in 2.048 us steps" % reps}
 
 
 def reduction_trace_measure(torch, salt, log2ns=(4, 12, 16, 20, 22, 24, 26), reps: int = 7) -> dict:
@@ -1059,11 +1146,12 @@ def cg_measure(torch, salt, log2n: int = 28, iters: int = 16, reps: int = 3) -> 
                 ts.append(e0.elapsed_time(e1))
             return float(np.median(ts[1:]))  # first run: warm-up (and JIT compilation)
 
+        prev = salt.salt_jit_stats()["mode"]
         salt.salt_set_jit(salt.JIT_ON)
         try:
             ms_u = timed(unfused)
         finally:
-            salt.salt_set_jit(salt.JIT_OFF)
+            salt.salt_set_jit(prev)
         ms_f = timed(fused)
         passes = 4 + 4 + 6 + 11 * (iters - 1)
         abytes = passes * es * n

@@ -159,8 +159,8 @@ const char* salt_last_error(void);
  *   compiled_out  1 if the program (after hoisting its scalar
  *                 subexpressions) has a compile-time instantiation (the
  *                 fast path; the paper's expression templates, Section 2),
- *                 0 if it runs on the generic interpreter kernel (or, with
- *                 SALT_JIT_ON, a run-time compiled one).
+ *                 0 if it runs on a run-time compiled instantiation (the
+ *                 default, see salt_set_jit) or the generic interpreter.
  * Returns SALT_OK or SALT_ERR_PROGRAM / SALT_ERR_ARG. */
 salt_status salt_check_program(const salt_insn* prog, int32_t nprog, int32_t nvecs,
                                int32_t nscal, int32_t* nred_out, int32_t* compiled_out);
@@ -453,22 +453,40 @@ salt_status salt_dot_noalloc(int32_t dtype, int64_t n, const void* x, const void
 /* ---------------------------------------------------------------------------
  * Run-time compilation of programs without a compile-time instantiation.
  * The paper's expression templates generate each expression's loop at
- * compile time (Section 2); with SALT_JIT_ON, salt_eval does the same at run
- * time for any program that has no compiled instantiation: the program is
- * written out as the template arguments of the same fused kernel, compiled
- * by NVRTC for the current GPU on the first call per (program, dtype, launch
- * shape) -- tens to hundreds of milliseconds, so make that call before any
- * stream capture -- and cached for the process.  Results are bit-identical to
- * the interpreter's.  SALT_JIT_OFF (the default): such programs run on the
- * interpreter kernel.  salt_set_jit returns SALT_ERR_ARG for another mode;
- * salt_eval returns SALT_ERR_CUDA with NVRTC's log if compilation fails or
- * NVRTC cannot be loaded. */
+ * compile time (Section 2); salt_eval does the same at run time for any
+ * program that has no compiled instantiation: the program is written out as
+ * the template arguments of the same fused kernel and compiled by NVRTC for
+ * the current GPU on the first call per (program, dtype, launch shape) --
+ * tens to hundreds of milliseconds, so make that call before any stream
+ * capture -- then cached for the process and on disk (see
+ * salt_jit_cache_dir), so later processes load it in about a millisecond.
+ * Results are bit-identical to the interpreter's.
+ *   SALT_JIT_AUTO (the default): compile; where NVRTC cannot be loaded or a
+ *                 compilation fails, run the program on the interpreter.
+ *   SALT_JIT_ON:  compile; salt_eval returns SALT_ERR_CUDA with NVRTC's log
+ *                 if compilation fails or NVRTC cannot be loaded.
+ *   SALT_JIT_OFF: such programs run on the interpreter kernel.
+ * salt_set_jit returns SALT_ERR_ARG for another mode. */
 #define SALT_JIT_OFF 0
 #define SALT_JIT_ON 1
+#define SALT_JIT_AUTO 2
 salt_status salt_set_jit(int32_t mode);
 /* Current mode, kernels compiled so far and their total compile time (ms);
  * any pointer may be NULL. */
 salt_status salt_jit_stats(int32_t* mode, int64_t* kernels, double* compile_ms);
+/* The directory of compiled kernels kept on disk: `dir` (created on the
+ * first write), or NULL / "" to keep none.  Without this call the
+ * directory is $SALT_JIT_CACHE ("0" or "off": none), else
+ * $XDG_CACHE_HOME/salt-jit, else $HOME/.cache/salt-jit.  A file is named by
+ * a hash of the kernel, the GPU architecture, the NVRTC version and the
+ * library's kernel sources, and is checked (magic word, payload hash) before
+ * it is loaded; a file that fails the check or does not load is recompiled
+ * and rewritten.  Files are written under a temporary name and renamed, so
+ * processes may share the directory.  Returns SALT_OK. */
+salt_status salt_jit_cache_dir(const char* dir);
+/* Kernels loaded from and written to the on-disk cache since the library
+ * was loaded, and the directory in use ("" if none; dir may be NULL). */
+salt_status salt_jit_cache_stats(int64_t* disk_hits, int64_t* disk_writes, char* dir, int32_t dir_len);
 
 /* Free every workspace the library holds (call with no library work in
  * flight).  Returns SALT_OK or SALT_ERR_CUDA. */

@@ -252,7 +252,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
   // faster (dot at 2^28: 6.8 against 6.5 TB/s), while for FP32 they lose a
   // fifth (5.3 against 6.4 TB/s).
   int64_t head = 0;
-  if (sizeof(T) == 4 && elementwise && !strided && (shape >= 0 || jit_mode() == SALT_JIT_ON)) {
+  if (sizeof(T) == 4 && elementwise && !strided && (shape >= 0 || jit_mode() != SALT_JIT_OFF)) {
     uintptr_t span = 0;
     for (uintptr_t A : {(uintptr_t)128, (uintptr_t)32}) {
       const uintptr_t off = (uintptr_t)a.vecs[c.vec_user[0]] % A;
@@ -280,7 +280,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
     if (st != SALT_OK) return st;
   }
 
-  if (elementwise && (shape >= 0 || jit_mode() == SALT_JIT_ON)) {
+  if (elementwise && (shape >= 0 || jit_mode() != SALT_JIT_OFF)) {
     MapParams<T> p;
     memset(&p, 0, sizeof p);
     for (int k = 0; k < c.nvec; ++k) {
@@ -376,7 +376,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
     return SALT_OK;
   }
 
-  if (jit_mode() == SALT_JIT_ON) {
+  if (jit_mode() != SALT_JIT_OFF) {
     // The fused kernel instantiated for this program at run time.  Launch
     // shape: the tuned defaults of the compiled shapes (32-byte vectors when
     // every operand allows, unroll 4 for F32 and 2 for F64, 256 threads).
@@ -538,6 +538,22 @@ salt_status validate_eval(const EvalArgs& a, Analysis* an_out) {
   return SALT_OK;
 }
 
+// In SALT_JIT_AUTO mode a program whose run-time compilation fails (NVRTC
+// missing, or a compile error) runs on the interpreter instead: the call is
+// redone with run-time compilation off for this thread.  The failure is
+// detected before anything is launched, so nothing runs twice.
+template <class F>
+static salt_status with_jit_fallback(F run) {
+  jit_failure_reset();
+  salt_status st = run();
+  if (st != SALT_OK && jit_failed() && jit_mode() == SALT_JIT_AUTO) {
+    jit_suspend(true);
+    st = run();
+    jit_suspend(false);
+  }
+  return st;
+}
+
 salt_status eval_impl(const EvalArgs& a) {
   Analysis an;
   salt_status st = validate_eval(a, &an);
@@ -562,8 +578,9 @@ salt_status eval_impl(const EvalArgs& a) {
   if (!an.scalar_nodes) {
     Canonical c;
     canonicalise(a.prog, a.nprog, &c);
-    return a.dt == SALT_F32 ? run_eval<float>(a, c, nullptr, dev, info)
-                            : run_eval<double>(a, c, nullptr, dev, info);
+    return with_jit_fallback([&] {
+      return a.dt == SALT_F32 ? run_eval<float>(a, c, nullptr, dev, info) : run_eval<double>(a, c, nullptr, dev, info);
+    });
   }
   // Scalar subexpressions: each became one scalar slot, computed here when
   // it reads only by-value scalars, else at kernel start on the device.
@@ -585,7 +602,9 @@ salt_status eval_impl(const EvalArgs& a) {
   if (h.device && !build_scalar_code(a.prog, h, c, a.nscal, sc2, a.dscal, &code))
     return set_error(SALT_ERR_PROGRAM, "scalar subexpressions too long for the device scalar code");
   const ScalarCode* pc = h.device ? &code : nullptr;
-  return a.dt == SALT_F32 ? run_eval<float>(a2, c, pc, dev, info) : run_eval<double>(a2, c, pc, dev, info);
+  return with_jit_fallback([&] {
+    return a.dt == SALT_F32 ? run_eval<float>(a2, c, pc, dev, info) : run_eval<double>(a2, c, pc, dev, info);
+  });
 }
 
 // Canonical form of a program after hoisting its scalar subexpressions (the

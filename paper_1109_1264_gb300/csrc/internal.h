@@ -61,9 +61,15 @@ void count_launch();
 unsigned cg_barrier_polls(int64_t set);
 
 // Run-time compiled fused kernels (csrc/jit.cu): the current mode
-// (SALT_JIT_OFF / SALT_JIT_ON) and the kernel for a canonical program
-// (compiled and cached on first use).
+// (SALT_JIT_OFF / SALT_JIT_ON / SALT_JIT_AUTO; SALT_JIT_OFF while this
+// thread has suspended run-time compilation) and the kernel for a canonical
+// program (compiled, or read from the on-disk cache, on first use).
 int32_t jit_mode();
+// This thread's record of a failed run-time compilation since the last reset,
+// and its suspension of run-time compilation (the SALT_JIT_AUTO fallback).
+void jit_failure_reset();
+bool jit_failed();
+void jit_suspend(bool on);
 // ds: the variant that computes scalar slots on the device (fused kernel
 // only; the element-access kernel always can).
 salt_status jit_kernel(const Canonical& c, int is_f32, int unroll, int vec_bytes, bool ds,

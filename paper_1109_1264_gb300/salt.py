@@ -775,13 +775,18 @@ def salt_tune_load(path: str) -> None:
 
 # --------------------------------------------------------- run-time compile --
 
-JIT_OFF, JIT_ON = 0, 1
+JIT_OFF, JIT_ON, JIT_AUTO = 0, 1, 2
 lib.salt_set_jit.restype = ctypes.c_int32
 lib.salt_set_jit.argtypes = [ctypes.c_int32]
 lib.salt_jit_stats.restype = ctypes.c_int32
 lib.salt_jit_stats.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
                                ctypes.POINTER(ctypes.c_double)]
-EXPORTS += ["salt_set_jit", "salt_jit_stats"]
+lib.salt_jit_cache_dir.restype = ctypes.c_int32
+lib.salt_jit_cache_dir.argtypes = [ctypes.c_char_p]
+lib.salt_jit_cache_stats.restype = ctypes.c_int32
+lib.salt_jit_cache_stats.argtypes = [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.c_char_p, ctypes.c_int32]
+EXPORTS += ["salt_set_jit", "salt_jit_stats", "salt_jit_cache_dir", "salt_jit_cache_stats"]
 
 
 def salt_set_jit(mode: int) -> None:
@@ -791,4 +796,13 @@ def salt_set_jit(mode: int) -> None:
 def salt_jit_stats() -> dict:
     m, k, t = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double()
     _check(lib.salt_jit_stats(ctypes.byref(m), ctypes.byref(k), ctypes.byref(t)))
-    return {"mode": m.value, "kernels": k.value, "compile_ms": t.value}
+    h, w = ctypes.c_int64(), ctypes.c_int64()
+    d = ctypes.create_string_buffer(4096)
+    _check(lib.salt_jit_cache_stats(ctypes.byref(h), ctypes.byref(w), d, len(d)))
+    return {"mode": m.value, "kernels": k.value, "compile_ms": t.value, "disk_hits": h.value,
+            "disk_writes": w.value, "cache_dir": d.value.decode()}
+
+
+def salt_jit_cache_dir(path) -> None:
+    """On-disk cache of run-time compiled kernels in ``path`` (None: none)."""
+    _check(lib.salt_jit_cache_dir(None if path is None else str(path).encode()))

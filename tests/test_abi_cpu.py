@@ -212,12 +212,24 @@ def test_autotune_argument_errors(saltlib):
 
 def test_jit_mode_switch(saltlib):
     s = saltlib
-    assert s.salt_jit_stats()["mode"] == s.JIT_OFF
+    assert s.salt_jit_stats()["mode"] == s.JIT_AUTO  # the default
     with pytest.raises(s.SaltError):
         s.salt_set_jit(5)
-    s.salt_set_jit(s.JIT_ON)
-    assert s.salt_jit_stats()["mode"] == s.JIT_ON
-    s.salt_set_jit(s.JIT_OFF)
+    for m in (s.JIT_ON, s.JIT_OFF, s.JIT_AUTO):
+        s.salt_set_jit(m)
+        assert s.salt_jit_stats()["mode"] == m
+
+
+def test_jit_cache_dir_setting(saltlib, tmp_path):
+    s = saltlib
+    before = s.salt_jit_stats()["cache_dir"]
+    try:
+        s.salt_jit_cache_dir(tmp_path / "k")
+        assert s.salt_jit_stats()["cache_dir"] == str(tmp_path / "k")
+        s.salt_jit_cache_dir(None)
+        assert s.salt_jit_stats()["cache_dir"] == ""
+    finally:
+        s.salt_jit_cache_dir(before or None)
 
 
 def test_strided_argument_errors(saltlib):

@@ -18,9 +18,10 @@ torch = pytest.importorskip("torch")
 
 @pytest.fixture
 def jit(saltlib, cuda_dev):
+    prev = saltlib.salt_jit_stats()["mode"]
     saltlib.salt_set_jit(saltlib.JIT_ON)
     yield saltlib
-    saltlib.salt_set_jit(saltlib.JIT_OFF)
+    saltlib.salt_set_jit(prev)
 
 
 def test_jit_random_programs_match_oracle(jit):
@@ -93,3 +94,53 @@ def test_jit_cache_and_speed_over_interpreter(jit, cuda_dev):
     gbs = lambda ms: 6 * 4 * n / (ms * 1e-3) / 1e9  # algorithmic: 5 reads + 1 write of 4 B
     print(f"jit {t_jit:.3f} ms ({gbs(t_jit):.0f} GB/s), interpreter {t_int:.3f} ms ({gbs(t_int):.0f} GB/s)")
     assert t_jit < t_int
+
+
+_CHILD = r"""
+import hashlib, json, sys
+import torch
+from paper_1109_1264_gb300 import salt
+prog = [("VEC", 0), ("VEC", 1), ("ADD", 0), ("VEC", 1), ("MUL", 0), ("NEG", 0), ("VEC", 0), ("SUB", 0),
+        ("STORE", 2)]
+x, y, z = (torch.empty(100003, dtype=torch.float64, device="cuda") for _ in range(3))
+salt.salt_fill_uniform(x, 1)
+salt.salt_fill_uniform(y, 2)
+salt.salt_eval(prog, [x, y, z])
+torch.cuda.synchronize()
+st = salt.salt_jit_stats()
+print(json.dumps({"kernels": st["kernels"], "hits": st["disk_hits"], "writes": st["disk_writes"],
+                  "dir": st["cache_dir"], "digest": hashlib.sha256(z.cpu().numpy().tobytes()).hexdigest()}))
+"""
+
+
+def test_jit_disk_cache_across_processes(saltlib, cuda_dev, tmp_path):
+    """A program compiled in one process is loaded from the on-disk cache by
+    the next (no compile) with the same results; a cache file whose payload
+    was altered fails its check and is recompiled, never loaded."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, SALT_JIT_CACHE=str(tmp_path / "jit"), PYTHONPATH=root)
+
+    def child():
+        r = subprocess.run([sys.executable, "-c", _CHILD], env=env, cwd=root, capture_output=True, text=True,
+                           timeout=300)
+        assert r.returncode == 0, r.stderr[-2000:]
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+    first = child()
+    assert first["dir"] == str(tmp_path / "jit")
+    assert (first["kernels"], first["hits"], first["writes"]) == (1, 0, 1)
+    files = list((tmp_path / "jit").glob("*.cubin"))
+    assert len(files) == 1
+    second = child()
+    assert (second["kernels"], second["hits"], second["writes"]) == (0, 1, 0)
+    assert second["digest"] == first["digest"]
+    data = bytearray(files[0].read_bytes())
+    data[-100] ^= 0x5A  # inside the cubin payload: the stored hash no longer matches
+    files[0].write_bytes(bytes(data))
+    third = child()
+    assert (third["kernels"], third["hits"], third["writes"]) == (1, 0, 1)
+    assert third["digest"] == first["digest"]

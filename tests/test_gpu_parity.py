@@ -148,7 +148,17 @@ def test_every_launch_configuration(salt, name, dt):
         salt.salt_tune_clear()
 
 
-def test_interpreter_random_programs(salt):
+@pytest.fixture
+def interpreter(salt):
+    """Run-time compilation off: programs without a compiled instantiation
+    run on the interpreter kernel."""
+    prev = salt.salt_jit_stats()["mode"]
+    salt.salt_set_jit(salt.JIT_OFF)
+    yield salt
+    salt.salt_set_jit(prev)
+
+
+def test_interpreter_random_programs(salt, interpreter):
     """Programs without a compiled instantiation run on the interpreter and
     must match the oracle bit for bit (reductions within tolerance)."""
     rng = random.Random(11)
@@ -175,7 +185,7 @@ def test_interpreter_random_programs(salt):
     assert ran_interp > 50
 
 
-def test_interpreter_reductions_exact_reference(salt):
+def test_interpreter_reductions_exact_reference(salt, interpreter):
     """Interpreter-only programs with reductions, judged against the exact
     reference of their operands."""
     progs = [

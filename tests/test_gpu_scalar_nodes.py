@@ -57,6 +57,7 @@ def test_random_extended_programs(saltlib, cuda_dev, dt, jit):
     s = saltlib
     rng = random.Random(31 + jit)
     nrng = np.random.default_rng(31)
+    prev = s.salt_jit_stats()["mode"]
     s.salt_set_jit(s.JIT_ON if jit else s.JIT_OFF)
     try:
         done = 0
@@ -75,7 +76,7 @@ def test_random_extended_programs(saltlib, cuda_dev, dt, jit):
                 _check(prog, vecs, scalars, dscalars, got, red, dt, f"{prog} n={n}")
             done += 1
     finally:
-        s.salt_set_jit(s.JIT_OFF)
+        s.salt_set_jit(prev)
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])

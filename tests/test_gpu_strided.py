@@ -54,8 +54,11 @@ def test_unaligned_and_strided(saltlib, cuda_dev, layout, name, dt):
         prog, nv, ns = ODD, 3, 0
     else:
         prog, nv, ns = PROGS[name]
+    prev = s.salt_jit_stats()["mode"]
     if name == "ODD_JIT":
         s.salt_set_jit(s.JIT_ON)
+    elif name == "ODD":
+        s.salt_set_jit(s.JIT_OFF)  # the interpreter's element mode
     try:
         for n in (1, 2, 3, 4, 5, 1000, 70001):
             vecs = inputs.uniform_vectors(50 + n, n, nv, dt)
@@ -78,7 +81,7 @@ def test_unaligned_and_strided(saltlib, cuda_dev, layout, name, dt):
                 assert np.all(rest == 7.0), f"{name} {layout}: elements outside the view were written"
             check_reductions(prog, vecs, scalars, red.cpu().numpy(), dt, f"{name} {layout}")
     finally:
-        s.salt_set_jit(s.JIT_OFF)
+        s.salt_set_jit(prev)
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
@@ -115,8 +118,11 @@ def test_negative_strides(saltlib, cuda_dev, name, dt):
         prog, nv, ns = PROGS[name]
     es = np.dtype(dt).itemsize
     code = s.F32 if dt == np.float32 else s.F64
+    prev = s.salt_jit_stats()["mode"]
     if name == "ODD_JIT":
         s.salt_set_jit(s.JIT_ON)
+    elif name == "ODD":
+        s.salt_set_jit(s.JIT_OFF)  # the interpreter's element mode
     try:
         for n in (1, 5, 1000, 70001):
             vecs = inputs.uniform_vectors(90 + n, n, nv, dt)
@@ -152,4 +158,4 @@ def test_negative_strides(saltlib, cuda_dev, name, dt):
                 assert np.all(np.delete(b, idx) == 7.0), f"{name}: elements outside the strided positions written"
             check_reductions(prog, vecs, scalars, red.cpu().numpy()[:nred], dt, f"{name} negative strides")
     finally:
-        s.salt_set_jit(s.JIT_OFF)
+        s.salt_set_jit(prev)
