@@ -42,6 +42,19 @@
  *    and kept until salt_release_workspaces() or process exit.  Calls that
  *    reduce on the SAME stream are ordered; calls on different streams use
  *    different workspaces.
+ *  - Environment (read once per process):
+ *      SALT_TUNE_CACHE  a tuning-table file (salt_tune_save format) merged
+ *                       into the launch-shape table on first use and
+ *                       rewritten after every salt_autotune, so tuned shapes
+ *                       persist across processes; unreadable files are ignored.
+ *      SALT_JIT_CACHE   directory of run-time compiled kernels ("0" or "off":
+ *                       none; see salt_jit_cache_dir).
+ *      SALT_DEBUG       "1": salt_eval, salt_eval_strided, salt_eval_ex,
+ *                       salt_axpby, salt_dot, salt_nrm2 and salt_cg_diag
+ *                       synchronise their stream before returning and report
+ *                       a failure of their kernels as SALT_ERR_CUDA from the
+ *                       call that caused it (otherwise such an error surfaces
+ *                       at a later synchronisation).
  *  - n == 0 is valid: nothing is written to vectors and every reduction
  *    result is 0.
  */

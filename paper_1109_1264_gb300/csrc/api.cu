@@ -5,6 +5,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -156,7 +157,47 @@ static salt_launch_cfg default_cfg(int family, int dt) {
   return c;
 }
 
+// SALT_TUNE_CACHE: a tuning table file merged into the table on first use
+// and rewritten after every salt_autotune.
+static const char* tune_cache_path() {
+  static const char* p = [] {
+    const char* e = getenv("SALT_TUNE_CACHE");
+    return (e && *e) ? e : nullptr;
+  }();
+  return p;
+}
+static void tune_cache_load_once() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    if (const char* path = tune_cache_path()) {
+      if (FILE* f = fopen(path, "r")) {
+        fclose(f);
+        const std::string keep = t_last_error;
+        if (salt_tune_load(path) != SALT_OK) t_last_error = keep;  // a bad cache file is ignored
+      }
+    }
+  });
+}
+
+// SALT_DEBUG=1: every main entry point synchronises its stream after its
+// launches and reports a failure of its kernels at the call that caused it.
+static bool debug_sync() {
+  static const bool on = [] {
+    const char* e = getenv("SALT_DEBUG");
+    return e && *e && strcmp(e, "0") != 0;
+  }();
+  return on;
+}
+static salt_status debug_check(salt_status st, cudaStream_t s, const char* what) {
+  if (st != SALT_OK || !debug_sync()) return st;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(SALT_ERR_CUDA, std::string(what) + " (SALT_DEBUG check): " + cudaGetErrorString(e));
+  return st;
+}
+
 static salt_launch_cfg lookup_cfg(int family, int dt, int64_t n) {
+  tune_cache_load_once();
   std::lock_guard<std::mutex> lk(g_tune_mu);
   auto it = g_tune.find(TuneKey(family, dt, bucket_of(n)));
   return it != g_tune.end() ? it->second : default_cfg(family, dt);
@@ -778,7 +819,7 @@ salt_status salt_eval(const salt_insn* prog, int32_t nprog, int32_t dtype, int64
                       void* const* vecs, int32_t nvecs, const double* scalars, int32_t nscal,
                       double* red_out, void* stream) {
   EvalArgs a{prog, nprog, dtype, n, vecs, nvecs, scalars, nscal, red_out, (cudaStream_t)stream};
-  return eval_impl(a);
+  return debug_check(eval_impl(a), a.stream, "salt_eval");
 }
 
 salt_status salt_eval_strided(const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
@@ -786,7 +827,7 @@ salt_status salt_eval_strided(const salt_insn* prog, int32_t nprog, int32_t dtyp
                               int32_t nscal, double* red_out, void* stream) {
   if (!strides && nvecs > 0) return set_error(SALT_ERR_ARG, "strides is NULL");
   EvalArgs a{prog, nprog, dtype, n, vecs, nvecs, scalars, nscal, red_out, (cudaStream_t)stream, strides};
-  return eval_impl(a);
+  return debug_check(eval_impl(a), a.stream, "salt_eval_strided");
 }
 
 salt_status salt_explain(const salt_insn* prog, int32_t nprog, int32_t dtype, int32_t nvecs, const double* scalars,
@@ -834,7 +875,7 @@ salt_status salt_eval_ex(const salt_insn* prog, int32_t nprog, int32_t dtype, in
   EvalArgs a{prog, nprog, dtype, n, vecs, nvecs, scalars, nscal, red_out, (cudaStream_t)stream, strides};
   a.dscal = dscalars;
   a.ndscal = ndscal;
-  return eval_impl(a);
+  return debug_check(eval_impl(a), a.stream, "salt_eval_ex");
 }
 
 salt_status salt_cg_diag(int32_t dtype, int64_t n, const void* d, const void* b, void* x, void* r, void* p,
@@ -852,7 +893,7 @@ salt_status salt_cg_diag(int32_t dtype, int64_t n, const void* d, const void* b,
                 : cg_call(kCgPQ, 15, dtype, n, vecs, pq, rho + 2 * k, rho + 2 * k - 2, s, false);
     if (st == SALT_OK) st = cg_call(kCgXR, 18, dtype, n, vecs, rho + 2 * k + 2, rho + 2 * k, pq, s, false);
   }
-  return st;
+  return debug_check(st, s, "salt_cg_diag");
 }
 
 salt_status salt_axpby(int32_t dtype, int64_t n, double alpha, const void* x, double beta, void* y,
@@ -869,10 +910,10 @@ salt_status salt_axpby(int32_t dtype, int64_t n, double alpha, const void* x, do
                                       {SALT_OP_SCAL, 1}, {SALT_OP_VEC, 0}, {SALT_OP_SMUL, 0},
                                       {SALT_OP_ADD, 0},  {SALT_OP_STORE, 0}};
     EvalArgs a{prog1, 8, dtype, n, vecs, 1, sc, 2, nullptr, (cudaStream_t)stream};
-    return eval_impl(a);
+    return debug_check(eval_impl(a), a.stream, "salt_axpby");
   }
   EvalArgs a{prog, 8, dtype, n, vecs, 2, sc, 2, nullptr, (cudaStream_t)stream};
-  return eval_impl(a);
+  return debug_check(eval_impl(a), a.stream, "salt_axpby");
 }
 
 salt_status salt_dot(int32_t dtype, int64_t n, const void* x, const void* y, double* out,
@@ -889,17 +930,18 @@ salt_status salt_dot(int32_t dtype, int64_t n, const void* x, const void* y, dou
   if (dtype == SALT_F32 && flags == SALT_PLAIN) {
     if (!aligned(x, 16) || !aligned(y, 16))
       return set_error(SALT_ERR_ALIGN, "SALT_PLAIN needs 16-byte aligned x and y");
-    return run_special(SPECIAL_DOT_PLAIN, DT_F32, n, x, y, out, (cudaStream_t)stream);
+    return debug_check(run_special(SPECIAL_DOT_PLAIN, DT_F32, n, x, y, out, (cudaStream_t)stream),
+                       (cudaStream_t)stream, "salt_dot");
   }
   static const salt_insn prog[] = {{SALT_OP_VEC, 0}, {SALT_OP_VEC, 1}, {SALT_OP_DOT, 0}};
   void* vecs[2] = {const_cast<void*>(x), const_cast<void*>(y)};
   EvalArgs a{prog, 3, dtype, n, vecs, 2, nullptr, 0, out, (cudaStream_t)stream};
-  return eval_impl(a);
+  return debug_check(eval_impl(a), a.stream, "salt_dot");
 }
 
 salt_status salt_nrm2(int32_t dtype, int64_t n, const void* x, double* out, int32_t flags,
                       void* stream) {
-  return nrm2_impl(dtype, n, x, out, flags, (cudaStream_t)stream);
+  return debug_check(nrm2_impl(dtype, n, x, out, flags, (cudaStream_t)stream), (cudaStream_t)stream, "salt_nrm2");
 }
 
 }  // extern "C"
@@ -1151,6 +1193,10 @@ salt_status salt_autotune(int32_t kernel, const salt_insn* prog, int32_t nprog, 
   if (st != SALT_OK) return st;
   if (best_out) *best_out = best;
   if (best_ms) *best_ms = best_t;
+  if (const char* path = tune_cache_path()) {
+    const std::string keep = t_last_error;
+    if (salt_tune_save(path) != SALT_OK) t_last_error = keep;  // the cache is best effort
+  }
   return SALT_OK;
 }
 

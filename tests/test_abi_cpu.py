@@ -318,3 +318,38 @@ def test_wait_limits(saltlib):
     assert s.lib.salt_get_wait_limit(s.WAIT_STAGED, None) == s.ERR_ARG
     # without a GPU the status query fails like every device call
     assert s.lib.salt_cg_status(None) == s.ERR_CUDA
+
+
+def test_tune_cache_environment(tmp_path):
+    """SALT_TUNE_CACHE: a saved tuning table is merged into a fresh process's
+    table on first use (no GPU needed: the table lives on the host)."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    child = (
+        "import json\n"
+        "from paper_1109_1264_gb300 import salt\n"
+        "from paper_1109_1264_gb300.programs import PROG_E\n"
+        "import sys\n"
+        "if sys.argv[1] == 'save':\n"
+        "    salt.salt_tune_set(PROG_E, salt.F64, 1 << 20, 4, 32, 128, 3, 0)\n"
+        "    salt.salt_tune_save(sys.argv[2])\n"
+        "print(json.dumps(salt.salt_tune_get(PROG_E, salt.F64, 1 << 20)))\n")
+    env = dict(os.environ, PYTHONPATH=root)
+    env.pop("SALT_TUNE_CACHE", None)
+    r = subprocess.run([sys.executable, "-c", child, "save", str(cache)], env=env, cwd=root, capture_output=True,
+                       text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    want = json.loads(r.stdout.strip().splitlines()[-1])
+    assert want["unroll"] == 4 and want["blocks_per_sm"] == 3
+    r = subprocess.run([sys.executable, "-c", child, "load"], env=dict(env, SALT_TUNE_CACHE=str(cache)), cwd=root,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert json.loads(r.stdout.strip().splitlines()[-1]) == want
+    # without the variable the default shape is back
+    r = subprocess.run([sys.executable, "-c", child, "load"], env=env, cwd=root, capture_output=True, text=True,
+                       timeout=120)
+    assert json.loads(r.stdout.strip().splitlines()[-1]) != want

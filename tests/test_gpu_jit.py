@@ -144,3 +144,25 @@ def test_jit_disk_cache_across_processes(saltlib, cuda_dev, tmp_path):
     third = child()
     assert (third["kernels"], third["hits"], third["writes"]) == (1, 0, 1)
     assert third["digest"] == first["digest"]
+
+
+def test_debug_mode_checks_each_call(saltlib, cuda_dev):
+    """SALT_DEBUG=1 (a child process): calls synchronise and still return
+    the same results."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    child = (
+        "import torch\n"
+        "from paper_1109_1264_gb300 import salt\n"
+        "x = torch.arange(1000, dtype=torch.float64, device='cuda')\n"
+        "out = torch.zeros(2, dtype=torch.float64, device='cuda')\n"
+        "salt.salt_dot(x, x, out[0:1]); salt.salt_nrm2(x, out[1:2])\n"
+        "print(out[0].item(), out[1].item())\n")
+    r = subprocess.run([sys.executable, "-c", child], env=dict(os.environ, SALT_DEBUG="1", PYTHONPATH=root),
+                       cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d, nr = (float(v) for v in r.stdout.split())
+    import math
+    assert d == 999 * 1000 * 1999 // 6 and nr == math.sqrt(d)
