@@ -29,6 +29,20 @@ template <> struct Blue<double> {
 struct Nrm2F32 {
   AccF32 med;
   float sml = 0.f, big = 0.f;
+  // x^2 added to the medium sum, error-free: the square by TwoProduct (FMA)
+  // and, because both addends are non-negative, the sum by Fast2Sum with the
+  // larger addend first (exact whenever |a| >= |b|; Dekker 1971) -- two
+  // min/max instead of TwoSum's three extra additions.  Same error bound as
+  // the general compensated product (Ogita, Rump and Oishi's Dot2).
+  __device__ __forceinline__ void add_sq(float x) {
+    const float p = __fmul_rn(x, x);
+    const float ep = __fmaf_rn(x, x, -p);  // x*x - p exactly
+    const float t = __fadd_rn(med.s, p);
+    const float hi = fmaxf(med.s, p), lo = fminf(med.s, p);
+    const float es = __fadd_rn(__fsub_rn(hi, t), lo);  // med.s + p - t exactly
+    med.s = t;
+    med.c = __fadd_rn(med.c, __fadd_rn(es, ep));
+  }
   __device__ __forceinline__ void add(float x) {
     const float ax = fabsf(x);
     if (ax > Blue<float>::tbig) {
@@ -38,7 +52,28 @@ struct Nrm2F32 {
       const float t = __fmul_rn(ax, Blue<float>::ssml);
       sml = __fmaf_rn(t, t, sml);
     } else {
-      med.add_prod(ax, ax);
+      add_sq(ax);
+    }
+  }
+  // A whole vector: one range test for all its elements (the largest and
+  // smallest magnitude), then the medium path without per-element tests; a
+  // vector with any element outside the medium range takes the per-element
+  // path.  A NaN (which fmaxf / fminf pass over) reaches add_sq on either
+  // path and makes the sum NaN, as the per-element path does.
+  template <int N>
+  __device__ __forceinline__ void add_vec(const float (&v)[N]) {
+    float mx = fabsf(v[0]), mn = mx;
+#pragma unroll
+    for (int e = 1; e < N; ++e) {
+      mx = fmaxf(mx, fabsf(v[e]));
+      mn = fminf(mn, fabsf(v[e]));
+    }
+    if (mx <= Blue<float>::tbig && mn >= Blue<float>::tsml) {
+#pragma unroll
+      for (int e = 0; e < N; ++e) add_sq(v[e]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < N; ++e) add(v[e]);
     }
   }
   // The whole sum of squares in FP64, where it cannot overflow for F32 data.
@@ -174,10 +209,7 @@ __global__ void __launch_bounds__(256) nrm2_kernel(const NrmParams p) {
   } else if constexpr (sizeof(T) == 4) {
     Nrm2F32 acc;
     reduce_loop<T, U, VB, 1>(x, nullptr, p.n,
-        [&](const V& a, const V&) {
-#pragma unroll
-          for (int e = 0; e < VEC; ++e) acc.add(a.e[e]);
-        },
+        [&](const V& a, const V&) { acc.add_vec<VEC>(a.e); },
         [&](T a, T) { acc.add(a); }, p.trace);
     __shared__ double smem[kMaxBlock];
     double vals[1] = {acc.value()};
