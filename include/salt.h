@@ -645,6 +645,13 @@ salt_status salt_batch_set_config(salt_batch* b, int32_t unroll, int32_t block, 
                                   int64_t tile_bytes);
 salt_status salt_batch_get_config(const salt_batch* b, int32_t* unroll, int32_t* block, int32_t* blocks_per_sm,
                                   int64_t* tile_bytes);
+/* Vector width of the batch's accesses: 32 (the default) lets FP32 items
+ * whose operands are all 32-byte aligned use 32-byte accesses (at half the
+ * unroll, so the same bytes are in flight); 16 keeps every item on 16-byte
+ * accesses.  Elementwise results are the same bits either way; reductions
+ * are summed in another order (same error bounds).  Errors: SALT_ERR_ARG. */
+salt_status salt_batch_set_vec_bytes(salt_batch* b, int32_t vec_bytes);
+salt_status salt_batch_get_vec_bytes(const salt_batch* b, int32_t* vec_bytes);
 
 /* One persistent launch over all items (a CUDA graph: counter reset + kernel)
  * on `stream`.  red_out: device array of >= nresults doubles. */
@@ -653,10 +660,11 @@ salt_status salt_batch_launch(salt_batch* b, double* red_out, void* stream);
  * item order (the plain per-call path, for comparison). */
 salt_status salt_batch_launch_plain(salt_batch* b, double* red_out, void* stream);
 /* Times every launch shape over unroll {1,2,4} x block {128,256} x
- * tile_bytes {16,32,64,128} KiB (reps launches each, after one warm-up) and
- * keeps the fastest; *best_ms (may be NULL) receives its time per launch.
- * The items' programs run (1 + reps) x 24 times: in-place programs update
- * their operands each time. */
+ * tile_bytes {16,32,64,128} KiB, and vector width {32,16} bytes when the
+ * batch has FP32 items (reps launches each, after one warm-up), and keeps
+ * the fastest; *best_ms (may be NULL) receives its time per launch.  The
+ * items' programs run (1 + reps) x 24 (FP64 only) or x 48 times: in-place
+ * programs update their operands each time. */
 salt_status salt_batch_autotune(salt_batch* b, double* red_out, int32_t reps, double* best_ms, void* stream);
 
 /* ===========================================================================

@@ -49,6 +49,7 @@ struct salt_batch {
   // launch shape
   int32_t unroll = 2, block = 256, blocks_per_sm = 0;
   int64_t tile_bytes = 64 * 1024;
+  int32_t vec_bytes = 32;  // widest access for 32-byte aligned FP32 items (16 or 32)
   // device state
   int device = -1;
   void* dmem = nullptr;           // header | items | counter+tickets | partials
@@ -169,6 +170,7 @@ salt_status rebuild(salt_batch* b, cudaStream_t s) {
   h.nitems = (int32_t)b->items.size();
   h.total_tiles = b->total_tiles;
   h.tile_bytes = b->tile_bytes;
+  h.narrow = b->vec_bytes == 16 ? 1 : 0;
   std::vector<BatchItem> table(b->items.size());
   for (size_t i = 0; i < b->items.size(); ++i) table[i] = b->items[i].dev;
   e = cudaMemcpy(b->d_hdr, &h, sizeof h, cudaMemcpyHostToDevice);
@@ -456,6 +458,23 @@ salt_status salt_batch_launch_plain(salt_batch* b, double* red_out, void* stream
   return SALT_OK;
 }
 
+salt_status salt_batch_set_vec_bytes(salt_batch* b, int32_t vec_bytes) {
+  if (!b) return fail(SALT_ERR_ARG, "batch is NULL");
+  if (vec_bytes != 16 && vec_bytes != 32) return fail(SALT_ERR_ARG, "vec_bytes must be 16 or 32");
+  if (vec_bytes != b->vec_bytes) {
+    b->vec_bytes = vec_bytes;
+    b->dirty = true;  // the header carries it
+    drop_graph(b);
+  }
+  return SALT_OK;
+}
+
+salt_status salt_batch_get_vec_bytes(const salt_batch* b, int32_t* vec_bytes) {
+  if (!b || !vec_bytes) return fail(SALT_ERR_ARG, "batch or vec_bytes is NULL");
+  *vec_bytes = b->vec_bytes;
+  return SALT_OK;
+}
+
 salt_status salt_batch_autotune(salt_batch* b, double* red_out, int32_t reps, double* best_ms, void* stream) {
   if (!b) return fail(SALT_ERR_ARG, "batch is NULL");
   if (reps < 1) return fail(SALT_ERR_ARG, "reps must be >= 1");
@@ -466,43 +485,55 @@ salt_status salt_batch_autotune(salt_batch* b, double* red_out, int32_t reps, do
   const int32_t unrolls[] = {1, 2, 4};
   const int32_t blocks[] = {128, 256};
   const int64_t tiles[] = {16 * 1024, 32 * 1024, 64 * 1024, 128 * 1024};
+  // the vector width matters only for FP32 items whose operands are all
+  // 32-byte aligned: search it only when the batch has FP32 items
+  bool any_f32 = false;
+  for (const auto& it : b->items) any_f32 = any_f32 || it.dev.dtype == DT_F32;
+  const int32_t widths[] = {32, 16};
+  const int nwidths = any_f32 ? 2 : 1;
   float best = 1e30f;
-  int32_t bu = b->unroll, bb = b->block;
+  int32_t bu = b->unroll, bb = b->block, bv = b->vec_bytes;
   int64_t bt = b->tile_bytes;
   salt_status st = SALT_OK;
-  for (int32_t u : unrolls) {
-    for (int32_t blk : blocks) {
-      for (int64_t t : tiles) {
-        st = salt_batch_set_config(b, u, blk, 0, t);
-        if (st != SALT_OK) break;
-        st = launch(b, red_out, s);  // warm-up (builds the table and graph)
-        if (st != SALT_OK) break;
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && st == SALT_OK; ++r) st = launch(b, red_out, s);
-        cudaEventRecord(e1, s);
-        if (st != SALT_OK) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-          st = fail(SALT_ERR_CUDA, "cudaEventSynchronize");
-          break;
+  for (int wi = 0; wi < nwidths && st == SALT_OK; ++wi) {
+    st = salt_batch_set_vec_bytes(b, widths[wi]);
+    for (int32_t u : unrolls) {
+      if (st != SALT_OK) break;
+      for (int32_t blk : blocks) {
+        for (int64_t t : tiles) {
+          st = salt_batch_set_config(b, u, blk, 0, t);
+          if (st != SALT_OK) break;
+          st = launch(b, red_out, s);  // warm-up (builds the table and graph)
+          if (st != SALT_OK) break;
+          cudaEventRecord(e0, s);
+          for (int r = 0; r < reps && st == SALT_OK; ++r) st = launch(b, red_out, s);
+          cudaEventRecord(e1, s);
+          if (st != SALT_OK) break;
+          if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = fail(SALT_ERR_CUDA, "cudaEventSynchronize");
+            break;
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms /= (float)reps;
+          if (ms < best) {
+            best = ms;
+            bu = u;
+            bb = blk;
+            bt = t;
+            bv = widths[wi];
+          }
         }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= (float)reps;
-        if (ms < best) {
-          best = ms;
-          bu = u;
-          bb = blk;
-          bt = t;
-        }
+        if (st != SALT_OK) break;
       }
       if (st != SALT_OK) break;
     }
-    if (st != SALT_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != SALT_OK) return st;
-  st = salt_batch_set_config(b, bu, bb, 0, bt);
+  st = salt_batch_set_vec_bytes(b, bv);
+  if (st == SALT_OK) st = salt_batch_set_config(b, bu, bb, 0, bt);
   if (best_ms) *best_ms = best;
   return st;
 }

@@ -41,7 +41,7 @@ struct BatchItem {
 
 struct BatchHeader {
   int32_t nitems;
-  int32_t pad;
+  int32_t narrow;      // 1: 16-byte accesses only; 0: 32-byte accesses for 32-byte aligned FP32 items
   int64_t total_tiles;
   int64_t tile_bytes;  // bytes per operand per tile (multiple of 16 * block * unroll)
 };
@@ -145,7 +145,8 @@ __device__ __forceinline__ void range_eval(T* const* v, const T (&sc)[kMaxScals]
 // Program item: returns the number of partial values produced (its
 // reductions) in vals.
 template <class P, typename T, int U>
-__device__ __forceinline__ int item_program(const BatchItem& it, int64_t lo, int64_t hi, double (&vals)[kBatchPartials]) {
+__device__ __forceinline__ int item_program(const BatchItem& it, int64_t lo, int64_t hi, double (&vals)[kBatchPartials],
+                                            bool narrow) {
   T* v[kMaxVecs];
 #pragma unroll
   for (int k = 0; k < kMaxVecs; ++k) v[k] = k < kBatchOps ? (T*)it.v[k] : nullptr;
@@ -154,15 +155,16 @@ __device__ __forceinline__ int item_program(const BatchItem& it, int64_t lo, int
   for (int k = 0; k < kMaxScals; ++k) sc[k] = k < 2 ? (T)it.sc[k] : T(0);
   typename AccOf<T>::type acc[kMaxReds];
   // FP32 items: 32-byte accesses (at half the unroll: the same bytes in
-  // flight) when every operand is 32-byte aligned, else 16-byte accesses.
-  // (FP64 items are bound by the FP64 pipe; 32-byte accesses measured no
-  // better there.)
+  // flight) when every operand is 32-byte aligned and the batch allows them
+  // (its vector width, a tuning parameter), else 16-byte accesses.  (FP64
+  // items are bound by the FP64 pipe; 32-byte accesses measured no better
+  // there.)
   uintptr_t align = 0;
 #pragma unroll
   for (int k = 0; k < kBatchOps; ++k)
     if (k < P::nvec()) align |= (uintptr_t)it.v[k];
   if constexpr (U >= 2 && sizeof(T) == 4) {
-    if ((align & 31u) == 0) range_eval<P, T, U / 2, 32>(v, sc, lo, hi, acc);
+    if (!narrow && (align & 31u) == 0) range_eval<P, T, U / 2, 32>(v, sc, lo, hi, acc);
     else range_eval<P, T, U, 16>(v, sc, lo, hi, acc);
   } else {
     range_eval<P, T, U, 16>(v, sc, lo, hi, acc);
@@ -229,11 +231,12 @@ __device__ __forceinline__ int item_fill(const BatchItem& it, int64_t lo, int64_
 }
 
 template <typename T, int U>
-__device__ __forceinline__ int dispatch_item(const BatchItem& it, int64_t lo, int64_t hi, double (&vals)[kBatchPartials]) {
+__device__ __forceinline__ int dispatch_item(const BatchItem& it, int64_t lo, int64_t hi, double (&vals)[kBatchPartials],
+                                             bool narrow) {
   switch (it.kind) {
 #define SALT_BATCH_CASE(name, ...) \
   case SHAPE_##name:               \
-    return item_program<Prog_##name, T, U>(it, lo, hi, vals);
+    return item_program<Prog_##name, T, U>(it, lo, hi, vals, narrow);
     SALT_BATCH_SHAPE_LIST(SALT_BATCH_CASE)
 #undef SALT_BATCH_CASE
     case kKindFill:
@@ -272,6 +275,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchParams p) {
   const int64_t total = p.hdr->total_tiles;
   const int nitems = p.hdr->nitems;
   const int64_t tile_bytes = p.hdr->tile_bytes;
+  const bool narrow = p.hdr->narrow != 0;
   // Tile numbers come from an atomic counter (no waiting).  Thread 0 asks
   // for the next one when a tile starts and hands it over when the tile
   // ends, so the atomic's latency hides behind the tile's work; warp 0 then
@@ -295,8 +299,8 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchParams p) {
     const int64_t lo = (tile - it.tile_begin) * tile_elems;
     const int64_t hi = lo + tile_elems < it.n ? lo + tile_elems : it.n;
     double vals[kBatchPartials] = {0.0, 0.0, 0.0};
-    const int nv = it.dtype == DT_F32 ? dispatch_item<float, U>(it, lo, hi, vals)
-                                      : dispatch_item<double, U>(it, lo, hi, vals);
+    const int nv = it.dtype == DT_F32 ? dispatch_item<float, U>(it, lo, hi, vals, narrow)
+                                      : dispatch_item<double, U>(it, lo, hi, vals, narrow);
     if (nv > 0) {
       // this tile's partials, then the per-item ticket
       for (int r = 0; r < nv; ++r) {

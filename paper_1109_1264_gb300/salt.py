@@ -510,6 +510,8 @@ _BATCH_SIGS = {
     "salt_batch_set_config": [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64],
     "salt_batch_get_config": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                               ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)],
+    "salt_batch_set_vec_bytes": [ctypes.c_void_p, ctypes.c_int32],
+    "salt_batch_get_vec_bytes": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)],
     "salt_batch_launch": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "salt_batch_launch_plain": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
     "salt_batch_autotune": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
@@ -582,7 +584,13 @@ class Batch:
         u, b, p, t = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
         _check(lib.salt_batch_get_config(self.handle, ctypes.byref(u), ctypes.byref(b), ctypes.byref(p),
                                          ctypes.byref(t)))
-        return {"unroll": u.value, "block": b.value, "blocks_per_sm": p.value, "tile_bytes": t.value}
+        v = ctypes.c_int32()
+        _check(lib.salt_batch_get_vec_bytes(self.handle, ctypes.byref(v)))
+        return {"unroll": u.value, "block": b.value, "blocks_per_sm": p.value, "tile_bytes": t.value,
+                "vec_bytes": v.value}
+
+    def set_vec_bytes(self, vec_bytes: int):
+        _check(lib.salt_batch_set_vec_bytes(self.handle, int(vec_bytes)))
 
     def launch(self, red_out=None, stream=None):
         _check(lib.salt_batch_launch(self.handle, _ptr(red_out), _stream_ptr(stream)))

@@ -57,11 +57,17 @@ def test_result_slots_capacity_and_info(saltlib, batch):
 
 def test_config_validation(saltlib, batch):
     batch.set_config(4, 128, 2, 32768)
-    assert batch.get_config() == {"unroll": 4, "block": 128, "blocks_per_sm": 2, "tile_bytes": 32768}
+    assert batch.get_config() == {"unroll": 4, "block": 128, "blocks_per_sm": 2, "tile_bytes": 32768,
+                                  "vec_bytes": 32}
+    batch.set_vec_bytes(16)
+    assert batch.get_config()["vec_bytes"] == 16
     for bad in ((3, 128, 2, 32768), (2, 96, 2, 32768), (2, 512, 2, 32768), (2, 128, 33, 32768),
                 (2, 128, 2, 1000), (2, 128, 2, 512)):
         with pytest.raises(saltlib.SaltError):
             batch.set_config(*bad)
+    for bad in (0, 8, 24, 64):
+        with pytest.raises(saltlib.SaltError):
+            batch.set_vec_bytes(bad)
 
 
 def test_cross_item_overlap_rejected_at_launch(saltlib, batch):

@@ -277,3 +277,34 @@ def test_reductions_after_divergent_tails(salt, cuda_dev, dt):
             _, refs, scales = reference((prog, dt, vecs, scal))
             tolerance.check(r.item(), refs[0], scales[0], dt, (prog, n, unroll))
         salt.salt_tune_clear()
+
+
+def test_batch_vector_width(salt, cuda_dev):
+    """The batch's vector width: 32-byte accesses for 32-byte aligned FP32
+    items, or 16-byte accesses throughout -- the same bits for every
+    elementwise result, both within tolerance of the exact reductions; the
+    autotuner reports the width it keeps."""
+    items = make_items(71, dtypes=(np.float32,), lengths=[8, 1000, 4096 + 8, 70000, (1 << 20) + 8])
+    outs = {}
+    for vb in (32, 16):
+        b, tensors, slots = build(salt, items, cuda_dev)
+        b.set_vec_bytes(vb)
+        assert b.get_config()["vec_bytes"] == vb
+        red = torch.full((len(items),), float("nan"), dtype=torch.float64, device=cuda_dev)
+        b.launch(red)
+        torch.cuda.synchronize()
+        check(items, tensors, slots, red.cpu().numpy())
+        outs[vb] = [[t.cpu().numpy() for t in tv] for tv in tensors]
+        if vb == 16:
+            b.autotune(red, reps=1)
+            assert b.get_config()["vec_bytes"] in (16, 32)
+        b.close()
+    for a, c in zip(outs[32], outs[16]):
+        for x, y in zip(a, c):
+            assert_bits_equal(x, y, "vector widths 32 and 16")
+    with pytest.raises(salt.SaltError):
+        bb = salt.Batch(1)
+        try:
+            bb.set_vec_bytes(8)
+        finally:
+            bb.close()
