@@ -125,3 +125,42 @@ def test_cg_barrier_runs_out(salt, cuda_dev, dt, one_reduction):
         xs = b.astype(np.float64) / d.astype(np.float64)
         xg = tx.cpu().numpy().astype(np.float64)
         assert np.linalg.norm(xg - xs) / np.linalg.norm(xs) < (1e-11 if dt == np.float64 else 1e-4)
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64], ids=["f32", "f64"])
+def test_trace_timeline(salt, cuda_dev, dt):
+    """salt_trace_set: a traced launch writes one record per block -- start
+    <= whole tiles done <= before the combine <= end, an SM id below the
+    SM count, exactly one block marked as the final combine -- and the
+    traced call's results equal the untraced call's."""
+    s = salt
+    n = (1 << 22) + 5
+    x, y = (torch.from_numpy(v).to(cuda_dev) for v in inputs.uniform_vectors(93, n, 2, dt))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cap = sms * 32
+    trace = torch.zeros(cap * s.TRACE_WORDS, dtype=torch.int64, device=cuda_dev)
+    out = torch.zeros(4, dtype=torch.float64, device=cuda_dev)
+    s.salt_dot(x, y, out[0:1])
+    s.salt_nrm2(x, out[1:2])
+    for k, fn in ((2, lambda r: s.salt_dot(x, y, r)), (3, lambda r: s.salt_nrm2(x, r))):
+        trace.zero_()
+        s.salt_trace_set(trace, cap)
+        try:
+            fn(out[k:k + 1])
+            torch.cuda.synchronize()
+        finally:
+            s.salt_trace_set(None)
+        w = trace.view(-1, s.TRACE_WORDS).cpu().numpy()
+        w = w[w[:, 0] != 0]
+        assert w.shape[0] >= 2
+        assert np.all(w[:, 0] <= w[:, 1]) and np.all(w[:, 1] <= w[:, 2]) and np.all(w[:, 2] <= w[:, 3])
+        assert np.all(w[:, 4] < sms) and int(w[:, 5].sum()) == 1
+        # the final combine ends last
+        assert w[w[:, 5] == 1, 3][0] == w[:, 3].max()
+    got = out.cpu().numpy()
+    assert got[2] == got[0] and got[3] == got[1]
+    # tracing off: nothing is written
+    trace.zero_()
+    s.salt_dot(x, y, out[0:1])
+    torch.cuda.synchronize()
+    assert int(trace.abs().sum().item()) == 0
