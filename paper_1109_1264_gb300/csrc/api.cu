@@ -265,6 +265,18 @@ static salt_status check_dtype(int32_t dt) {
 }
 
 // ------------------------------------------------------------ execution ---
+// Which by-value scalar slots of an FP64 launch are powers of two (the
+// register-tiled loop then issues X +- s*v as one FMA on chunks where that
+// gives the same bits).  Launches that compute slots on the device get none.
+template <typename T>
+static void set_pow2(MapParams<T>& p, int nscal, const ScalarCode* scode) {
+  memset(&p.p2, 0, sizeof p.p2);
+  if (sizeof(T) != 8 || scode) return;
+  double v[kMaxScals] = {};
+  for (int k = 0; k < nscal && k < kMaxScals; ++k) v[k] = (double)p.sc[k];
+  p.p2 = pow2_info(v, nscal);
+}
+
 template <typename T>
 static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarCode* scode, int dev,
                             const DevInfo& info) {
@@ -329,6 +341,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
       p.stride[k] = a.strides ? a.strides[c.vec_user[k]] : 1;
     }
     for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
+    set_pow2(p, c.nscal, scode);
     if (scode) p.scode = *scode;
     p.n = a.n;
     p.red_out = a.red_out;
@@ -375,6 +388,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
       MapParams<T>& p = sp.m;
       for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]] + head;
       for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
+      set_pow2(p, c.nscal, scode);
       if (scode) p.scode = *scode;
       p.n = a.n - head;
       p.head = (int32_t)head;
@@ -404,6 +418,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
     memset(&p, 0, sizeof p);
     for (int k = 0; k < c.nvec; ++k) p.v[k] = (T*)a.vecs[c.vec_user[k]] + head;
     for (int k = 0; k < c.nscal; ++k) p.sc[k] = (T)a.scalars[c.scal_user[k]];
+    set_pow2(p, c.nscal, scode);
     if (scode) p.scode = *scode;
     p.n = a.n - head;
     p.head = (int32_t)head;
@@ -435,6 +450,7 @@ static salt_status run_eval(const EvalArgs& a, const Canonical& c, const ScalarC
     memset(&p, 0, sizeof p);
     for (int j = 0; j < c.nvec; ++j) p.v[j] = (T*)a.vecs[c.vec_user[j]] + head;
     for (int j = 0; j < c.nscal; ++j) p.sc[j] = (T)a.scalars[c.scal_user[j]];
+    set_pow2(p, c.nscal, scode);
     if (scode) p.scode = *scode;
     p.n = a.n - head;
     p.head = (int32_t)head;

@@ -8,7 +8,7 @@
 // x = x + alpha*p; r = r - alpha*q), and alpha = rho / (p.q), beta =
 // rho' / rho are the same one-division-in-T scalar nodes.  The reductions
 // are the library's accumulators (compensated FP32, FP64 FMA) combined per
-// block by the shared-memory tree and across blocks in block order, which
+// block by the warp-shuffle block sums and across blocks in block order, which
 // every block does for itself, so all blocks hold the same scalars.
 //
 // Barrier: a monotonic arrival counter (zeroed before the launch); barrier
@@ -101,7 +101,7 @@ __device__ bool grid_sum(double v, double* partials, int slot, unsigned long lon
   if (!grid_barrier(counter, status, target, max_polls)) return false;
   const volatile double* part = (const volatile double*)partials + (size_t)slot * gridDim.x;
   if (gridDim.x <= 32) {
-    // few blocks: one thread adds them in block order (no tree, one barrier)
+    // few blocks: one thread adds them in block order (one barrier)
     __shared__ double s_tot;
     if (threadIdx.x == 0) {
       double a = 0.0;
@@ -114,14 +114,14 @@ __device__ bool grid_sum(double v, double* partials, int slot, unsigned long lon
   }
   double a = 0.0;
   for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) a += part[k];
-  // the same fixed-order tree in every block: identical totals
+  // the same fixed-order block sum in every block: identical totals
   *out = block_sum<double>(a, smem);
   return true;
 }
 
 // Two block sums written to partials[slot0 * G + block] and
 // partials[(slot0 + 1) * G + block], then ONE barrier, then every block adds
-// each set of G partials in block order (the same fixed-order tree as
+// each set of G partials in block order (the same fixed-order block sum as
 // grid_sum, so every block holds the same totals).
 __device__ bool grid_sum2(double v0, double v1, double* partials, int slot0, unsigned long long* counter,
                           unsigned* status, unsigned long long target, unsigned max_polls, double* smem,

@@ -9,6 +9,7 @@ typedef long long int64_t;
 typedef unsigned long long uint64_t;
 typedef int int32_t;
 typedef unsigned int uint32_t;
+typedef short int16_t;
 typedef unsigned char uint8_t;
 typedef decltype(sizeof(0)) size_t;
 #else
@@ -104,6 +105,30 @@ __device__ __forceinline__ void load_scalars(const T (&psc)[kMaxScals], const Sc
 #pragma unroll
     for (int k = 0; k < kMaxScals; ++k) sc[k] = s_sc[k];
   }
+}
+
+// ---------------------------------------------------------------------------
+// By-value FP64 scalar slots that are exact powers of two, s = +-2^e (found on
+// the host).  For such a slot a node pair X + s*v (or X - s*v) may run as one
+// FMA with the same bits: s*v is exact whenever its exponent stays in the
+// normal range, and then round(X + round(s*v)) = round(X + s*v).  The kernel
+// checks that range per element from the exponent bits of v (integer
+// instructions) and otherwise runs the two rounded operations.  On GB300 this
+// saves an instruction on the FP64 pipe, which bounds the FP64 shapes with
+// several nodes per element.
+struct Pow2Info {
+  uint32_t mask;              // bit k: slot k is +-2^exp[k]
+  int16_t exp[kMaxScals];     // -1022 .. 1023
+};
+
+// s*v is exact (s = +-2^e): v is normal, NaN or infinite, and v*2^e keeps a
+// biased exponent in 1 .. 2046 -- a normal number (or, for v infinite or
+// NaN, the same infinity or NaN; its sign and the NaN-ness are the same on
+// both paths).
+__device__ __forceinline__ bool exact_pow2_scale(double v, int e) {
+  const int be = (__double2hiint(v) >> 20) & 0x7FF;
+  const int r = be + e;
+  return be >= 1 && r >= 1 && (r <= 2046 || be == 2047);
 }
 
 // ---------------------------------------------------------------------------

@@ -29,14 +29,21 @@ struct MapParams {
                              // v[k] points at element `head` of operand k, and elements
                              // 0 .. head-1 sit just before it; 0 for the strided kernel
   unsigned long long* trace; // per-block timeline (kTraceWords per block), or NULL
+  Pow2Info p2;               // scalar slots that are powers of two (FP64 programs)
 };
 
 // Per-element evaluation of program P: node I at compile-time stack depth.
-template <class P, int I, typename T, class Acc>
-__device__ __forceinline__ void exec_node(T (&st)[kMaxStack + 1], T (&v)[kMaxVecs],
-                                          const T (&sc)[kMaxScals], Acc (&acc)[kMaxReds]) {
+// FMA = true (FP64 only; exec_chunk_p2 decides): every scaled add (X +- s*v,
+// or s*v +- w with w the next vector load; Prog::scaled_add /
+// scaled_add_load) is one FMA, which gives the rounded nodes' bits when s*v
+// is exact (Pow2Info).  FMA = false: every node its own rounded operation.
+template <class P, int I, typename T, class Acc, bool FMA = false>
+__device__ __forceinline__ void exec_node(T (&st)[kMaxStack + 1], T (&v)[kMaxVecs], const T (&sc)[kMaxScals],
+                                          Acc (&acc)[kMaxReds]) {
   if constexpr (I < P::len) {
     constexpr int op = P::op(I), a = P::arg(I), d = P::depth_before(I);
+    constexpr bool fuse = FMA && sizeof(T) == 8 && P::scaled_add(I);
+    constexpr bool fuse_load = FMA && sizeof(T) == 8 && P::scaled_add_load(I);
     if constexpr (op == OP_VEC) {
       st[d] = v[a];
     } else if constexpr (op == OP_SCAL) {
@@ -45,6 +52,12 @@ __device__ __forceinline__ void exec_node(T (&st)[kMaxStack + 1], T (&v)[kMaxVec
       st[d - 2] = Arith<T>::add(st[d - 2], st[d - 1]);
     } else if constexpr (op == OP_SUB) {
       st[d - 2] = Arith<T>::sub(st[d - 2], st[d - 1]);
+    } else if constexpr (fuse) {  // SMUL, then ADD / SUB
+      const T s = st[d - 2];
+      st[d - 3] = __fma_rn(P::op(I + 1) == OP_SUB ? -s : s, st[d - 1], st[d - 3]);
+    } else if constexpr (fuse_load) {  // SMUL, VEC, then ADD / SUB
+      const T w = v[P::arg(I + 1)];
+      st[d - 2] = __fma_rn(st[d - 2], st[d - 1], P::op(I + 2) == OP_SUB ? -w : w);
     } else if constexpr (op == OP_MUL || op == OP_SMUL) {
       st[d - 2] = Arith<T>::mul(st[d - 2], st[d - 1]);
     } else if constexpr (op == OP_DIV) {
@@ -58,31 +71,66 @@ __device__ __forceinline__ void exec_node(T (&st)[kMaxStack + 1], T (&v)[kMaxVec
     } else if constexpr (op == OP_SUMSQ) {
       acc[P::red_index(I)].add_prod(st[d - 1], st[d - 1]);
     }
-    exec_node<P, I + 1>(st, v, sc, acc);
+    exec_node<P, I + (fuse ? 2 : fuse_load ? 3 : 1), T, Acc, FMA>(st, v, sc, acc);
   }
 }
 
-template <class P, typename T, class Acc>
-__device__ __forceinline__ void exec_elem(T (&v)[kMaxVecs], const T (&sc)[kMaxScals],
-                                          Acc (&acc)[kMaxReds]) {
+template <class P, typename T, class Acc, bool FMA = false>
+__device__ __forceinline__ void exec_elem(T (&v)[kMaxVecs], const T (&sc)[kMaxScals], Acc (&acc)[kMaxReds]) {
   T st[kMaxStack + 1];
-  exec_node<P, 0>(st, v, sc, acc);
+  exec_node<P, 0, T, Acc, FMA>(st, v, sc, acc);
 }
 
 // One thread's work on NE consecutive elements held in per-operand arrays.
-template <class P, typename T, class Acc, int NE>
-__device__ __forceinline__ void exec_chunk(T (&x)[kMaxVecs][NE], const T (&sc)[kMaxScals],
-                                           Acc (&acc)[kMaxReds]) {
+template <class P, typename T, class Acc, int NE, bool FMA = false>
+__device__ __forceinline__ void exec_chunk(T (&x)[kMaxVecs][NE], const T (&sc)[kMaxScals], Acc (&acc)[kMaxReds]) {
 #pragma unroll
   for (int e = 0; e < NE; ++e) {
     T v[kMaxVecs];
 #pragma unroll
     for (int s = 0; s < kMaxVecs; ++s) v[s] = x[s][e];
-    exec_elem<P>(v, sc, acc);
+    exec_elem<P, T, Acc, FMA>(v, sc, acc);
 #pragma unroll
     for (int s = 0; s < kMaxVecs; ++s)
       if ((P::store_mask() >> s) & 1u) x[s][e] = v[s];
   }
+}
+
+// At every scaled add of P from node I on, the slot is a power of two and s*v
+// is exact for every element of the chunk (v as loaded: Prog::scaled_vec).
+template <class P, int I, int NE>
+__device__ __forceinline__ bool pow2_chunk_ok(const double (&x)[kMaxVecs][NE], const Pow2Info& p2) {
+  if constexpr (I >= P::len) {
+    return true;
+  } else {
+    bool ok = true;
+    if constexpr (P::scaled_add(I) || P::scaled_add_load(I)) {
+      constexpr int k = P::scaled_add_slot(I), a = P::scaled_add_vec(I);
+      ok = ((p2.mask >> k) & 1u) != 0u;
+#pragma unroll
+      for (int e = 0; e < NE; ++e) ok = ok & exact_pow2_scale(x[a][e], p2.exp[k]);
+    }
+    return ok & pow2_chunk_ok<P, I + 1, NE>(x, p2);
+  }
+}
+
+// exec_chunk with the scaled adds as FMAs when the whole chunk allows it
+// (FP64).  The test runs on the loaded operands before any arithmetic and
+// picks one of two complete chunk bodies, so each element runs one form only
+// (a test per element let the compiler compute both forms and select, one
+// FP64 instruction more instead of one less).  Programs with reductions keep
+// one body: the second doubled the register count of the CG-update shape
+// (80 to 157 at unroll 4).
+template <class P, typename T, class Acc, int NE>
+__device__ __forceinline__ void exec_chunk_p2(T (&x)[kMaxVecs][NE], const T (&sc)[kMaxScals], Acc (&acc)[kMaxReds],
+                                              const Pow2Info& p2) {
+  if constexpr (sizeof(T) == 8 && P::nred() == 0 && P::any_scaled_add()) {
+    if (p2.mask != 0u && pow2_chunk_ok<P, 0, NE>(x, p2)) {
+      exec_chunk<P, T, Acc, NE, true>(x, sc, acc);
+      return;
+    }
+  }
+  exec_chunk<P, T, Acc, NE>(x, sc, acc);
 }
 
 // The head of operands that share one misalignment: the host moved every
@@ -157,7 +205,7 @@ __global__ void __launch_bounds__(256) fused_kernel(const MapParams<T> p) {
       }
     }
     // operation burst
-    exec_chunk<P, T, Acc, U * VEC>(x, sc, acc);
+    exec_chunk_p2<P, T, Acc, U * VEC>(x, sc, acc, p.p2);
     // store burst
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -283,7 +331,7 @@ __global__ void __launch_bounds__(256) strided_kernel(const MapParams<T> p) {
         T v[kMaxVecs];
 #pragma unroll
         for (int s = 0; s < kMaxVecs; ++s) v[s] = x[s][u];
-        exec_elem<P>(v, sc, acc);
+        exec_elem<P, T, Acc>(v, sc, acc);
 #pragma unroll
         for (int s = 0; s < kMaxVecs; ++s)
           if ((SMASK >> s) & 1u) x[s][u] = v[s];

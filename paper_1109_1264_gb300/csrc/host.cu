@@ -1,4 +1,6 @@
 // Program validation, canonicalisation and lowering (host only).
+#include <cmath>
+
 #include "host.h"
 
 #include <cstdio>
@@ -376,5 +378,64 @@ bool build_scalar_code(const salt_insn* prog, const Hoisted& h, const Canonical&
   *out = sc;
   return true;
 }
+
+bool exact_pow2(double s, int* e) {
+  if (s == 0.0 || !std::isfinite(s)) return false;
+  int ex = 0;
+  const double m = std::frexp(s, &ex);  // s = m 2^ex, 0.5 <= |m| < 1
+  if (std::fabs(m) != 0.5) return false;
+  ex -= 1;
+  if (ex < -1022 || ex > 1023) return false;
+  *e = ex;
+  return true;
+}
+
+Pow2Info pow2_info(const double* sc, int nscal) {
+  Pow2Info p{};
+  for (int k = 0; k < nscal && k < kMaxScals; ++k) {
+    int e = 0;
+    if (sc && exact_pow2(sc[k], &e)) {
+      p.mask |= 1u << k;
+      p.exp[k] = (int16_t)e;
+    }
+  }
+  return p;
+}
+
+// Which node pairs the kernels take as one scaled add (Prog::scaled_add /
+// scaled_add_load), pinned at compile time.
+namespace {
+constexpr int V(int k) { return pack(OP_VEC, k); }
+constexpr int S(int k) { return pack(OP_SCAL, k); }
+constexpr int ST(int k) { return pack(OP_STORE, k); }
+constexpr int ADD = pack(OP_ADD, 0), SUB = pack(OP_SUB, 0), MUL = pack(OP_MUL, 0), SMUL = pack(OP_SMUL, 0),
+              NEG = pack(OP_NEG, 0);
+// e = alpha*a + beta*b - c o d: only beta*b is added at once (alpha*a is not
+// followed by an add).
+using ProgE = Prog<S(0), V(0), SMUL, S(1), V(1), SMUL, ADD, V(2), V(3), MUL, SUB, ST(4)>;
+static_assert(!ProgE::scaled_add(2) && !ProgE::scaled_add_load(2), "alpha*a");
+static_assert(ProgE::scaled_add(5) && ProgE::scaled_add_slot(5) == 1, "+ beta*b");
+// r - alpha*q, then r + beta*p
+using ProgCg = Prog<V(0), S(0), V(1), SMUL, SUB, ST(0), V(0), S(1), V(2), SMUL, ADD, ST(2)>;
+static_assert(ProgCg::scaled_add(3) && ProgCg::scaled_add_slot(3) == 0, "r - alpha*q");
+static_assert(ProgCg::scaled_add(9) && ProgCg::scaled_add_slot(9) == 1, "r + beta*p");
+// s*v - w, the next load subtracted
+using ProgSvw = Prog<S(0), V(0), SMUL, V(1), SUB, ST(2)>;
+static_assert(ProgSvw::scaled_add_load(2) && !ProgSvw::scaled_add(2) && ProgSvw::scaled_add_slot(2) == 0, "s*v - w");
+// a scale computed from two slots, or negated, is not a by-value slot
+using ProgProd = Prog<V(0), S(0), S(1), MUL, V(1), SMUL, ADD, ST(2)>;
+static_assert(ProgProd::producer(5, 1) == 3 && !ProgProd::scaled_add(5), "(s0*s1)*v");
+using ProgNeg = Prog<V(0), S(0), NEG, V(1), SMUL, ADD, ST(2)>;
+static_assert(ProgNeg::producer(4, 1) == 2 && !ProgNeg::scaled_add(4), "(-s0)*v");
+// x*v + w with x a vector is a plain MUL, never a scaled add
+using ProgVv = Prog<V(0), V(1), MUL, V(2), ADD, ST(3)>;
+static_assert(!ProgVv::scaled_add_load(2), "a o b + c");
+// v must be an operand as loaded: not a computed value, not one stored before
+using ProgSum = Prog<V(0), S(0), V(1), V(2), ADD, SMUL, ADD, ST(3)>;
+static_assert(ProgSum::producer(5, 2) == 4 && !ProgSum::scaled_add(5), "s*(b+c)");
+using ProgStored = Prog<V(0), V(1), ADD, ST(1), V(2), S(0), V(1), SMUL, ADD, ST(2)>;
+static_assert(!ProgStored::scaled_add(7) && ProgStored::stored_before(7, 1), "s*b after b is stored");
+static_assert(ProgE::any_scaled_add() && !ProgVv::any_scaled_add(), "any");
+}  // namespace
 
 }  // namespace salt

@@ -79,6 +79,11 @@ double host_scalar_value_f32(const salt_insn* prog, const Hoisted& h, int j, con
 double host_scalar_value_f64(const salt_insn* prog, const Hoisted& h, int j, const double* scalars,
                              const double* dvals = nullptr);
 
+// s = +-2^e exactly, with e in the normal range [-1022, 1023]: true and *e.
+bool exact_pow2(double s, int* e);
+// Pow2Info of an FP64 launch's by-value scalar slots sc[0 .. nscal-1].
+Pow2Info pow2_info(const double* sc, int nscal);
+
 // Device code that computes the hoisted slots of canonical program `c`
 // (made from h.prog) into canonical scalar slots; user_nscal scalars by
 // value, `dscal` device pointers.  False if it would exceed kMaxScalarCode.

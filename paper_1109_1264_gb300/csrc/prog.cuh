@@ -67,6 +67,57 @@ struct Prog {
     return r;
   }
   __host__ __device__ static constexpr int nred() { return red_index(len); }
+  // The stack slot node k writes its result to, or -1 (STORE, DOT, SUMSQ
+  // only pop).
+  __host__ __device__ static constexpr int writes_slot(int k) {
+    return op(k) == OP_VEC || op(k) == OP_SCAL || op(k) == OP_DSCAL ? depth_before(k)
+         : op(k) == OP_NEG ? depth_before(k) - 1
+         : op(k) == OP_STORE || op(k) == OP_DOT || op(k) == OP_SUMSQ ? -1
+         : depth_before(k) - 2;  // ADD SUB MUL DIV SMUL
+  }
+  // The node whose result stack slot `slot` holds when node i runs (the slot
+  // is live there): the last node k < i that wrote that slot.
+  __host__ __device__ static constexpr int producer(int i, int slot) {
+    int p = -1;
+    for (int k = 0; k < i; ++k)
+      if (writes_slot(k) == slot) p = k;
+    return p;
+  }
+  // Operand a is stored by a node before node i.
+  __host__ __device__ static constexpr bool stored_before(int i, int a) {
+    for (int k = 0; k < i; ++k)
+      if (op(k) == OP_STORE && arg(k) == a) return true;
+    return false;
+  }
+  // Node i is a scalar-times-vector s*v with s a by-value scalar slot (a SCAL
+  // token) and v an operand as loaded (a VEC token of an operand not stored
+  // before node i), so both are known before the element's nodes run.
+  __host__ __device__ static constexpr bool scaled_vec(int i) {
+    if (i >= len || op(i) != OP_SMUL) return false;
+    const int d = depth_before(i);
+    const int ks = producer(i, d - 2), kv = producer(i, d - 1);
+    return ks >= 0 && op(ks) == OP_SCAL && kv >= 0 && op(kv) == OP_VEC && !stored_before(i, arg(kv));
+  }
+  // A scaled_vec node whose result is at once added to, or subtracted from,
+  // the value below it (node i + 1 is ADD or SUB): X + s*v, X - s*v.
+  __host__ __device__ static constexpr bool scaled_add(int i) {
+    return scaled_vec(i) && depth_before(i) >= 3 && (op(i + 1) == OP_ADD || op(i + 1) == OP_SUB);
+  }
+  // A scaled_vec node whose result is at once added to, or has subtracted
+  // from it, the next vector load (nodes i + 1, i + 2: VEC, ADD / SUB):
+  // s*v + w, s*v - w.
+  __host__ __device__ static constexpr bool scaled_add_load(int i) {
+    return scaled_vec(i) && i + 2 < len && op(i + 1) == OP_VEC && (op(i + 2) == OP_ADD || op(i + 2) == OP_SUB);
+  }
+  // The scalar slot and the vector operand of a scaled_vec node i.
+  __host__ __device__ static constexpr int scaled_add_slot(int i) { return arg(producer(i, depth_before(i) - 2)); }
+  __host__ __device__ static constexpr int scaled_add_vec(int i) { return arg(producer(i, depth_before(i) - 1)); }
+  // Some node of the program is a scaled add.
+  __host__ __device__ static constexpr bool any_scaled_add() {
+    for (int i = 0; i < len; ++i)
+      if (scaled_add(i) || scaled_add_load(i)) return true;
+    return false;
+  }
   // Vector operands whose first reference is a read: loaded from memory.
   __host__ __device__ static constexpr unsigned load_mask() {
     unsigned seen = 0, m = 0;

@@ -465,3 +465,93 @@ def test_concurrent_host_threads_on_separate_streams(salt):
         want_z = [xh.copy(), np.zeros(n)]
         oracle.eval_program(oracle.PROG_SCALE, want_z, [0.5 + t])
         assert_bits_equal(z, want_z[1], f"thread {t}")
+
+
+POW2_PROGS = {
+    "E": (oracle.PROG_E, 5, 2),
+    "AXPBY": (oracle.PROG_AXPBY, 2, 2),
+    "AXPY": ([("SCAL", 0), ("VEC", 0), ("SMUL", 0), ("VEC", 1), ("ADD", 0), ("STORE", 1)], 2, 1),
+    "CG": (oracle.PROG_CG, 3, 2),
+    "X_MINUS_SV": ([("VEC", 0), ("SCAL", 0), ("VEC", 1), ("SMUL", 0), ("SUB", 0), ("STORE", 2)], 3, 1),
+    "SV_MINUS_W": ([("SCAL", 0), ("VEC", 0), ("SMUL", 0), ("VEC", 1), ("SUB", 0), ("STORE", 2)], 3, 1),
+    # no compiled shape: the run-time compiled kernel
+    "JIT": ([("VEC", 0), ("SCAL", 0), ("VEC", 1), ("SMUL", 0), ("ADD", 0), ("VEC", 2), ("MUL", 0),
+             ("SCAL", 1), ("VEC", 2), ("SMUL", 0), ("VEC", 0), ("SUB", 0), ("ADD", 0), ("STORE", 3)], 4, 2),
+}
+
+
+def edge_values(rng, n, runs=False):
+    """FP64 values spread over the whole exponent range: ordinary values,
+    normals near the bottom and the top of the range, subnormals, signed
+    zeros, infinities and NaN -- each element's class drawn on its own, or
+    (runs) one class for runs of 1 to 64 elements, so that whole chunks of
+    a thread hold one class."""
+    kind = rng.integers(0, 8, n)
+    if runs:
+        kind = np.repeat(kind, rng.integers(1, 65, n))[:n]
+    sign = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    v = rng.uniform(-1, 1, n)
+    frac = 1.0 + rng.random(n)
+    lo = np.ldexp(frac, rng.integers(-1022, -1000, n))
+    hi = np.ldexp(frac * 0.99, rng.integers(1000, 1023, n))
+    sub = np.ldexp(rng.random(n), -1022)
+    v = np.where(kind == 1, sign * lo, v)
+    v = np.where(kind == 2, sign * hi, v)
+    v = np.where(kind == 3, sign * sub, v)
+    v = np.where(kind == 4, sign * 0.0, v)
+    v = np.where(kind == 5, sign * np.inf, v)
+    v = np.where(kind == 6, np.nan, v)
+    return v
+
+
+@pytest.mark.parametrize("name", list(POW2_PROGS))
+def test_power_of_two_scalars_bit_exact(salt, name):
+    """FP64 programs whose by-value scalars are powers of two run X +- s*v as
+    one FMA on chunks where s*v is exact, and as the two rounded nodes
+    elsewhere: the results must be the oracle's bits for every scalar
+    exponent (both ends of the range, both signs, mixed with scalars that
+    are not powers of two) and every operand class (ordinary, tiny and huge
+    normals, subnormals, zeros, infinities, NaN), on the register-tiled
+    loop and the run-time compiled kernel; the strided and staged loops and
+    the batch kernel, which take every node as its own operation, must give
+    the same bits."""
+    prog, nv, ns = POW2_PROGS[name]
+    import zlib
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    n = 4096 * 3 + 37
+    scalar_sets = [[2.0 ** e, -(2.0 ** f)] for e, f in ((-2, 3), (0, -1), (-1022, 1023), (1000, -1000), (5, 0))]
+    scalar_sets += [[1.5, -0.25], [-0.25, 1.5], [3.0, 0.1]]
+    _, compiled = salt.salt_check_program(prog, nv, ns)
+    # the staged loop and the batch kernel take compiled shapes only
+    scheds = ("register", "strided", "staged", "batch") if compiled else ("register", "strided")
+    try:
+        for sched in scheds:
+            if sched == "staged":
+                salt.salt_tune_set(prog, salt.F64, n, 1, 16, 128, 0, 4096)
+            for sc, runs in ((sc, runs) for sc in scalar_sets for runs in (False, True)):
+                scalars = sc[:ns]
+                vecs = [edge_values(rng, n, runs) for _ in range(nv)]
+                want, _ = run_oracle(prog, vecs, scalars)
+                if sched == "batch":
+                    tv = [torch.from_numpy(v.copy()).cuda() for v in vecs]
+                    b = salt.Batch(1)
+                    b.add(prog, tv, scalars)
+                    red = torch.zeros(4, dtype=torch.float64, device="cuda")
+                    b.launch(red)
+                    torch.cuda.synchronize()
+                    got = [t.cpu().numpy() for t in tv]
+                    b.close()
+                elif sched == "strided":  # every other element of a buffer twice as long
+                    bufs = [torch.zeros(2 * n, dtype=torch.float64, device="cuda") for _ in vecs]
+                    for bb, v in zip(bufs, vecs):
+                        bb[::2] = torch.from_numpy(v)
+                    red = torch.zeros(4, dtype=torch.float64, device="cuda")
+                    salt.salt_eval(prog, [bb[::2] for bb in bufs], scalars, red_out=red)
+                    torch.cuda.synchronize()
+                    got = [bb[::2].cpu().numpy() for bb in bufs]
+                else:
+                    got, _ = run_gpu(salt, prog, vecs, scalars, np.float64)
+                for k, (g, w) in enumerate(zip(got, want)):
+                    assert_bits_equal(g, w, f"{name} {sched} scalars {scalars} runs {runs} operand {k}")
+    finally:
+        salt.salt_tune_clear()
