@@ -74,6 +74,8 @@ def f64_alu_peak_gops(sm_mhz: float) -> float:
 KERNEL_SOURCES = {
     "e_f64": ["prog.cuh", "common.cuh", "fused.cuh", "reduce.cuh", "shapes.h", "registry.h", "inst.cuh",
               "inst_f64_vb16.cu", "inst_f64_vb32.cu"],
+    "axpby_f64": ["prog.cuh", "common.cuh", "fused.cuh", "reduce.cuh", "shapes.h", "registry.h", "inst.cuh",
+                  "inst_f64_vb16.cu", "inst_f64_vb32.cu"],
     "e_f64_staged": ["prog.cuh", "common.cuh", "fused.cuh", "staged.cuh", "shapes.h", "registry.h",
                      "inst_staged.cu"],
     "dot_f64_staged": ["prog.cuh", "common.cuh", "fused.cuh", "staged.cuh", "shapes.h", "registry.h",
