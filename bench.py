@@ -846,8 +846,10 @@ def sweep_measure(torch, salt, reps: int = 21, max_log2: int = 28) -> dict:
     copy = [("VEC", 0), ("STORE", 1)]
     hbm_peak, _, sm_max = load_peaks()
     alu_peak = f64_alu_peak_gops(sm_max)
-    # FP64 instructions per element (one per node; the reductions' FMA)
-    f64_instr = {"axpy": 2, "dot": 1, "nrm2": 1, "e": 5, "scal": 1, "copy_scal_fused": 1}
+    # FP64 instructions per element (one per node; the reductions' FMA; e as
+    # in the step, with beta a power of two; axpy's alpha = 1e-3 is not one)
+    f64_instr = {"axpy": 2 - is_pow2(1e-3), "dot": 1, "nrm2": 1, "e": F64_INSTR["e"], "scal": 1,
+                 "copy_scal_fused": 1}
     # L2 flush: READ a 256 MiB buffer before each timed call, so that L2 holds
     # clean lines of another buffer (a write-based flush would leave up to
     # the whole L2 dirty, and the timed kernel would pay its write-back).
