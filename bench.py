@@ -632,6 +632,14 @@ def summary_of(r: dict) -> dict:
     if sv:
         out["served"] = {"saturation_gbs": sv["saturation_gbs"], "vs_unbatched": sv["batched_vs_unbatched"],
                          "p50_p99_us": {str(pt["load"]): [pt["p50_us"], pt["p99_us"]] for pt in sv["points"]}}
+        if "one_at_a_time" in sv:
+            out["served"]["one_at_a_time_p50_p99_us"] = [sv["one_at_a_time"]["p50_us"], sv["one_at_a_time"]["p99_us"]]
+        pz = sv.get("persistent")
+        if pz:
+            out["served_persistent"] = {
+                "saturation_gbs": pz["saturation_gbs"],
+                "p50_p99_us": {str(pt["load"]): [pt["p50_us"], pt["p99_us"]] for pt in pz["points"]},
+                "one_at_a_time_p50_p99_us": [pz["one_at_a_time"]["p50_us"], pz["one_at_a_time"]["p99_us"]]}
     if "config1_figure1" in r:
         c = r["config1_figure1"]
         out["figure1_us"] = {k: c[k] for k in ("l2_warm_us", "l2_flushed_us") if k in c}
@@ -1466,6 +1474,31 @@ def served_measure(salt, count: int = 3000, seed: int = 0, collect: list | None 
         lat, _, wall = srv.replay(zeros, shapes, d32, lens, seed, store=st)
         return lat, wall, srv.stats()["steps"] - s0
 
+    def load_points(srv, sat_rps):
+        pts = []
+        for k, frac in enumerate((0.1, 0.3, 0.5, 0.7, 0.9, 1.2)):
+            rate = frac * sat_rps
+            arr = inputs.poisson_arrivals(seed + 1 + k, count, rate) * 1e6
+            lat, _, wall_k = srv.replay(arr, shapes, d32, lens, seed, store=store)
+            pts.append({"load": frac, "rate_rps": round(rate, 1), "p50_us": round(float(np.percentile(lat, 50)), 1),
+                        "p99_us": round(float(np.percentile(lat, 99)), 1),
+                        "gbs": round(total_bytes / (wall_k * 1e-6) / 1e9, 1)})
+        return pts
+
+    def one_at_a_time(srv, reps=300):
+        """One FP32 dot of n = 256 at a time, its operands read in place from
+        the store: latency from submission to observed completion."""
+        x, y = store[0][0][:256], store[0][1][:256]
+        lat = []
+        for i in range(reps + 20):
+            rid = srv.submit([("VEC", 0), ("VEC", 1), ("DOT", 0)], salt.F32, 256, [0, 0], ptrs=[x, y])
+            srv.wait(rid, 10_000_000)
+            if i >= 20:
+                lat.append(srv.poll(rid)[1])
+            srv.release(rid)
+        return {"n": 256, "requests": reps, "p50_us": round(float(np.percentile(lat, 50)), 1),
+                "p99_us": round(float(np.percentile(lat, 99)), 1)}
+
     srv = salt.Server()
     try:
         _, wall, steps = saturation(srv, True)
@@ -1484,17 +1517,24 @@ def served_measure(salt, count: int = 3000, seed: int = 0, collect: list | None 
                                     "n": int(lens[i]), "operands": ops_, "got": float(red[i])})
         sat_rps = count / (wall * 1e-6)
         sat_gbs = total_bytes / (wall * 1e-6) / 1e9
-        points = []
-        for k, frac in enumerate((0.1, 0.3, 0.5, 0.7, 0.9, 1.2)):
-            rate = frac * sat_rps
-            arr = inputs.poisson_arrivals(seed + 1 + k, count, rate) * 1e6
-            lat, _, wall_k = srv.replay(arr, shapes, d32, lens, seed, store=store)
-            points.append({"load": frac, "rate_rps": round(rate, 1), "p50_us": round(float(np.percentile(lat, 50)), 1),
-                           "p99_us": round(float(np.percentile(lat, 99)), 1),
-                           "gbs": round(total_bytes / (wall_k * 1e-6) / 1e9, 1)})
+        points = load_points(srv, sat_rps)
+        single = one_at_a_time(srv)
         _, wall_f, steps_f = saturation(srv, False)
     finally:
         srv.stop()
+    # persistent mode: the same stream, the load points at the default mode's rates
+    srvp = salt.Server(persistent=1)
+    try:
+        _, wall_p, steps_p = saturation(srvp, True)
+        points_p = load_points(srvp, sat_rps)
+        single_p = one_at_a_time(srvp)
+        launches_p = srvp.launches()[0]
+    finally:
+        srvp.stop()
+    persistent = {"saturation_gbs": round(total_bytes / (wall_p * 1e-6) / 1e9, 1), "saturation_steps": steps_p,
+                  "points": points_p, "one_at_a_time": single_p, "kernel_launches": launches_p,
+                  "note": "one resident launch runs the steps posted to a ring in mapped host memory; load points "
+                          "at the default mode's arrival rates"}
     srv1 = salt.Server(max_batch=1)
     try:
         _, wall1, _ = saturation(srv1, True)
@@ -1514,6 +1554,7 @@ def served_measure(salt, count: int = 3000, seed: int = 0, collect: list | None 
             "four_streams_saturation_gbs": round(total_bytes / (wall4 * 1e-6) / 1e9, 1),
             "fill_per_request_steps": steps_f,
             "requests_per_point": count, "bytes_per_point": total_bytes, "points": points,
+            "one_at_a_time": single, "persistent": persistent,
             "workload": "5 shapes uniform, n log-uniform [2^8, 2^24], 70% FP32 / 30% FP64; inputs from an 8 GiB "
                         "resident store of counter-filled vectors (slices at hashed offsets), outputs in an 8 GiB "
                         "arena, 2 streams; latency from arrival to observed completion"}

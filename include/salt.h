@@ -334,8 +334,8 @@ salt_status salt_cg_autotune(int32_t dtype, int64_t n, const void* d, const void
  * SALT_ERR_CUDA. */
 salt_status salt_cg_status(void* stream);
 
-/* Limits of the two bounded device waits, for tests that make a wait run out
- * on purpose (both are process-wide and read at each launch):
+/* Limits of the bounded device waits, for tests that make a wait run out on
+ * purpose (all are process-wide and read at each launch):
  *   SALT_WAIT_STAGED      polls thread 0 of a staged-loop block spends on a
  *                         tile's bulk copies before it stops staging and
  *                         computes from direct loads (results unchanged;
@@ -345,7 +345,12 @@ salt_status salt_cg_status(void* stream);
  *   SALT_WAIT_CG_BARRIER  polls of one grid barrier of the cooperative CG
  *                         launches before it records a timeout (see
  *                         salt_cg_status); 0: give up unless already passed.
- * Default for both: 2^26 polls (besides the staged wait's one-second timer
+ *   SALT_WAIT_SERVE       polls of each wait of the persistent serving
+ *                         kernel (salt_serve_config.persistent) before it
+ *                         ends its launch; a wait other than the idle wait
+ *                         for the next step that runs out fails the server
+ *                         (its requests report SALT_ERR_CUDA).
+ * Default for all: 2^26 polls (besides the staged wait's one-second timer
  * bound).  polls in [0, 2^32); errors: SALT_ERR_ARG (unknown wait, polls
  * out of range or NULL).  Not in the paper. */
 /* Per-block timeline of launches, for finding where a kernel's time goes
@@ -365,6 +370,7 @@ salt_status salt_trace_set(void* buf, int64_t max_blocks);
 
 #define SALT_WAIT_STAGED 1
 #define SALT_WAIT_CG_BARRIER 2
+#define SALT_WAIT_SERVE 3
 #define SALT_WAIT_DEFAULT_POLLS 67108864
 salt_status salt_set_wait_limit(int32_t which, int64_t polls);
 salt_status salt_get_wait_limit(int32_t which, int64_t* polls);
@@ -685,7 +691,19 @@ salt_status salt_batch_autotune(salt_batch* b, double* red_out, int32_t reps, do
  * meanwhile join the next step.  All requests use one tile size, so a
  * request's results are the same bits alone or in any mix.
  * Latency = host time at which the scheduler observed the step's completion
- * event minus the request's submission time. */
+ * event minus the request's submission time.
+ *
+ * Persistent mode (`persistent` = 1): one cooperative launch stays resident
+ * and runs the steps, which the scheduler posts to a ring of `streams`
+ * entries in mapped pinned host memory (no launch, table upload or event
+ * per step); the launch polls the ring, copies each step's tables to the
+ * device, runs the fill and compute phases with the batch kernel's tile
+ * loop and writes the step's completion to host memory.  Every device wait
+ * is bounded; the launch ends after `idle_us` microseconds with nothing
+ * posted (the GPU is then free for other work) and the scheduler launches
+ * it again with the next step.  Results are the same bits as in the default
+ * mode.  While a launch is resident it occupies every SM it was given, so
+ * other kernels on the device wait for SMs until it ends. */
 typedef struct salt_server salt_server;
 
 typedef struct {
@@ -697,10 +715,15 @@ typedef struct {
   int32_t unroll;       /* batch kernel unroll: 1, 2, 4                            */
   int32_t block;        /* batch kernel block: 64, 128, 256                        */
   int64_t max_n;        /* longest request accepted                                */
+  int32_t persistent;   /* 1: steps run in one resident launch (see above); 0: one  */
+                        /* graph launch per step                                   */
+  int32_t idle_us;      /* persistent mode: the resident launch ends after this     */
+                        /* long with nothing posted (1 .. 10^7)                    */
 } salt_serve_config;
 
 /* Defaults: 8 GiB budget, 4096 resident requests, 256 per step, 2 streams,
- * 64 KiB tiles, unroll 2, 256 threads, n <= 2^24. */
+ * 64 KiB tiles, unroll 2, 256 threads, n <= 2^24, not persistent, 10 ms
+ * idle time. */
 salt_status salt_serve_default_config(salt_serve_config* cfg);
 /* Allocates the arena and per-stream tables on the current device and starts
  * the scheduler thread.  Errors: SALT_ERR_ARG, SALT_ERR_CUDA. */
@@ -708,6 +731,11 @@ salt_status salt_serve_start(salt_server** out, const salt_serve_config* cfg);
 /* Drains the steps in flight, stops the scheduler, frees everything
  * (requests not yet complete are dropped). */
 salt_status salt_serve_stop(salt_server* s);
+/* Persistent mode: *launches = launches of the resident kernel so far (one,
+ * plus one after each idle end), *live = 1 while one is running (as the
+ * scheduler last saw it); 0 and 0 in the default mode.  Either pointer may
+ * be NULL.  Errors: SALT_ERR_ARG. */
+salt_status salt_serve_launches(salt_server* s, int64_t* launches, int32_t* live);
 
 /* Submits a request.  prog/nprog: a program with a compiled instantiation
  * among the batch kernel's shapes (<= 5 vector operands, <= 2 scalars) once
@@ -729,8 +757,10 @@ salt_status salt_serve_submit(salt_server* s, const salt_insn* prog, int32_t npr
  * Operands whose pointer is NULL are server-owned and keyed by keys[k] as in
  * salt_serve_submit (keys may be NULL if every operand has a pointer).  The
  * caller keeps caller-owned memory valid and unmodified until the request
- * is done; two requests in flight must not write memory another one reads
- * or writes (not checked).  salt_serve_read copies caller-owned operands
+ * is done, and its contents ready when submitting (the server's work is not
+ * ordered after the caller's streams: synchronize the writes first); two
+ * requests in flight must not write memory another one reads or writes (not
+ * checked).  salt_serve_read copies caller-owned operands
  * too. */
 salt_status salt_serve_submit_ex(salt_server* s, const salt_insn* prog, int32_t nprog, int32_t dtype, int64_t n,
                                  const void* const* ptrs, const uint64_t* keys, int32_t nops,

@@ -1281,14 +1281,19 @@ salt_status salt_set_wait_limit(int32_t which, int64_t polls) {
     cg_barrier_polls(polls);
     return SALT_OK;
   }
-  return set_error(SALT_ERR_ARG, "unknown wait (SALT_WAIT_STAGED or SALT_WAIT_CG_BARRIER)");
+  if (which == SALT_WAIT_SERVE) {
+    serve_polls(polls);
+    return SALT_OK;
+  }
+  return set_error(SALT_ERR_ARG, "unknown wait (SALT_WAIT_STAGED, SALT_WAIT_CG_BARRIER or SALT_WAIT_SERVE)");
 }
 
 salt_status salt_get_wait_limit(int32_t which, int64_t* polls) {
   if (!polls) return set_error(SALT_ERR_ARG, "polls is NULL");
   if (which == SALT_WAIT_STAGED) *polls = staged_tile_polls(-1);
   else if (which == SALT_WAIT_CG_BARRIER) *polls = cg_barrier_polls(-1);
-  else return set_error(SALT_ERR_ARG, "unknown wait (SALT_WAIT_STAGED or SALT_WAIT_CG_BARRIER)");
+  else if (which == SALT_WAIT_SERVE) *polls = serve_polls(-1);
+  else return set_error(SALT_ERR_ARG, "unknown wait (SALT_WAIT_STAGED, SALT_WAIT_CG_BARRIER or SALT_WAIT_SERVE)");
   return SALT_OK;
 }
 

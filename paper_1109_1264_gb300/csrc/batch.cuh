@@ -59,7 +59,7 @@ struct BatchParams {
 // One block evaluates program P on elements [lo, hi) of an item: whole
 // sub-tiles of U vectors per thread (load burst, op burst, store burst), then
 // single vectors, then single elements.
-template <class P, typename T, int U, int VB = 16>
+template <class P, typename T, int U, int VB = 16, bool NC = true>
 __device__ __forceinline__ void range_eval(T* const* v, const T (&sc)[kMaxScals], int64_t lo, int64_t hi,
                                            typename AccOf<T>::type (&acc)[kMaxReds]) {
   constexpr int VEC = VB / (int)sizeof(T);
@@ -78,8 +78,8 @@ __device__ __forceinline__ void range_eval(T* const* v, const T (&sc)[kMaxScals]
       for (int k = 0; k < kMaxVecs; ++k) {
         if ((LM >> k) & 1u) {
           V t;
-          if ((SMASK >> k) & 1u) vload<false>(t, v[k] + base + u * bd * VEC);
-          else vload<true>(t, v[k] + base + u * bd * VEC);
+          if (NC && !((SMASK >> k) & 1u)) vload<true>(t, v[k] + base + u * bd * VEC);
+          else vload<false>(t, v[k] + base + u * bd * VEC);
 #pragma unroll
           for (int e = 0; e < VEC; ++e) x[k][u * VEC + e] = t.e[e];
         } else {
@@ -111,8 +111,8 @@ __device__ __forceinline__ void range_eval(T* const* v, const T (&sc)[kMaxScals]
     for (int k = 0; k < kMaxVecs; ++k) {
       if ((LM >> k) & 1u) {
         V t;
-        if ((SMASK >> k) & 1u) vload<false>(t, v[k] + off);
-        else vload<true>(t, v[k] + off);
+        if (NC && !((SMASK >> k) & 1u)) vload<true>(t, v[k] + off);
+        else vload<false>(t, v[k] + off);
 #pragma unroll
         for (int e = 0; e < VEC; ++e) x[k][e] = t.e[e];
       } else {
@@ -144,7 +144,9 @@ __device__ __forceinline__ void range_eval(T* const* v, const T (&sc)[kMaxScals]
 
 // Program item: returns the number of partial values produced (its
 // reductions) in vals.
-template <class P, typename T, int U>
+// NC = false: no read-only (non-coherent) loads, for a kernel that also
+// writes the data it reads (the persistent serving kernel).
+template <class P, typename T, int U, bool NC = true>
 __device__ __forceinline__ int item_program(const BatchItem& it, int64_t lo, int64_t hi, double (&vals)[kBatchPartials],
                                             bool narrow) {
   T* v[kMaxVecs];
@@ -164,10 +166,10 @@ __device__ __forceinline__ int item_program(const BatchItem& it, int64_t lo, int
   for (int k = 0; k < kBatchOps; ++k)
     if (k < P::nvec()) align |= (uintptr_t)it.v[k];
   if constexpr (U >= 2 && sizeof(T) == 4) {
-    if (!narrow && (align & 31u) == 0) range_eval<P, T, U / 2, 32>(v, sc, lo, hi, acc);
-    else range_eval<P, T, U, 16>(v, sc, lo, hi, acc);
+    if (!narrow && (align & 31u) == 0) range_eval<P, T, U / 2, 32, NC>(v, sc, lo, hi, acc);
+    else range_eval<P, T, U, 16, NC>(v, sc, lo, hi, acc);
   } else {
-    range_eval<P, T, U, 16>(v, sc, lo, hi, acc);
+    range_eval<P, T, U, 16, NC>(v, sc, lo, hi, acc);
   }
   constexpr int NR = P::nred();
 #pragma unroll
@@ -175,7 +177,7 @@ __device__ __forceinline__ int item_program(const BatchItem& it, int64_t lo, int
   return NR;
 }
 
-template <typename T>
+template <typename T, bool NC = true>
 __device__ __forceinline__ int item_nrm2(const BatchItem& it, int64_t lo, int64_t hi, double (&vals)[kBatchPartials]) {
   constexpr int VEC = 16 / (int)sizeof(T);
   using V = VecT<T, 16>;
@@ -185,7 +187,7 @@ __device__ __forceinline__ int item_nrm2(const BatchItem& it, int64_t lo, int64_
     for (int64_t i = lo + (int64_t)threadIdx.x * VEC; i < hi; i += (int64_t)blockDim.x * VEC) {
       if (i + VEC <= hi) {
         V a;
-        vload<true>(a, x + i);
+        vload<NC>(a, x + i);
 #pragma unroll
         for (int e = 0; e < VEC; ++e) acc.add(a.e[e]);
       } else {
@@ -199,7 +201,7 @@ __device__ __forceinline__ int item_nrm2(const BatchItem& it, int64_t lo, int64_
     for (int64_t i = lo + (int64_t)threadIdx.x * VEC; i < hi; i += (int64_t)blockDim.x * VEC) {
       if (i + VEC <= hi) {
         V a;
-        vload<true>(a, x + i);
+        vload<NC>(a, x + i);
 #pragma unroll
         for (int e = 0; e < VEC; ++e) acc.add(a.e[e]);
       } else {
@@ -230,19 +232,19 @@ __device__ __forceinline__ int item_fill(const BatchItem& it, int64_t lo, int64_
   return 0;
 }
 
-template <typename T, int U>
+template <typename T, int U, bool NC = true>
 __device__ __forceinline__ int dispatch_item(const BatchItem& it, int64_t lo, int64_t hi, double (&vals)[kBatchPartials],
                                              bool narrow) {
   switch (it.kind) {
 #define SALT_BATCH_CASE(name, ...) \
   case SHAPE_##name:               \
-    return item_program<Prog_##name, T, U>(it, lo, hi, vals, narrow);
+    return item_program<Prog_##name, T, U, NC>(it, lo, hi, vals, narrow);
     SALT_BATCH_SHAPE_LIST(SALT_BATCH_CASE)
 #undef SALT_BATCH_CASE
     case kKindFill:
       return item_fill<T>(it, lo, hi);
     default:
-      return item_nrm2<T>(it, lo, hi, vals);
+      return item_nrm2<T, NC>(it, lo, hi, vals);
   }
 }
 
@@ -266,8 +268,13 @@ __device__ __forceinline__ int find_item(const BatchItem* items, int nitems, int
   return a;
 }
 
-template <int U>
-__global__ void __launch_bounds__(256) batch_kernel(const BatchParams p) {
+// The tile loop of one batch launch (or of one phase of a step of the
+// persistent serving kernel): tiles from p.counter until it passes the
+// header's total.  Returns once this block has taken its last tile; the
+// counter is then past the total, and the caller zeroes it once every block
+// has returned.
+template <int U, bool NC = true>
+__device__ __forceinline__ void run_tiles(const BatchParams& p) {
   __shared__ int64_t s_tile;
   __shared__ int s_item;
   __shared__ bool s_last;
@@ -299,8 +306,8 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchParams p) {
     const int64_t lo = (tile - it.tile_begin) * tile_elems;
     const int64_t hi = lo + tile_elems < it.n ? lo + tile_elems : it.n;
     double vals[kBatchPartials] = {0.0, 0.0, 0.0};
-    const int nv = it.dtype == DT_F32 ? dispatch_item<float, U>(it, lo, hi, vals, narrow)
-                                      : dispatch_item<double, U>(it, lo, hi, vals, narrow);
+    const int nv = it.dtype == DT_F32 ? dispatch_item<float, U, NC>(it, lo, hi, vals, narrow)
+                                      : dispatch_item<double, U, NC>(it, lo, hi, vals, narrow);
     if (nv > 0) {
       // this tile's partials, then the per-item ticket
       for (int r = 0; r < nv; ++r) {
@@ -336,6 +343,11 @@ __global__ void __launch_bounds__(256) batch_kernel(const BatchParams p) {
     if (threadIdx.x == 0) s_tile = (int64_t)next;
     __syncthreads();
   }
+}
+
+template <int U>
+__global__ void __launch_bounds__(256) batch_kernel(const BatchParams p) {
+  run_tiles<U>(p);
   // Every counter is zero again when the launch ends, so the next launch
   // needs no reset: the tickets are cleared by each item's last tile, and
   // the last block to finish (its tile fetches are all done) clears the tile

@@ -59,6 +59,8 @@ void count_launch();
 // Polls one grid barrier of the cooperative CG kernels spends before it
 // records a timeout; `set` >= 0 replaces the limit first.  Returns the limit.
 unsigned cg_barrier_polls(int64_t set);
+// Poll bound of the persistent serving kernel's waits (read at each launch).
+unsigned serve_polls(int64_t set);
 
 // Run-time compiled fused kernels (csrc/jit.cu): the current mode
 // (SALT_JIT_OFF / SALT_JIT_ON / SALT_JIT_AUTO; SALT_JIT_OFF while this

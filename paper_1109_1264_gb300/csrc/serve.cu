@@ -33,6 +33,7 @@
 #include "../../include/salt.h"
 #include "batch.cuh"
 #include "internal.h"
+#include "persist.cuh"
 #include "registry.h"
 
 using namespace salt;
@@ -158,6 +159,50 @@ KernelFn kernel_for(int unroll) {
   }
 }
 
+using PersistFn = void (*)(const PersistParams);
+PersistFn persist_for(int unroll) {
+  switch (unroll) {
+    case 1: return &persist_kernel<1>;
+    case 2: return &persist_kernel<2>;
+    default: return &persist_kernel<4>;
+  }
+}
+
+// Bound on the waits of the persistent kernel other than block 0's wait for
+// a posted step (which the configuration's idle time bounds).
+constexpr unsigned long long kPersistWaitNs = 1000000000ull;
+std::atomic<unsigned> g_serve_polls{67108864u};
+
+// Persistent mode (salt_serve_config.persistent): steps are posted to a ring
+// of `streams` entries in mapped pinned host memory and run by one resident
+// launch of persist_kernel (persist.cuh) until it has been idle for idle_us.
+struct PersistState {
+  bool on = false;
+  int nring = 0;
+  int grid = 0;
+  PersistCtl* ctl = nullptr;  // mapped pinned host memory
+  PersistCtl* ctl_dev = nullptr;
+  char* ring = nullptr;       // nring entries of entry_bytes, mapped
+  char* ring_dev = nullptr;
+  size_t entry_bytes = 0;
+  double* red = nullptr;      // nring x red_stride results, mapped
+  double* red_dev = nullptr;
+  size_t red_stride = 0;
+  char* d_mem = nullptr;      // device: table (entry_bytes) | counters | partials | sync words
+  size_t off_counters = 0, off_partials = 0, off_sync = 0, counters_stride = 0;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ended = nullptr;  // recorded after each launch
+  std::atomic<bool> live{false};
+  std::atomic<int64_t> launches{0};
+  uint64_t epoch = 0, posted = 0;
+  struct Entry {
+    std::vector<Request*> reqs;
+    uint64_t step = 0;
+  };
+  std::deque<Entry> inflight;  // posted and not complete, in step order
+  std::vector<BatchItem> comps;
+};
+
 salt_status fail(salt_status st, const std::string& m) { return report_error(st, m); }
 salt_status cuda_fail(cudaError_t e, const char* where) {
   return fail(SALT_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
@@ -173,6 +218,7 @@ struct salt_server {
   char* arena_base = nullptr;
   Arena arena;
   std::vector<Slot> slots;
+  PersistState ps;
   int64_t items_cap = 0, tiles_cap = 0;
   // shared state
   std::mutex mu;
@@ -267,24 +313,19 @@ cudaError_t build_step_graph(salt_server* s, Slot& slot, bool with_fill, Slot::S
   return cudaSuccess;
 }
 
-// Builds and launches one step on `slot` from the front of `pending`
-// (scheduler thread, lock not held while launching).
-salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch) {
-  size_t off_items[2], off_counters[2], off_partials;
-  slot_device_bytes(s, off_items, off_counters, &off_partials);
-  // Host tables in the pinned staging area, packed so that one copy of
-  // only the bytes in use moves them: [hdr0 | hdr1 | fill items | compute
-  // items].  Compute items are built aside, then placed after the fills.
-  BatchHeader* h_hdr[2] = {(BatchHeader*)slot.h_mem, (BatchHeader*)(slot.h_mem + 256)};
-  BatchItem* h_items[2] = {(BatchItem*)(slot.h_mem + 512), slot.compute_items.data()};
-  int nitems[2] = {0, 0};
-  int64_t tiles[2] = {0, 0};
+// The item tables of one step: a fill item per server-owned input operand
+// (fills[0 .. nitems[0])) and a compute item per request (comps[0 ..
+// nitems[1])), with their global tile numbers and result slots.
+void build_items(const salt_server* s, const std::vector<Request*>& batch, BatchItem* fills, BatchItem* comps,
+                 int (&nitems)[2], int64_t (&tiles)[2]) {
+  nitems[0] = nitems[1] = 0;
+  tiles[0] = tiles[1] = 0;
   int nred = 0;
   for (Request* r : batch) {
     const int dt = r->dtype == SALT_F32 ? DT_F32 : DT_F64;
     for (int k = 0; k < r->nvec; ++k) {
       if (!((r->load_mask >> k) & 1u) || r->ext[k]) continue;  // caller-owned inputs are already there
-      BatchItem& f = h_items[0][nitems[0]++];
+      BatchItem& f = fills[nitems[0]++];
       memset(&f, 0, sizeof f);
       f.kind = kKindFill;
       f.dtype = dt;
@@ -297,7 +338,7 @@ salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch
       memcpy(&f.sc[0], &key, sizeof key);
       tiles[0] += f.ntiles;
     }
-    BatchItem& c = h_items[1][nitems[1]++];
+    BatchItem& c = comps[nitems[1]++];
     memset(&c, 0, sizeof c);
     c.kind = r->kind;
     c.dtype = dt;
@@ -311,6 +352,21 @@ salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch
     tiles[1] += c.ntiles;
     nred += r->nred;
   }
+}
+
+// Builds and launches one step on `slot` from the front of `pending`
+// (scheduler thread, lock not held while launching).
+salt_status launch_step(salt_server* s, Slot& slot, std::vector<Request*>& batch) {
+  size_t off_items[2], off_counters[2], off_partials;
+  slot_device_bytes(s, off_items, off_counters, &off_partials);
+  // Host tables in the pinned staging area, packed so that one copy of
+  // only the bytes in use moves them: [hdr0 | hdr1 | fill items | compute
+  // items].  Compute items are built aside, then placed after the fills.
+  BatchHeader* h_hdr[2] = {(BatchHeader*)slot.h_mem, (BatchHeader*)(slot.h_mem + 256)};
+  BatchItem* h_items[2] = {(BatchItem*)(slot.h_mem + 512), slot.compute_items.data()};
+  int nitems[2];
+  int64_t tiles[2];
+  build_items(s, batch, h_items[0], h_items[1], nitems, tiles);
   const size_t off_compute = 512 + round_up(sizeof(BatchItem) * (size_t)nitems[0]);
   memcpy(slot.h_mem + off_compute, slot.compute_items.data(), sizeof(BatchItem) * (size_t)nitems[1]);
   const size_t used = off_compute + sizeof(BatchItem) * (size_t)nitems[1];
@@ -373,6 +429,244 @@ void complete_slot(salt_server* s, Slot& slot) {
   slot.reqs.clear();
   slot.busy = false;
   s->cv.notify_all();
+}
+
+// ---------------------------------------------------------- persistent ---
+
+void persist_free(salt_server* s) {
+  PersistState& ps = s->ps;
+  if (ps.stream) cudaStreamSynchronize(ps.stream);
+  if (ps.d_mem) cudaFree(ps.d_mem);
+  if (ps.ring) cudaFreeHost(ps.ring);
+  if (ps.red) cudaFreeHost(ps.red);
+  if (ps.ctl) cudaFreeHost(ps.ctl);
+  if (ps.ended) cudaEventDestroy(ps.ended);
+  if (ps.stream) cudaStreamDestroy(ps.stream);
+  ps.d_mem = ps.ring = nullptr;
+  ps.red = nullptr;
+  ps.ctl = nullptr;
+  ps.ended = nullptr;
+  ps.stream = nullptr;
+}
+
+salt_status persist_init(salt_server* s) {
+  PersistState& ps = s->ps;
+  int coop = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+  if (!coop) return fail(SALT_ERR_CUDA, "persistent serving needs cooperative launches");
+  int bps = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, (const void*)persist_for(s->cfg.unroll), s->cfg.block, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent kernel occupancy");
+  if (bps < 1) return fail(SALT_ERR_CUDA, "the persistent kernel does not fit on an SM");
+  ps.grid = s->sms * bps;
+  ps.nring = s->cfg.streams;
+  ps.entry_bytes = round_up((size_t)(kStepHead + 2 * kHdrSlot) +
+                            sizeof(BatchItem) * (size_t)(s->items_cap + s->cfg.max_batch) + 32);
+  ps.red_stride = (size_t)kBatchPartials * (size_t)s->cfg.max_batch;
+  ps.counters_stride = (size_t)s->items_cap + 2;
+  ps.off_counters = ps.entry_bytes;
+  ps.off_partials = ps.off_counters + round_up(sizeof(unsigned) * 2 * ps.counters_stride);
+  ps.off_sync = ps.off_partials + round_up(sizeof(double) * kBatchPartials * (size_t)s->tiles_cap);
+  const size_t dbytes = ps.off_sync + kAlign;
+  e = cudaHostAlloc(&ps.ctl, sizeof(PersistCtl), cudaHostAllocMapped);
+  if (e == cudaSuccess) {
+    memset(ps.ctl, 0, sizeof(PersistCtl));
+    e = cudaHostGetDevicePointer((void**)&ps.ctl_dev, ps.ctl, 0);
+  }
+  if (e == cudaSuccess) e = cudaHostAlloc(&ps.ring, ps.entry_bytes * (size_t)ps.nring, cudaHostAllocMapped);
+  if (e == cudaSuccess) {
+    memset(ps.ring, 0, ps.entry_bytes * (size_t)ps.nring);
+    e = cudaHostGetDevicePointer((void**)&ps.ring_dev, ps.ring, 0);
+  }
+  if (e == cudaSuccess) e = cudaHostAlloc(&ps.red, sizeof(double) * ps.red_stride * (size_t)ps.nring, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&ps.red_dev, ps.red, 0);
+  if (e == cudaSuccess) e = cudaMalloc(&ps.d_mem, dbytes);
+  // counters and sync words start at zero; every step leaves the counters at zero
+  if (e == cudaSuccess) e = cudaMemset(ps.d_mem, 0, dbytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ps.stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ps.ended, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    persist_free(s);
+    return cuda_fail(e, "persistent serving resources");
+  }
+  ps.comps.resize((size_t)s->cfg.max_batch);
+  ps.on = true;
+  return SALT_OK;
+}
+
+// Writes the step's tables into its ring entry and posts it (scheduler
+// thread; the entry is free: fewer than nring steps are in flight).
+void post_step(salt_server* s, std::vector<Request*>& batch) {
+  PersistState& ps = s->ps;
+  const uint64_t step = ps.posted + 1;
+  char* base = ps.ring + (size_t)((step - 1) % (uint64_t)ps.nring) * ps.entry_bytes;
+  StepDesc* d = (StepDesc*)base;
+  BatchHeader* hdr[2] = {(BatchHeader*)(base + kStepHead), (BatchHeader*)(base + kStepHead + kHdrSlot)};
+  const size_t off0 = (size_t)(kStepHead + 2 * kHdrSlot);
+  int nitems[2];
+  int64_t tiles[2];
+  build_items(s, batch, (BatchItem*)(base + off0), ps.comps.data(), nitems, tiles);
+  const size_t off1 = off0 + (sizeof(BatchItem) * (size_t)nitems[0] + 15) / 16 * 16;
+  memcpy(base + off1, ps.comps.data(), sizeof(BatchItem) * (size_t)nitems[1]);
+  for (int t = 0; t < 2; ++t) {
+    memset(hdr[t], 0, sizeof(BatchHeader));
+    hdr[t]->nitems = nitems[t];
+    hdr[t]->total_tiles = tiles[t];
+    hdr[t]->tile_bytes = s->cfg.tile_bytes;
+  }
+  d->off_items[0] = off0;
+  d->off_items[1] = off1;
+  d->used = (off1 + sizeof(BatchItem) * (size_t)nitems[1] + 15) / 16 * 16;
+  // the entry's bytes before the step number that publishes them
+  __atomic_thread_fence(__ATOMIC_SEQ_CST);
+  __atomic_store_n(&ps.ctl->posted, (unsigned long long)step, __ATOMIC_RELEASE);
+  ps.posted = step;
+  ps.inflight.push_back(PersistState::Entry{batch, step});
+  s->n_steps.fetch_add(1);
+}
+
+// Starts a launch of the persistent kernel at the first step not complete.
+salt_status launch_persist(salt_server* s) {
+  PersistState& ps = s->ps;
+  PersistParams prm{};
+  prm.ctl = ps.ctl_dev;
+  prm.ring = ps.ring_dev;
+  prm.entry_bytes = ps.entry_bytes;
+  prm.red = ps.red_dev;
+  prm.red_stride = ps.red_stride;
+  prm.nring = (unsigned long long)ps.nring;
+  prm.table = ps.d_mem;
+  prm.counters = (unsigned*)(ps.d_mem + ps.off_counters);
+  prm.counters_stride = ps.counters_stride;
+  prm.partials = (double*)(ps.d_mem + ps.off_partials);
+  prm.sync = (unsigned long long*)(ps.d_mem + ps.off_sync);
+  prm.first_step = __atomic_load_n(&ps.ctl->done, __ATOMIC_ACQUIRE) + 1;
+  prm.epoch = ++ps.epoch;
+  prm.idle_ns = (unsigned long long)s->cfg.idle_us * 1000ull;
+  prm.wait_ns = kPersistWaitNs;
+  prm.max_polls = g_serve_polls.load();
+  void* args[] = {&prm};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)persist_for(s->cfg.unroll), dim3((unsigned)ps.grid),
+                                              dim3((unsigned)s->cfg.block), args, 0, ps.stream);
+  if (e == cudaSuccess) e = cudaEventRecord(ps.ended, ps.stream);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent serving kernel");
+  count_launch();
+  ps.live.store(true);
+  ps.launches.fetch_add(1);
+  return SALT_OK;
+}
+
+void complete_entry(salt_server* s, const PersistState::Entry& en) {
+  const double t = now_us();
+  const double* red = s->ps.red + (size_t)((en.step - 1) % (uint64_t)s->ps.nring) * s->ps.red_stride;
+  std::lock_guard<std::mutex> lk(s->mu);
+  int idx = 0;
+  for (Request* r : en.reqs) {
+    for (int j = 0; j < r->nred; ++j) r->red[j] = red[idx + j];
+    idx += r->nred;
+    r->state = RS_DONE;
+    r->t_done = t;
+    s->completed.push_back(r->id);
+    s->n_done.fetch_add(1);
+    s->bytes_done.fetch_add(r->bytes_alg);
+  }
+  s->cv.notify_all();
+}
+
+// The scheduler of persistent mode: the same admission and batching as
+// `scheduler`, with ring entries in place of streams.  Completions are read
+// from the control block (in step order); a launch that has ended (idle, or
+// the host's stop) is replaced when a posted step is not complete.
+void scheduler_persist(salt_server* s) {
+  cudaSetDevice(s->device);
+  PersistState& ps = s->ps;
+  std::vector<Request*> batch;
+  double last_active = now_us();
+  for (;;) {
+    bool did = false;
+    std::string err;
+    if (ps.live.load()) {
+      const cudaError_t q = cudaEventQuery(ps.ended);
+      if (q == cudaSuccess) ps.live.store(false);
+      else if (q != cudaErrorNotReady) err = std::string("persistent serving kernel failed: ") + cudaGetErrorString(q);
+    }
+    const uint64_t done = __atomic_load_n(&ps.ctl->done, __ATOMIC_ACQUIRE);
+    while (!ps.inflight.empty() && ps.inflight.front().step <= done) {
+      complete_entry(s, ps.inflight.front());
+      ps.inflight.pop_front();
+      did = true;
+    }
+    if (err.empty() && __atomic_load_n(&ps.ctl->status, __ATOMIC_ACQUIRE) != 0u)
+      err = "persistent serving kernel: a bounded wait ran out in step " +
+            std::to_string(__atomic_load_n(&ps.ctl->fail_step, __ATOMIC_ACQUIRE));
+    if (err.empty() && !ps.live.load() && ps.posted > done) {
+      const salt_status st = launch_persist(s);
+      if (st != SALT_OK) err = salt_last_error();
+    }
+    if (!err.empty()) {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->sched_error = err;
+      s->stop = true;
+      s->cv.notify_all();
+      break;
+    }
+    batch.clear();
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      while (!s->waiting.empty() && s->resident < s->cfg.max_requests) {
+        Request* r = s->waiting.front();
+        if (!arena_take(s, r)) break;
+        s->waiting.pop_front();
+        r->resident = true;
+        ++s->resident;
+        s->pending.push_back(r);
+      }
+      const bool any_busy = !ps.inflight.empty();
+      if (s->stop && !any_busy) break;
+      if ((int)ps.inflight.size() < ps.nring && !s->pending.empty() && !s->stop) {
+        int64_t tiles = 0, fills = 0;
+        while (!s->pending.empty() && (int32_t)batch.size() < s->cfg.max_batch) {
+          Request* r = s->pending.front();
+          const int64_t t = tiles_of(s, r->dtype, r->n);
+          int nf = 0;
+          for (int k = 0; k < r->nvec; ++k) nf += ((r->load_mask >> k) & 1u) && !r->ext[k];
+          if (!batch.empty() && (tiles + t > s->tiles_cap || fills + nf > s->items_cap)) break;
+          s->pending.pop_front();
+          r->state = RS_RUNNING;
+          batch.push_back(r);
+          tiles += t;
+          fills += nf;
+        }
+      }
+      if (batch.empty() && !did) {
+        if (any_busy || now_us() - last_active < kIdleSpinUs) {
+          lk.unlock();
+          std::this_thread::yield();
+        } else {
+          s->cv.wait_for(lk, std::chrono::microseconds(200));
+        }
+        continue;
+      }
+    }
+    last_active = now_us();
+    if (!batch.empty()) {
+      post_step(s, batch);
+      if (!ps.live.load()) {
+        const salt_status st = launch_persist(s);
+        if (st != SALT_OK) {
+          std::lock_guard<std::mutex> lk(s->mu);
+          s->sched_error = salt_last_error();
+          s->stop = true;
+          s->cv.notify_all();
+          break;
+        }
+      }
+    }
+  }
+  // a live launch ends at its next look at the ring
+  __atomic_store_n(&ps.ctl->stop, 1u, __ATOMIC_RELEASE);
 }
 
 void scheduler(salt_server* s) {
@@ -589,6 +883,13 @@ void release_locked(salt_server* s, Request* r) {
 
 }  // namespace
 
+namespace salt {
+unsigned serve_polls(int64_t set) {
+  if (set >= 0) g_serve_polls.store((unsigned)set);
+  return g_serve_polls.load();
+}
+}  // namespace salt
+
 extern "C" {
 
 salt_status salt_serve_default_config(salt_serve_config* cfg) {
@@ -601,6 +902,8 @@ salt_status salt_serve_default_config(salt_serve_config* cfg) {
   cfg->unroll = 2;
   cfg->block = 256;
   cfg->max_n = (int64_t)1 << 24;
+  cfg->persistent = 0;
+  cfg->idle_us = 10000;
   return SALT_OK;
 }
 
@@ -609,7 +912,8 @@ salt_status salt_serve_start(salt_server** out, const salt_serve_config* cfg) {
   if (cfg->budget_bytes < (1 << 20) || cfg->max_requests < 1 || cfg->max_batch < 1 || cfg->max_batch > 65536 ||
       cfg->streams < 1 || cfg->streams > 8 || cfg->tile_bytes < 1024 || cfg->tile_bytes % 256 ||
       (cfg->unroll != 1 && cfg->unroll != 2 && cfg->unroll != 4) ||
-      (cfg->block != 64 && cfg->block != 128 && cfg->block != 256) || cfg->max_n < 1)
+      (cfg->block != 64 && cfg->block != 128 && cfg->block != 256) || cfg->max_n < 1 ||
+      (cfg->persistent != 0 && cfg->persistent != 1) || cfg->idle_us < 1 || cfg->idle_us > 10000000)
     return fail(SALT_ERR_ARG, "invalid server configuration");
   int dev = 0, sms = 0;
   salt_status st = current_device(&dev, &sms);
@@ -630,7 +934,7 @@ salt_status salt_serve_start(salt_server** out, const salt_serve_config* cfg) {
     return cuda_fail(e, "cudaMalloc(arena)");
   }
   s->arena.init((size_t)cfg->budget_bytes);
-  s->slots.resize((size_t)cfg->streams);
+  s->slots.resize(cfg->persistent ? 0 : (size_t)cfg->streams);
   size_t off_items[2], off_counters[2], off_partials;
   const size_t dbytes = slot_device_bytes(s, off_items, off_counters, &off_partials);
   for (Slot& slot : s->slots) {
@@ -666,7 +970,15 @@ salt_status salt_serve_start(salt_server** out, const salt_serve_config* cfg) {
     delete s;
     return cuda_fail(e, "server resources");
   }
-  s->sched = std::thread(scheduler, s);
+  if (cfg->persistent) {
+    st = persist_init(s);
+    if (st != SALT_OK) {
+      cudaFree(s->arena_base);
+      delete s;
+      return st;
+    }
+  }
+  s->sched = std::thread(cfg->persistent ? scheduler_persist : scheduler, s);
   *out = s;
   return SALT_OK;
 }
@@ -770,6 +1082,13 @@ salt_status salt_serve_stats(salt_server* s, int64_t* completed, int64_t* steps,
   return SALT_OK;
 }
 
+salt_status salt_serve_launches(salt_server* s, int64_t* launches, int32_t* live) {
+  if (!s) return fail(SALT_ERR_ARG, "server is NULL");
+  if (launches) *launches = s->ps.launches.load();
+  if (live) *live = s->ps.live.load() ? 1 : 0;
+  return SALT_OK;
+}
+
 salt_status salt_serve_stop(salt_server* s) {
   if (!s) return SALT_OK;
   {
@@ -781,6 +1100,7 @@ salt_status salt_serve_stop(salt_server* s) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(s->device);
+  if (s->ps.on) persist_free(s);
   for (Slot& slot : s->slots) {
     if (slot.stream) cudaStreamSynchronize(slot.stream);
     if (slot.d_mem) cudaFree(slot.d_mem);

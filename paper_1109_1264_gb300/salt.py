@@ -363,7 +363,7 @@ def salt_trace_set(buf, max_blocks: int = 0) -> None:
     _check(lib.salt_trace_set(_ptr(buf), int(max_blocks or cap)))
 
 
-WAIT_STAGED, WAIT_CG_BARRIER = 1, 2
+WAIT_STAGED, WAIT_CG_BARRIER, WAIT_SERVE = 1, 2, 3
 WAIT_DEFAULT_POLLS = 1 << 26
 
 
@@ -610,7 +610,8 @@ class Batch:
 class ServeConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_int64), ("max_requests", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("streams", ctypes.c_int32), ("tile_bytes", ctypes.c_int32), ("unroll", ctypes.c_int32),
-                ("block", ctypes.c_int32), ("max_n", ctypes.c_int64)]
+                ("block", ctypes.c_int32), ("max_n", ctypes.c_int64), ("persistent", ctypes.c_int32),
+                ("idle_us", ctypes.c_int32)]
 
 
 _vp, _i32, _i64, _dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)
@@ -630,6 +631,7 @@ _SERVE_SIGS = {
                           ctypes.c_uint64, _dp, _dp, _dp],
     "salt_serve_submit_ex": [_vp, ctypes.POINTER(Insn), _i32, _i32, _i64, ctypes.POINTER(_vp),
                              ctypes.POINTER(ctypes.c_uint64), _i32, _dp, _i32, ctypes.POINTER(_i64)],
+    "salt_serve_launches": [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32)],
     "salt_serve_replay_store": [_vp, _i32, _dp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64),
                                 ctypes.c_uint64, ctypes.POINTER(_vp), _i32, _i64, ctypes.POINTER(_vp), _i32, _i64,
                                 _dp, _dp, _dp],
@@ -712,6 +714,12 @@ class Server:
                                     ctypes.byref(w)))
         return {"completed": c.value, "steps": s.value, "bytes": b.value, "resident_bytes": r.value,
                 "waiting": w.value}
+
+    def launches(self) -> tuple[int, bool]:
+        """Persistent mode: (launches of the resident kernel, one running now)."""
+        n, live = ctypes.c_int64(), ctypes.c_int32()
+        _check(lib.salt_serve_launches(self.handle, ctypes.byref(n), ctypes.byref(live)))
+        return n.value, bool(live.value)
 
     def replay(self, arrival_us, shape, dtype, n, seed: int, store=None):
         """Returns (latency_us array, first results array, wall_us).  ``store``

@@ -303,16 +303,16 @@ def test_binding_operand_checks(saltlib):
 
 
 def test_wait_limits(saltlib):
-    """The poll limits of the two bounded device waits: defaults, round
-    trip, argument errors (no GPU needed)."""
+    """The poll limits of the bounded device waits: defaults, round trip,
+    argument errors (no GPU needed)."""
     s = saltlib
-    for which in (s.WAIT_STAGED, s.WAIT_CG_BARRIER):
+    for which in (s.WAIT_STAGED, s.WAIT_CG_BARRIER, s.WAIT_SERVE):
         assert s.salt_get_wait_limit(which) == s.WAIT_DEFAULT_POLLS
         s.salt_set_wait_limit(which, 0)
         assert s.salt_get_wait_limit(which) == 0
         s.salt_set_wait_limit(which, s.WAIT_DEFAULT_POLLS)
         assert s.salt_get_wait_limit(which) == s.WAIT_DEFAULT_POLLS
-    assert s.lib.salt_set_wait_limit(3, 5) == s.ERR_ARG
+    assert s.lib.salt_set_wait_limit(4, 5) == s.ERR_ARG
     assert s.lib.salt_set_wait_limit(s.WAIT_STAGED, -1) == s.ERR_ARG
     assert s.lib.salt_set_wait_limit(s.WAIT_STAGED, 1 << 32) == s.ERR_ARG
     assert s.lib.salt_get_wait_limit(s.WAIT_STAGED, None) == s.ERR_ARG
@@ -353,3 +353,18 @@ def test_tune_cache_environment(tmp_path):
     r = subprocess.run([sys.executable, "-c", child, "load"], env=env, cwd=root, capture_output=True, text=True,
                        timeout=120)
     assert json.loads(r.stdout.strip().splitlines()[-1]) != want
+
+
+def test_serve_config_persistent_fields(saltlib):
+    """The server configuration's persistent-mode fields: defaults and the
+    checks made before any device is touched (no GPU needed)."""
+    import ctypes
+    s = saltlib
+    cfg = s.serve_default_config()
+    assert cfg.persistent == 0 and cfg.idle_us == 10000
+    h = ctypes.c_void_p()
+    for field, bad in (("persistent", 2), ("persistent", -1), ("idle_us", 0), ("idle_us", 10_000_001)):
+        c = s.serve_default_config()
+        setattr(c, field, bad)
+        assert s.lib.salt_serve_start(ctypes.byref(h), ctypes.byref(c)) == s.ERR_ARG, (field, bad)
+    assert s.lib.salt_serve_launches(None, None, None) == s.ERR_ARG

@@ -49,8 +49,9 @@ def expected(shape_i, keys, n, dt):
     return want, out, None, None
 
 
-def test_served_results_match_oracle(salt):
-    srv = salt.Server(budget_bytes=1 << 28, max_n=1 << 20)
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_served_results_match_oracle(salt, persistent):
+    srv = salt.Server(budget_bytes=1 << 28, max_n=1 << 20, persistent=persistent)
     try:
         reqs = []
         for dt, code in ((np.float64, salt.F64), (np.float32, salt.F32)):
@@ -76,10 +77,11 @@ def test_served_results_match_oracle(salt):
         srv.stop()
 
 
-def test_alone_vs_mix_bit_identical(salt):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_alone_vs_mix_bit_identical(salt, persistent):
     """>= 200 requests, each run alone (one request per step) and then all
     submitted at once (steps of many requests on two streams)."""
-    srv = salt.Server(budget_bytes=1 << 30, max_n=1 << 16)
+    srv = salt.Server(budget_bytes=1 << 30, max_n=1 << 16, persistent=persistent)
     try:
         shapes, is64, lens = inputs.request_mix(5, 240, lo=2 ** 8, hi=2 ** 16)
         def submit_all():
@@ -114,8 +116,11 @@ def test_alone_vs_mix_bit_identical(salt):
         mix = collect(submit_all())
         steps = srv.stats()["steps"] - before
         # Python submits one request every few tens of microseconds while
-        # small steps finish quickly, so steps carry a few requests each.
-        assert steps < 0.6 * len(lens), f"the mix ran in {steps} steps: requests were not batched"
+        # small steps finish quickly, so steps carry a few requests each (a
+        # persistent step can end before the next submission: no bound there;
+        # the replay tests load it enough to batch).
+        if not persistent:
+            assert steps < 0.6 * len(lens), f"the mix ran in {steps} steps: requests were not batched"
         for i, ((ra, va), (rm, vm)) in enumerate(zip(alone, mix)):
             if SHAPES[int(shapes[i])][0] in (P.PROG_DOT, None):
                 assert np.float64(ra).view(np.uint64) == np.float64(rm).view(np.uint64), i
@@ -135,8 +140,9 @@ def collect_one(srv, rid, shape, is64, n):
     return [(red[0], vec)]
 
 
-def test_budget_admission_timeout_and_cancel(salt):
-    srv = salt.Server(budget_bytes=4 << 20, max_n=1 << 20)
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_budget_admission_timeout_and_cancel(salt, persistent):
+    srv = salt.Server(budget_bytes=4 << 20, max_n=1 << 20, persistent=persistent)
     try:
         n = 300_000  # 2 FP32 operands = 2.4 MB: two such requests do not fit in 4 MiB
         keys = [1, 2]
@@ -163,8 +169,9 @@ def test_budget_admission_timeout_and_cancel(salt):
         srv.stop()
 
 
-def test_replay_poisson_trace(salt):
-    srv = salt.Server(budget_bytes=1 << 30, max_n=1 << 18)
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_replay_poisson_trace(salt, persistent):
+    srv = salt.Server(budget_bytes=1 << 30, max_n=1 << 18, persistent=persistent)
     try:
         count = 400
         shapes, is64, lens = inputs.request_mix(9, count, lo=2 ** 8, hi=2 ** 18)
@@ -195,10 +202,11 @@ def store_place(seed, i, k, n, length, count, itemsize):
     return (i * 5 + k) % count, o - o % (32 // itemsize)
 
 
-def test_caller_owned_operands(salt, cuda_dev):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_caller_owned_operands(salt, cuda_dev, persistent):
     """Inputs in caller-owned device memory (no fill), the output server-owned
     or caller-owned: the same bits as the oracle."""
-    srv = salt.Server(budget_bytes=1 << 28, max_n=1 << 20)
+    srv = salt.Server(budget_bytes=1 << 28, max_n=1 << 20, persistent=persistent)
     try:
         for dt, code, tdt in ((np.float32, salt.F32, torch.float32), (np.float64, salt.F64, torch.float64)):
             for n in (1, 1000, (1 << 20) - 3):
@@ -208,6 +216,9 @@ def test_caller_owned_operands(salt, cuda_dev):
                 out_dev = torch.zeros(n, dtype=tdt, device=cuda_dev)
                 want = [h.copy() for h in host[:4]] + [np.zeros(n, dt)]
                 oracle.eval_program(P.PROG_E, want, SC)
+                # caller-owned operands are ready when submitted: the server does
+                # not order its work after the caller's streams
+                torch.cuda.current_stream().synchronize()
                 # inputs caller-owned, output server-owned
                 a = srv.submit(P.PROG_E, code, n, keys, SC, ptrs=dev[:4] + [None])
                 # everything caller-owned (keys unused)
@@ -232,10 +243,11 @@ def test_caller_owned_operands(salt, cuda_dev):
         srv.stop()
 
 
-def test_replay_resident_store(salt, cuda_dev):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_replay_resident_store(salt, cuda_dev, persistent):
     """The load generator reading inputs from a resident store: dot and norm
     results against the exact values of the store slices they read."""
-    srv = salt.Server(budget_bytes=1 << 30, max_n=1 << 18)
+    srv = salt.Server(budget_bytes=1 << 30, max_n=1 << 18, persistent=persistent)
     try:
         length = (1 << 20) + 8
         skeys = {np.float32: [901, 902, 903], np.float64: [911, 912]}
@@ -244,6 +256,7 @@ def test_replay_resident_store(salt, cuda_dev):
         for dt in skeys:
             for t, k in zip(store[dt], skeys[dt]):
                 salt.salt_fill_uniform(t, k)
+        torch.cuda.current_stream().synchronize()  # the server does not order its work after other streams
         count = 400
         shapes, is64, lens = inputs.request_mix(13, count, lo=2 ** 8, hi=2 ** 18)
         arr = inputs.poisson_arrivals(13, count, 20_000.0) * 1e6
@@ -311,3 +324,83 @@ def test_server_folds_by_value_scalar_subexpressions(salt):
             srv.release(rid)
     finally:
         srv.stop()
+
+
+def test_persistent_same_bits_as_default(salt):
+    """The same requests (every served shape, both dtypes, empty, tiny and
+    multi-tile lengths), all submitted at once, through the default mode and
+    through persistent mode with 2 and 4 ring entries: the same bits."""
+    reqs = [(si, dt, n) for si in range(len(SHAPES)) for dt in (np.float32, np.float64)
+            for n in (0, 1, 7, 4099, (1 << 18) + 5)]
+    results = []
+    for persistent, streams in ((0, 2), (1, 2), (1, 4)):
+        srv = salt.Server(budget_bytes=1 << 28, max_n=1 << 20, persistent=persistent, streams=streams)
+        try:
+            ids = []
+            for i, (si, dt, n) in enumerate(reqs):
+                prog, nv, _ = SHAPES[si]
+                keys = [inputs.vector_key(61, i, k) for k in range(nv)]
+                ids.append(srv.submit(prog, salt.F32 if dt == np.float32 else salt.F64, n, keys,
+                                      SC if prog is not None else ()))
+            res = []
+            for (si, dt, n), rid in zip(reqs, ids):
+                srv.wait(rid, 20_000_000)
+                red = np.array(srv.poll(rid)[2][:1])
+                out = SHAPES[si][2]
+                res.append((red, srv.read(rid, out, np.empty(n, dt)) if out is not None else None))
+                srv.release(rid)
+            results.append(res)
+        finally:
+            srv.stop()
+    for other in results[1:]:
+        for req, (ra, va), (rb, vb) in zip(reqs, results[0], other):
+            assert ra.view(np.uint64)[0] == rb.view(np.uint64)[0], req
+            if va is not None:
+                assert_bits_equal(vb, va, str(req))
+
+
+def test_persistent_idle_end_and_relaunch(salt):
+    """Persistent mode: the resident launch ends after idle_us with nothing
+    posted, and the next request launches it again (from the first step not
+    complete); results stay within tolerance of the exact value."""
+    import time
+    srv = salt.Server(budget_bytes=1 << 26, max_n=1 << 16, persistent=1, idle_us=2000)
+    try:
+        for rnd in range(3):
+            n = 1000 + rnd
+            keys = [inputs.vector_key(41, rnd, k) for k in range(2)]
+            rid = srv.submit(P.PROG_DOT, salt.F64, n, keys)
+            srv.wait(rid, 10_000_000)
+            x, y = host_inputs(keys, 2, n, np.float64)
+            tolerance.check_dot(srv.poll(rid)[2][0], x, y, np.float64, ("persistent dot", rnd))
+            srv.release(rid)
+            time.sleep(0.05)  # 50 ms, far beyond the 2 ms idle time: the launch has ended
+            launches, live = srv.launches()
+            assert launches == rnd + 1 and not live, (rnd, launches, live)
+        assert srv.stats()["steps"] == 3
+    finally:
+        srv.stop()
+
+
+def test_persistent_wait_runs_out(salt, cuda_dev):
+    """A wait of the persistent kernel that runs out (poll limit 0: the other
+    blocks stop waiting for block 0's release of the step at once) ends the
+    launch and fails the server with an error; no fault, and the device keeps
+    working."""
+    prev = salt.salt_get_wait_limit(salt.WAIT_SERVE)
+    salt.salt_set_wait_limit(salt.WAIT_SERVE, 0)
+    try:
+        srv = salt.Server(budget_bytes=1 << 26, max_n=1 << 20, persistent=1)
+        try:
+            rid = srv.submit(P.PROG_DOT, salt.F32, 1 << 20, [1, 2])
+            with pytest.raises(salt.SaltError) as ei:
+                srv.wait(rid, 10_000_000)
+            assert ei.value.status == salt.ERR_CUDA and "bounded wait ran out" in ei.value.message
+        finally:
+            srv.stop()
+    finally:
+        salt.salt_set_wait_limit(salt.WAIT_SERVE, prev)
+    x = torch.arange(1000, dtype=torch.float64, device=cuda_dev)
+    out = torch.zeros(1, dtype=torch.float64, device=cuda_dev)
+    salt.salt_dot(x, x, out)
+    assert out.item() == 999 * 1000 * 1999 // 6
