@@ -309,34 +309,40 @@ __device__ __forceinline__ void run_tiles(const BatchParams& p) {
     const int nv = it.dtype == DT_F32 ? dispatch_item<float, U, NC>(it, lo, hi, vals, narrow)
                                       : dispatch_item<double, U, NC>(it, lo, hi, vals, narrow);
     if (nv > 0) {
-      // this tile's partials, then the per-item ticket
-      for (int r = 0; r < nv; ++r) {
-        const double t = block_sum<double>(vals[r], smem);
-        if (threadIdx.x == 0) p.partials[tile * kBatchPartials + r] = t;
-      }
-      if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned k = atomicAdd(&p.tickets[item], 1u);
-        s_last = (k == (unsigned)it.ntiles - 1u);
-      }
-      __syncthreads();
-      if (s_last) {
-        __threadfence();
-        double tot[kBatchPartials] = {0.0, 0.0, 0.0};
-        for (int r = 0; r < nv; ++r) {
-          double a = 0.0;
-          for (int64_t k = threadIdx.x; k < it.ntiles; k += blockDim.x)
-            a += ((volatile double*)p.partials)[(it.tile_begin + k) * kBatchPartials + r];
-          tot[r] = block_sum<double>(a, smem);
-        }
+      double tot[kBatchPartials] = {0.0, 0.0, 0.0};
+      for (int r = 0; r < nv; ++r) tot[r] = block_sum<double>(vals[r], smem);
+      bool last = true;
+      if (it.ntiles == 1) {
+        // the item's only tile: its totals are this block's sums, added to
+        // 0.0 as the combine below adds a single partial (the same bits)
+        for (int r = 0; r < nv; ++r) tot[r] = 0.0 + tot[r];
+      } else {
+        // this tile's partials, then the per-item ticket
         if (threadIdx.x == 0) {
-          if (it.kind == kKindNrm2) {
-            p.red_out[it.red_index] = it.dtype == DT_F32 ? __dsqrt_rn(tot[0]) : blue_finish(tot[0], tot[1], tot[2]);
-          } else {
-            for (int r = 0; r < nv; ++r) p.red_out[it.red_index + r] = tot[r];
-          }
-          p.tickets[item] = 0u;
+          for (int r = 0; r < nv; ++r) p.partials[tile * kBatchPartials + r] = tot[r];
+          __threadfence();
+          const unsigned k = atomicAdd(&p.tickets[item], 1u);
+          s_last = (k == (unsigned)it.ntiles - 1u);
         }
+        __syncthreads();
+        last = s_last;
+        if (last) {
+          __threadfence();
+          for (int r = 0; r < nv; ++r) {
+            double a = 0.0;
+            for (int64_t k = threadIdx.x; k < it.ntiles; k += blockDim.x)
+              a += ((volatile double*)p.partials)[(it.tile_begin + k) * kBatchPartials + r];
+            tot[r] = block_sum<double>(a, smem);
+          }
+        }
+      }
+      if (last && threadIdx.x == 0) {
+        if (it.kind == kKindNrm2) {
+          p.red_out[it.red_index] = it.dtype == DT_F32 ? __dsqrt_rn(tot[0]) : blue_finish(tot[0], tot[1], tot[2]);
+        } else {
+          for (int r = 0; r < nv; ++r) p.red_out[it.red_index + r] = tot[r];
+        }
+        if (it.ntiles != 1) p.tickets[item] = 0u;
       }
     }
     __syncthreads();  // every thread has read s_tile / s_item / s_last of this tile

@@ -3,16 +3,22 @@
 // memory, so a step costs no launch, no table upload through a copy engine
 // and no event.  One launch runs steps first_step, first_step + 1, ... :
 //
-//   block 0   waits (bounded) until the previous step's compute phase is
-//             complete, then until the host has posted the step (or asked
-//             to stop, or nothing came for idle_ns: the launch ends), copies
-//             the step's tables from the ring entry into device memory and
-//             releases the step to every block (sync[0] = step);
+//   block 0   waits (bounded) until the step two before is complete (the
+//             device tables, tile counters and partials alternate between
+//             two sets by step parity), then until the host has posted the
+//             step (or asked to stop, or nothing came for idle_ns: the launch
+//             ends), copies the step's tables from the ring entry into its
+//             set and releases the step to every block (sync[0] = step);
 //   all       wait (bounded) for that release, then run the fill phase
 //             (when the step has fill items) and the compute phase with the
 //             batch kernel's tile loop; between the phases every block waits
 //             (bounded) for the last one; the compute phase's last block
 //             publishes the step's completion to the host (ctl->done).
+//
+// A block that has taken its last tile of a step goes on to the next step
+// while others finish theirs, so consecutive steps overlap (like steps on
+// two streams).  Completion stays in step order: a step's last arrival comes
+// after every block's arrival in the step before.
 //
 // A wait that runs out sets ctl->status and the launch ends.  The host
 // relaunches the kernel when it has posted a step and the previous launch
@@ -50,10 +56,11 @@ struct PersistParams {
   double* red;                        // device address of ring entry 0's results (mapped host memory)
   unsigned long long red_stride;      // doubles per ring entry
   unsigned long long nring;
-  char* table;                        // device copy of the current step's ring entry
-  unsigned* counters;                 // per phase: tile counter, arrivals, per-item tickets
-  unsigned long long counters_stride; // unsigned per phase
-  double* partials;
+  char* table;                        // two device copies of ring entries (entry_bytes each), by step parity
+  unsigned* counters;                 // per parity and phase: tile counter, arrivals, per-item tickets
+  unsigned long long counters_stride; // unsigned per (parity, phase)
+  double* partials;                   // per parity: partials_stride doubles
+  unsigned long long partials_stride;
   unsigned long long* sync;           // [0] step released, [1] epoch of an exit, [2 + ph] step whose phase ph is complete
   unsigned long long first_step;      // this launch's first step (steps complete + 1)
   unsigned long long epoch;           // this launch's number
@@ -125,18 +132,31 @@ __device__ __forceinline__ void note_timeout(const PersistParams& p, unsigned lo
   __threadfence_system();
 }
 
-// Block 0: copies ring entry (s - 1) % nring into the device table (at most
-// entry_bytes, the table's size).  16-byte volatile loads of the host's data
-// (relaxed, system scope; no read-only path: the entry is rewritten for
-// later steps), eight in flight per thread.
+// Block 0: copies ring entry (s - 1) % nring into the device table of step
+// s's parity (at most entry_bytes, the table's size), with 16-byte volatile loads of the host's
+// data (relaxed, system scope; no read-only path: the entry is rewritten for
+// later steps).  The first blockDim x 16 bytes are loaded together with the
+// entry's size, in one round trip; the rest, if any, eight loads in flight
+// per thread.
 __device__ __forceinline__ void copy_entry(const PersistParams& p, unsigned long long s) {
-  const char* src = p.ring + ((s - 1) % p.nring) * p.entry_bytes;
-  const unsigned long long want = ((const volatile StepDesc*)src)->used;
-  const unsigned long long used = want < p.entry_bytes ? want : p.entry_bytes;
-  const uint4* from = (const uint4*)src;
-  uint4* to = (uint4*)p.table;
-  const long long nv = (long long)(used / 16);
-  for (long long base = 0; base < nv; base += 8LL * blockDim.x) {
+  __shared__ unsigned long long s_used;
+  const uint4* from = (const uint4*)(p.ring + ((s - 1) % p.nring) * p.entry_bytes);
+  uint4* to = (uint4*)(p.table + (s & 1ull) * p.entry_bytes);
+  const long long cap = (long long)(p.entry_bytes / 16), first = cap < blockDim.x ? cap : blockDim.x;
+  uint4 r0 = make_uint4(0u, 0u, 0u, 0u);
+  if ((long long)threadIdx.x < first)
+    asm volatile("ld.volatile.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0.x), "=r"(r0.y), "=r"(r0.z), "=r"(r0.w)
+                 : "l"(from + threadIdx.x)
+                 : "memory");
+  if (threadIdx.x == 0) {
+    const unsigned long long want = ((unsigned long long)r0.y << 32) | r0.x;  // StepDesc::used
+    s_used = want < p.entry_bytes ? want : p.entry_bytes;
+  }
+  __syncthreads();
+  const long long nv = (long long)(s_used / 16);
+  if ((long long)threadIdx.x < first && (long long)threadIdx.x < nv) to[threadIdx.x] = r0;
+  for (long long base = first; base < nv; base += 8LL * blockDim.x) {
     uint4 r[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -157,7 +177,7 @@ __device__ __forceinline__ void copy_entry(const PersistParams& p, unsigned long
 }
 
 template <int U>
-__global__ void __launch_bounds__(256) persist_kernel(const PersistParams p) {
+__global__ void __launch_bounds__(256, 3) persist_kernel(const PersistParams p) {
   __shared__ int s_cmd;
   for (unsigned long long s = p.first_step;; ++s) {
     __syncthreads();  // every thread has read s_cmd of the previous step
@@ -165,8 +185,8 @@ __global__ void __launch_bounds__(256) persist_kernel(const PersistParams p) {
     if (blockIdx.x == 0) {
       if (threadIdx.x == 0) {
         int cmd = 0;
-        // the previous step's compute phase reads the device table until it is complete
-        if (s > p.first_step && !wait_ge(&p.sync[3], s - 1, p.wait_ns, p.max_polls)) cmd = 2;
+        // the step two before used this parity's tables, counters and partials
+        if (s >= p.first_step + 2 && !wait_ge(&p.sync[3], s - 2, p.wait_ns, p.max_polls)) cmd = 2;
         if (cmd == 0) cmd = wait_posted(p, s);
         s_cmd = cmd;
       }
@@ -193,25 +213,33 @@ __global__ void __launch_bounds__(256) persist_kernel(const PersistParams p) {
     __syncthreads();
     if (s_cmd != 0) return;
     // ---- the step: fill phase (if any), then compute phase
-    const StepDesc* d = (const StepDesc*)p.table;
+    const unsigned long long par = s & 1ull;
+    const char* tab = p.table + par * p.entry_bytes;
+    const StepDesc* d = (const StepDesc*)tab;
     for (int ph = 0; ph < 2; ++ph) {
-      const BatchHeader* hdr = (const BatchHeader*)(p.table + kStepHead + kHdrSlot * ph);
+      const BatchHeader* hdr = (const BatchHeader*)(tab + kStepHead + kHdrSlot * ph);
       if (ph == 0 && hdr->nitems == 0) continue;  // the same decision in every block
-      unsigned* cnt = p.counters + (unsigned long long)ph * p.counters_stride;
-      const BatchParams bp{hdr,           (const BatchItem*)(p.table + d->off_items[ph]), cnt, cnt + 1, cnt + 2,
-                           p.partials,    p.red + ((s - 1) % p.nring) * p.red_stride};
+      unsigned* cnt = p.counters + (par * 2 + (unsigned long long)ph) * p.counters_stride;
+      const BatchParams bp{hdr,
+                           (const BatchItem*)(tab + d->off_items[ph]),
+                           cnt,
+                           cnt + 1,
+                           cnt + 2,
+                           p.partials + par * p.partials_stride,
+                           p.red + ((s - 1) % p.nring) * p.red_stride};
       run_tiles<U, false>(bp);
       __syncthreads();
       if (threadIdx.x == 0) {
-        // this block's writes (results in mapped host memory included) before its arrival
-        __threadfence_system();
+        // The arrival releases this block's writes (results in mapped host
+        // memory included) at GPU scope; the last block acquires every
+        // arrival, and its system-scope release of ctl->done passes them on
+        // to the host (causality order is transitive across the scopes).
         const bool last = ticket_add_acq_rel(cnt + 1, 1u) == gridDim.x - 1u;
         int r = 0;
         if (last) {
           // every block has taken its last tile of the phase: counters back to zero
           cnt[0] = 0u;
           cnt[1] = 0u;
-          __threadfence_system();
           if (ph == 1) st_release_sys(&p.ctl->done, s);
           st_release_gpu(&p.sync[2 + ph], s);
         } else if (ph == 0) {

@@ -188,8 +188,8 @@ struct PersistState {
   double* red = nullptr;      // nring x red_stride results, mapped
   double* red_dev = nullptr;
   size_t red_stride = 0;
-  char* d_mem = nullptr;      // device: table (entry_bytes) | counters | partials | sync words
-  size_t off_counters = 0, off_partials = 0, off_sync = 0, counters_stride = 0;
+  char* d_mem = nullptr;      // device: 2 tables (entry_bytes each) | 4 counter sets | 2 partials | sync words
+  size_t off_counters = 0, off_partials = 0, off_sync = 0, counters_stride = 0, partials_stride = 0;
   cudaStream_t stream = nullptr;
   cudaEvent_t ended = nullptr;  // recorded after each launch
   std::atomic<bool> live{false};
@@ -465,9 +465,10 @@ salt_status persist_init(salt_server* s) {
                             sizeof(BatchItem) * (size_t)(s->items_cap + s->cfg.max_batch) + 32);
   ps.red_stride = (size_t)kBatchPartials * (size_t)s->cfg.max_batch;
   ps.counters_stride = (size_t)s->items_cap + 2;
-  ps.off_counters = ps.entry_bytes;
-  ps.off_partials = ps.off_counters + round_up(sizeof(unsigned) * 2 * ps.counters_stride);
-  ps.off_sync = ps.off_partials + round_up(sizeof(double) * kBatchPartials * (size_t)s->tiles_cap);
+  ps.partials_stride = (size_t)kBatchPartials * (size_t)s->tiles_cap;
+  ps.off_counters = 2 * ps.entry_bytes;
+  ps.off_partials = ps.off_counters + round_up(sizeof(unsigned) * 4 * ps.counters_stride);
+  ps.off_sync = ps.off_partials + round_up(sizeof(double) * 2 * ps.partials_stride);
   const size_t dbytes = ps.off_sync + kAlign;
   e = cudaHostAlloc(&ps.ctl, sizeof(PersistCtl), cudaHostAllocMapped);
   if (e == cudaSuccess) {
@@ -541,6 +542,7 @@ salt_status launch_persist(salt_server* s) {
   prm.counters = (unsigned*)(ps.d_mem + ps.off_counters);
   prm.counters_stride = ps.counters_stride;
   prm.partials = (double*)(ps.d_mem + ps.off_partials);
+  prm.partials_stride = ps.partials_stride;
   prm.sync = (unsigned long long*)(ps.d_mem + ps.off_sync);
   prm.first_step = __atomic_load_n(&ps.ctl->done, __ATOMIC_ACQUIRE) + 1;
   prm.epoch = ++ps.epoch;
