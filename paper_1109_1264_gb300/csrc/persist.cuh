@@ -3,22 +3,25 @@
 // memory, so a step costs no launch, no table upload through a copy engine
 // and no event.  One launch runs steps first_step, first_step + 1, ... :
 //
-//   block 0   waits (bounded) until the step two before is complete (the
-//             device tables, tile counters and partials alternate between
-//             two sets by step parity), then until the host has posted the
-//             step (or asked to stop, or nothing came for idle_ns: the launch
-//             ends), copies the step's tables from the ring entry into its
-//             set and releases the step to every block (sync[0] = step);
-//   all       wait (bounded) for that release, then run the fill phase
-//             (when the step has fill items) and the compute phase with the
-//             batch kernel's tile loop; between the phases every block waits
-//             (bounded) for the last one; the compute phase's last block
-//             publishes the step's completion to the host (ctl->done).
+//   block 0   (the dispatcher, which takes no tiles) waits (bounded) until
+//             the step two before is complete (the device tables, tile
+//             counters and partials alternate between two sets by step
+//             parity), then until the host has posted the step (or asked to
+//             stop, or nothing came for idle_ns: the launch ends), copies the
+//             step's tables from the ring entry into its set and releases
+//             the step (sync[0] = step), usually while the workers still run
+//             the step before;
+//   workers   (every other block) wait (bounded) for that release, then run
+//             the fill phase (when the step has fill items) and the compute
+//             phase with the batch kernel's tile loop; between the phases
+//             every worker waits (bounded) for the last one; the compute
+//             phase's last worker publishes the step's completion to the
+//             host (ctl->done).
 //
-// A block that has taken its last tile of a step goes on to the next step
+// A worker that has taken its last tile of a step goes on to the next step
 // while others finish theirs, so consecutive steps overlap (like steps on
 // two streams).  Completion stays in step order: a step's last arrival comes
-// after every block's arrival in the step before.
+// after every worker's arrival in the step before.
 //
 // A wait that runs out sets ctl->status and the launch ends.  The host
 // relaunches the kernel when it has posted a step and the previous launch
@@ -111,7 +114,7 @@ __device__ __forceinline__ int wait_posted(const PersistParams& p, unsigned long
   }
 }
 
-// Every block, thread 0: waits for block 0 to release step s (0) or to end
+// Every worker, thread 0: waits for block 0 to release step s (0) or to end
 // the launch (1); 2 when the bound ran out.
 __device__ __forceinline__ int wait_release(const PersistParams& p, unsigned long long s) {
   const unsigned long long t0 = global_ns();
@@ -179,10 +182,12 @@ __device__ __forceinline__ void copy_entry(const PersistParams& p, unsigned long
 template <int U>
 __global__ void __launch_bounds__(256, 3) persist_kernel(const PersistParams p) {
   __shared__ int s_cmd;
-  for (unsigned long long s = p.first_step;; ++s) {
-    __syncthreads();  // every thread has read s_cmd of the previous step
-    // ---- block 0 releases step s to every block, or ends the launch
-    if (blockIdx.x == 0) {
+  if (blockIdx.x == 0) {
+    // ---- the dispatcher (block 0, no tiles): releases the steps in order,
+    // each as soon as it is posted and the step two before is complete, or
+    // ends the launch
+    for (unsigned long long s = p.first_step;; ++s) {
+      __syncthreads();  // every thread has read s_cmd of the previous step
       if (threadIdx.x == 0) {
         int cmd = 0;
         // the step two before used this parity's tables, counters and partials
@@ -202,9 +207,14 @@ __global__ void __launch_bounds__(256, 3) persist_kernel(const PersistParams p) 
           st_release_gpu(&p.sync[1], p.epoch);
         }
       }
-      __syncthreads();  // s_cmd is rewritten below
+      __syncthreads();
+      if (s_cmd != 0) return;
     }
-    // ---- every block: wait for the release
+  }
+  // ---- the workers (blocks 1 ..): the released steps, in order
+  const unsigned workers = gridDim.x - 1u;
+  for (unsigned long long s = p.first_step;; ++s) {
+    __syncthreads();  // every thread has read s_cmd of the previous step
     if (threadIdx.x == 0) {
       const int r = wait_release(p, s);
       if (r == 2) note_timeout(p, s);
@@ -212,13 +222,13 @@ __global__ void __launch_bounds__(256, 3) persist_kernel(const PersistParams p) 
     }
     __syncthreads();
     if (s_cmd != 0) return;
-    // ---- the step: fill phase (if any), then compute phase
+    // the step: fill phase (if any), then compute phase
     const unsigned long long par = s & 1ull;
     const char* tab = p.table + par * p.entry_bytes;
     const StepDesc* d = (const StepDesc*)tab;
     for (int ph = 0; ph < 2; ++ph) {
       const BatchHeader* hdr = (const BatchHeader*)(tab + kStepHead + kHdrSlot * ph);
-      if (ph == 0 && hdr->nitems == 0) continue;  // the same decision in every block
+      if (ph == 0 && hdr->nitems == 0) continue;  // the same decision in every worker
       unsigned* cnt = p.counters + (par * 2 + (unsigned long long)ph) * p.counters_stride;
       const BatchParams bp{hdr,
                            (const BatchItem*)(tab + d->off_items[ph]),
@@ -231,13 +241,13 @@ __global__ void __launch_bounds__(256, 3) persist_kernel(const PersistParams p) 
       __syncthreads();
       if (threadIdx.x == 0) {
         // The arrival releases this block's writes (results in mapped host
-        // memory included) at GPU scope; the last block acquires every
+        // memory included) at GPU scope; the last worker acquires every
         // arrival, and its system-scope release of ctl->done passes them on
         // to the host (causality order is transitive across the scopes).
-        const bool last = ticket_add_acq_rel(cnt + 1, 1u) == gridDim.x - 1u;
+        const bool last = ticket_add_acq_rel(cnt + 1, 1u) == workers - 1u;
         int r = 0;
         if (last) {
-          // every block has taken its last tile of the phase: counters back to zero
+          // every worker has taken its last tile of the phase: counters back to zero
           cnt[0] = 0u;
           cnt[1] = 0u;
           if (ph == 1) st_release_sys(&p.ctl->done, s);
