@@ -180,7 +180,7 @@ __device__ __forceinline__ void copy_entry(const PersistParams& p, unsigned long
 }
 
 template <int U>
-__global__ void __launch_bounds__(256, 3) persist_kernel(const PersistParams p) {
+__global__ void __launch_bounds__(256, 4) persist_kernel(const PersistParams p) {
   __shared__ int s_cmd;
   if (blockIdx.x == 0) {
     // ---- the dispatcher (block 0, no tiles): releases the steps in order,
