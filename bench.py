@@ -589,10 +589,22 @@ def main():
         torch.cuda.empty_cache()
         result["generic"] = generic_measure(torch, salt)
     probe = fp64_probe(torch, salt)
+    try:
+        # the FP64 pipe's rate from registers, per instruction kind
+        probe["register_gops"] = {k: round(salt.salt_fp64_rate(op), 1) for k, op in
+                                  (("dfma", salt.FP64_FMA), ("dadd", salt.FP64_ADD), ("dmul", salt.FP64_MUL))}
+    except salt.SaltError as e:
+        probe["register_gops"] = {"error": e.message[:200]}
     result["fp64_probe"] = probe
     if roof["bound"] == "alu" and probe.get("gops"):
         roof["probe_gops"] = probe["gops"]
         roof["frac_vs_probe"] = round(roof["achieved"] * 1e3 / probe["gops"], 4)
+        reg = probe["register_gops"].get("dfma")
+        if reg:
+            # every FP64 node issues as a DFMA: the register-only DFMA rate is
+            # the measured ceiling beside the derived peak
+            roof["register_dfma_gops"] = reg
+            roof["frac_vs_register_dfma"] = round(roof["achieved"] * 1e3 / reg, 4)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         # The CPU-oracle leg: the oracle timed on the host, and the oracle's
@@ -621,7 +633,8 @@ def summary_of(r: dict) -> dict:
     ends with: the step, batched vs plain, served saturation and p50 / p99
     per load, Figure 1, the CG forms and the precision of every reduction."""
     out = {"step_gbs": r["value"], "frac_of_measured_hbm": r.get("frac_of_measured_hbm"),
-           "roofline": {k: r["roofline"].get(k) for k in ("kernel", "bound", "frac", "hbm_frac", "frac_vs_probe")}}
+           "roofline": {k: r["roofline"].get(k) for k in ("kernel", "bound", "frac", "hbm_frac", "frac_vs_probe",
+                                                           "frac_vs_register_dfma")}}
     if "e2e" in r:
         out["e2e_gbs"] = r["e2e"]["value"]
     b = r.get("batched")

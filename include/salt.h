@@ -368,6 +368,21 @@ salt_status salt_cg_status(void* stream);
 #define SALT_TRACE_WORDS 8
 salt_status salt_trace_set(void* buf, int64_t max_blocks);
 
+/* salt_fp64_rate -- the FP64 pipe's issue rate of one instruction kind,
+ * measured from registers: every thread of 4 blocks of 256 threads per SM
+ * runs 8 independent chains of DFMA (SALT_FP64_FMA), DADD or DMUL, timed
+ * with events on `stream` after a warm-up launch; *gops receives G
+ * instructions per second.  The measured counterpart of the FP64 peak
+ * derived from unit counts and the clock, for the roofline of the FP64
+ * shapes (on GB300 DFMA issues faster than DADD and DMUL, which is why the
+ * kernels issue every FP64 node as an FMA with an exact product).
+ * Synchronizes the stream; about 50 ms.  Not in the paper.  Errors:
+ * SALT_ERR_ARG, SALT_ERR_CUDA. */
+#define SALT_FP64_FMA 0
+#define SALT_FP64_ADD 1
+#define SALT_FP64_MUL 2
+salt_status salt_fp64_rate(int32_t op, double* gops, void* stream);
+
 #define SALT_WAIT_STAGED 1
 #define SALT_WAIT_CG_BARRIER 2
 #define SALT_WAIT_SERVE 3

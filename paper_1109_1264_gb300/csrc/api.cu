@@ -1297,6 +1297,19 @@ salt_status salt_get_wait_limit(int32_t which, int64_t* polls) {
   return SALT_OK;
 }
 
+salt_status salt_fp64_rate(int32_t op, double* gops, void* stream) {
+  if (!gops) return set_error(SALT_ERR_ARG, "gops is NULL");
+  if (op < SALT_FP64_FMA || op > SALT_FP64_MUL) return set_error(SALT_ERR_ARG, "op must be SALT_FP64_FMA, _ADD or _MUL");
+  int dev = 0, sms = 0;
+  salt_status st = current_device(&dev, &sms);
+  if (st != SALT_OK) return st;
+  cudaError_t e = fp64_rate(op, sms, gops, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_error(e, "FP64 rate probe");
+  count_launch();
+  count_launch();
+  return SALT_OK;
+}
+
 salt_status salt_staged_timeouts(uint64_t* count) {
   if (!count) return set_error(SALT_ERR_ARG, "count is NULL");
   unsigned long long v = 0;

@@ -55,6 +55,8 @@ void register_staged(Registry&);
 // Reads `bytes` of `buf` on `s` (16-byte multiple) so that L2 holds other,
 // clean lines afterwards; one word of `sink` may be written.
 cudaError_t launch_l2_flush(const void* buf, size_t bytes, unsigned* sink, int sms, cudaStream_t s);
+// Register-only FP64 issue rate of one instruction kind (0 DFMA, 1 DADD, 2 DMUL), G instructions/s.
+cudaError_t fp64_rate(int op, int sms, double* gops, cudaStream_t s);
 
 // Timed-out stage waits of staged kernels since the library was loaded
 // (synchronous read of a device counter).

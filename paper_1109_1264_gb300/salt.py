@@ -24,7 +24,7 @@ MAX_PROG, MAX_VECS, MAX_SCALS, MAX_STACK, MAX_REDS, MAX_DSCALS = 32, 8, 8, 8, 4,
 # Symbols that include/salt.h declares (checked by the test suite).
 EXPORTS = ["salt_version", "salt_status_str", "salt_last_error", "salt_check_program", "salt_eval",
            "salt_axpby", "salt_dot", "salt_nrm2", "salt_fill_uniform", "salt_release_workspaces",
-           "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_staged_timeouts",
+           "salt_tune_set", "salt_tune_get", "salt_tune_clear", "salt_launch_count", "salt_staged_timeouts", "salt_fp64_rate",
            "salt_dot_noalloc", "salt_eval_strided", "salt_eval_ex", "salt_explain", "salt_cg_diag", "salt_cg_diag_persistent",
            "salt_cg_diag_one_reduction", "salt_cg_status", "salt_set_wait_limit", "salt_get_wait_limit", "salt_trace_set",
            "salt_cg_diag_auto", "salt_cg_form_set", "salt_cg_form_get", "salt_cg_autotune"]
@@ -73,6 +73,7 @@ def _load() -> ctypes.CDLL:
         "salt_tune_clear": (i32, []),
         "salt_launch_count": (i64, []),
         "salt_staged_timeouts": (i32, [ctypes.POINTER(u64)]),
+        "salt_fp64_rate": (i32, [i32, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
         "salt_dot_noalloc": (i32, [i32, i64, vp, vp, vp, vp]),
         "salt_eval_strided": (i32, [ip, i32, i32, i64, ctypes.POINTER(vp), ctypes.POINTER(i64), i32, dp, i32, vp,
                                     vp]),
@@ -361,6 +362,16 @@ def salt_trace_set(buf, max_blocks: int = 0) -> None:
         return
     cap = buf.numel() // TRACE_WORDS
     _check(lib.salt_trace_set(_ptr(buf), int(max_blocks or cap)))
+
+
+FP64_FMA, FP64_ADD, FP64_MUL = 0, 1, 2
+
+
+def salt_fp64_rate(op: int, stream=None) -> float:
+    """G FP64 instructions per second of one kind, from registers."""
+    g = ctypes.c_double()
+    _check(lib.salt_fp64_rate(int(op), ctypes.byref(g), _stream_ptr(stream)))
+    return g.value
 
 
 WAIT_STAGED, WAIT_CG_BARRIER, WAIT_SERVE = 1, 2, 3

@@ -368,3 +368,13 @@ def test_serve_config_persistent_fields(saltlib):
         setattr(c, field, bad)
         assert s.lib.salt_serve_start(ctypes.byref(h), ctypes.byref(c)) == s.ERR_ARG, (field, bad)
     assert s.lib.salt_serve_launches(None, None, None) == s.ERR_ARG
+
+
+def test_fp64_rate_argument_errors(saltlib):
+    """The FP64 issue-rate probe checks its arguments before touching a device."""
+    import ctypes
+    s = saltlib
+    g = ctypes.c_double()
+    assert s.lib.salt_fp64_rate(3, ctypes.byref(g), None) == s.ERR_ARG
+    assert s.lib.salt_fp64_rate(-1, ctypes.byref(g), None) == s.ERR_ARG
+    assert s.lib.salt_fp64_rate(s.FP64_FMA, None, None) == s.ERR_ARG
