@@ -589,12 +589,17 @@ def main():
         torch.cuda.empty_cache()
         result["generic"] = generic_measure(torch, salt)
     probe = fp64_probe(torch, salt)
+    sampler = ClockSampler(gpu_id_for_smi(torch))
+    time.sleep(0.3)  # the sampler's first reading
     try:
-        # the FP64 pipe's rate from registers, per instruction kind
+        # the FP64 pipe's rate from registers, per instruction kind (the SM
+        # clock during these loops beside it: under the power cap it can sit
+        # below the maximum after the legs before)
         probe["register_gops"] = {k: round(salt.salt_fp64_rate(op), 1) for k, op in
                                   (("dfma", salt.FP64_FMA), ("dadd", salt.FP64_ADD), ("dmul", salt.FP64_MUL))}
     except salt.SaltError as e:
         probe["register_gops"] = {"error": e.message[:200]}
+    probe["register_clocks"] = sampler.stop()
     result["fp64_probe"] = probe
     if roof["bound"] == "alu" and probe.get("gops"):
         roof["probe_gops"] = probe["gops"]

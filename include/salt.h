@@ -376,7 +376,7 @@ salt_status salt_trace_set(void* buf, int64_t max_blocks);
  * derived from unit counts and the clock, for the roofline of the FP64
  * shapes (on GB300 DFMA issues faster than DADD and DMUL, which is why the
  * kernels issue every FP64 node as an FMA with an exact product).
- * Synchronizes the stream; about 50 ms.  Not in the paper.  Errors:
+ * Synchronizes the stream; about 150 ms.  Not in the paper.  Errors:
  * SALT_ERR_ARG, SALT_ERR_CUDA. */
 #define SALT_FP64_FMA 0
 #define SALT_FP64_ADD 1

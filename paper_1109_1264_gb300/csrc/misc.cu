@@ -69,7 +69,7 @@ __global__ void fp64_rate_kernel(int iters, double b, double c) {
 // SM (after a short warm-up launch) with events on stream s; *gops receives
 // G instructions per second.
 cudaError_t fp64_rate(int op, int sms, double* gops, cudaStream_t s) {
-  const int grid = sms * 4, block = 256, iters = 20000;
+  const int grid = sms * 4, block = 256, iters = 60000;
   void (*k)(int, double, double) = op == 0 ? &fp64_rate_kernel<0> : op == 1 ? &fp64_rate_kernel<1> : &fp64_rate_kernel<2>;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
