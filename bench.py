@@ -1670,7 +1670,7 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
             out[dt] = (sum(r[0::2]), sum(v * v for v in r[1::2]) ** 0.5)
         return out
 
-    k = max(3, min(args.steps, 10))
+    k = max(3, min(args.steps, 20))
     for s_ in (up, comp, down):
         s_.wait_stream(stream)
     for _ in range(3):
@@ -1679,8 +1679,8 @@ def e2e_measure(torch, salt, loads, args, world, steps, abytes):
     # Step j ends when its last read-back has landed; with steps overlapping,
     # the interval between consecutive ends is the steady-state step time.
     # The host link is shared with the machine's other GPUs' jobs; the
-    # median interval is reported (the mean beside it) so that a transient
-    # contention does not decide it.
+    # median interval over up to 20 steps is reported (the mean beside it)
+    # so that a transient contention does not decide it.
     start = torch.cuda.Event(enable_timing=True)
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(k)]
     start.record(up)
