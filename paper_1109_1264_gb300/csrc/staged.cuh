@@ -26,6 +26,11 @@
 
 namespace salt {
 
+template <bool B>
+struct BoolTag {
+  static constexpr bool value = B;
+};
+
 constexpr int kStages = 2;
 constexpr unsigned kStageSpins = 1u << 26;           // polls
 constexpr uint64_t kStageWaitNs = 1000000000ull;     // one second of the global timer
@@ -175,35 +180,69 @@ __global__ void __launch_bounds__(256) staged_kernel(const StagedParams<T> sp) {
 
     const int64_t base = tile * te;
     const int nj = (int)(te / VEC);
-    for (int j = threadIdx.x; j < nj; j += blockDim.x) {
-      T x[kMaxVecs][VEC];
-      int b = 0;
+    // one pass over this thread's elements of the tile; FMA: the scaled adds
+    // as FMAs (exec_node)
+    auto run = [&](auto fma) {
+      constexpr bool FMA = decltype(fma)::value;
+      for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+        T x[kMaxVecs][VEC];
+        int b = 0;
 #pragma unroll
-      for (int s = 0; s < kMaxVecs; ++s) {
-        if ((LM >> s) & 1u) {
-          V t;
-          if (from_smem) t = *reinterpret_cast<const V*>(buf(st, b) + j * VEC);
-          else if ((SMASK >> s) & 1u) vload<false>(t, p.v[s] + base + j * VEC);
-          else vload<true>(t, p.v[s] + base + j * VEC);
+        for (int s = 0; s < kMaxVecs; ++s) {
+          if ((LM >> s) & 1u) {
+            V t;
+            if (from_smem) t = *reinterpret_cast<const V*>(buf(st, b) + j * VEC);
+            else if ((SMASK >> s) & 1u) vload<false>(t, p.v[s] + base + j * VEC);
+            else vload<true>(t, p.v[s] + base + j * VEC);
 #pragma unroll
-          for (int e = 0; e < VEC; ++e) x[s][e] = t.e[e];
-          ++b;
-        } else {
+            for (int e = 0; e < VEC; ++e) x[s][e] = t.e[e];
+            ++b;
+          } else {
 #pragma unroll
-          for (int e = 0; e < VEC; ++e) x[s][e] = T(0);
+            for (int e = 0; e < VEC; ++e) x[s][e] = T(0);
+          }
+        }
+        exec_chunk<P, T, Acc, VEC, FMA>(x, sc, acc);
+#pragma unroll
+        for (int s = 0; s < kMaxVecs; ++s) {
+          if ((SMASK >> s) & 1u) {
+            V t;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) t.e[e] = x[s][e];
+            vstore(p.v[s] + base + j * VEC, t);
+          }
         }
       }
-      exec_chunk<P, T, Acc, VEC>(x, sc, acc);
+    };
+    // FP64 programs without reductions whose by-value scalars include a power
+    // of two (exec_chunk_p2): this thread's operands of the tile, already in
+    // shared memory, are checked first, and the whole tile then runs one of
+    // the two bodies, so no element computes both forms.
+    bool fma_ok = false;
+    if constexpr (sizeof(T) == 8 && P::nred() == 0 && P::any_scaled_add()) {
+      if (from_smem && p.p2.mask != 0u) {
+        fma_ok = true;
+        for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+          T x[kMaxVecs][VEC];
+          int b = 0;
 #pragma unroll
-      for (int s = 0; s < kMaxVecs; ++s) {
-        if ((SMASK >> s) & 1u) {
-          V t;
+          for (int s = 0; s < kMaxVecs; ++s) {
+            if ((LM >> s) & 1u) {
+              const V t = *reinterpret_cast<const V*>(buf(st, b) + j * VEC);
 #pragma unroll
-          for (int e = 0; e < VEC; ++e) t.e[e] = x[s][e];
-          vstore(p.v[s] + base + j * VEC, t);
+              for (int e = 0; e < VEC; ++e) x[s][e] = t.e[e];
+              ++b;
+            } else {
+#pragma unroll
+              for (int e = 0; e < VEC; ++e) x[s][e] = T(0);
+            }
+          }
+          fma_ok = fma_ok & pow2_chunk_ok<P, 0, VEC>(x, p.p2);
         }
       }
     }
+    if (fma_ok) run(BoolTag<true>{});
+    else run(BoolTag<false>{});
     __syncthreads();  // stage st is free again
     if (threadIdx.x == 0 && staging && tile + kStages * gstep < ntiles) {
       issue(st, tile + kStages * gstep);
