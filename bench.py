@@ -78,6 +78,8 @@ KERNEL_SOURCES = {
                   "inst_f64_vb16.cu", "inst_f64_vb32.cu"],
     "e_f64_staged": ["prog.cuh", "common.cuh", "fused.cuh", "staged.cuh", "shapes.h", "registry.h",
                      "inst_staged.cu"],
+    "axpby_f64_staged": ["prog.cuh", "common.cuh", "fused.cuh", "staged.cuh", "shapes.h", "registry.h",
+                         "inst_staged.cu"],
     "dot_f64_staged": ["prog.cuh", "common.cuh", "fused.cuh", "staged.cuh", "shapes.h", "registry.h",
                        "inst_staged.cu"],
 }
